@@ -1,0 +1,276 @@
+"""CPU FP64 oracle for block ILU(0) by fixed-point sweeps, block triangular
+sweeps, BSR SpMV and FGMRES.
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg use this package; the CUDA library never imports, links or
+calls it, and it imports nothing from the CUDA side.  The arithmetic lives in
+``abilu_oracle.c`` (plain C, FP64, no FMA contraction); this module compiles it
+with gcc on first use and wraps it with ctypes.  ``dense`` holds an independent
+numpy brute force used to pin the C code.
+
+Factor layout: X has A's pattern (L_ij at column < row, U_ij at column >= row),
+Dinv holds inv(U_ii) per row.  Arrays are numpy: rowptr/colind int32,
+A/X float64 (nnzb, 4, 4), Dinv float64 (n, 4, 4), vectors float64 (n, 4).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "abilu_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_PI = C.POINTER(C.c_int32)
+_PD = C.POINTER(C.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, -O2, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Res(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("rel_resid_est", C.c_double), ("rel_resid_true", C.c_double)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        i32, f64 = C.c_int32, C.c_double
+        lib.orc_inv4.argtypes = [_PD, _PD]
+        lib.orc_inv4.restype = C.c_int
+        for nm in ("orc_bilu0_seq", "orc_bilu_init"):
+            getattr(lib, nm).argtypes = [i32, _PI, _PI, _PD, _PD, _PD]
+            getattr(lib, nm).restype = C.c_int
+        lib.orc_bilu_sync_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD, _PD]
+        lib.orc_bilu_sync_sweep.restype = C.c_int
+        lib.orc_bilu_chunked_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, i32, _PI, i32]
+        lib.orc_bilu_chunked_sweep.restype = C.c_int
+        lib.orc_lower_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
+        lib.orc_upper_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD, _PD]
+        lib.orc_lower_solve.argtypes = [i32, _PI, _PI, _PD, _PD, _PD]
+        lib.orc_upper_solve.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
+        lib.orc_apply.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD, C.c_int, C.c_int, _PD]
+        lib.orc_spmv.argtypes = [i32, _PI, _PI, _PD, _PD, _PD]
+        lib.orc_fgmres.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, C.c_int, C.c_int, _PD, _PD,
+                                   C.c_int, C.c_int, f64, C.POINTER(_Res), _PD]
+        lib.orc_fgmres.restype = C.c_int
+        lib.orc_ilu_residual_l1.argtypes = [i32, _PI, _PI, _PD, _PD, _PD]
+        lib.orc_ilu_residual_l1.restype = f64
+        lib.orc_lu_defect_max.argtypes = [i32, _PI, _PI, _PD, _PD]
+        lib.orc_lu_defect_max.restype = f64
+        lib.orc_jacobi_norms.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
+        for nm in ("orc_lower_sweep", "orc_upper_sweep", "orc_lower_solve", "orc_upper_solve",
+                   "orc_apply", "orc_spmv", "orc_jacobi_norms"):
+            getattr(lib, nm).restype = None
+        _lib = lib
+    return _lib
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_PI)
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_PD)
+
+
+def _pattern(rowptr, colind):
+    rp, prp = _i(rowptr)
+    ci, pci = _i(colind)
+    return len(rp) - 1, (rp, ci), prp, pci
+
+
+def inv4(a):
+    """(inverse, singular flag) of one 4x4 block."""
+    a, pa = _d(np.asarray(a, np.float64).reshape(4, 4))
+    out = np.empty((4, 4))
+    s = _load().orc_inv4(pa, out.ctypes.data_as(_PD))
+    return out, bool(s)
+
+
+def bilu0_seq(rowptr, colind, A):
+    """Sequential block ILU(0) -> (X, Dinv, n_singular)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X = np.empty_like(A)
+    Dinv = np.empty((n, 4, 4))
+    s = _load().orc_bilu0_seq(n, prp, pci, pA, X.ctypes.data_as(_PD), Dinv.ctypes.data_as(_PD))
+    return X, Dinv, s
+
+
+def bilu_init(rowptr, colind, A):
+    """Initial guess X^0 = A, Dinv^0 = inv(A_ii) -> (X, Dinv, n_singular)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X = np.empty_like(A)
+    Dinv = np.empty((n, 4, 4))
+    s = _load().orc_bilu_init(n, prp, pci, pA, X.ctypes.data_as(_PD), Dinv.ctypes.data_as(_PD))
+    return X, Dinv, s
+
+
+def bilu_sync_sweep(rowptr, colind, A, X, Dinv):
+    """One synchronous sweep (X, Dinv) -> (X', Dinv', n_singular)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X, pX = _d(X)
+    Dinv, pD = _d(Dinv)
+    Xo = np.empty_like(X)
+    Do = np.empty_like(Dinv)
+    s = _load().orc_bilu_sync_sweep(n, prp, pci, pA, pX, pD, Xo.ctypes.data_as(_PD),
+                                     Do.ctypes.data_as(_PD))
+    return Xo, Do, s
+
+
+def bilu_sync(rowptr, colind, A, nsweeps, X0=None, Dinv0=None):
+    """``nsweeps`` synchronous sweeps from X^0 = A (or the given warm start)."""
+    if X0 is None:
+        X, Dinv, s = bilu_init(rowptr, colind, A)
+    else:
+        X, Dinv, s = np.array(X0, np.float64), np.array(Dinv0, np.float64), 0
+    tot = s
+    for _ in range(nsweeps):
+        X, Dinv, s = bilu_sync_sweep(rowptr, colind, A, X, Dinv)
+        tot += s
+    return X, Dinv, tot
+
+
+def bilu_chunked_sweep(rowptr, colind, A, X, Dinv, chunk, chunk_order):
+    """In-place chunked sweep (deterministic emulation of the asynchronous one).
+    X, Dinv are modified in place (they must be C-contiguous float64)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    assert X.dtype == np.float64 and X.flags.c_contiguous
+    assert Dinv.dtype == np.float64 and Dinv.flags.c_contiguous
+    co, pco = _i(chunk_order)
+    return _load().orc_bilu_chunked_sweep(n, prp, pci, pA, X.ctypes.data_as(_PD),
+                                          Dinv.ctypes.data_as(_PD), int(chunk), pco, len(co))
+
+
+def lower_sweep(rowptr, colind, X, r, y_in):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    r, pr = _d(r)
+    y_in, py = _d(y_in)
+    out = np.empty((n, 4))
+    _load().orc_lower_sweep(n, prp, pci, pX, pr, py, out.ctypes.data_as(_PD))
+    return out
+
+
+def upper_sweep(rowptr, colind, X, Dinv, y, x_in):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    Dinv, pD = _d(Dinv)
+    y, py = _d(y)
+    x_in, px = _d(x_in)
+    out = np.empty((n, 4))
+    _load().orc_upper_sweep(n, prp, pci, pX, pD, py, px, out.ctypes.data_as(_PD))
+    return out
+
+
+def lower_solve(rowptr, colind, X, r):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    r, pr = _d(r)
+    out = np.empty((n, 4))
+    _load().orc_lower_solve(n, prp, pci, pX, pr, out.ctypes.data_as(_PD))
+    return out
+
+
+def upper_solve(rowptr, colind, X, Dinv, y):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    Dinv, pD = _d(Dinv)
+    y, py = _d(y)
+    out = np.empty((n, 4))
+    _load().orc_upper_solve(n, prp, pci, pX, pD, py, out.ctypes.data_as(_PD))
+    return out
+
+
+def apply(rowptr, colind, X, Dinv, r, n_lower, n_upper):
+    """z ~= (LU)^{-1} r with the given sweep counts (negative: exact)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    Dinv, pD = _d(Dinv)
+    r, pr = _d(r)
+    z = np.empty((n, 4))
+    work = np.empty(2 * n * 4)
+    _load().orc_apply(n, prp, pci, pX, pD, pr, z.ctypes.data_as(_PD), int(n_lower),
+                      int(n_upper), work.ctypes.data_as(_PD))
+    return z
+
+
+def spmv(rowptr, colind, A, x):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    x, px = _d(x)
+    y = np.empty((n, 4))
+    _load().orc_spmv(n, prp, pci, pA, px, y.ctypes.data_as(_PD))
+    return y
+
+
+@dataclass
+class FgmresResult:
+    iters: int
+    restarts: int
+    converged: bool
+    rel_resid_est: float
+    rel_resid_true: float
+    history: np.ndarray
+
+
+def fgmres(rowptr, colind, A, X, Dinv, b, n_lower, n_upper, restart=30, max_iters=2500,
+           rtol=1e-6, x0=None):
+    """FGMRES(restart) with the block ILU preconditioner (X, Dinv) -> (x, result)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X, pX = _d(X)
+    Dinv, pD = _d(Dinv)
+    b, pb = _d(b)
+    x = np.zeros((n, 4)) if x0 is None else np.array(x0, np.float64)
+    res = _Res()
+    hist = np.full(max_iters + 1, np.nan)
+    _load().orc_fgmres(n, prp, pci, pA, pX, pD, int(n_lower), int(n_upper), pb,
+                       x.ctypes.data_as(_PD), int(restart), int(max_iters), float(rtol),
+                       C.byref(res), hist.ctypes.data_as(_PD))
+    return x, FgmresResult(res.iters, res.restarts, bool(res.converged), res.rel_resid_est,
+                           res.rel_resid_true, hist[: res.iters + 1])
+
+
+def ilu_residual_l1(rowptr, colind, A, X):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X, pX = _d(X)
+    work = np.empty(len(keep[1]) * 16 + n * 16)
+    return _load().orc_ilu_residual_l1(n, prp, pci, pA, pX, work.ctypes.data_as(_PD))
+
+
+def lu_defect_max(rowptr, colind, A, X):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X, pX = _d(X)
+    return _load().orc_lu_defect_max(n, prp, pci, pA, pX)
+
+
+def jacobi_norms(rowptr, colind, X, Dinv):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    Dinv, pD = _d(Dinv)
+    ln, un = C.c_double(), C.c_double()
+    _load().orc_jacobi_norms(n, prp, pci, pX, pD, C.byref(ln), C.byref(un))
+    return ln.value, un.value

@@ -1,0 +1,634 @@
+/*
+ * CPU oracle for the asynchronous block ILU(0) preconditioner with FGMRES
+ * (Kashi & Nadarajah, "An asynchronous incomplete block LU preconditioner for
+ * computational fluid dynamics on unstructured grids").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, single-threaded FP64
+ * statement of what the method computes.  It shares no code with the CUDA
+ * library; only the test suite, the smoke check and the benchmark's CPU-baseline
+ * leg load it.  The product path never calls it.
+ *
+ * Storage: block CSR with b = 4 (Sec. 2: all d+2 = 4 unknowns of a cell
+ * contiguous), rowptr/colind int32, colind sorted inside each row, the diagonal
+ * block present in every row, each 4x4 block row-major (16 doubles).
+ * The factors X are held in a copy of A's pattern: positions with column < row
+ * hold L_ij (L_ii = I is implicit), positions with column >= row hold U_ij.
+ * Dinv holds one 4x4 block per row, the inverse of U_ii.
+ *
+ * Every sum runs in ascending column order and accumulates in a local FP64
+ * variable that is written once (Sec. 4.2 notes that accumulating a partial sum
+ * in place slows the asynchronous iteration; a local accumulator is the form the
+ * paper uses).  Build with -O2 -ffp-contract=off so no FMA contraction changes
+ * the rounding between machines.
+ *
+ * Parity status: every function below is pinned by tests against an
+ * independent statement (dense numpy elimination, numpy.linalg, scipy, closed
+ * forms, the paper's theorems); see tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define BS 4
+#define BB 16
+
+typedef int32_t idx_t;
+
+/* ---------------------------------------------------------------- 4x4 blocks */
+
+/* S -= X * Y  (4x4 row-major) */
+static void blk_sub_mul(double *S, const double *X, const double *Y)
+{
+    for (int r = 0; r < BS; r++)
+        for (int c = 0; c < BS; c++) {
+            double acc = 0.0;
+            for (int k = 0; k < BS; k++)
+                acc += X[r * BS + k] * Y[k * BS + c];
+            S[r * BS + c] -= acc;
+        }
+}
+
+/* out = X * Y */
+static void blk_mul(double *out, const double *X, const double *Y)
+{
+    for (int r = 0; r < BS; r++)
+        for (int c = 0; c < BS; c++) {
+            double acc = 0.0;
+            for (int k = 0; k < BS; k++)
+                acc += X[r * BS + k] * Y[k * BS + c];
+            out[r * BS + c] = acc;
+        }
+}
+
+/* s -= X * v  (4x4 times 4-vector) */
+static void blk_sub_matvec(double *s, const double *X, const double *v)
+{
+    for (int r = 0; r < BS; r++) {
+        double acc = 0.0;
+        for (int k = 0; k < BS; k++)
+            acc += X[r * BS + k] * v[k];
+        s[r] -= acc;
+    }
+}
+
+/* out = X * v */
+static void blk_matvec(double *out, const double *X, const double *v)
+{
+    for (int r = 0; r < BS; r++) {
+        double acc = 0.0;
+        for (int k = 0; k < BS; k++)
+            acc += X[r * BS + k] * v[k];
+        out[r] = acc;
+    }
+}
+
+/*
+ * Exact inverse of a 4x4 block by Gauss-Jordan elimination with partial
+ * pivoting (the paper inverts diagonal blocks exactly, Sec. 4.1 / Eq. (bilu)).
+ * Pivot: the first row of largest |entry| in the column.  A zero or non-finite
+ * pivot marks the block singular; then, following the "modified iteration" of
+ * Sec. 4.2 (a singular diagonal block is replaced by an arbitrary non-singular
+ * one), the block is replaced by the identity and out = I.
+ * Returns 1 if the block was singular, else 0.
+ */
+int orc_inv4(const double *a, double *out)
+{
+    double m[BS][2 * BS];
+    for (int r = 0; r < BS; r++)
+        for (int c = 0; c < BS; c++) {
+            m[r][c] = a[r * BS + c];
+            m[r][BS + c] = (r == c) ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < BS; c++) {
+        int p = c;
+        for (int r = c + 1; r < BS; r++)
+            if (fabs(m[r][c]) > fabs(m[p][c]))
+                p = r;
+        double piv = m[p][c];
+        if (piv == 0.0 || !isfinite(piv)) {
+            for (int r = 0; r < BS; r++)
+                for (int k = 0; k < BS; k++)
+                    out[r * BS + k] = (r == k) ? 1.0 : 0.0;
+            return 1;
+        }
+        if (p != c)
+            for (int k = 0; k < 2 * BS; k++) {
+                double t = m[p][k];
+                m[p][k] = m[c][k];
+                m[c][k] = t;
+            }
+        for (int k = 0; k < 2 * BS; k++)
+            m[c][k] = m[c][k] / piv;
+        for (int r = 0; r < BS; r++) {
+            if (r == c)
+                continue;
+            double f = m[r][c];
+            for (int k = 0; k < 2 * BS; k++)
+                m[r][k] = m[r][k] - f * m[c][k];
+        }
+    }
+    for (int r = 0; r < BS; r++)
+        for (int c = 0; c < BS; c++)
+            out[r * BS + c] = m[r][BS + c];
+    return 0;
+}
+
+/* Position of block (i, j) in the pattern, or -1 (linear search in row i). */
+static long find_block(const idx_t *rowptr, const idx_t *colind, idx_t i, idx_t j)
+{
+    for (long p = rowptr[i]; p < rowptr[i + 1]; p++)
+        if (colind[p] == j)
+            return p;
+    return -1;
+}
+
+static long diag_pos(const idx_t *rowptr, const idx_t *colind, idx_t i)
+{
+    return find_block(rowptr, colind, i, i);
+}
+
+/*
+ * S = A_ij - sum_{k < min(i,j), (i,k),(k,j) in S_B} Xsrc_ik Xsrc_kj, the common
+ * part of both lines of Eq. (bilu) / H_ij.  k runs in ascending order over the
+ * blocks of row i.
+ */
+static void bilu_residual_block(idx_t i, idx_t j, long p, const idx_t *rowptr,
+                                const idx_t *colind, const double *A,
+                                const double *Xsrc, double *S)
+{
+    memcpy(S, A + p * BB, sizeof(double) * BB);
+    idx_t kmax = i < j ? i : j;
+    for (long q = rowptr[i]; q < rowptr[i + 1]; q++) {
+        idx_t k = colind[q];
+        if (k >= kmax)
+            break;
+        long r = find_block(rowptr, colind, k, j);
+        if (r < 0)
+            continue;
+        blk_sub_mul(S, Xsrc + q * BB, Xsrc + r * BB);
+    }
+}
+
+/*
+ * Sequential block ILU(0): Eq. (bilu) evaluated in the block Gaussian
+ * elimination (row-major) ordering, each block from the values already
+ * computed.  This is the unique fixed point of h (Sec. 4.2, uniqueness
+ * theorem) and what one thread running one sweep of the asynchronous
+ * iteration produces (Sec. 3.3 / Sec. 6 setup).
+ * X (nnzb*16) and Dinv (n*16) are outputs.  Returns the number of singular
+ * diagonal blocks that were replaced.
+ */
+int orc_bilu0_seq(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                  const double *A, double *X, double *Dinv)
+{
+    int nsing = 0;
+    double S[BB];
+    for (idx_t i = 0; i < n; i++) {
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            bilu_residual_block(i, j, p, rowptr, colind, A, X, S);
+            if (j < i) {
+                blk_mul(X + p * BB, S, Dinv + (long)j * BB);
+            } else {
+                memcpy(X + p * BB, S, sizeof S);
+                if (j == i)
+                    nsing += orc_inv4(S, Dinv + (long)i * BB);
+            }
+        }
+    }
+    return nsing;
+}
+
+/*
+ * Initial guess of the factorisation (Sec. 6 setup: "the Jacobian itself"):
+ * X^0 = A on S_B, L^0 unscaled, and Dinv^0 = inv(A_ii).
+ */
+int orc_bilu_init(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                  const double *A, double *X, double *Dinv)
+{
+    long nnzb = rowptr[n];
+    int nsing = 0;
+    memcpy(X, A, sizeof(double) * BB * nnzb);
+    for (idx_t i = 0; i < n; i++) {
+        long d = diag_pos(rowptr, colind, i);
+        nsing += orc_inv4(A + d * BB, Dinv + (long)i * BB);
+    }
+    return nsing;
+}
+
+/*
+ * One synchronous (Jacobi-type) sweep x^{n+1} = h(x^n), Eq. (seq_blockilu_fp)
+ * with H_ij of Eq. (blockH): every block from the previous iterate; the L
+ * update multiplies by inv(U_jj^n) = Dinv_in[j].  After U_ii^{n+1} is formed
+ * its inverse becomes Dinv_out[i].  Returns the number of singular blocks.
+ */
+int orc_bilu_sync_sweep(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                        const double *A, const double *Xin, const double *Dinv_in,
+                        double *Xout, double *Dinv_out)
+{
+    int nsing = 0;
+    double S[BB];
+    for (idx_t i = 0; i < n; i++) {
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            bilu_residual_block(i, j, p, rowptr, colind, A, Xin, S);
+            if (j < i) {
+                blk_mul(Xout + p * BB, S, Dinv_in + (long)j * BB);
+            } else {
+                memcpy(Xout + p * BB, S, sizeof S);
+                if (j == i)
+                    nsing += orc_inv4(S, Dinv_out + (long)i * BB);
+            }
+        }
+    }
+    return nsing;
+}
+
+/*
+ * Deterministic emulation of the asynchronous in-place sweep (Algorithm 4 with
+ * blocks): the rows are cut into chunks of `chunk` consecutive rows; the chunks
+ * are visited in the order chunk_order[0..nchunks-1]; each chunk's rows are
+ * processed in ascending order, blocks of a row in ascending column order,
+ * every read taking the latest value in memory (in place).  This is what one
+ * thread taking chunks in that order does.  Returns singular count.
+ */
+int orc_bilu_chunked_sweep(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                           const double *A, double *X, double *Dinv,
+                           idx_t chunk, const idx_t *chunk_order, idx_t nchunks)
+{
+    int nsing = 0;
+    double S[BB];
+    for (idx_t c = 0; c < nchunks; c++) {
+        idx_t i0 = chunk_order[c] * chunk;
+        idx_t i1 = i0 + chunk < n ? i0 + chunk : n;
+        for (idx_t i = i0; i < i1; i++) {
+            for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+                idx_t j = colind[p];
+                bilu_residual_block(i, j, p, rowptr, colind, A, X, S);
+                if (j < i) {
+                    blk_mul(X + p * BB, S, Dinv + (long)j * BB);
+                } else {
+                    memcpy(X + p * BB, S, sizeof S);
+                    if (j == i)
+                        nsing += orc_inv4(S, Dinv + (long)i * BB);
+                }
+            }
+        }
+    }
+    return nsing;
+}
+
+/* ------------------------------------------------------- triangular apply */
+
+/*
+ * One synchronous (Jacobi) sweep of the lower block triangular solve L y = r
+ * (Algorithm 5 with every read from the previous iterate; L_ii = I):
+ *   y_out_i = r_i - sum_{j<i} L_ij y_in_j.
+ */
+void orc_lower_sweep(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                     const double *X, const double *r, const double *y_in,
+                     double *y_out)
+{
+    for (idx_t i = 0; i < n; i++) {
+        double s[BS];
+        memcpy(s, r + (long)i * BS, sizeof s);
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            if (j >= i)
+                break;
+            blk_sub_matvec(s, X + p * BB, y_in + (long)j * BS);
+        }
+        memcpy(y_out + (long)i * BS, s, sizeof s);
+    }
+}
+
+/*
+ * One synchronous (Jacobi) sweep of the upper block triangular solve U x = y
+ * (the backward analogue of Algorithm 5):
+ *   x_out_i = U_ii^{-1} (y_i - sum_{j>i} U_ij x_in_j).
+ */
+void orc_upper_sweep(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                     const double *X, const double *Dinv, const double *y,
+                     const double *x_in, double *x_out)
+{
+    for (idx_t i = 0; i < n; i++) {
+        double s[BS];
+        memcpy(s, y + (long)i * BS, sizeof s);
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            if (j <= i)
+                continue;
+            blk_sub_matvec(s, X + p * BB, x_in + (long)j * BS);
+        }
+        blk_matvec(x_out + (long)i * BS, Dinv + (long)i * BB, s);
+    }
+}
+
+/* Exact forward substitution L y = r with unit diagonal blocks (Algorithm 1). */
+void orc_lower_solve(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                     const double *X, const double *r, double *y)
+{
+    for (idx_t i = 0; i < n; i++) {
+        double s[BS];
+        memcpy(s, r + (long)i * BS, sizeof s);
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            if (j >= i)
+                break;
+            blk_sub_matvec(s, X + p * BB, y + (long)j * BS);
+        }
+        memcpy(y + (long)i * BS, s, sizeof s);
+    }
+}
+
+/* Exact backward substitution U x = y, rows in descending order. */
+void orc_upper_solve(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                     const double *X, const double *Dinv, const double *y, double *x)
+{
+    for (idx_t i = n - 1; i >= 0; i--) {
+        double s[BS];
+        memcpy(s, y + (long)i * BS, sizeof s);
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            if (j <= i)
+                continue;
+            blk_sub_matvec(s, X + p * BB, x + (long)j * BS);
+        }
+        blk_matvec(x + (long)i * BS, Dinv + (long)i * BB, s);
+    }
+}
+
+/*
+ * Preconditioner application z = (LU)^{-1} r, approximately: n_lower Jacobi
+ * sweeps on L y = r from y = 0, then n_upper Jacobi sweeps on U z = y from
+ * z = 0 (zero initial guesses every application, Sec. 6 setup).  A negative
+ * sweep count means the exact substitution.  work: 2*n*4 doubles.
+ */
+void orc_apply(idx_t n, const idx_t *rowptr, const idx_t *colind,
+               const double *X, const double *Dinv, const double *r, double *z,
+               int n_lower, int n_upper, double *work)
+{
+    long nv = (long)n * BS;
+    double *y = work, *t = work + nv;
+    if (n_lower < 0) {
+        orc_lower_solve(n, rowptr, colind, X, r, y);
+    } else {
+        memset(y, 0, sizeof(double) * nv);
+        for (int s = 0; s < n_lower; s++) {
+            orc_lower_sweep(n, rowptr, colind, X, r, y, t);
+            memcpy(y, t, sizeof(double) * nv);
+        }
+    }
+    if (n_upper < 0) {
+        orc_upper_solve(n, rowptr, colind, X, Dinv, y, z);
+    } else {
+        memset(z, 0, sizeof(double) * nv);
+        for (int s = 0; s < n_upper; s++) {
+            orc_upper_sweep(n, rowptr, colind, X, Dinv, y, z, t);
+            memcpy(z, t, sizeof(double) * nv);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ SpMV */
+
+/* y = A x, block rows independent, j ascending within a row. */
+void orc_spmv(idx_t n, const idx_t *rowptr, const idx_t *colind,
+              const double *A, const double *x, double *y)
+{
+    for (idx_t i = 0; i < n; i++) {
+        double s[BS] = {0.0, 0.0, 0.0, 0.0};
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            const double *a = A + p * BB;
+            const double *xj = x + (long)colind[p] * BS;
+            for (int r = 0; r < BS; r++) {
+                double acc = 0.0;
+                for (int k = 0; k < BS; k++)
+                    acc += a[r * BS + k] * xj[k];
+                s[r] += acc;
+            }
+        }
+        memcpy(y + (long)i * BS, s, sizeof s);
+    }
+}
+
+/* --------------------------------------------------------------- FGMRES */
+
+static double dot(long nv, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (long k = 0; k < nv; k++)
+        s += a[k] * b[k];
+    return s;
+}
+
+typedef struct {
+    int iters;             /* Arnoldi steps over all restarts */
+    int restarts;          /* completed restart cycles */
+    int converged;         /* 1 if the true relative residual <= rtol */
+    double rel_resid_est;  /* last Givens estimate |g_{j+1}| / ||b|| */
+    double rel_resid_true; /* ||b - A x|| / ||b|| at exit */
+} orc_fgmres_result;
+
+/*
+ * Right-preconditioned flexible GMRES(m) (Saad's FGMRES, used by the paper
+ * through PETSc, Sec. 2 / Sec. 6 setup), with modified Gram-Schmidt and Givens
+ * rotations.  The preconditioner is the block ILU given by (X, Dinv), applied
+ * with n_lower / n_upper Jacobi sweeps (negative: exact).  x holds x0 on entry
+ * and the solution on exit.  Stops when the Givens residual estimate drops to
+ * rtol*||b||, confirmed at the end of the cycle by the explicit residual; an
+ * unconfirmed estimate restarts.  Stops at max_iters Arnoldi steps.
+ * hist (may be NULL, max_iters+1 entries) receives |g_{j+1}| / ||b|| per step.
+ */
+int orc_fgmres(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+               const double *X, const double *Dinv, int n_lower, int n_upper,
+               const double *b, double *x, int m, int max_iters, double rtol,
+               orc_fgmres_result *res, double *hist)
+{
+    long nv = (long)n * BS;
+    double *V = calloc((size_t)(m + 1) * nv, sizeof(double));
+    double *Z = calloc((size_t)m * nv, sizeof(double));
+    double *w = calloc((size_t)nv, sizeof(double));
+    double *work = calloc((size_t)2 * nv, sizeof(double));
+    double *H = calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
+    double *cs = calloc((size_t)m, sizeof(double));
+    double *sn = calloc((size_t)m, sizeof(double));
+    double *g = calloc((size_t)m + 1, sizeof(double));
+    double *yv = calloc((size_t)m, sizeof(double));
+    if (!V || !Z || !w || !work || !H || !cs || !sn || !g || !yv) {
+        free(V); free(Z); free(w); free(work); free(H); free(cs); free(sn); free(g); free(yv);
+        return -1;
+    }
+    memset(res, 0, sizeof *res);
+    double bnorm = sqrt(dot(nv, b, b));
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * nv);
+        res->converged = 1;
+        goto done;
+    }
+    /* r0 = b - A x0 */
+    orc_spmv(n, rowptr, colind, A, x, w);
+    for (long k = 0; k < nv; k++)
+        w[k] = b[k] - w[k];
+    double beta = sqrt(dot(nv, w, w));
+    res->rel_resid_true = beta / bnorm;
+    res->rel_resid_est = res->rel_resid_true;
+    if (hist)
+        hist[0] = res->rel_resid_est;
+    if (beta <= rtol * bnorm) {
+        res->converged = 1;
+        goto done;
+    }
+    while (res->iters < max_iters) {
+        for (long k = 0; k < nv; k++)
+            V[k] = w[k] / beta;
+        memset(g, 0, sizeof(double) * (m + 1));
+        g[0] = beta;
+        int kdim = 0;
+        for (int j = 0; j < m; j++) {
+            double *vj = V + (long)j * nv, *zj = Z + (long)j * nv;
+            orc_apply(n, rowptr, colind, X, Dinv, vj, zj, n_lower, n_upper, work);
+            orc_spmv(n, rowptr, colind, A, zj, w);
+            for (int i = 0; i <= j; i++) { /* modified Gram-Schmidt */
+                double hij = dot(nv, w, V + (long)i * nv);
+                H[i * m + j] = hij;
+                const double *vi = V + (long)i * nv;
+                for (long k = 0; k < nv; k++)
+                    w[k] -= hij * vi[k];
+            }
+            double hn = sqrt(dot(nv, w, w));
+            H[(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; i++) { /* previous rotations */
+                double a = H[i * m + j], c = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * c;
+                H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[j * m + j], c = H[(j + 1) * m + j];
+            double d = sqrt(a * a + c * c);
+            if (d == 0.0) { cs[j] = 1.0; sn[j] = 0.0; }
+            else { cs[j] = a / d; sn[j] = c / d; }
+            H[j * m + j] = cs[j] * a + sn[j] * c;
+            H[(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            res->iters++;
+            kdim = j + 1;
+            res->rel_resid_est = fabs(g[j + 1]) / bnorm;
+            if (hist)
+                hist[res->iters] = res->rel_resid_est;
+            if (fabs(g[j + 1]) <= rtol * bnorm || hn == 0.0 || res->iters >= max_iters)
+                break;
+            double *vn = V + (long)(j + 1) * nv;
+            for (long k = 0; k < nv; k++)
+                vn[k] = w[k] / hn;
+        }
+        /* y = H^{-1} g (upper triangular, back substitution), x += Z y */
+        for (int i = kdim - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int k = i + 1; k < kdim; k++)
+                s -= H[i * m + k] * yv[k];
+            yv[i] = s / H[i * m + i];
+        }
+        for (int i = 0; i < kdim; i++) {
+            const double *zi = Z + (long)i * nv;
+            for (long k = 0; k < nv; k++)
+                x[k] += yv[i] * zi[k];
+        }
+        res->restarts++;
+        orc_spmv(n, rowptr, colind, A, x, w);
+        for (long k = 0; k < nv; k++)
+            w[k] = b[k] - w[k];
+        beta = sqrt(dot(nv, w, w));
+        res->rel_resid_true = beta / bnorm;
+        if (beta <= rtol * bnorm) {
+            res->converged = 1;
+            break;
+        }
+    }
+done:
+    free(V); free(Z); free(w); free(work); free(H); free(cs); free(sn); free(g); free(yv);
+    return res->converged ? 0 : 1;
+}
+
+/* ------------------------------------------------------------ diagnostics */
+
+/*
+ * ||x - h(x)||_1 over all entries of L and U (the ILU fixed-point residual of
+ * Sec. 6.2, whose ratio to the initial one the paper plots).  h uses the
+ * inverses of x's own diagonal blocks.  work: nnzb*16 + n*16 doubles.
+ */
+double orc_ilu_residual_l1(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                           const double *A, const double *X, double *work)
+{
+    long nnzb = rowptr[n];
+    double *Xh = work, *Dx = work + nnzb * BB;
+    double *Dunused = malloc(sizeof(double) * BB * (size_t)(n > 0 ? n : 1));
+    for (idx_t i = 0; i < n; i++)
+        orc_inv4(X + diag_pos(rowptr, colind, i) * BB, Dx + (long)i * BB);
+    orc_bilu_sync_sweep(n, rowptr, colind, A, X, Dx, Xh, Dunused);
+    free(Dunused);
+    double s = 0.0;
+    for (long k = 0; k < nnzb * BB; k++)
+        s += fabs(X[k] - Xh[k]);
+    return s;
+}
+
+/*
+ * Largest |(LU)_ij - A_ij| over (i,j) in S_B and over the 16 entries, with
+ * L_ii = I: (LU)_ij = sum_{k<min(i,j)} L_ik U_kj + (L_ij U_jj if i>j, U_ij if
+ * i<=j).  Zero at the fixed point, Eq. (bilu).
+ */
+double orc_lu_defect_max(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                         const double *A, const double *X)
+{
+    double worst = 0.0, S[BB];
+    for (idx_t i = 0; i < n; i++)
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            bilu_residual_block(i, j, p, rowptr, colind, A, X, S); /* A - sum */
+            if (j < i)
+                blk_sub_mul(S, X + p * BB, X + diag_pos(rowptr, colind, j) * BB);
+            else
+                for (int k = 0; k < BB; k++)
+                    S[k] -= X[p * BB + k];
+            for (int k = 0; k < BB; k++)
+                if (fabs(S[k]) > worst)
+                    worst = fabs(S[k]);
+        }
+    return worst;
+}
+
+/*
+ * Max-norms of the block-Jacobi iteration matrices of the triangular solves
+ * (the "diagonal dominance" measure of Sec. 6): for L (unit diagonal blocks)
+ * || L - I ||_inf; for U, || D_U^{-1} (U - D_U) ||_inf with D_U the block
+ * diagonal, i.e. the largest scalar row sum of |Dinv_i U_ij| over j > i.
+ */
+void orc_jacobi_norms(idx_t n, const idx_t *rowptr, const idx_t *colind,
+                      const double *X, const double *Dinv, double *lnorm, double *unorm)
+{
+    double ln = 0.0, un = 0.0, P[BB];
+    for (idx_t i = 0; i < n; i++) {
+        double rl[BS] = {0, 0, 0, 0}, ru[BS] = {0, 0, 0, 0};
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            if (j < i) {
+                for (int r = 0; r < BS; r++)
+                    for (int c = 0; c < BS; c++)
+                        rl[r] += fabs(X[p * BB + r * BS + c]);
+            } else if (j > i) {
+                blk_mul(P, Dinv + (long)i * BB, X + p * BB);
+                for (int r = 0; r < BS; r++)
+                    for (int c = 0; c < BS; c++)
+                        ru[r] += fabs(P[r * BS + c]);
+            }
+        }
+        for (int r = 0; r < BS; r++) {
+            if (rl[r] > ln) ln = rl[r];
+            if (ru[r] > un) un = ru[r];
+        }
+    }
+    *lnorm = ln;
+    *unorm = un;
+}
