@@ -1,0 +1,414 @@
+"""Benchmark: preconditioned FGMRES solves/s on the 512x512 inviscid-like grid.
+
+One step = one full solve through the C ABI: block ILU(0) built from A by 6
+sweeps (FP32 factors, FP64 inversion), FGMRES(30) to a relative residual of
+1e-6 with 4+4 triangular sweeps per preconditioner application, FP64 SpMV,
+Arnoldi and Givens.  The pattern is analysed once (values change per
+pseudo-time step, the pattern does not); A and b are resident in HBM when the
+timed region starts.  A (268 MB) is larger than L2, so no L2 flush is needed.
+
+Also reported: the same solve end to end with A and b copied from pinned host
+memory and x copied back every step ("e2e"); per-kernel achieved bandwidth
+against the measured HBM copy peak ("roofline", "kernels"); the CPU oracle's
+solve rate on the host ("cpu_baseline"); p50/p99 solve latency; other
+precision/mode variants.  ``--impl reference`` times the CPU oracle instead.
+Under torchrun every rank solves its own replica (the systems are independent),
+value = solves of all ranks / max wall time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "inviscid_512x512"
+BUILD_SWEEPS, APPLY_SWEEPS, RESTART, RTOL = 6, 4, 30, 1e-6
+METRIC = "preconditioned FGMRES solves/s at 1e-6; sweep GB/s vs HBM peak; p50/p99 latency"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _system():
+    import abilu_inputs as gen
+    return gen.workload(WORKLOAD)
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_solve(s, max_iters=2500):
+    import oracle
+    X, D, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, BUILD_SWEEPS)
+    x, r = oracle.fgmres(s.rowptr, s.colind, s.vals, X, D, s.b, APPLY_SWEEPS, APPLY_SWEEPS,
+                         restart=RESTART, max_iters=max_iters, rtol=RTOL)
+    return r
+
+
+def cpu_baseline(s, budget_s=12.0):
+    """Full oracle solves (FP64, one host thread) until ~budget_s of CPU time."""
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        r = oracle_solve(s)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or n >= 5:
+            break
+    return {"value": n / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full FP64 oracle solves of the 512x512 workload (sync build "
+                      f"{BUILD_SWEEPS} sweeps, {APPLY_SWEEPS}+{APPLY_SWEEPS} apply sweeps, "
+                      f"FGMRES({RESTART}) to {RTOL:g}, {r.iters} iterations each) in {el:.1f} s "
+                      f"on one host core"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    s = _system()
+    for _ in range(args.warmup):
+        oracle_solve(s)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_solve(s)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": s.n, "blocks": s.nnzb,
+                       "build_sweeps": BUILD_SWEEPS, "apply_sweeps": APPLY_SWEEPS,
+                       "restart": RESTART, "rtol": RTOL, "iters": r.iters},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step one full FP64 oracle solve ({r.iters} "
+                                       "FGMRES iterations) on one host core"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# -------------------------------------------------------------------- GPU arm
+
+def _events(torch, n):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def kernel_rooflines(torch, ab, pat, A, fac, s, peak):
+    """Average duration of single launches of each hot kernel (CUDA events on
+    the launching stream, back-to-back launches after warm-up) and achieved
+    GB/s from the algorithmic bytes of one launch."""
+    N, nnzb = s.n, s.nnzb
+    E = (nnzb - N) // 2
+    f, v = 4, 4   # FP32 factors, FP32 apply vectors
+    x = torch.randn(N, 4, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    reps = 50
+
+    def avg_us(fn):
+        for _ in range(5):
+            fn()
+        e0, e1 = _events(torch, 2)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e3
+
+    out = {}
+    t = avg_us(lambda: ab.bsr_spmv(pat, A, x, y))
+    b = nnzb * (128 + 4) + 4 * (N + 1) + 2 * 32 * N
+    out["spmv_f64"] = {"us": t, "bytes": b, "launches_per_call": 1}
+    t = avg_us(lambda: fac.build(A, 1, "sync", init="previous"))
+    b = nnzb * 132 + 4 * (N + 1) + 2 * 16 * f * (nnzb + N)
+    out["build_sweep_f32"] = {"us": t, "bytes": b, "launches_per_call": 1}
+    # one lower and one upper sweep: apply(2, 2) runs one lower sweep kernel
+    # (with x^1 = Dinv y fused) and one upper sweep kernel
+    t = avg_us(lambda: fac.apply(x, z, 2, 2, "sync"))
+    bl = E * (16 * f + 4) + 4 * (N + 1) + 3 * N * 4 * v
+    bu = E * (16 * f + 4) + 16 * f * N + 4 * (N + 1) + 3 * N * 4 * v
+    out["lower+upper_sweep_f32"] = {"us": t, "bytes": bl + bu, "launches_per_call": 2}
+    for k in out.values():
+        k["GBs"] = k["bytes"] / (k["us"] * 1e-6) / 1e9
+        k["frac"] = k["GBs"] / peak
+    return out
+
+
+def run_kernels_only(args):
+    """Per-kernel timings only (the target of the ncu captures)."""
+    import torch
+    import paper_1912_00539_gb300 as ab
+    peak, _ = _peaks()
+    s = _system()
+    pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+    A = torch.from_numpy(s.vals).cuda()
+    fk = ab.Factors(pat, "f32")
+    fk.build(A, BUILD_SWEEPS, "sync")
+    kern = kernel_rooflines(torch, ab, pat, A, fk, s, peak)
+    print(json.dumps({k: {kk: round(vv, 3) for kk, vv in v.items()} for k, v in kern.items()}))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1912_00539_gb300 as ab
+    peak, peak_kind = _peaks()
+    s = _system()
+    dev = torch.device("cuda", local)
+    rowptr = torch.from_numpy(s.rowptr).to(dev)
+    colind = torch.from_numpy(s.colind).to(dev)
+    A = torch.from_numpy(s.vals).to(dev)
+    b = torch.from_numpy(s.b).to(dev)
+    x = torch.zeros_like(b)
+    pat = ab.Pattern(rowptr, colind)
+    fac = ab.Factors(pat, args.dtype)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        x.zero_()
+        return ab.fgmres_solve(pat, A, fac, b, x, restart=RESTART, rtol=RTOL,
+                               build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=APPLY_SWEEPS,
+                               apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode,
+                               raise_on_noconv=True)
+
+    for _ in range(args.warmup):
+        res = solve()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    evs = _events(torch, args.steps + 1)
+    barrier()
+    clocks.start()
+    l0 = ab.kernel_launches()
+    evs[0].record(stream)
+    iters = []
+    for k in range(args.steps):
+        res = solve()
+        iters.append(res.iters)
+        evs[k + 1].record(stream)
+    barrier()
+    launches = ab.kernel_launches() - l0
+    clk = clocks.stop()
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms * 1e-3)
+
+    # ---- end to end: A and b from pinned host memory, x back, every step
+    hA = torch.from_numpy(s.vals).pin_memory()
+    hb = torch.from_numpy(s.b).pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    dA = torch.empty_like(A)
+    db = torch.empty_like(b)
+    dx = torch.empty_like(b)
+
+    def e2e_step():
+        dA.copy_(hA, non_blocking=True)
+        db.copy_(hb, non_blocking=True)
+        dx.zero_()
+        ab.fgmres_solve(pat, dA, fac, db, dx, restart=RESTART, rtol=RTOL,
+                        build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=APPLY_SWEEPS,
+                        apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode, raise_on_noconv=True)
+        hx.copy_(dx, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    e0, e1 = _events(torch, 2)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * args.steps / (e2e_ms * 1e-3), "unit": "solves/s",
+           "h2d_bytes_per_step": hA.numel() * 8 + hb.numel() * 8,
+           "d2h_bytes_per_step": hx.numel() * 8}
+
+    # ---- per-kernel rooflines (the dominant kernel by solve time share)
+    fk = ab.Factors(pat, "f32")
+    fk.build(A, BUILD_SWEEPS, "sync")
+    kern = kernel_rooflines(torch, ab, pat, A, fk, s, peak)
+    it = statistics.median(iters)
+    per_solve = {"spmv_f64": it + 2, "build_sweep_f32": BUILD_SWEEPS,
+                 "lower+upper_sweep_f32": it * (APPLY_SWEEPS - 1)}
+    share = {k: kern[k]["us"] * per_solve[k] for k in kern}
+    dom = max(share, key=share.get)
+    dk = kern[dom]
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(dk["GBs"], 1), "peak": peak,
+            "unit": "GB/s", "frac": round(dk["frac"], 4),
+            "traffic": None, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": dk["bytes"] / dk["launches_per_call"]}
+    kernels = {k: {"us_per_call": round(v["us"], 2), "GBs": round(v["GBs"], 1),
+                   "frac_of_measured_peak": round(v["frac"], 4),
+                   "us_per_solve": round(share[k], 1)} for k, v in kern.items()}
+
+    # ---- variants (same workload, fewer steps)
+    variants = {}
+    if args.variants:
+        for dt, md in (("f64", "sync"), ("f32", "sync"), ("f32", "async"), ("bf16", "sync"),
+                       ("f64", "async")):
+            fv = ab.Factors(pat, dt)
+            xv = torch.zeros_like(b)
+
+            def sv():
+                xv.zero_()
+                return ab.fgmres_solve(pat, A, fv, b, xv, restart=RESTART, rtol=RTOL,
+                                       build_sweeps=BUILD_SWEEPS,
+                                       apply_sweeps_lower=APPLY_SWEEPS,
+                                       apply_sweeps_upper=APPLY_SWEEPS, mode=md)
+            r = sv()
+            sv()
+            torch.cuda.synchronize()
+            a0, a1 = _events(torch, 2)
+            a0.record(stream)
+            for _ in range(5):
+                r = sv()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            variants[f"{dt}_{md}"] = {"solves_per_s": round(5 / (a0.elapsed_time(a1) * 1e-3), 1),
+                                      "iters": r.iters, "rel_resid_true": r.rel_resid_true}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s)
+
+    if rank == 0:
+        sorted_ms = sorted(step_ms)
+        p50 = statistics.median(sorted_ms)
+        p99 = sorted_ms[min(len(sorted_ms) - 1, int(round(0.99 * (len(sorted_ms) - 1))))]
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells": s.n, "blocks": s.nnzb,
+                           "factor_dtype": args.dtype, "mode": args.mode,
+                           "build_sweeps": BUILD_SWEEPS, "apply_sweeps": APPLY_SWEEPS,
+                           "restart": RESTART, "rtol": RTOL, "iters": iters[-1],
+                           "rel_resid_true": res.rel_resid_true,
+                           "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (A = %.0f MB)" % (s.nnzb * 128 / 1e6)},
+                "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4)},
+                "gpu_launches": int(launches),
+                "e2e": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in e2e.items()},
+                "roofline": roof, "kernels": kernels, "variants": variants,
+                "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--mode", default="async", choices=["sync", "async"])
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.kernels_only:
+        return run_kernels_only(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

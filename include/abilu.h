@@ -1,0 +1,203 @@
+/*
+ * abilu.h — C ABI of the GB300 (sm_103a) asynchronous block ILU(0) library.
+ *
+ * The method: Kashi & Nadarajah, "An asynchronous incomplete block LU
+ * preconditioner for computational fluid dynamics on unstructured grids".
+ * A 4x4 block-sparse system A x = b (Sec. 2: the d+2 = 4 unknowns of a cell are
+ * contiguous) is solved by right-preconditioned flexible GMRES (Sec. 2, Sec. 6)
+ * with M = L U, where L and U are computed by fixed-point sweeps of Eq. (bilu)
+ * (Sec. 4.2) and applied by block triangular sweeps (Algorithm 5, Sec. 4.1).
+ *
+ * Conventions that hold for every entry point
+ * -------------------------------------------
+ * Storage. Block CSR with 4x4 blocks: rowptr int32[n+1], colind int32[nnzb],
+ *   column indices strictly increasing inside each row, the diagonal block
+ *   present in every row; values double[nnzb][4][4], each block row-major.
+ *   Vectors are double[n][4] (all 4 unknowns of a cell contiguous).
+ * Memory. Unless a parameter says "host", every pointer is a DEVICE pointer on
+ *   the current CUDA device, owned by the caller, and must stay valid until the
+ *   work enqueued on `stream` has finished.  Value and vector pointers must be
+ *   16-byte aligned.  Handles (abilu_pattern, abilu_factors) are owned by the
+ *   library and hold their own device memory, released by *_destroy.
+ * Streams. `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *   calls enqueue work on it and return without waiting, except the ones whose
+ *   description says they synchronise (they return a result that lives on the
+ *   device: pattern validation, fgmres_solve, abilu_factors_status).
+ * Errors. Every call returns an abilu_status; nothing aborts or throws across
+ *   the ABI and no kernel traps.  abilu_last_error() gives a message for the
+ *   last non-OK status of the calling thread.  ABILU_WARN_SINGULAR means the
+ *   call succeeded but a singular (or non-finite) diagonal block was replaced
+ *   by the identity for its inversion: the "modified iteration" of Sec. 4.2.
+ * Threads. Handles are not thread-safe: one host thread (or external locking)
+ *   per handle.  Different handles may be used concurrently on different streams.
+ */
+#ifndef ABILU_H
+#define ABILU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *abilu_stream; /* a cudaStream_t */
+
+typedef enum {
+    ABILU_OK = 0,
+    ABILU_EINVAL = 1,          /* bad argument or malformed pattern */
+    ABILU_ENOMEM = 2,          /* device allocation failed */
+    ABILU_ECUDA = 3,           /* a CUDA runtime call failed */
+    ABILU_ENOCONV = 4,         /* FGMRES stopped at max_iters above rtol */
+    ABILU_ETIMEOUT = 5,        /* a bounded device-side wait ran out */
+    ABILU_WARN_SINGULAR = 6    /* success, but singular diagonal blocks were replaced */
+} abilu_status;
+
+typedef enum {
+    ABILU_F64 = 0,             /* factors stored in FP64, sweeps in FP64 */
+    ABILU_F32 = 1,             /* factors stored in FP32, apply sweeps in FP32 */
+    ABILU_BF16 = 2             /* factors stored in BF16, apply sweeps in FP32 */
+} abilu_dtype;
+
+typedef enum {
+    ABILU_SYNC = 0,            /* Jacobi-type sweeps: every update reads the previous iterate */
+    ABILU_ASYNC = 1            /* in-place sweeps reading the latest values, no barrier between sweeps */
+} abilu_mode;
+
+typedef enum {
+    ABILU_INIT_FROM_A = 0,          /* X^0 = A (L^0 = strictly lower part of A, unscaled) */
+    ABILU_INIT_FROM_PREVIOUS = 1    /* X^0 = the factors currently in the handle (warm start) */
+} abilu_init;
+
+typedef struct abilu_pattern_s *abilu_pattern;
+typedef struct abilu_factors_s *abilu_factors;
+
+/* Library version string, e.g. "abilu-gb300 0.1". Host memory, static. */
+const char *abilu_version(void);
+
+/* Message for the last non-OK status returned to the calling thread (static). */
+const char *abilu_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads, all devices).  Instrumentation: the difference across a region
+ * is how many of the library's kernels ran in it. */
+uint64_t abilu_kernel_launches(void);
+
+/*
+ * Pattern analysis (the block sparsity pattern S_B of Sec. 4.2, which must
+ * contain every diagonal block).  Copies rowptr/colind (device pointers) into
+ * the handle, checks them, finds the diagonal of each row, splits every row
+ * into its strictly lower (L) and strictly upper (U) blocks, and lists for
+ * every block (i,j) the product pairs (L_ik, U_kj), k < min(i,j), of Eq. (bilu)
+ * whose two blocks are both in S_B.  Synchronises `stream` (it reads back the
+ * validation result).  ABILU_EINVAL for n < 1, nnzb < n, unsorted or
+ * out-of-range columns or a missing diagonal block.  *out is set on success.
+ */
+abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int32_t *rowptr,
+                                  const int32_t *colind, abilu_stream stream,
+                                  abilu_pattern *out);
+void abilu_pattern_destroy(abilu_pattern p);
+
+/* Host-side counts of a pattern: n, nnzb, strictly-lower blocks, strictly-upper
+ * blocks, product pairs, largest row length.  `out` is host int64_t[6]. */
+abilu_status abilu_pattern_counts(abilu_pattern p, int64_t *out);
+
+/*
+ * Factor storage for one pattern: L (strictly lower blocks), U (strictly upper
+ * blocks), inv(U_ii) and U_ii, in `dtype`, plus the work vectors of the
+ * triangular sweeps.  The inversions and the build arithmetic are FP64 in every
+ * dtype; only storage (and, for F32/BF16, the apply sweeps) is narrower.
+ */
+abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype, abilu_factors *out);
+void abilu_factors_destroy(abilu_factors f);
+
+/*
+ * Build the preconditioner: `nsweeps` fixed-point sweeps of Eq. (bilu),
+ *   U_ij = A_ij - sum_{k<i} L_ik U_kj            (i <= j),
+ *   L_ij = (A_ij - sum_{k<j} L_ik U_kj) U_jj^-1  (i > j),
+ * over every block of S_B at once.  ABILU_SYNC: x^{n+1} = h(x^n) (Eq.
+ * seq_blockilu_fp), deterministic and bit-reproducible; ABILU_ASYNC: in-place
+ * updates reading whatever values are current, work items = block rows taken
+ * in chunks from a queue, no barrier between sweeps (Algorithm 4 with blocks,
+ * Eq. async_blockilu_fp).  `A_vals` double[nnzb][4][4] on the device.
+ * nsweeps >= 0 (0 leaves X^0).  Singular diagonal blocks met during the build
+ * are counted on the device; read them with abilu_factors_status.
+ */
+abilu_status abilu_build(abilu_factors f, const double *A_vals, int nsweeps, abilu_mode mode,
+                         abilu_init init, abilu_stream stream);
+
+/*
+ * Apply the preconditioner, z ~= (L U)^{-1} r: `nsweeps_lower` sweeps on
+ * L y = r from y = 0, then `nsweeps_upper` sweeps on U z = y from z = 0
+ * (Algorithm 5 and its backward analogue, zero initial guesses, Sec. 6 setup).
+ * ABILU_SYNC: Jacobi sweeps; ABILU_ASYNC: in-place sweeps (backward row order
+ * for U) with no barrier between sweeps.  r and z are double[n][4], distinct.
+ * Sweep counts >= 0; 0 lower sweeps gives y = 0.
+ */
+abilu_status abilu_apply(abilu_factors f, const double *r, double *z, int nsweeps_lower,
+                         int nsweeps_upper, abilu_mode mode, abilu_stream stream);
+
+/*
+ * Block sparse matrix-vector product y = alpha * A x + beta * y (FP64), the
+ * product FGMRES needs once per iteration (Sec. 6 setup).  x and y distinct.
+ * beta == 0 does not read y.
+ */
+abilu_status bsr_spmv(abilu_pattern p, const double *A_vals, double alpha, const double *x,
+                      double beta, double *y, abilu_stream stream);
+
+/*
+ * Copy the factors out in A's pattern layout, FP64: X[nnzb][4][4] holds L_ij at
+ * positions with column < row and U_ij at column >= row; Dinv[n][4][4] holds
+ * inv(U_ii).  Either pointer may be NULL.
+ */
+abilu_status abilu_factors_export(abilu_factors f, double *X, double *Dinv, abilu_stream stream);
+
+/* Synchronises `stream`, then returns in *singular_blocks (host) how many
+ * singular diagonal blocks the builds since the last call replaced, and resets
+ * the count. */
+abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_blocks, abilu_stream stream);
+
+typedef struct {
+    int32_t restart;            /* m of FGMRES(m); 1..64 */
+    int32_t max_iters;          /* total Arnoldi steps over all restarts */
+    double rtol;                /* stop at ||b - A x|| <= rtol ||b|| */
+    int32_t build_sweeps;       /* sweeps of abilu_build done inside the solve */
+    int32_t apply_sweeps_lower; /* sweeps on L per preconditioner application */
+    int32_t apply_sweeps_upper; /* sweeps on U per preconditioner application */
+    int32_t mode;               /* abilu_mode for build and apply */
+    int32_t build;              /* 1: build the factors from A inside the solve; 0: use them as they are */
+    int32_t init;               /* abilu_init for that build */
+    int32_t reorth;             /* 0: one classical Gram-Schmidt pass; 1: two passes (CGS2) */
+} fgmres_opts;
+
+typedef struct {
+    int32_t iters;              /* Arnoldi steps over all restarts */
+    int32_t restarts;           /* restart cycles completed */
+    double rel_resid_est;       /* last Givens estimate / ||b|| */
+    double rel_resid_true;      /* ||b - A x|| / ||b|| computed in FP64 at exit */
+    int64_t singular_blocks;    /* singular diagonal blocks replaced in the build */
+    int32_t status;             /* abilu_status of the solve */
+} fgmres_result;
+
+/* Defaults: restart 30, max_iters 2500, rtol 1e-6, 1 build / 3+3 apply sweeps
+ * (the paper's choice, Sec. 6.1), ABILU_ASYNC, build from A, reorth 0. */
+void fgmres_default_opts(fgmres_opts *opts);
+
+/*
+ * Solve A x = b by FGMRES(m) right-preconditioned with block ILU(0) (Sec. 2,
+ * Sec. 6 setup): x holds x0 on entry (double[n][4], device) and the solution
+ * on return.  `f` is a factors handle of pattern `p` (built inside the solve
+ * when opts->build is 1).  Arnoldi, Givens rotations, the SpMV and the true
+ * residual are FP64 whatever the factor dtype.  `res` (host) is filled.
+ * Synchronises `stream`.  Returns ABILU_ENOCONV (with res filled) when
+ * max_iters is reached above rtol; ABILU_WARN_SINGULAR on a converged solve
+ * whose build replaced singular blocks.
+ */
+abilu_status fgmres_solve(abilu_pattern p, const double *A_vals, abilu_factors f,
+                          const double *b, double *x, const fgmres_opts *opts,
+                          fgmres_result *res, abilu_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ABILU_H */

@@ -1,0 +1,230 @@
+"""Thin Python binding of libabilu (the C ABI in include/abilu.h).
+
+Argument marshalling only: torch tensors supply device memory and
+``torch.cuda`` streams supply the stream handle; every step of the
+computation runs in the library's CUDA kernels.  There is no CPU fallback:
+if libabilu.so is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libabilu.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; "
+                      "g.build()'` (needs nvcc)")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ETIMEOUT, WARN_SINGULAR = range(7)
+STATUS_NAMES = {0: "ABILU_OK", 1: "ABILU_EINVAL", 2: "ABILU_ENOMEM", 3: "ABILU_ECUDA",
+                4: "ABILU_ENOCONV", 5: "ABILU_ETIMEOUT", 6: "ABILU_WARN_SINGULAR"}
+DTYPES = {"f64": 0, "f32": 1, "bf16": 2}
+MODES = {"sync": 0, "async": 1}
+INITS = {"a": 0, "previous": 1}
+
+# every symbol the header declares
+EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_pattern_create", "abilu_pattern_destroy",
+           "abilu_pattern_counts", "abilu_factors_create", "abilu_factors_destroy", "abilu_build",
+           "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
+           "fgmres_default_opts", "fgmres_solve")
+
+
+class FgmresOpts(C.Structure):
+    _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
+                ("build_sweeps", C.c_int32), ("apply_sweeps_lower", C.c_int32),
+                ("apply_sweeps_upper", C.c_int32), ("mode", C.c_int32), ("build", C.c_int32),
+                ("init", C.c_int32), ("reorth", C.c_int32)]
+
+
+class FgmresResult(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("restarts", C.c_int32), ("rel_resid_est", C.c_double),
+                ("rel_resid_true", C.c_double), ("singular_blocks", C.c_int64),
+                ("status", C.c_int32)]
+
+
+_vp, _i32, _i64, _f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_lib.abilu_version.restype = C.c_char_p
+_lib.abilu_last_error.restype = C.c_char_p
+_lib.abilu_kernel_launches.restype = C.c_uint64
+_lib.abilu_kernel_launches.argtypes = []
+_lib.abilu_pattern_create.argtypes = [_i32, _i32, _vp, _vp, _vp, C.POINTER(_vp)]
+_lib.abilu_pattern_destroy.argtypes = [_vp]
+_lib.abilu_pattern_destroy.restype = None
+_lib.abilu_pattern_counts.argtypes = [_vp, C.POINTER(_i64)]
+_lib.abilu_factors_create.argtypes = [_vp, C.c_int, C.POINTER(_vp)]
+_lib.abilu_factors_destroy.argtypes = [_vp]
+_lib.abilu_factors_destroy.restype = None
+_lib.abilu_build.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
+_lib.abilu_apply.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
+_lib.bsr_spmv.argtypes = [_vp, _vp, _f64, _vp, _f64, _vp, _vp]
+_lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
+_lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
+_lib.fgmres_default_opts.argtypes = [C.POINTER(FgmresOpts)]
+_lib.fgmres_default_opts.restype = None
+_lib.fgmres_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, C.POINTER(FgmresOpts),
+                              C.POINTER(FgmresResult), _vp]
+for _nm in ("abilu_pattern_create", "abilu_pattern_counts", "abilu_factors_create", "abilu_build",
+            "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
+            "fgmres_solve"):
+    getattr(_lib, _nm).restype = C.c_int
+
+
+class AbiluError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def version() -> str:
+    return _lib.abilu_version().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(_lib.abilu_kernel_launches())
+
+
+def _check(status, allow=(OK,)):
+    if status not in allow:
+        raise AbiluError(status, _lib.abilu_last_error().decode())
+    return status
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype, numel=None, what="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} must have {numel} elements, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Pattern:
+    """Analysed block pattern (abilu_pattern_create)."""
+
+    def __init__(self, rowptr, colind, stream=None):
+        import torch
+        n = rowptr.numel() - 1
+        nnzb = colind.numel()
+        h = C.c_void_p()
+        _check(_lib.abilu_pattern_create(n, nnzb, _ptr(rowptr, torch.int32, what="rowptr"),
+                                         _ptr(colind, torch.int32, what="colind"),
+                                         _stream(stream), C.byref(h)))
+        self.handle = h
+        self.n, self.nnzb = n, nnzb
+
+    def counts(self) -> dict:
+        out = (C.c_int64 * 6)()
+        _check(_lib.abilu_pattern_counts(self.handle, out))
+        return dict(zip(("n", "nnzb", "nl", "nu", "npairs", "max_row"), list(out)))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.abilu_pattern_destroy(h)
+            self.handle = None
+
+
+class Factors:
+    """Factor storage of one pattern (abilu_factors_create)."""
+
+    def __init__(self, pattern: Pattern, dtype: str = "f32"):
+        h = C.c_void_p()
+        _check(_lib.abilu_factors_create(pattern.handle, DTYPES[dtype], C.byref(h)))
+        self.handle = h
+        self.pattern = pattern
+        self.dtype = dtype
+
+    def build(self, A, nsweeps, mode="sync", init="a", stream=None):
+        import torch
+        _check(_lib.abilu_build(self.handle, _ptr(A, torch.float64, 16 * self.pattern.nnzb, "A"),
+                                int(nsweeps), MODES[mode], INITS[init], _stream(stream)))
+
+    def apply(self, r, z, nsweeps_lower, nsweeps_upper, mode="sync", stream=None):
+        import torch
+        nv = 4 * self.pattern.n
+        _check(_lib.abilu_apply(self.handle, _ptr(r, torch.float64, nv, "r"),
+                                _ptr(z, torch.float64, nv, "z"), int(nsweeps_lower),
+                                int(nsweeps_upper), MODES[mode], _stream(stream)))
+
+    def export(self, stream=None):
+        import torch
+        X = torch.empty((self.pattern.nnzb, 4, 4), dtype=torch.float64, device="cuda")
+        D = torch.empty((self.pattern.n, 4, 4), dtype=torch.float64, device="cuda")
+        _check(_lib.abilu_factors_export(self.handle, _ptr(X, torch.float64),
+                                         _ptr(D, torch.float64), _stream(stream)))
+        return X, D
+
+    def singular_blocks(self, stream=None) -> int:
+        v = C.c_int64()
+        _check(_lib.abilu_factors_status(self.handle, C.byref(v), _stream(stream)))
+        return v.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.abilu_factors_destroy(h)
+            self.handle = None
+
+
+def bsr_spmv(pattern: Pattern, A, x, y, alpha=1.0, beta=0.0, stream=None):
+    import torch
+    nv = 4 * pattern.n
+    _check(_lib.bsr_spmv(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
+                         float(alpha), _ptr(x, torch.float64, nv, "x"), float(beta),
+                         _ptr(y, torch.float64, nv, "y"), _stream(stream)))
+
+
+@dataclass
+class SolveResult:
+    iters: int
+    restarts: int
+    rel_resid_est: float
+    rel_resid_true: float
+    singular_blocks: int
+    status: int
+
+    @property
+    def converged(self) -> bool:
+        return self.status in (OK, WARN_SINGULAR)
+
+
+def default_opts() -> FgmresOpts:
+    o = FgmresOpts()
+    _lib.fgmres_default_opts(C.byref(o))
+    return o
+
+
+def fgmres_solve(pattern: Pattern, A, factors: Factors, b, x, restart=30, max_iters=2500,
+                 rtol=1e-6, build_sweeps=1, apply_sweeps_lower=3, apply_sweeps_upper=3,
+                 mode="async", build=True, init="a", reorth=False, stream=None,
+                 raise_on_noconv=False) -> SolveResult:
+    import torch
+    o = FgmresOpts(int(restart), int(max_iters), float(rtol), int(build_sweeps),
+                   int(apply_sweeps_lower), int(apply_sweeps_upper), MODES[mode], int(bool(build)),
+                   INITS[init], int(bool(reorth)))
+    r = FgmresResult()
+    nv = 4 * pattern.n
+    st = _lib.fgmres_solve(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
+                           factors.handle, _ptr(b, torch.float64, nv, "b"),
+                           _ptr(x, torch.float64, nv, "x"), C.byref(o), C.byref(r),
+                           _stream(stream))
+    _check(st, allow=(OK, WARN_SINGULAR) if raise_on_noconv else (OK, WARN_SINGULAR, ENOCONV))
+    return SolveResult(r.iters, r.restarts, r.rel_resid_est, r.rel_resid_true,
+                       r.singular_blocks, st)

@@ -1,0 +1,161 @@
+// C ABI entry points: factor handles and their device memory, build, apply,
+// SpMV, export.  Pattern analysis lives in pattern.cu, FGMRES in fgmres.cu.
+#include <string.h>
+
+#include "common.cuh"
+
+namespace abilu {
+
+abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
+                            abilu_init init, cudaStream_t st);
+abilu_status apply_dispatch(abilu_factors f, const double *r, double *z, int nl, int nu,
+                            abilu_mode mode, cudaStream_t st, const int *skip);
+abilu_status export_dispatch(abilu_factors f, double *X, double *Dinv, cudaStream_t st);
+abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
+                         double beta, double *y, cudaStream_t st, const int *skip);
+size_t solve_state_bytes();
+size_t host_status_bytes();
+int max_restart();
+
+constexpr int MAXM_PARTIAL_STRIDE = 66;  // MAXM + 2 doubles per CTA
+
+int red_ctas() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached = 4 * (sms > 0 ? sms : 1);
+    }
+    return cached;
+}
+
+static inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+abilu_status ensure_krylov(abilu_factors f, int m) {
+    if (f->krylov && f->krylov_m >= m) return ABILU_OK;
+    if (f->krylov) cudaFree(f->krylov);
+    f->krylov = nullptr;
+    f->krylov_m = 0;
+    const size_t nv = (size_t)f->p->v.n * BS;
+    // V: m+1 vectors, Z: m vectors, w: 1 vector
+    ABILU_CUDA(cudaMalloc(&f->krylov, sizeof(double) * nv * (2 * (size_t)m + 2)));
+    f->krylov_m = m;
+    return ABILU_OK;
+}
+
+}  // namespace abilu
+
+using namespace abilu;
+
+static void factors_free(abilu_factors f) {
+    if (!f) return;
+    if (f->krylov) cudaFree(f->krylov);
+    if (f->mem) cudaFree(f->mem);
+    if (f->host_status) cudaFreeHost(f->host_status);
+    delete f;
+}
+
+extern "C" void abilu_factors_destroy(abilu_factors f) { factors_free(f); }
+
+extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype, abilu_factors *out) {
+    if (!p || !out) return fail(ABILU_EINVAL, "factors_create: NULL argument");
+    *out = nullptr;
+    size_t esz;
+    switch (dtype) {
+    case ABILU_F64: esz = 8; break;
+    case ABILU_F32: esz = 4; break;
+    case ABILU_BF16: esz = 2; break;
+    default: return fail(ABILU_EINVAL, "factors_create: bad dtype %d", (int)dtype);
+    }
+    const PatternView &v = p->v;
+    const size_t vt = dtype == ABILU_F64 ? 8 : 4;
+    auto rnd = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t bl = rnd(esz * BB * (size_t)(v.nl > 0 ? v.nl : 1));
+    const size_t bu = rnd(esz * BB * (size_t)(v.nu > 0 ? v.nu : 1));
+    const size_t bd = rnd(esz * BB * (size_t)v.n);
+    const size_t bv = rnd(vt * BS * (size_t)v.n);
+    const size_t bc = rnd(sizeof(unsigned long long) * 4);
+    const size_t bs = rnd(solve_state_bytes());
+    const size_t bp = rnd(sizeof(double) * MAXM_PARTIAL_STRIDE * (size_t)red_ctas());
+    const size_t total = 2 * bl + 2 * bu + 3 * bd + 4 * bv + bc + bs + bp;
+    abilu_factors f = new abilu_factors_s();
+    memset(f, 0, sizeof *f);
+    f->p = p;
+    f->dtype = dtype;
+    f->esz = esz;
+    cudaError_t e = cudaMalloc(&f->mem, total);
+    if (e != cudaSuccess) { factors_free(f); return cuda_fail(e, "factors_create: cudaMalloc"); }
+    char *m = reinterpret_cast<char *>(f->mem);
+    f->L[0] = m; m += bl;
+    f->L[1] = m; m += bl;
+    f->U[0] = m; m += bu;
+    f->U[1] = m; m += bu;
+    f->D[0] = m; m += bd;
+    f->D[1] = m; m += bd;
+    f->Udiag = m; m += bd;
+    f->y[0] = m; m += bv;
+    f->y[1] = m; m += bv;
+    f->x[0] = m; m += bv;
+    f->x[1] = m; m += bv;
+    f->ctr = reinterpret_cast<unsigned long long *>(m); m += bc;
+    f->scal = reinterpret_cast<double *>(m); m += bs;
+    f->partials = reinterpret_cast<double *>(m); m += bp;
+    e = cudaMemset(f->mem, 0, total);
+    if (e == cudaSuccess) e = cudaHostAlloc(&f->host_status, host_status_bytes(), cudaHostAllocMapped);
+    if (e != cudaSuccess) { factors_free(f); return cuda_fail(e, "factors_create"); }
+    memset(f->host_status, 0, host_status_bytes());
+    f->cur = 0;
+    *out = f;
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_build(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
+                                    abilu_init init, abilu_stream stream) {
+    if (!f || !A) return fail(ABILU_EINVAL, "build: NULL argument");
+    if (!aligned16(A)) return fail(ABILU_EINVAL, "build: A_vals must be 16-byte aligned");
+    if (nsweeps < 0) return fail(ABILU_EINVAL, "build: nsweeps < 0");
+    if (mode != ABILU_SYNC && mode != ABILU_ASYNC) return fail(ABILU_EINVAL, "build: bad mode");
+    if (init != ABILU_INIT_FROM_A && init != ABILU_INIT_FROM_PREVIOUS)
+        return fail(ABILU_EINVAL, "build: bad init");
+    return build_dispatch(f, A, nsweeps, mode, init, S(stream));
+}
+
+extern "C" abilu_status abilu_apply(abilu_factors f, const double *r, double *z, int nl, int nu,
+                                    abilu_mode mode, abilu_stream stream) {
+    if (!f || !r || !z) return fail(ABILU_EINVAL, "apply: NULL argument");
+    if (r == z) return fail(ABILU_EINVAL, "apply: r and z must be distinct");
+    if (!aligned16(r) || !aligned16(z)) return fail(ABILU_EINVAL, "apply: vectors must be 16-byte aligned");
+    if (nl < 0 || nu < 0) return fail(ABILU_EINVAL, "apply: negative sweep count");
+    if (mode != ABILU_SYNC && mode != ABILU_ASYNC) return fail(ABILU_EINVAL, "apply: bad mode");
+    return apply_dispatch(f, r, z, nl, nu, mode, S(stream), nullptr);
+}
+
+extern "C" abilu_status bsr_spmv(abilu_pattern p, const double *A, double alpha, const double *x,
+                                 double beta, double *y, abilu_stream stream) {
+    if (!p || !A || !x || !y) return fail(ABILU_EINVAL, "spmv: NULL argument");
+    if (x == y) return fail(ABILU_EINVAL, "spmv: x and y must be distinct");
+    if (!aligned16(A) || !aligned16(x) || !aligned16(y))
+        return fail(ABILU_EINVAL, "spmv: pointers must be 16-byte aligned");
+    return spmv_launch(p->v, A, alpha, x, beta, y, S(stream), nullptr);
+}
+
+extern "C" abilu_status abilu_factors_export(abilu_factors f, double *X, double *Dinv,
+                                             abilu_stream stream) {
+    if (!f) return fail(ABILU_EINVAL, "export: NULL factors");
+    if ((X && !aligned16(X)) || (Dinv && !aligned16(Dinv)))
+        return fail(ABILU_EINVAL, "export: pointers must be 16-byte aligned");
+    if (!X && !Dinv) return ABILU_OK;
+    return export_dispatch(f, X, Dinv, S(stream));
+}
+
+extern "C" abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_blocks,
+                                             abilu_stream stream) {
+    if (!f || !singular_blocks) return fail(ABILU_EINVAL, "factors_status: NULL argument");
+    unsigned long long v = 0;
+    ABILU_CUDA(cudaMemcpyAsync(&v, f->ctr, sizeof v, cudaMemcpyDeviceToHost, S(stream)));
+    ABILU_CUDA(cudaStreamSynchronize(S(stream)));
+    ABILU_CUDA(cudaMemsetAsync(f->ctr, 0, sizeof v, S(stream)));
+    *singular_blocks = (int64_t)v;
+    return ABILU_OK;
+}

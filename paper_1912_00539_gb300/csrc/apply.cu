@@ -1,0 +1,308 @@
+// Preconditioner application by block triangular sweeps (Sec. 4.1).
+//
+//   lower:  y_i <- b_i - sum_{j<i} L_ij y_j          (L_ii = I, Sec. 2)
+//   upper:  x_i <- U_ii^{-1} (y_i - sum_{j>i} U_ij x_j)
+//
+// from zero initial guesses (Sec. 6 setup), n_L sweeps then n_U sweeps.  SYNC
+// runs Jacobi sweeps (every read from the previous sweep's vector, double
+// buffered); ASYNC runs in-place sweeps with no barrier between them
+// (Algorithm 5; backward row order for U), chunks of rows handed out in order
+// by a ticket counter.
+//
+// Sync-mode shortcuts that do not change the result: from y^0 = 0 the first
+// lower sweep gives y^1 = b exactly, so it is not run (the second sweep reads b
+// as y^1); and x^1 = Dinv_i y_i needs only row i, so it is fused into the last
+// lower sweep.  The last upper sweep writes the FP64 output directly.
+//
+// Thread mapping: a quad per block row, thread q computes unknown q of the
+// row: it reads row q of each factor block (one 16-byte load for FP32, 32 for
+// FP64, 8 for BF16; contiguous across the quad) and the neighbour's 4 unknowns
+// (one vector load, shared by the quad).  FP32 and BF16 factors run in FP32;
+// FP64 factors in FP64.
+#include "common.cuh"
+
+namespace abilu {
+
+constexpr int APPLY_THREADS = 256;
+constexpr int APPLY_ROWS = APPLY_THREADS / 4;
+
+template <typename T> struct ApplyArith { using VT = float; };
+template <> struct ApplyArith<double> { using VT = double; };
+
+__device__ __forceinline__ bool skipped(const int *skip) {
+    return skip && *reinterpret_cast<const volatile int *>(skip);
+}
+
+// 4 unknowns of cell j as the compute type
+template <typename VT, typename YT>
+__device__ __forceinline__ void ld_cell(const YT *v, int j, VT out[4]) {
+    ld_row(v + (size_t)j * BS, out);
+}
+
+template <typename VT>
+__device__ __forceinline__ VT dot4(const VT a[4], const VT b[4]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
+}
+
+// x_i = Dinv_i t_i where thread q holds t_i[q]; returns x_i[q]
+template <typename T, typename VT>
+__device__ __forceinline__ VT dinv_times(const T *__restrict__ D, int i, VT t) {
+    const int q = threadIdx.x & 3;
+    VT d[4], tv[4];
+    ld_row(D + (size_t)i * BB + q * BS, d);
+    tv[0] = qshfl(t, 0); tv[1] = qshfl(t, 1); tv[2] = qshfl(t, 2); tv[3] = qshfl(t, 3);
+    return dot4(d, tv);
+}
+
+// one Jacobi lower sweep; optionally x^1 = Dinv y fused (into x1 or, when
+// it is the last upper result, into z as FP64)
+template <typename T, typename VT, typename YIN>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_lower_sync(PatternView P, const T *__restrict__ L, const double *__restrict__ r,
+             const YIN *__restrict__ yin, VT *__restrict__ yout, const T *__restrict__ D,
+             VT *__restrict__ x1, double *__restrict__ z, const int *skip) {
+    if (skipped(skip)) return;
+    const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    if (i >= P.n) return;
+    VT s = (VT)r[(size_t)i * BS + q];
+    const int l1 = P.lrow[i + 1];
+    for (int l = P.lrow[i]; l < l1; l++) {
+        const int j = P.lcol[l];
+        VT lr[4], yj[4];
+        ld_row(L + (size_t)l * BB + q * BS, lr);
+        ld_cell(yin, j, yj);
+        s -= dot4(lr, yj);
+    }
+    yout[(size_t)i * BS + q] = s;
+    if (x1 || z) {
+        VT x = dinv_times<T, VT>(D, i, s);
+        if (x1) x1[(size_t)i * BS + q] = x;
+        if (z) z[(size_t)i * BS + q] = (double)x;
+    }
+}
+
+// x^1 = Dinv y (used when fewer than two lower sweeps run)
+template <typename T, typename VT, typename YIN>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_diag_apply(PatternView P, const T *__restrict__ D, const YIN *__restrict__ y,
+             VT *__restrict__ x1, double *__restrict__ z, const int *skip) {
+    if (skipped(skip)) return;
+    const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    if (i >= P.n) return;
+    VT t = (VT)y[(size_t)i * BS + q];
+    VT x = dinv_times<T, VT>(D, i, t);
+    if (x1) x1[(size_t)i * BS + q] = x;
+    if (z) z[(size_t)i * BS + q] = (double)x;
+}
+
+template <typename T, typename VT, typename YT>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
+             const YT *__restrict__ y, const VT *__restrict__ xin, VT *__restrict__ xout,
+             double *__restrict__ z, const int *skip) {
+    if (skipped(skip)) return;
+    const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    if (i >= P.n) return;
+    VT s = (VT)y[(size_t)i * BS + q];
+    const int u1 = P.urow[i + 1];
+    for (int u = P.urow[i]; u < u1; u++) {
+        const int j = P.ucol[u];
+        VT ur[4], xj[4];
+        ld_row(U + (size_t)u * BB + q * BS, ur);
+        ld_cell(xin, j, xj);
+        s -= dot4(ur, xj);
+    }
+    VT x = dinv_times<T, VT>(D, i, s);
+    if (xout) xout[(size_t)i * BS + q] = x;
+    if (z) z[(size_t)i * BS + q] = (double)x;
+}
+
+// ---------------------------------------------------------------- async
+template <typename VT> __device__ __forceinline__ void st_vol(VT *p, VT v);
+template <> __device__ __forceinline__ void st_vol<float>(float *p, float v) {
+    asm volatile("st.volatile.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+template <> __device__ __forceinline__ void st_vol<double>(double *p, double v) {
+    asm volatile("st.volatile.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// In-place lower sweeps over all nsweeps, y must hold 0 on entry.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_lower_async(PatternView P, const T *__restrict__ L, const double *__restrict__ r, VT *y,
+              int nsweeps, unsigned long long *ticket, const int *skip) {
+    if (skipped(skip)) return;
+    __shared__ unsigned long long s_t;
+    const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
+    const long long total = nchunks * nsweeps;
+    const int q = threadIdx.x & 3;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const long long t = (long long)s_t;
+        __syncthreads();
+        if (t >= total) break;
+        const int i = (int)(t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
+        if (i < P.n) {
+            VT s = (VT)r[(size_t)i * BS + q];
+            const int l1 = P.lrow[i + 1];
+            for (int l = P.lrow[i]; l < l1; l++) {
+                const int j = P.lcol[l];
+                VT lr[4], yj[4];
+                ld_row(L + (size_t)l * BB + q * BS, lr);
+                ld_row_volatile(y + (size_t)j * BS, yj);
+                s -= dot4(lr, yj);
+            }
+            st_vol(y + (size_t)i * BS + q, s);
+        }
+    }
+}
+
+// In-place upper sweeps, chunks in backward order; x must hold 0 on entry.
+// The last sweep of each chunk also writes the FP64 result z.
+template <typename T, typename VT, typename YT>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
+              const YT *__restrict__ y, VT *x, double *__restrict__ z, int nsweeps,
+              unsigned long long *ticket, const int *skip) {
+    if (skipped(skip)) return;
+    __shared__ unsigned long long s_t;
+    const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
+    const long long total = nchunks * nsweeps;
+    const int q = threadIdx.x & 3;
+    for (;;) {
+        if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1ull);
+        __syncthreads();
+        const long long t = (long long)s_t;
+        __syncthreads();
+        if (t >= total) break;
+        const bool last = t / nchunks == nsweeps - 1;
+        const int i = (int)(nchunks - 1 - t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
+        if (i < P.n) {  // quads of one row stay together: the shuffles below are quad-local
+            VT s = (VT)y[(size_t)i * BS + q];
+            const int u1 = P.urow[i + 1];
+            for (int u = P.urow[i]; u < u1; u++) {
+                const int j = P.ucol[u];
+                VT ur[4], xj[4];
+                ld_row(U + (size_t)u * BB + q * BS, ur);
+                ld_row_volatile(x + (size_t)j * BS, xj);
+                s -= dot4(ur, xj);
+            }
+            VT xi = dinv_times<T, VT>(D, i, s);
+            st_vol(x + (size_t)i * BS + q, xi);
+            if (last) z[(size_t)i * BS + q] = (double)xi;
+        }
+    }
+}
+
+template <typename K>
+static int resident_ctas(K kernel, int threads) {
+    int dev = 0, per_sm = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int c = per_sm * sms;
+    return c > 0 ? c : 1;
+}
+
+template <typename T>
+static abilu_status apply_t(abilu_factors f, const double *r, double *z, int nl, int nu,
+                            abilu_mode mode, cudaStream_t st, const int *skip) {
+    using VT = typename ApplyArith<T>::VT;
+    const PatternView &P = f->p->v;
+    const int c = f->cur;
+    const T *L = reinterpret_cast<const T *>(f->L[c]);
+    const T *U = reinterpret_cast<const T *>(f->U[c]);
+    const T *D = reinterpret_cast<const T *>(f->D[c]);
+    VT *y[2] = {reinterpret_cast<VT *>(f->y[0]), reinterpret_cast<VT *>(f->y[1])};
+    VT *x[2] = {reinterpret_cast<VT *>(f->x[0]), reinterpret_cast<VT *>(f->x[1])};
+    const size_t vbytes = sizeof(VT) * (size_t)P.n * BS;
+    const int grid = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
+
+    if (mode == ABILU_ASYNC) {
+        const long long nchunks = grid;
+        if (nl > 0) {
+            ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
+            ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, 8, st));
+            static int ctas_l = resident_ctas(k_lower_async<T, VT>, APPLY_THREADS);
+            int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
+            k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, r, y[0], nl, f->ctr + 1, skip);
+            ABILU_LAUNCH_CHECK("k_lower_async");
+        } else {
+            ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
+        }
+        if (nu > 0) {
+            ABILU_CUDA(cudaMemsetAsync(x[0], 0, vbytes, st));
+            ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, 8, st));
+            static int ctas_u = resident_ctas(k_upper_async<T, VT, VT>, APPLY_THREADS);
+            int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
+            k_upper_async<T, VT, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, U, D, y[0], x[0], z, nu,
+                                                                 f->ctr + 1, skip);
+            ABILU_LAUNCH_CHECK("k_upper_async");
+        } else {
+            ABILU_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)P.n * BS, st));
+        }
+        return ABILU_OK;
+    }
+
+    // ---- synchronous: y^s lives in y[s & 1] (s >= 2), y^1 = r
+    const VT *yfin = nullptr;     // y^{n_L} when it is a VT vector
+    bool yfin_is_r = false;
+    bool x1_done = false;
+    if (nl == 0) {
+        ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
+        yfin = y[0];
+    } else if (nl == 1) {
+        yfin_is_r = true;
+    } else {
+        for (int s = 2; s <= nl; s++) {
+            const bool fuse = (s == nl) && nu >= 1;
+            VT *x1 = fuse && nu >= 2 ? x[1] : nullptr;
+            double *zz = fuse && nu == 1 ? z : nullptr;
+            if (s == 2)
+                k_lower_sync<T, VT, double><<<counted(grid), APPLY_THREADS, 0, st>>>(P, L, r, r, y[0], D, x1, zz, skip);
+            else
+                k_lower_sync<T, VT, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, L, r, y[(s - 1) & 1], y[s & 1], D, x1, zz, skip);
+            ABILU_LAUNCH_CHECK("k_lower_sync");
+            x1_done = fuse;
+        }
+        yfin = (nl == 2) ? y[0] : y[nl & 1];
+    }
+    // note: for s == 2 the output went to y[0] = y[2 & 1]; indices stay consistent
+    if (nu == 0) {
+        ABILU_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)P.n * BS, st));
+        return ABILU_OK;
+    }
+    if (!x1_done) {
+        VT *x1 = nu >= 2 ? x[1] : nullptr;
+        double *zz = nu == 1 ? z : nullptr;
+        if (yfin_is_r)
+            k_diag_apply<T, VT, double><<<counted(grid), APPLY_THREADS, 0, st>>>(P, D, r, x1, zz, skip);
+        else
+            k_diag_apply<T, VT, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, D, yfin, x1, zz, skip);
+        ABILU_LAUNCH_CHECK("k_diag_apply");
+    }
+    for (int s = 2; s <= nu; s++) {  // x^s in x[s & 1], last one to z
+        const bool last = s == nu;
+        VT *xo = last ? nullptr : x[s & 1];
+        double *zz = last ? z : nullptr;
+        if (yfin_is_r)
+            k_upper_sync<T, VT, double><<<counted(grid), APPLY_THREADS, 0, st>>>(P, U, D, r, x[(s - 1) & 1], xo, zz, skip);
+        else
+            k_upper_sync<T, VT, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, U, D, yfin, x[(s - 1) & 1], xo, zz, skip);
+        ABILU_LAUNCH_CHECK("k_upper_sync");
+    }
+    return ABILU_OK;
+}
+
+abilu_status apply_dispatch(abilu_factors f, const double *r, double *z, int nl, int nu,
+                            abilu_mode mode, cudaStream_t st, const int *skip) {
+    switch (f->dtype) {
+    case ABILU_F64: return apply_t<double>(f, r, z, nl, nu, mode, st, skip);
+    case ABILU_F32: return apply_t<float>(f, r, z, nl, nu, mode, st, skip);
+    case ABILU_BF16: return apply_t<__nv_bfloat16>(f, r, z, nl, nu, mode, st, skip);
+    }
+    return fail(ABILU_EINVAL, "apply: bad dtype");
+}
+
+}  // namespace abilu

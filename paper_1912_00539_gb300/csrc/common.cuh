@@ -1,0 +1,191 @@
+// Internal definitions shared by the CUDA translation units of libabilu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/abilu.h"
+
+namespace abilu {
+
+constexpr int BS = 4;    // block size b = d + 2 (Sec. 2)
+constexpr int BB = 16;   // entries per block
+
+// thread-local error message, set by fail()
+abilu_status fail(abilu_status s, const char *fmt, ...);
+abilu_status cuda_fail(cudaError_t e, const char *what);
+
+#define ABILU_CUDA(call)                                              \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::abilu::cuda_fail(e_, #call);  \
+    } while (0)
+
+#define ABILU_LAUNCH_CHECK(what)                                      \
+    do {                                                              \
+        cudaError_t e_ = cudaGetLastError();                          \
+        if (e_ != cudaSuccess) return ::abilu::cuda_fail(e_, what);   \
+    } while (0)
+
+inline cudaStream_t S(abilu_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Host-side count of kernel launches made by the library (every launch site
+// wraps its grid size in counted()); read through abilu_kernel_launches().
+void note_launch();
+template <typename G> inline G counted(G grid) { note_launch(); return grid; }
+
+// Device view of an analysed pattern.  Positions: "p" indexes A's blocks,
+// "lpos" indexes the compact strictly-lower array, "upos" the compact
+// strictly-upper array.  Row i's L blocks are lpos lrow[i]..lrow[i+1]-1 (the
+// first diagpos[i]-rowptr[i] blocks of row i in A's order), its U blocks are
+// upos urow[i]..urow[i+1]-1 (the blocks after the diagonal).
+struct PatternView {
+    int32_t n, nnzb, nl, nu;
+    int64_t npairs;
+    const int32_t *rowptr, *colind, *diagpos;
+    const int32_t *lrow, *urow, *lcol, *ucol;
+    const int32_t *pair_ptr;   // [nnzb+1] product pairs of block p
+    const int2 *pairs;         // (lpos of L_ik, upos of U_kj)
+};
+
+}  // namespace abilu
+
+struct abilu_pattern_s {
+    abilu::PatternView v;
+    int32_t max_row;
+    int device;
+    void *mem;                 // one allocation holding every array
+};
+
+struct abilu_factors_s {
+    abilu_pattern p;
+    abilu_dtype dtype;
+    size_t esz;                // bytes per stored scalar
+    // factor storage; [cur] is the current iterate, [1-cur] the sync target
+    void *L[2], *U[2], *D[2];
+    void *Udiag;
+    int cur;
+    // apply work vectors (VT = double for F64, float otherwise)
+    void *y[2], *x[2];
+    // device counters: [0] singular blocks, [1] async ticket counter,
+    // [2..3] spare
+    unsigned long long *ctr;
+    // FGMRES workspace (grown on demand)
+    double *krylov;            // V (m+1 vectors) then Z (m vectors)
+    int krylov_m;
+    double *scal;              // small device scalars (Hessenberg, Givens, ...)
+    double *partials;          // per-CTA reduction partials
+    void *host_status;         // pinned host mirror of the solve status
+    void *mem;
+};
+
+// ---------------------------------------------------------------- device helpers
+namespace abilu {
+
+__device__ __forceinline__ void ld_row(const double *p, double v[4]) {
+    double2 a = reinterpret_cast<const double2 *>(p)[0];
+    double2 b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld_row(const float *p, double v[4]) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld_row(const __nv_bfloat16 *p, double v[4]) {
+    uint2 u = *reinterpret_cast<const uint2 *>(p);
+    float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.x));
+    float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld_row(const float *p, float v[4]) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld_row(const __nv_bfloat16 *p, float v[4]) {
+    uint2 u = *reinterpret_cast<const uint2 *>(p);
+    float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.x));
+    float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld_row(const double *p, float v[4]) {
+    double w[4];
+    ld_row(p, w);
+    v[0] = (float)w[0]; v[1] = (float)w[1]; v[2] = (float)w[2]; v[3] = (float)w[3];
+}
+
+// volatile (relaxed, uncached-in-L1) loads for data other threads may be
+// writing concurrently: the in-place asynchronous sweeps.
+__device__ __forceinline__ void ld_row_volatile(const double *p, double v[4]) {
+    asm volatile("ld.volatile.global.v2.f64 {%0,%1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "l"(p));
+    asm volatile("ld.volatile.global.v2.f64 {%0,%1}, [%2];" : "=d"(v[2]), "=d"(v[3]) : "l"(p + 2));
+}
+__device__ __forceinline__ void ld_row_volatile(const float *p, float v[4]) {
+    asm volatile("ld.volatile.global.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
+}
+__device__ __forceinline__ void ld_row_volatile(const float *p, double v[4]) {
+    float w[4];
+    ld_row_volatile(p, w);
+    v[0] = w[0]; v[1] = w[1]; v[2] = w[2]; v[3] = w[3];
+}
+__device__ __forceinline__ void ld_row_volatile(const __nv_bfloat16 *p, double v[4]) {
+    unsigned a, b;
+    asm volatile("ld.volatile.global.v2.u32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "l"(p));
+    float2 x = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a));
+    float2 y = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&b));
+    v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+}
+__device__ __forceinline__ void ld_row_volatile(const __nv_bfloat16 *p, float v[4]) {
+    double w[4];
+    ld_row_volatile(p, w);
+    v[0] = (float)w[0]; v[1] = (float)w[1]; v[2] = (float)w[2]; v[3] = (float)w[3];
+}
+__device__ __forceinline__ void ld_row_volatile(const double *p, float v[4]) {
+    double w[4];
+    ld_row_volatile(p, w);
+    v[0] = (float)w[0]; v[1] = (float)w[1]; v[2] = (float)w[2]; v[3] = (float)w[3];
+}
+
+template <bool VOL, typename T, typename C>
+__device__ __forceinline__ void ld_row_sel(const T *p, C v[4]) {
+    if constexpr (VOL) ld_row_volatile(p, v); else ld_row(p, v);
+}
+
+// stores: one 4-entry row of a block (or one cell's 4 unknowns) from registers
+__device__ __forceinline__ void st_row(double *p, const double v[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void st_row(float *p, const double v[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+}
+__device__ __forceinline__ void st_row(float *p, const float v[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st_row(__nv_bfloat16 *p, const double v[4]) {
+    __nv_bfloat162 a = __floats2bfloat162_rn((float)v[0], (float)v[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&a);
+    u.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ void st_row(double *p, const float v[4]) {
+    double w[4] = {v[0], v[1], v[2], v[3]};
+    st_row(p, w);
+}
+
+// Quad helpers: the 4 threads of an aligned group of 4 lanes cooperate on one
+// block row; thread q of the quad owns row q of every 4x4 block.
+__device__ __forceinline__ unsigned quad_mask() {
+    unsigned lane = threadIdx.x & 31u;
+    return 0xFu << (lane & ~3u);
+}
+template <typename C>
+__device__ __forceinline__ C qshfl(C v, int src_q) {
+    unsigned lane = threadIdx.x & 31u;
+    return __shfl_sync(quad_mask(), v, (int)(lane & ~3u) + src_q);
+}
+
+}  // namespace abilu

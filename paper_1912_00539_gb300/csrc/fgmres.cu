@@ -1,0 +1,436 @@
+// Right-preconditioned flexible GMRES(m) (Saad's FGMRES, which the paper uses
+// through PETSc with restart 30, Sec. 2 and Sec. 6 setup), FP64 on the device.
+//
+// Per Arnoldi step j:  z_j = M^{-1} v_j (block ILU sweeps, any precision),
+// w = A z_j (FP64 SpMV), classical Gram-Schmidt h = V^T w, w -= V h (one pass,
+// or two with reorth), h_{j+1,j} = ||w||, Givens rotation of the new column,
+// residual estimate |g_{j+1}|, v_{j+1} = w / h_{j+1,j}.  At the end of a cycle
+// y = R^{-1} g, x += Z y, and the true residual b - A x is formed in FP64; an
+// estimate that passed but is not confirmed by it restarts the cycle.
+//
+// Every reduction runs on a fixed grid with a fixed order (per-thread partial
+// sums, warp shuffles, per-CTA partials, and the last CTA to finish adding the
+// partials in CTA order), so a synchronous-mode solve is bit-reproducible run
+// to run.  The small Hessenberg/Givens state lives on the device; the last CTA
+// of each reduction updates it, so the host only enqueues kernels.  The host
+// learns that a cycle ended from a pinned host-mapped status word, read one
+// step late (after step j+1 is already enqueued), so the GPU never idles on
+// the host; kernels of steps past the end of a cycle see the device flag and
+// return at once.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace abilu {
+
+abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
+                            abilu_init init, cudaStream_t st);
+abilu_status apply_dispatch(abilu_factors f, const double *r, double *z, int nl, int nu,
+                            abilu_mode mode, cudaStream_t st, const int *skip);
+abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
+                         double beta, double *y, cudaStream_t st, const int *skip);
+abilu_status ensure_krylov(abilu_factors f, int m);
+int red_ctas();
+
+constexpr int MAXM = 64;
+constexpr int RED_THREADS = 256;
+constexpr int RED_WARPS = RED_THREADS / 32;
+constexpr int TILE = 8;   // Krylov vectors per pass of the dot kernel
+
+struct HostStatus {       // pinned, host-mapped mirror
+    int done, iters, converged, kdim, restarts, breakdown;
+    double est, beta, bnorm;
+};
+
+struct SolveState {       // device
+    double H[MAXM * MAXM]; // R after rotations, H[i*MAXM + j], i <= j
+    double cs[MAXM], sn[MAXM], g[MAXM + 1];
+    double h[MAXM + 1];    // current column (first Gram-Schmidt pass)
+    double h2[MAXM + 1];   // second pass (reorthogonalisation)
+    double bnorm, beta, hn_inv, est, rtol;
+    int done, iters, max_iters, converged, kdim, restarts, m, breakdown;
+    unsigned counter;      // last-CTA detection for the reductions
+    HostStatus *hs;        // host-mapped mirror
+};
+
+__device__ __forceinline__ void publish(SolveState *S) {
+    HostStatus *h = S->hs;
+    volatile HostStatus *vh = h;
+    vh->done = S->done;
+    vh->iters = S->iters;
+    vh->converged = S->converged;
+    vh->kdim = S->kdim;
+    vh->restarts = S->restarts;
+    vh->breakdown = S->breakdown;
+    vh->est = S->est;
+    vh->beta = S->beta;
+    vh->bnorm = S->bnorm;
+    __threadfence_system();
+}
+
+// block-wide sum of K values per thread; result in sh_out[k] (valid after sync)
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *sh_w, double *sh_out, int kn) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) sh_w[warp * K + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < kn) {
+        double s = 0.0;
+        for (int w = 0; w < RED_WARPS; w++) s += sh_w[w * K + threadIdx.x];
+        sh_out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// last-CTA election after this CTA stored its partials
+__device__ __forceinline__ bool last_cta(SolveState *S) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = atomicAdd(&S->counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+// sum over CTAs in order of partials[c*stride + k]
+__device__ __forceinline__ double sum_partials(const double *partials, int stride, int k) {
+    double s = 0.0;
+    for (int c = 0; c < (int)gridDim.x; c++) s += __ldcg(partials + (size_t)c * stride + k);
+    return s;
+}
+
+// ---------------------------------------------------------------- residual
+// r = b - A x into r_out (= V_0 unnormalised), ||r||^2 and (init) ||b||^2.
+// The last CTA sets beta, the convergence flag and starts the next cycle.
+__global__ void __launch_bounds__(RED_THREADS)
+k_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
+           const double *__restrict__ x, double *__restrict__ r_out, SolveState *S,
+           double *partials, int init) {
+    __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
+    const int q = threadIdx.x & 3;
+    double v[2] = {0.0, 0.0};
+    const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
+    for (int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2); i < P.n; i += rows_per_grid) {
+        // same arithmetic as the SpMV kernel: per block a 4-term dot, summed in row order
+        const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1];
+        double s = 0.0;
+        for (int p = p0; p < p1; p++) {
+            const int j = __ldg(P.colind + p);
+            const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
+            const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)j * BS);
+            double2 a0 = __ldg(ap), a1 = __ldg(ap + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
+            s += a0.x * x0.x + a0.y * x0.y + a1.x * x1.x + a1.y * x1.y;
+        }
+        const size_t o = (size_t)i * BS + q;
+        const double bi = b[o];
+        const double ri = bi - s;
+        r_out[o] = ri;
+        v[0] += ri * ri;
+        v[1] += bi * bi;
+    }
+    block_sum<2>(v, sh_w, sh_o, 2);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x * 2 + 0] = sh_o[0];
+        partials[blockIdx.x * 2 + 1] = sh_o[1];
+    }
+    if (!last_cta(S)) return;
+    if (threadIdx.x == 0) {
+        const double rr = sum_partials(partials, 2, 0);
+        if (init) S->bnorm = sqrt(sum_partials(partials, 2, 1));
+        else S->restarts += 1;
+        S->beta = sqrt(rr);
+        S->converged = S->beta <= S->rtol * S->bnorm ? 1 : 0;
+        if (S->bnorm == 0.0) S->converged = 1;
+        S->done = (S->converged || S->iters >= S->max_iters) ? 1 : 0;
+        S->hn_inv = S->beta > 0.0 ? 1.0 / S->beta : 0.0;
+        S->kdim = 0;
+        S->breakdown = 0;
+        S->g[0] = S->beta;
+        for (int k = 1; k <= MAXM; k++) S->g[k] = 0.0;
+        if (init) S->est = S->bnorm > 0.0 ? S->beta / S->bnorm : 0.0;
+        S->counter = 0;
+        publish(S);
+    }
+}
+
+// v_out = v_in * S->hn_inv
+__global__ void __launch_bounds__(RED_THREADS)
+k_scale(const double *vin, double *vout, long long nv2, SolveState *S) {
+    if (*reinterpret_cast<volatile int *>(&S->done)) return;
+    const double s = S->hn_inv;
+    const double2 *a = reinterpret_cast<const double2 *>(vin);
+    double2 *o = reinterpret_cast<double2 *>(vout);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 t = a[e];
+        o[e] = make_double2(t.x * s, t.y * s);
+    }
+}
+
+// h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2)
+__global__ void __launch_bounds__(RED_THREADS)
+k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
+       SolveState *S, double *partials, int pass) {
+    if (*reinterpret_cast<volatile int *>(&S->done)) return;
+    __shared__ double sh_w[RED_WARPS * TILE], sh_o[TILE];
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    const double2 *V2 = reinterpret_cast<const double2 *>(V);
+    for (int k0 = 0; k0 < jp1; k0 += TILE) {
+        const int kn = jp1 - k0 < TILE ? jp1 - k0 : TILE;
+        double acc[TILE];
+#pragma unroll
+        for (int k = 0; k < TILE; k++) acc[k] = 0.0;
+        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
+             e += (long long)gridDim.x * blockDim.x) {
+            const double2 wv = w2[e];
+#pragma unroll
+            for (int k = 0; k < TILE; k++)
+                if (k < kn) {
+                    const double2 v = V2[(size_t)(k0 + k) * nv2 + e];
+                    acc[k] += v.x * wv.x + v.y * wv.y;
+                }
+        }
+        block_sum<TILE>(acc, sh_w, sh_o, kn);
+        if (threadIdx.x < kn) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
+    }
+    if (!last_cta(S)) return;
+    double *h = pass == 0 ? S->h : S->h2;
+    for (int k = threadIdx.x; k < jp1; k += blockDim.x) h[k] = sum_partials(partials, MAXM + 2, k);
+    __syncthreads();
+    if (threadIdx.x == 0) S->counter = 0;
+}
+
+// w -= sum_k h[k] V_k; on the final pass also ||w||^2, and the last CTA
+// performs the Givens update of column j and the convergence test.
+__global__ void __launch_bounds__(RED_THREADS)
+k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict__ w,
+         SolveState *S, double *partials, int pass, int final_pass) {
+    if (*reinterpret_cast<volatile int *>(&S->done)) return;
+    __shared__ double sh_h[MAXM + 1];
+    __shared__ double sh_w[RED_WARPS], sh_o[1];
+    const int jp1 = j + 1;
+    const double *hsrc = pass == 0 ? S->h : S->h2;
+    for (int k = threadIdx.x; k < jp1; k += blockDim.x) sh_h[k] = hsrc[k];
+    __syncthreads();
+    double2 *w2 = reinterpret_cast<double2 *>(w);
+    const double2 *V2 = reinterpret_cast<const double2 *>(V);
+    double nrm[1] = {0.0};
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 t = w2[e];
+        for (int k = 0; k < jp1; k++) {
+            const double2 v = V2[(size_t)k * nv2 + e];
+            t.x -= sh_h[k] * v.x;
+            t.y -= sh_h[k] * v.y;
+        }
+        w2[e] = t;
+        nrm[0] += t.x * t.x + t.y * t.y;
+    }
+    if (!final_pass) return;
+    block_sum<1>(nrm, sh_w, sh_o, 1);
+    if (threadIdx.x == 0) partials[(size_t)blockIdx.x * (MAXM + 2) + MAXM + 1] = sh_o[0];
+    if (!last_cta(S)) return;
+    if (threadIdx.x != 0) return;
+    const double hn = sqrt(sum_partials(partials, MAXM + 2, MAXM + 1));
+    double col[MAXM + 1];
+    for (int i = 0; i <= j; i++) col[i] = S->h[i] + (pass == 1 ? S->h2[i] : 0.0);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; i++) {  // previous rotations
+        const double a = col[i], c = col[i + 1];
+        col[i] = S->cs[i] * a + S->sn[i] * c;
+        col[i + 1] = -S->sn[i] * a + S->cs[i] * c;
+    }
+    const double a = col[j], c = col[j + 1];
+    const double d = sqrt(a * a + c * c);
+    double cs = 1.0, sn = 0.0;
+    if (d != 0.0) { cs = a / d; sn = c / d; }
+    S->cs[j] = cs;
+    S->sn[j] = sn;
+    col[j] = cs * a + sn * c;
+    for (int i = 0; i <= j; i++) S->H[i * MAXM + j] = col[i];
+    const double gj = S->g[j];
+    S->g[j + 1] = -sn * gj;
+    S->g[j] = cs * gj;
+    S->iters += 1;
+    S->kdim = j + 1;
+    S->est = fabs(S->g[j + 1]) / S->bnorm;
+    S->breakdown = hn == 0.0 ? 1 : 0;
+    S->done = (fabs(S->g[j + 1]) <= S->rtol * S->bnorm || hn == 0.0 ||
+               S->iters >= S->max_iters || j + 1 >= S->m) ? 1 : 0;
+    S->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
+    S->counter = 0;
+    publish(S);
+}
+
+// y = R^{-1} g (every CTA, redundantly, in shared memory), then x += Z y
+__global__ void __launch_bounds__(RED_THREADS)
+k_xupdate(const double *__restrict__ Z, long long nv2, double *__restrict__ x, SolveState *S) {
+    __shared__ double y[MAXM];
+    const int kd = S->kdim;
+    if (kd == 0) return;
+    if (threadIdx.x == 0) {
+        for (int i = kd - 1; i >= 0; i--) {
+            double s = S->g[i];
+            for (int k = i + 1; k < kd; k++) s -= S->H[i * MAXM + k] * y[k];
+            y[i] = s / S->H[i * MAXM + i];
+        }
+    }
+    __syncthreads();
+    const double2 *Z2 = reinterpret_cast<const double2 *>(Z);
+    double2 *x2 = reinterpret_cast<double2 *>(x);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
+         e += (long long)gridDim.x * blockDim.x) {
+        double2 t = x2[e];
+        for (int k = 0; k < kd; k++) {
+            const double2 z = Z2[(size_t)k * nv2 + e];
+            t.x += y[k] * z.x;
+            t.y += y[k] * z.y;
+        }
+        x2[e] = t;
+    }
+}
+
+__global__ void k_solve_init(SolveState *S, HostStatus *hs, double rtol, int max_iters, int m) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    S->rtol = rtol;
+    S->max_iters = max_iters;
+    S->m = m;
+    S->hs = hs;
+}
+
+}  // namespace abilu
+
+using namespace abilu;
+
+extern "C" void fgmres_default_opts(fgmres_opts *o) {
+    if (!o) return;
+    o->restart = 30;
+    o->max_iters = 2500;
+    o->rtol = 1e-6;
+    o->build_sweeps = 1;
+    o->apply_sweeps_lower = 3;
+    o->apply_sweeps_upper = 3;
+    o->mode = ABILU_ASYNC;
+    o->build = 1;
+    o->init = ABILU_INIT_FROM_A;
+    o->reorth = 0;
+}
+
+namespace abilu {
+static HostStatus read_status(const HostStatus *p) {
+    const volatile HostStatus *v = p;
+    HostStatus h;
+    h.done = v->done; h.iters = v->iters; h.converged = v->converged; h.kdim = v->kdim;
+    h.restarts = v->restarts; h.breakdown = v->breakdown;
+    h.est = v->est; h.beta = v->beta; h.bnorm = v->bnorm;
+    return h;
+}
+size_t solve_state_bytes() { return sizeof(SolveState); }
+size_t host_status_bytes() { return sizeof(HostStatus); }
+int max_restart() { return MAXM; }
+}  // namespace abilu
+
+extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_factors f,
+                                     const double *b, double *x, const fgmres_opts *opts,
+                                     fgmres_result *res, abilu_stream stream) {
+    if (!p || !A || !f || !b || !x || !opts || !res)
+        return fail(ABILU_EINVAL, "fgmres_solve: NULL argument");
+    memset(res, 0, sizeof *res);
+    if (f->p != p) return fail(ABILU_EINVAL, "fgmres_solve: factors belong to another pattern");
+    const int m = opts->restart;
+    if (m < 1 || m > MAXM) return fail(ABILU_EINVAL, "fgmres_solve: restart must be in 1..%d", MAXM);
+    if (opts->max_iters < 0 || !(opts->rtol >= 0.0) || opts->apply_sweeps_lower < 0 ||
+        opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 ||
+        (opts->mode != ABILU_SYNC && opts->mode != ABILU_ASYNC))
+        return fail(ABILU_EINVAL, "fgmres_solve: bad options");
+    cudaStream_t st = S(stream);
+    abilu_status s = ensure_krylov(f, m);
+    if (s != ABILU_OK) return s;
+    const PatternView &P = p->v;
+    const long long nv = (long long)P.n * BS, nv2 = nv / 2;
+    double *V = f->krylov;
+    double *Z = V + (size_t)(m + 1) * nv;
+    double *w = Z + (size_t)m * nv;
+    SolveState *SS = reinterpret_cast<SolveState *>(f->scal);
+    HostStatus *hs = reinterpret_cast<HostStatus *>(f->host_status);
+    const int nred = red_ctas();
+    const abilu_mode mode = (abilu_mode)opts->mode;
+    const int *skip = &SS->done;
+
+    if (opts->build) {
+        s = build_dispatch(f, A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
+        if (s != ABILU_OK) return s;
+    }
+    ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
+    k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
+    k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 1);
+    k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, nv2, SS);
+    ABILU_LAUNCH_CHECK("fgmres init");
+    cudaEvent_t ev[2];
+    ABILU_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    ABILU_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    ABILU_CUDA(cudaStreamSynchronize(st));
+    HostStatus h = read_status(hs);
+    abilu_status ret = ABILU_OK;
+    if (h.bnorm == 0.0) {  // b = 0: the solution is x = 0
+        ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
+        h.converged = 1;
+    }
+    while (!h.converged && h.iters < opts->max_iters) {
+        int j = 0;
+        for (; j < m; j++) {
+            s = apply_dispatch(f, V + (size_t)j * nv, Z + (size_t)j * nv, opts->apply_sweeps_lower,
+                               opts->apply_sweeps_upper, mode, st, skip);
+            if (s != ABILU_OK) { ret = s; break; }
+            if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
+            k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, f->partials, 0);
+            k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, f->partials, 0, !opts->reorth);
+            if (opts->reorth) {
+                k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, f->partials, 1);
+                k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, f->partials, 1, 1);
+            }
+            k_scale<<<counted(nred), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, nv2, SS);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step"); break; }
+            cudaEventRecord(ev[j & 1], st);
+            if (j >= 1) {  // look at step j-1 while step j runs
+                cudaEventSynchronize(ev[(j - 1) & 1]);
+                if (reinterpret_cast<volatile HostStatus *>(hs)->done) { j++; break; }
+            }
+        }
+        if (ret != ABILU_OK) break;
+        k_xupdate<<<counted(nred), RED_THREADS, 0, st>>>(Z, nv2, x, SS);
+        k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 0);
+        k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, nv2, SS);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres restart"); break; }
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres sync"); break; }
+        h = read_status(hs);
+    }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    h = read_status(hs);
+    res->iters = h.iters;
+    res->restarts = h.restarts;
+    res->rel_resid_est = h.est;
+    res->rel_resid_true = h.bnorm > 0.0 ? h.beta / h.bnorm : 0.0;
+    unsigned long long ns = 0;
+    cudaMemcpy(&ns, f->ctr, sizeof ns, cudaMemcpyDeviceToHost);
+    res->singular_blocks = (int64_t)ns;
+    if (ret == ABILU_OK) {
+        if (!h.converged) ret = fail(ABILU_ENOCONV, "fgmres_solve: %d iterations, relative residual %.3e > rtol %.3e", h.iters, res->rel_resid_true, opts->rtol);
+        else if (ns > 0) ret = fail(ABILU_WARN_SINGULAR, "fgmres_solve: %llu singular diagonal blocks replaced", ns);
+    }
+    res->status = ret;
+    return ret;
+}

@@ -1,0 +1,76 @@
+// Block sparse matrix-vector product y = alpha A x + beta y, FP64, 4x4 blocks.
+//
+// FGMRES needs one product per iteration plus the residual at each restart
+// (Sec. 6 setup).  Bytes dominate: every block is 128 bytes of FP64 values
+// plus a 4-byte column index, read exactly once; x (4N doubles) is gathered
+// through L1/L2.  A quad of threads handles one block row: thread q reads row q
+// of every block of the row (32 contiguous bytes; the quad together reads each
+// 128-byte block as one fully used line), forms the 4-term dot product with
+// x_j, and writes y_i[q].  The first four blocks of a row are loaded before
+// any arithmetic so each thread keeps up to 8 independent 16-byte loads in
+// flight.  FP64 work is the minimum, 16 FMA per block.
+#include "common.cuh"
+
+namespace abilu {
+
+constexpr int SPMV_THREADS = 256;
+constexpr int SPMV_ROWS = SPMV_THREADS / 4;
+
+__device__ __forceinline__ double row_dot_blocks(const PatternView &P, const double *__restrict__ A,
+                                                 const double *__restrict__ x, int i, int q) {
+    const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1];
+    double acc[4];
+    double2 a0[4], a1[4];
+    int jj[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int p = p0 + k;
+        if (p < p1) {
+            jj[k] = __ldg(P.colind + p);
+            const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
+            a0[k] = __ldg(ap);
+            a1[k] = __ldg(ap + 1);
+        } else {
+            jj[k] = -1;
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (jj[k] >= 0) {
+            const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)jj[k] * BS);
+            double2 x0 = __ldg(xp), x1 = __ldg(xp + 1);
+            acc[k] = a0[k].x * x0.x + a0[k].y * x0.y + a1[k].x * x1.x + a1[k].y * x1.y;
+            s += acc[k];
+        }
+    }
+    for (int p = p0 + 4; p < p1; p++) {  // rows longer than four blocks
+        const int j = __ldg(P.colind + p);
+        const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
+        const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)j * BS);
+        double2 b0 = __ldg(ap), b1 = __ldg(ap + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
+        s += b0.x * x0.x + b0.y * x0.y + b1.x * x1.x + b1.y * x1.y;
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(SPMV_THREADS)
+k_spmv(PatternView P, const double *__restrict__ A, double alpha, const double *__restrict__ x,
+       double beta, double *__restrict__ y, const int *skip) {
+    if (skip && *reinterpret_cast<const volatile int *>(skip)) return;
+    const int i = blockIdx.x * SPMV_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    if (i >= P.n) return;
+    const double s = row_dot_blocks(P, A, x, i, q);
+    const size_t o = (size_t)i * BS + q;
+    y[o] = beta == 0.0 ? alpha * s : alpha * s + beta * y[o];
+}
+
+abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
+                         double beta, double *y, cudaStream_t st, const int *skip) {
+    const int grid = (P.n + SPMV_ROWS - 1) / SPMV_ROWS;
+    k_spmv<<<counted(grid), SPMV_THREADS, 0, st>>>(P, A, alpha, x, beta, y, skip);
+    ABILU_LAUNCH_CHECK("k_spmv");
+    return ABILU_OK;
+}
+
+}  // namespace abilu

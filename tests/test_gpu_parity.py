@@ -1,0 +1,405 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (max-norm error relative to the max-norm of the oracle's result):
+* FP64 synchronous build, FP64 apply: 1e-12 (the sync GPU sweeps evaluate the
+  same formulas in the same order; only FMA contraction and the adjugate vs
+  Gauss-Jordan inversion differ, a few ulps per sweep).
+* SpMV: 1e-14 (16 products per block row entry, FMA rounding only).
+* FP32 arithmetic on factors that the test exports from the GPU: 2e-6
+  (unit roundoff 6e-8 times the ~10-term sums and 4x4 products of a sweep
+  chain).
+* FP32 / BF16 factor storage against the FP64 oracle build: 1e-4 / 4e-2
+  (storage unit roundoff 6e-8 / 3.9e-3 amplified by the sweeps).
+Integer results (pattern counts, pair lists) are exact.
+"""
+import numpy as np
+import pytest
+
+import abilu_inputs as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ab():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_1912_00539_gb300 as m
+    return m
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+class Dev:
+    """A system on the device with its pattern handle."""
+
+    def __init__(self, ab, s):
+        import torch
+        self.s = s
+        self.rowptr = torch.from_numpy(s.rowptr).cuda()
+        self.colind = torch.from_numpy(s.colind).cuda()
+        self.A = torch.from_numpy(np.ascontiguousarray(s.vals)).cuda()
+        self.b = torch.from_numpy(np.ascontiguousarray(s.b)).cuda()
+        self.pat = ab.Pattern(self.rowptr, self.colind)
+
+    def vec(self, a=None):
+        import torch
+        if a is None:
+            return torch.zeros((self.s.n, 4), dtype=torch.float64, device="cuda")
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def one_block_system():
+    rowptr = np.array([0, 1], np.int32)
+    colind = np.array([0], np.int32)
+    vals = np.array([[[4.0, 1, 0, 0], [1, 5, 1, 0], [0, 1, 6, 1], [0, 0, 1, 7]]])
+    b = np.array([[1.0, 2, 3, 4]])
+    return gen.System("one_block", rowptr, colind, vals, b, np.arange(1), 1.0)
+
+
+SYSTEMS = {
+    "grid4x3": lambda: gen.small_system(4, 3, seed=1),
+    "grid37x11_ragged": lambda: gen.small_system(37, 11, seed=2),      # 814 cells: ragged CTA tail
+    "grid100x60": lambda: gen.small_system(100, 60, seed=3),           # 12,000 cells, many tiles
+    "random_triangles": lambda: gen.random_pattern_system(150, 400, seed=4),
+    "full8": lambda: gen.random_pattern_system(8, 0, seed=5, structure="full"),
+    "one_block": one_block_system,
+    "inviscid_64x64": lambda: gen.workload("inviscid_64x64"),
+}
+
+
+@pytest.fixture(scope="module", params=list(SYSTEMS))
+def dsys(request, ab):
+    return Dev(ab, SYSTEMS[request.param]())
+
+
+# ------------------------------------------------------------------ pattern
+
+def test_pattern_counts_exact(ab, dsys):
+    s = dsys.s
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    nbr = [set(s.colind[s.rowptr[i]:s.rowptr[i + 1]]) for i in range(s.n)]
+    npairs = 0
+    for i in range(s.n):
+        for j in s.colind[s.rowptr[i]:s.rowptr[i + 1]]:
+            npairs += sum(1 for k in nbr[i] if k < min(i, j) and j in nbr[k])
+    c = dsys.pat.counts()
+    assert c["n"] == s.n and c["nnzb"] == s.nnzb
+    assert c["nl"] == int(np.sum(rows > s.colind)) and c["nu"] == int(np.sum(rows < s.colind))
+    assert c["npairs"] == npairs
+    assert c["max_row"] == int(np.diff(s.rowptr).max())
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "no_diag", "col_range", "rowptr"])
+def test_malformed_pattern_rejected(ab, bad):
+    import torch
+    s = gen.small_system(3, 2, seed=6)
+    rp, ci = s.rowptr.copy(), s.colind.copy()
+    if bad == "unsorted":
+        ci[[0, 1]] = ci[[1, 0]]
+    elif bad == "no_diag":  # drop the diagonal block of row 2
+        d = rp[2] + int(np.flatnonzero(ci[rp[2]:rp[3]] == 2)[0])
+        ci = np.delete(ci, d)
+        rp[3:] -= 1
+    elif bad == "col_range":
+        ci[-1] = s.n + 3
+    else:
+        rp[3] = rp[4] + 1
+    with pytest.raises(ab.AbiluError) as e:
+        ab.Pattern(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda())
+    assert e.value.status == 1
+
+
+# --------------------------------------------------------------------- SpMV
+
+def test_spmv_parity(ab, dsys):
+    s = dsys.s
+    x = np.random.default_rng(11).standard_normal((s.n, 4))
+    y_ref = oracle.spmv(s.rowptr, s.colind, s.vals, x)
+    y = dsys.vec()
+    ab.bsr_spmv(dsys.pat, dsys.A, dsys.vec(x), y)
+    assert _rel(y.cpu().numpy(), y_ref) < 1e-14
+    # y = 2 A x - 0.5 y0
+    y0 = np.random.default_rng(12).standard_normal((s.n, 4))
+    yt = dsys.vec(y0)
+    ab.bsr_spmv(dsys.pat, dsys.A, dsys.vec(x), yt, alpha=2.0, beta=-0.5)
+    assert _rel(yt.cpu().numpy(), 2 * y_ref - 0.5 * y0) < 1e-14
+
+
+# -------------------------------------------------------------- build (sync)
+
+@pytest.mark.parametrize("nsweeps", [0, 1, 2, 4])
+def test_sync_build_f64_parity(ab, dsys, nsweeps):
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, "f64")
+    fac.build(dsys.A, nsweeps, mode="sync")
+    X, D = fac.export()
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, nsweeps)
+    assert _rel(X.cpu().numpy(), Xo) < 1e-12
+    assert _rel(D.cpu().numpy(), Do) < 1e-12
+
+
+def test_sync_build_converges_to_sequential(ab, dsys):
+    s = dsys.s
+    if s.n > 2000:
+        pytest.skip("sweep count to the fixed point grows with the chain depth")
+    fac = ab.Factors(dsys.pat, "f64")
+    fac.build(dsys.A, 2 * s.n + 4, mode="sync")
+    X, D = fac.export()
+    Xs, Ds, _ = oracle.bilu0_seq(s.rowptr, s.colind, s.vals)
+    assert _rel(X.cpu().numpy(), Xs) < 1e-12 and _rel(D.cpu().numpy(), Ds) < 1e-12
+
+
+def test_sync_build_bit_reproducible(ab, dsys):
+    fac = ab.Factors(dsys.pat, "f32")
+    fac.build(dsys.A, 3, mode="sync")
+    X1, D1 = fac.export()
+    fac.build(dsys.A, 3, mode="sync")
+    X2, D2 = fac.export()
+    assert (X1 == X2).all() and (D1 == D2).all()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-4), ("bf16", 4e-2)])
+def test_sync_build_narrow_storage(ab, dsys, dtype, tol):
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, dtype)
+    fac.build(dsys.A, 3, mode="sync")
+    X, D = fac.export()
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 3)
+    assert _rel(X.cpu().numpy(), Xo) < tol
+    assert _rel(D.cpu().numpy(), Do) < tol
+
+
+def test_warm_start_continues_the_iteration(ab, dsys):
+    """init=previous continues from the stored factors: 2 + 2 sweeps = 4 sweeps."""
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, "f64")
+    fac.build(dsys.A, 2, mode="sync")
+    fac.build(dsys.A, 2, mode="sync", init="previous")
+    X, D = fac.export()
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 4)
+    assert _rel(X.cpu().numpy(), Xo) < 1e-12 and _rel(D.cpu().numpy(), Do) < 1e-12
+
+
+# -------------------------------------------------------------- apply (sync)
+
+@pytest.mark.parametrize("nl,nu", [(0, 0), (1, 1), (1, 3), (2, 1), (2, 2), (3, 3), (4, 4), (5, 2)])
+def test_sync_apply_f64_parity(ab, dsys, nl, nu):
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, "f64")
+    fac.build(dsys.A, 2, mode="sync")
+    X, D = fac.export()
+    r = np.random.default_rng(13).standard_normal((s.n, 4))
+    z = dsys.vec()
+    fac.apply(dsys.vec(r), z, nl, nu, mode="sync")
+    z_ref = oracle.apply(s.rowptr, s.colind, X.cpu().numpy(), D.cpu().numpy(), r, nl, nu)
+    if nu == 0:
+        assert not z.cpu().numpy().any()
+    else:
+        assert _rel(z.cpu().numpy(), z_ref) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("nl,nu", [(1, 1), (3, 3), (4, 4)])
+def test_sync_apply_narrow_parity(ab, dsys, dtype, nl, nu):
+    """FP32 arithmetic on the stored (narrow) factors vs FP64 on the same factors."""
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, dtype)
+    fac.build(dsys.A, 2, mode="sync")
+    X, D = fac.export()
+    r = np.random.default_rng(14).standard_normal((s.n, 4))
+    z = dsys.vec()
+    fac.apply(dsys.vec(r), z, nl, nu, mode="sync")
+    z_ref = oracle.apply(s.rowptr, s.colind, X.cpu().numpy(), D.cpu().numpy(), r, nl, nu)
+    assert _rel(z.cpu().numpy(), z_ref) < 2e-6
+
+
+def test_sync_apply_exact_with_enough_sweeps(ab, dsys):
+    """Jacobi block triangular sweeps are exact after chain-depth + 1 sweeps
+    (Theorem of Sec. 4.1: at most n/b)."""
+    s = dsys.s
+    if s.n > 1000:
+        pytest.skip("depth-bound sweep counts are for small systems")
+    fac = ab.Factors(dsys.pat, "f64")
+    fac.build(dsys.A, s.n + 2, mode="sync")
+    X, D = fac.export()
+    Xn, Dn = X.cpu().numpy(), D.cpu().numpy()
+    r = np.random.default_rng(15).standard_normal((s.n, 4))
+    z = dsys.vec()
+    fac.apply(dsys.vec(r), z, s.n, s.n, mode="sync")
+    y = oracle.lower_solve(s.rowptr, s.colind, Xn, r)
+    z_ref = oracle.upper_solve(s.rowptr, s.colind, Xn, Dn, y)
+    assert _rel(z.cpu().numpy(), z_ref) < 1e-12
+
+
+# -------------------------------------------------------------------- async
+
+def test_async_build_reaches_fixed_point(ab, dsys):
+    """The asynchronous iteration converges to the unique fixed point (Sec.
+    4.2): with enough sweeps it matches sequential BILU(0)."""
+    s = dsys.s
+    if s.n > 2000:
+        pytest.skip("small systems only")
+    fac = ab.Factors(dsys.pat, "f64")
+    fac.build(dsys.A, 2 * s.n + 4, mode="async")
+    X, D = fac.export()
+    Xs, Ds, _ = oracle.bilu0_seq(s.rowptr, s.colind, s.vals)
+    assert _rel(X.cpu().numpy(), Xs) < 1e-12 and _rel(D.cpu().numpy(), Ds) < 1e-12
+
+
+def test_async_build_residual_not_worse_than_sync(ab, dsys):
+    """Async sweeps read newer values than Jacobi sweeps; over 10 runs the
+    ILU fixed-point residual after k sweeps stays within the sync one."""
+    s = dsys.s
+    k = 3
+    Xsync, _, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, k)
+    r_sync = oracle.ilu_residual_l1(s.rowptr, s.colind, s.vals, Xsync)
+    res = []
+    fac = ab.Factors(dsys.pat, "f64")
+    for _ in range(10):
+        fac.build(dsys.A, k, mode="async")
+        X, _ = fac.export()
+        res.append(oracle.ilu_residual_l1(s.rowptr, s.colind, s.vals, X.cpu().numpy()))
+    assert np.mean(res) <= 1.0 * r_sync + 1e-12 * max(r_sync, 1.0)
+
+
+def test_async_apply_exact_with_enough_sweeps(ab, dsys):
+    s = dsys.s
+    if s.n > 1000:
+        pytest.skip("small systems only")
+    fac = ab.Factors(dsys.pat, "f64")
+    fac.build(dsys.A, 3, mode="sync")
+    X, D = fac.export()
+    Xn, Dn = X.cpu().numpy(), D.cpu().numpy()
+    r = np.random.default_rng(16).standard_normal((s.n, 4))
+    z = dsys.vec()
+    fac.apply(dsys.vec(r), z, s.n + 1, s.n + 1, mode="async")
+    y = oracle.lower_solve(s.rowptr, s.colind, Xn, r)
+    z_ref = oracle.upper_solve(s.rowptr, s.colind, Xn, Dn, y)
+    assert _rel(z.cpu().numpy(), z_ref) < 1e-12
+
+
+# ------------------------------------------------------------------- FGMRES
+
+@pytest.mark.parametrize("dtype,mode", [("f64", "sync"), ("f32", "sync"), ("f32", "async"),
+                                        ("bf16", "sync"), ("f64", "async")])
+def test_fgmres_matches_oracle(ab, dsys, dtype, mode):
+    s = dsys.s
+    nb, na = 4, 3
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, nb)
+    xo, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, na, na, restart=30,
+                           rtol=1e-6)
+    fac = ab.Factors(dsys.pat, dtype)
+    x = dsys.vec()
+    res = ab.fgmres_solve(dsys.pat, dsys.A, fac, dsys.b, x, restart=30, rtol=1e-6,
+                          build_sweeps=nb, apply_sweeps_lower=na, apply_sweeps_upper=na,
+                          mode=mode)
+    assert res.converged and res.rel_resid_true <= 1e-6
+    xn = x.cpu().numpy()
+    r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, xn)
+    assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
+    if dtype == "bf16":  # optional narrow variant: must converge, count is reported only
+        assert res.iters <= 2 * ro.iters + 2
+        return
+    slack = max(1, int(np.ceil(0.1 * ro.iters)))
+    assert abs(res.iters - ro.iters) <= slack, (res.iters, ro.iters)
+    if dtype == "f64" and mode == "sync":
+        assert res.iters == ro.iters
+
+
+def test_fgmres_sync_bit_reproducible(ab):
+    d = Dev(ab, gen.small_system(30, 20, seed=7))
+    fac = ab.Factors(d.pat, "f32")
+    xs = []
+    for _ in range(2):
+        x = d.vec()
+        ab.fgmres_solve(d.pat, d.A, fac, d.b, x, build_sweeps=3, mode="sync")
+        xs.append(x.cpu().numpy())
+    np.testing.assert_array_equal(xs[0], xs[1])
+
+
+def test_fgmres_restarts_and_reorth(ab):
+    s = gen.small_system(12, 10, seed=8, cfl=1.0)
+    d = Dev(ab, s)
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 1)
+    xo, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, 1, 1, restart=4,
+                           max_iters=500, rtol=1e-8)
+    for reorth in (False, True):
+        fac = ab.Factors(d.pat, "f64")
+        x = d.vec()
+        res = ab.fgmres_solve(d.pat, d.A, fac, d.b, x, restart=4, max_iters=500, rtol=1e-8,
+                              build_sweeps=1, apply_sweeps_lower=1, apply_sweeps_upper=1,
+                              mode="sync", reorth=reorth)
+        assert res.converged and res.restarts >= 2
+        assert abs(res.iters - ro.iters) <= max(2, ro.iters // 10), (res.iters, ro.iters)
+
+
+def test_fgmres_max_iters_reports_noconv(ab):
+    d = Dev(ab, gen.small_system(12, 10, seed=9, cfl=1.0))
+    fac = ab.Factors(d.pat, "f64")
+    x = d.vec()
+    res = ab.fgmres_solve(d.pat, d.A, fac, d.b, x, restart=5, max_iters=3, rtol=1e-14,
+                          build_sweeps=1, apply_sweeps_lower=1, apply_sweeps_upper=1, mode="sync")
+    assert not res.converged and res.status == 4 and res.iters == 3
+
+
+def test_fgmres_zero_rhs(ab):
+    d = Dev(ab, gen.small_system(5, 5, seed=10))
+    fac = ab.Factors(d.pat, "f64")
+    x = d.vec(np.ones((d.s.n, 4)))
+    res = ab.fgmres_solve(d.pat, d.A, fac, d.vec(), x, mode="sync")
+    assert res.converged and res.iters == 0 and not x.cpu().numpy().any()
+
+
+def test_singular_block_is_replaced_and_counted(ab):
+    s = gen.small_system(4, 4, seed=11)
+    vals = s.vals.copy()
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    d0 = np.flatnonzero((rows == 5) & (s.colind == 5))[0]
+    vals[d0] = 0.0
+    s2 = gen.System("sing", s.rowptr, s.colind, vals, s.b, s.perm, s.cfl)
+    d = Dev(ab, s2)
+    fac = ab.Factors(d.pat, "f64")
+    fac.build(d.A, 0, mode="sync")
+    assert fac.singular_blocks() == 1
+    X, D = fac.export()
+    np.testing.assert_array_equal(D.cpu().numpy()[5], np.eye(4))
+    _, Do, ns = oracle.bilu_init(s2.rowptr, s2.colind, s2.vals)
+    assert ns == 1 and _rel(D.cpu().numpy(), Do) < 1e-12
+
+
+# ------------------------------------------------------------ full size
+
+@pytest.mark.slow
+def test_full_size_512x512_parity(ab):
+    """The 512x512 workload at its solver settings: SpMV and one FP64 build
+    sweep compared element by element; the FP32 solve (the benchmark's launch
+    configuration) converges with iteration count within 10% of the FP64
+    oracle's and a true FP64 residual below 1e-6."""
+    s = gen.workload("inviscid_512x512")
+    d = Dev(ab, s)
+    x = np.random.default_rng(17).standard_normal((s.n, 4))
+    y = d.vec()
+    ab.bsr_spmv(d.pat, d.A, d.vec(x), y)
+    assert _rel(y.cpu().numpy(), oracle.spmv(s.rowptr, s.colind, s.vals, x)) < 1e-14
+    fac = ab.Factors(d.pat, "f64")
+    fac.build(d.A, 1, mode="sync")
+    X, D = fac.export()
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 1)
+    assert _rel(X.cpu().numpy(), Xo) < 1e-12 and _rel(D.cpu().numpy(), Do) < 1e-12
+    Xo6, Do6, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 6)
+    _, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo6, Do6, s.b, 4, 4, restart=30, rtol=1e-6)
+    for mode in ("sync", "async"):
+        f32 = ab.Factors(d.pat, "f32")
+        xs = d.vec()
+        res = ab.fgmres_solve(d.pat, d.A, f32, d.b, xs, restart=30, rtol=1e-6, build_sweeps=6,
+                              apply_sweeps_lower=4, apply_sweeps_upper=4, mode=mode)
+        assert res.converged and res.rel_resid_true <= 1e-6
+        assert abs(res.iters - ro.iters) <= max(1, ro.iters // 10), (mode, res.iters, ro.iters)
+        xn = xs.cpu().numpy()
+        r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, xn)
+        assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
