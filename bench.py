@@ -224,6 +224,28 @@ def run_kernels_only(args):
     return 0
 
 
+def run_profile_solves(args):
+    """Warm-up plus --profile-solves solves of the timed step and nothing else:
+    the command the ncu launch list is taken on."""
+    import torch
+    import paper_1912_00539_gb300 as ab
+    s = _system()
+    pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+    A = torch.from_numpy(s.vals).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    x = torch.zeros_like(b)
+    fac = ab.Factors(pat, args.dtype)
+    for _ in range(args.warmup + args.profile_solves):
+        x.zero_()
+        r = ab.fgmres_solve(pat, A, fac, b, x, restart=RESTART, rtol=RTOL,
+                            build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=APPLY_SWEEPS,
+                            apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode, raise_on_noconv=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"solves": args.warmup + args.profile_solves, "iters": r.iters,
+                      "rel_resid_true": r.rel_resid_true}))
+    return 0
+
+
 def run_gpu(args):
     import torch
     rank, world, local = _dist()
@@ -402,11 +424,14 @@ def main():
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
+    ap.add_argument("--profile-solves", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.kernels_only:
         return run_kernels_only(args)
+    if args.profile_solves:
+        return run_profile_solves(args)
     return run_gpu(args)
 
 

@@ -8,8 +8,8 @@ namespace abilu {
 
 abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st);
-abilu_status apply_dispatch(abilu_factors f, const double *r, double *z, int nl, int nu,
-                            abilu_mode mode, cudaStream_t st, const int *skip);
+abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip);
 abilu_status export_dispatch(abilu_factors f, double *X, double *Dinv, cudaStream_t st);
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
                          double beta, double *y, cudaStream_t st, const int *skip);
@@ -78,7 +78,10 @@ extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype,
     const size_t bc = rnd(sizeof(unsigned long long) * 4);
     const size_t bs = rnd(solve_state_bytes());
     const size_t bp = rnd(sizeof(double) * MAXM_PARTIAL_STRIDE * (size_t)red_ctas());
-    const size_t total = 2 * bl + 2 * bu + 3 * bd + 4 * bv + bc + bs + bp;
+    const bool narrow = dtype != ABILU_F64;
+    const size_t ba = narrow ? rnd(sizeof(float) * BB * (size_t)v.nnzb) : 0;
+    const size_t br = narrow ? rnd(sizeof(float) * BS * (size_t)v.n) : 0;
+    const size_t total = 2 * bl + 2 * bu + 3 * bd + 4 * bv + bc + bs + bp + ba + br;
     abilu_factors f = new abilu_factors_s();
     memset(f, 0, sizeof *f);
     f->p = p;
@@ -101,6 +104,8 @@ extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype,
     f->ctr = reinterpret_cast<unsigned long long *>(m); m += bc;
     f->scal = reinterpret_cast<double *>(m); m += bs;
     f->partials = reinterpret_cast<double *>(m); m += bp;
+    f->A32 = narrow ? m : nullptr; m += ba;
+    f->r32 = narrow ? m : nullptr; m += br;
     e = cudaMemset(f->mem, 0, total);
     if (e == cudaSuccess) e = cudaHostAlloc(&f->host_status, host_status_bytes(), cudaHostAllocMapped);
     if (e != cudaSuccess) { factors_free(f); return cuda_fail(e, "factors_create"); }
@@ -128,7 +133,7 @@ extern "C" abilu_status abilu_apply(abilu_factors f, const double *r, double *z,
     if (!aligned16(r) || !aligned16(z)) return fail(ABILU_EINVAL, "apply: vectors must be 16-byte aligned");
     if (nl < 0 || nu < 0) return fail(ABILU_EINVAL, "apply: negative sweep count");
     if (mode != ABILU_SYNC && mode != ABILU_ASYNC) return fail(ABILU_EINVAL, "apply: bad mode");
-    return apply_dispatch(f, r, z, nl, nu, mode, S(stream), nullptr);
+    return apply_dispatch(f, r, nullptr, z, nl, nu, mode, S(stream), nullptr);
 }
 
 extern "C" abilu_status bsr_spmv(abilu_pattern p, const double *A, double alpha, const double *x,

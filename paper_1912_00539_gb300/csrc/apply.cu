@@ -12,7 +12,9 @@
 // Sync-mode shortcuts that do not change the result: from y^0 = 0 the first
 // lower sweep gives y^1 = b exactly, so it is not run (the second sweep reads b
 // as y^1); and x^1 = Dinv_i y_i needs only row i, so it is fused into the last
-// lower sweep.  The last upper sweep writes the FP64 output directly.
+// lower sweep.  The last upper sweep writes the FP64 output directly.  With
+// FP32/BF16 factors the FP64 right-hand side is converted to FP32 once per
+// application (FGMRES hands over the FP32 copy it already wrote).
 //
 // Thread mapping: a quad per block row, thread q computes unknown q of the
 // row: it reads row q of each factor block (one 16-byte load for FP32, 32 for
@@ -56,15 +58,15 @@ __device__ __forceinline__ VT dinv_times(const T *__restrict__ D, int i, VT t) {
 
 // one Jacobi lower sweep; optionally x^1 = Dinv y fused (into x1 or, when
 // it is the last upper result, into z as FP64)
-template <typename T, typename VT, typename YIN>
+template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_lower_sync(PatternView P, const T *__restrict__ L, const double *__restrict__ r,
-             const YIN *__restrict__ yin, VT *__restrict__ yout, const T *__restrict__ D,
+k_lower_sync(PatternView P, const T *__restrict__ L, const VT *__restrict__ r,
+             const VT *__restrict__ yin, VT *__restrict__ yout, const T *__restrict__ D,
              VT *__restrict__ x1, double *__restrict__ z, const int *skip) {
     if (skipped(skip)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
-    VT s = (VT)r[(size_t)i * BS + q];
+    VT s = r[(size_t)i * BS + q];
     const int l1 = P.lrow[i + 1];
     for (int l = P.lrow[i]; l < l1; l++) {
         const int j = P.lcol[l];
@@ -82,28 +84,28 @@ k_lower_sync(PatternView P, const T *__restrict__ L, const double *__restrict__ 
 }
 
 // x^1 = Dinv y (used when fewer than two lower sweeps run)
-template <typename T, typename VT, typename YIN>
+template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_diag_apply(PatternView P, const T *__restrict__ D, const YIN *__restrict__ y,
+k_diag_apply(PatternView P, const T *__restrict__ D, const VT *__restrict__ y,
              VT *__restrict__ x1, double *__restrict__ z, const int *skip) {
     if (skipped(skip)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
-    VT t = (VT)y[(size_t)i * BS + q];
+    VT t = y[(size_t)i * BS + q];
     VT x = dinv_times<T, VT>(D, i, t);
     if (x1) x1[(size_t)i * BS + q] = x;
     if (z) z[(size_t)i * BS + q] = (double)x;
 }
 
-template <typename T, typename VT, typename YT>
+template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
-             const YT *__restrict__ y, const VT *__restrict__ xin, VT *__restrict__ xout,
+             const VT *__restrict__ y, const VT *__restrict__ xin, VT *__restrict__ xout,
              double *__restrict__ z, const int *skip) {
     if (skipped(skip)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
-    VT s = (VT)y[(size_t)i * BS + q];
+    VT s = y[(size_t)i * BS + q];
     const int u1 = P.urow[i + 1];
     for (int u = P.urow[i]; u < u1; u++) {
         const int j = P.ucol[u];
@@ -129,7 +131,7 @@ template <> __device__ __forceinline__ void st_vol<double>(double *p, double v) 
 // In-place lower sweeps over all nsweeps, y must hold 0 on entry.
 template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
-k_lower_async(PatternView P, const T *__restrict__ L, const double *__restrict__ r, VT *y,
+k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, VT *y,
               int nsweeps, unsigned long long *ticket, const int *skip) {
     if (skipped(skip)) return;
     __shared__ unsigned long long s_t;
@@ -144,7 +146,7 @@ k_lower_async(PatternView P, const T *__restrict__ L, const double *__restrict__
         if (t >= total) break;
         const int i = (int)(t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
         if (i < P.n) {
-            VT s = (VT)r[(size_t)i * BS + q];
+            VT s = r[(size_t)i * BS + q];
             const int l1 = P.lrow[i + 1];
             for (int l = P.lrow[i]; l < l1; l++) {
                 const int j = P.lcol[l];
@@ -160,10 +162,10 @@ k_lower_async(PatternView P, const T *__restrict__ L, const double *__restrict__
 
 // In-place upper sweeps, chunks in backward order; x must hold 0 on entry.
 // The last sweep of each chunk also writes the FP64 result z.
-template <typename T, typename VT, typename YT>
+template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
-              const YT *__restrict__ y, VT *x, double *__restrict__ z, int nsweeps,
+              const VT *__restrict__ y, VT *x, double *__restrict__ z, int nsweeps,
               unsigned long long *ticket, const int *skip) {
     if (skipped(skip)) return;
     __shared__ unsigned long long s_t;
@@ -179,7 +181,7 @@ k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
         const bool last = t / nchunks == nsweeps - 1;
         const int i = (int)(nchunks - 1 - t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
         if (i < P.n) {  // quads of one row stay together: the shuffles below are quad-local
-            VT s = (VT)y[(size_t)i * BS + q];
+            VT s = y[(size_t)i * BS + q];
             const int u1 = P.urow[i + 1];
             for (int u = P.urow[i]; u < u1; u++) {
                 const int j = P.ucol[u];
@@ -195,6 +197,17 @@ k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
     }
 }
 
+// r32 = (float) r, once per application (the sweeps then read 16-byte FP32
+// rows and do no FP64 conversions on the slow FP64 pipe)
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_to_f32(const double *__restrict__ r, float *__restrict__ r32, long long n4) {
+    const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (e >= n4) return;
+    double v[4];
+    ld_row(r + e, v);
+    st_row(r32 + e, v);
+}
+
 template <typename K>
 static int resident_ctas(K kernel, int threads) {
     int dev = 0, per_sm = 0, sms = 0;
@@ -206,8 +219,8 @@ static int resident_ctas(K kernel, int threads) {
 }
 
 template <typename T>
-static abilu_status apply_t(abilu_factors f, const double *r, double *z, int nl, int nu,
-                            abilu_mode mode, cudaStream_t st, const int *skip) {
+static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_in, double *z,
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip) {
     using VT = typename ApplyArith<T>::VT;
     const PatternView &P = f->p->v;
     const int c = f->cur;
@@ -219,25 +232,39 @@ static abilu_status apply_t(abilu_factors f, const double *r, double *z, int nl,
     const size_t vbytes = sizeof(VT) * (size_t)P.n * BS;
     const int grid = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
 
+    // right-hand side in the compute type
+    const VT *rv;
+    if constexpr (sizeof(VT) == 8) {
+        rv = r;
+    } else {
+        if (r32_in) {
+            rv = r32_in;
+        } else {
+            const long long n4 = (long long)P.n * BS;
+            k_to_f32<<<counted((int)((n4 / 4 + APPLY_THREADS - 1) / APPLY_THREADS)), APPLY_THREADS,
+                       0, st>>>(r, reinterpret_cast<float *>(f->r32), n4);
+            ABILU_LAUNCH_CHECK("k_to_f32");
+            rv = reinterpret_cast<const float *>(f->r32);
+        }
+    }
+
     if (mode == ABILU_ASYNC) {
         const long long nchunks = grid;
+        ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
         if (nl > 0) {
-            ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
             ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, 8, st));
             static int ctas_l = resident_ctas(k_lower_async<T, VT>, APPLY_THREADS);
             int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
-            k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, r, y[0], nl, f->ctr + 1, skip);
+            k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl, f->ctr + 1, skip);
             ABILU_LAUNCH_CHECK("k_lower_async");
-        } else {
-            ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
         }
         if (nu > 0) {
             ABILU_CUDA(cudaMemsetAsync(x[0], 0, vbytes, st));
             ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, 8, st));
-            static int ctas_u = resident_ctas(k_upper_async<T, VT, VT>, APPLY_THREADS);
+            static int ctas_u = resident_ctas(k_upper_async<T, VT>, APPLY_THREADS);
             int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
-            k_upper_async<T, VT, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, U, D, y[0], x[0], z, nu,
-                                                                 f->ctr + 1, skip);
+            k_upper_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, U, D, y[0], x[0], z, nu,
+                                                                       f->ctr + 1, skip);
             ABILU_LAUNCH_CHECK("k_upper_async");
         } else {
             ABILU_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)P.n * BS, st));
@@ -245,62 +272,49 @@ static abilu_status apply_t(abilu_factors f, const double *r, double *z, int nl,
         return ABILU_OK;
     }
 
-    // ---- synchronous: y^s lives in y[s & 1] (s >= 2), y^1 = r
-    const VT *yfin = nullptr;     // y^{n_L} when it is a VT vector
-    bool yfin_is_r = false;
+    // ---- synchronous: y^1 = r (the first sweep from y = 0), y^s in y[s & 1]
+    const VT *yfin;
     bool x1_done = false;
     if (nl == 0) {
         ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
         yfin = y[0];
-    } else if (nl == 1) {
-        yfin_is_r = true;
     } else {
+        yfin = rv;
         for (int s = 2; s <= nl; s++) {
             const bool fuse = (s == nl) && nu >= 1;
             VT *x1 = fuse && nu >= 2 ? x[1] : nullptr;
             double *zz = fuse && nu == 1 ? z : nullptr;
-            if (s == 2)
-                k_lower_sync<T, VT, double><<<counted(grid), APPLY_THREADS, 0, st>>>(P, L, r, r, y[0], D, x1, zz, skip);
-            else
-                k_lower_sync<T, VT, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, L, r, y[(s - 1) & 1], y[s & 1], D, x1, zz, skip);
+            k_lower_sync<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, L, rv, yfin, y[s & 1], D,
+                                                                         x1, zz, skip);
             ABILU_LAUNCH_CHECK("k_lower_sync");
+            yfin = y[s & 1];
             x1_done = fuse;
         }
-        yfin = (nl == 2) ? y[0] : y[nl & 1];
     }
-    // note: for s == 2 the output went to y[0] = y[2 & 1]; indices stay consistent
     if (nu == 0) {
         ABILU_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)P.n * BS, st));
         return ABILU_OK;
     }
     if (!x1_done) {
-        VT *x1 = nu >= 2 ? x[1] : nullptr;
-        double *zz = nu == 1 ? z : nullptr;
-        if (yfin_is_r)
-            k_diag_apply<T, VT, double><<<counted(grid), APPLY_THREADS, 0, st>>>(P, D, r, x1, zz, skip);
-        else
-            k_diag_apply<T, VT, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, D, yfin, x1, zz, skip);
+        k_diag_apply<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
+            P, D, yfin, nu >= 2 ? x[1] : nullptr, nu == 1 ? z : nullptr, skip);
         ABILU_LAUNCH_CHECK("k_diag_apply");
     }
-    for (int s = 2; s <= nu; s++) {  // x^s in x[s & 1], last one to z
+    for (int s = 2; s <= nu; s++) {  // x^s in x[s & 1], the last one to z
         const bool last = s == nu;
-        VT *xo = last ? nullptr : x[s & 1];
-        double *zz = last ? z : nullptr;
-        if (yfin_is_r)
-            k_upper_sync<T, VT, double><<<counted(grid), APPLY_THREADS, 0, st>>>(P, U, D, r, x[(s - 1) & 1], xo, zz, skip);
-        else
-            k_upper_sync<T, VT, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, U, D, yfin, x[(s - 1) & 1], xo, zz, skip);
+        k_upper_sync<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
+            P, U, D, yfin, x[(s - 1) & 1], last ? nullptr : x[s & 1], last ? z : nullptr, skip);
         ABILU_LAUNCH_CHECK("k_upper_sync");
     }
     return ABILU_OK;
 }
 
-abilu_status apply_dispatch(abilu_factors f, const double *r, double *z, int nl, int nu,
-                            abilu_mode mode, cudaStream_t st, const int *skip) {
+abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip) {
     switch (f->dtype) {
-    case ABILU_F64: return apply_t<double>(f, r, z, nl, nu, mode, st, skip);
-    case ABILU_F32: return apply_t<float>(f, r, z, nl, nu, mode, st, skip);
-    case ABILU_BF16: return apply_t<__nv_bfloat16>(f, r, z, nl, nu, mode, st, skip);
+    case ABILU_F64: return apply_t<double>(f, r, r32, z, nl, nu, mode, st, skip);
+    case ABILU_F32: return apply_t<float>(f, r, r32, z, nl, nu, mode, st, skip);
+    case ABILU_BF16: return apply_t<__nv_bfloat16>(f, r, r32, z, nl, nu, mode, st, skip);
     }
     return fail(ABILU_EINVAL, "apply: bad dtype");
 }

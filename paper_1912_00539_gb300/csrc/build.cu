@@ -70,6 +70,106 @@ __device__ __forceinline__ bool inv4_adj(const double *a, double *r) {
     return false;
 }
 
+// Inverse of a 4x4 FP32 block accurate to FP32 rounding without FP64
+// instructions (FP64 and FP64<->FP32 conversions share this GPU's slow FP64
+// pipe).  The quad holding the block (thread q owns row q) computes
+//   X0 = adj(U)/det(U) in FP32 (every thread forms the minors; thread q its row),
+//   R  = I - U X0 with error-free products and sums (TwoProd by FMA, TwoSum),
+//   X1 = X0 + X0 R  (one Newton step),
+// so X1 carries an error of about (cond(U) u)^2 + u, u = 2^-24: the FP32
+// rounding of the exact inverse for every block with cond(U) << 1/sqrt(u).
+// det == 0 or non-finite: singular, replaced by the identity (modified
+// iteration, Sec. 4.2); all four threads reach the same decision.
+// `sh` is this quad's 48-float scratch (U, X0, R), shared within the warp.
+__device__ __forceinline__ bool quad_inv4_refined(const float u_row[4], float x_row[4],
+                                                  float *sh) {
+    const int q = threadIdx.x & 3;
+    const unsigned m = quad_mask();
+    float *shU = sh, *shX = sh + 16, *shR = sh + 32;
+    reinterpret_cast<float4 *>(shU)[q] = make_float4(u_row[0], u_row[1], u_row[2], u_row[3]);
+    __syncwarp(m);
+    float a[16];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float4 t = reinterpret_cast<const float4 *>(shU)[k];
+        a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+    }
+    float s0 = a[0] * a[5] - a[4] * a[1], s1 = a[0] * a[6] - a[4] * a[2];
+    float s2 = a[0] * a[7] - a[4] * a[3], s3 = a[1] * a[6] - a[5] * a[2];
+    float s4 = a[1] * a[7] - a[5] * a[3], s5 = a[2] * a[7] - a[6] * a[3];
+    float c5 = a[10] * a[15] - a[14] * a[11], c4 = a[9] * a[15] - a[13] * a[11];
+    float c3 = a[9] * a[14] - a[13] * a[10], c2 = a[8] * a[15] - a[12] * a[11];
+    float c1 = a[8] * a[14] - a[12] * a[10], c0 = a[8] * a[13] - a[12] * a[9];
+    float det = s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
+    if (det == 0.0f || !isfinite(det)) {
+#pragma unroll
+        for (int c = 0; c < 4; c++) x_row[c] = (c == q) ? 1.0f : 0.0f;
+        __syncwarp(m);
+        return true;
+    }
+    const float id = 1.0f / det;
+    // row q of adj(U): the cofactors of column q of U
+    float x0[4];
+    if (q == 0) {
+        x0[0] = a[5] * c5 - a[6] * c4 + a[7] * c3;   x0[1] = -a[1] * c5 + a[2] * c4 - a[3] * c3;
+        x0[2] = a[13] * s5 - a[14] * s4 + a[15] * s3; x0[3] = -a[9] * s5 + a[10] * s4 - a[11] * s3;
+    } else if (q == 1) {
+        x0[0] = -a[4] * c5 + a[6] * c2 - a[7] * c1;   x0[1] = a[0] * c5 - a[2] * c2 + a[3] * c1;
+        x0[2] = -a[12] * s5 + a[14] * s2 - a[15] * s1; x0[3] = a[8] * s5 - a[10] * s2 + a[11] * s1;
+    } else if (q == 2) {
+        x0[0] = a[4] * c4 - a[5] * c2 + a[7] * c0;    x0[1] = -a[0] * c4 + a[1] * c2 - a[3] * c0;
+        x0[2] = a[12] * s4 - a[13] * s2 + a[15] * s0; x0[3] = -a[8] * s4 + a[9] * s2 - a[11] * s0;
+    } else {
+        x0[0] = -a[4] * c3 + a[5] * c1 - a[6] * c0;   x0[1] = a[0] * c3 - a[1] * c1 + a[2] * c0;
+        x0[2] = -a[12] * s3 + a[13] * s1 - a[14] * s0; x0[3] = a[8] * s3 - a[9] * s1 + a[10] * s0;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) x0[c] *= id;
+    reinterpret_cast<float4 *>(shX)[q] = make_float4(x0[0], x0[1], x0[2], x0[3]);
+    __syncwarp(m);
+    float X[16];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float4 t = reinterpret_cast<const float4 *>(shX)[k];
+        X[4 * k] = t.x; X[4 * k + 1] = t.y; X[4 * k + 2] = t.z; X[4 * k + 3] = t.w;
+    }
+    // R[q][c] = delta_qc - sum_k U[q][k] X0[k][c], accumulated error-free
+    float r[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        float acc = (c == q) ? 1.0f : 0.0f, comp = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float uq = u_row[k], xk = X[4 * k + c];
+            const float p = __fmul_rn(uq, xk);
+            const float pe = __fmaf_rn(uq, xk, -p);          // uq*xk = p + pe exactly
+            const float t = __fsub_rn(acc, p);                // TwoSum(acc, -p)
+            const float bp = __fsub_rn(t, acc);
+            const float err = __fadd_rn(__fsub_rn(acc, __fsub_rn(t, bp)), __fsub_rn(-p, bp));
+            acc = t;
+            comp = __fsub_rn(__fadd_rn(comp, err), pe);
+        }
+        r[c] = acc + comp;
+    }
+    reinterpret_cast<float4 *>(shR)[q] = make_float4(r[0], r[1], r[2], r[3]);
+    __syncwarp(m);
+    float R[16];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        float4 t = reinterpret_cast<const float4 *>(shR)[k];
+        R[4 * k] = t.x; R[4 * k + 1] = t.y; R[4 * k + 2] = t.z; R[4 * k + 3] = t.w;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        float corr = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; k++) corr += x0[k] * R[4 * k + c];
+        x_row[c] = x0[c] + corr;
+    }
+    __syncwarp(m);
+    return false;
+}
+
 template <bool VOL, typename T, typename C>
 __device__ __forceinline__ void st_row_sel(T *p, const C v[4]) {
     if constexpr (VOL) {
@@ -90,32 +190,30 @@ __device__ __forceinline__ void st_row_sel(T *p, const C v[4]) {
             asm volatile("st.volatile.global.v2.u32 [%0], {%1,%2};" ::"l"(p), "r"(ua), "r"(ub) : "memory");
         }
     } else {
-        double w[4] = {(double)v[0], (double)v[1], (double)v[2], (double)v[3]};
-        st_row(p, w);
+        st_row(p, v);
     }
 }
 
-// One block row i handled by one quad.  Writes the row's L and U blocks,
-// leaves U_ii (row q) in sh_u[(row in CTA)*16 + q*4 ..].
-template <typename T, bool VOL>
+// One block row i handled by one quad.  Writes the row's L and U blocks and
+// returns row q of U_ii in udiag.
+template <typename T, bool VOL, typename AT>
 __device__ __forceinline__ void build_row_products(const PatternView &P, int i,
-                                                   const double *__restrict__ A, const T *Lin,
+                                                   const AT *__restrict__ A, const T *Lin,
                                                    const T *Uin, const T *Din, T *Lout, T *Uout,
-                                                   double *sh_u) {
+                                                   typename BuildArith<T>::C udiag[4]) {
     using C = typename BuildArith<T>::C;
     const int q = threadIdx.x & 3;
     const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1], dp = P.diagpos[i];
     const int lb = P.lrow[i], ub = P.urow[i];
     for (int p = p0; p < p1; p++) {
+        const int t0 = P.pair_ptr[p], t1 = P.pair_ptr[p + 1];
+        // U_ij with no product pair equals A_ij in every sweep: written once
+        // per build by k_build_prepare into every buffer, skipped here
+        if (p > dp && t0 == t1) continue;
         const int j = P.colind[p];
         C s[4];
-        {
-            double a[4];
-            ld_row(A + (size_t)p * BB + q * BS, a);
-            s[0] = (C)a[0]; s[1] = (C)a[1]; s[2] = (C)a[2]; s[3] = (C)a[3];
-        }
-        const int t1 = P.pair_ptr[p + 1];
-        for (int t = P.pair_ptr[p]; t < t1; t++) {
+        ld_row(A + (size_t)p * BB + q * BS, s);
+        for (int t = t0; t < t1; t++) {
             const int2 pr = P.pairs[t];
             C l[4], u[4];
             ld_row_sel<VOL>(Lin + (size_t)pr.x * BB + q * BS, l);  // row q of L_ik
@@ -140,8 +238,7 @@ __device__ __forceinline__ void build_row_products(const PatternView &P, int i,
             }
             st_row_sel<VOL>(Lout + (size_t)(lb + (p - p0)) * BB + q * BS, o);
         } else if (j == i) {
-            double *u = sh_u + (threadIdx.x >> 2) * BB + q * BS;
-            u[0] = (double)s[0]; u[1] = (double)s[1]; u[2] = (double)s[2]; u[3] = (double)s[3];
+            udiag[0] = s[0]; udiag[1] = s[1]; udiag[2] = s[2]; udiag[3] = s[3];
         } else {
             st_row_sel<VOL>(Uout + (size_t)(ub + (p - dp - 1)) * BB + q * BS, s);
         }
@@ -177,28 +274,61 @@ __device__ __forceinline__ void build_cta_invert(int row0, int n, T *Dout, T *Ud
     }
 }
 
-template <typename T>
+// Dinv_i = inv(U_ii) for the CTA's rows and (if Udiag) U_ii, from row q of
+// U_ii held by thread q of each row's quad.  Every thread of the CTA calls it.
+template <typename T, bool VOL>
+__device__ __forceinline__ void build_finish_rows(int row0, int n, const typename BuildArith<T>::C u[4],
+                                                  T *Dout, T *Udiag, double *sh_u, double *sh_d,
+                                                  float *sh_q, unsigned long long *nsing) {
+    const int i = row0 + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    if constexpr (sizeof(T) < 8) {
+        if (i < n) {
+            float d[4];
+            if (quad_inv4_refined(u, d, sh_q + (threadIdx.x >> 2) * 48) && q == 0)
+                atomicAdd(nsing, 1ull);
+            st_row_sel<VOL>(Dout + (size_t)i * BB + q * BS, d);
+            if (Udiag) st_row_sel<false>(Udiag + (size_t)i * BB + q * BS, u);
+        }
+    } else {
+        if (i < n) {
+            double *su = sh_u + (threadIdx.x >> 2) * BB + q * BS;
+            su[0] = u[0]; su[1] = u[1]; su[2] = u[2]; su[3] = u[3];
+        }
+        build_cta_invert<T, VOL>(row0, n, Dout, Udiag, sh_u, sh_d, nsing);
+    }
+}
+
+// shared memory of the build kernels: FP64 inversion scratch or FP32 quad scratch
+template <typename T> struct BuildShared {
+    static constexpr int D = sizeof(T) == 8 ? BUILD_ROWS * BB : 1;
+    static constexpr int F = sizeof(T) == 8 ? 1 : BUILD_ROWS * 48;
+};
+
+template <typename T, typename AT>
 __global__ void __launch_bounds__(BUILD_THREADS)
-k_build_sync(PatternView P, const double *__restrict__ A, const T *__restrict__ Lin,
+k_build_sync(PatternView P, const AT *__restrict__ A, const T *__restrict__ Lin,
              const T *__restrict__ Uin, const T *__restrict__ Din, T *__restrict__ Lout,
              T *__restrict__ Uout, T *__restrict__ Dout, T *__restrict__ Udiag,
              unsigned long long *nsing) {
-    __shared__ double sh_u[BUILD_ROWS * BB];
-    __shared__ double sh_d[BUILD_ROWS * BB];
+    __shared__ double sh_u[BuildShared<T>::D];
+    __shared__ double sh_d[BuildShared<T>::D];
+    __shared__ __align__(16) float sh_q[BuildShared<T>::F];
     const int row0 = blockIdx.x * BUILD_ROWS;
     const int i = row0 + (threadIdx.x >> 2);
-    if (i < P.n) build_row_products<T, false>(P, i, A, Lin, Uin, Din, Lout, Uout, sh_u);
-    build_cta_invert<T, false>(row0, P.n, Dout, Udiag, sh_u, sh_d, nsing);
+    typename BuildArith<T>::C u[4] = {0, 0, 0, 0};
+    if (i < P.n) build_row_products<T, false>(P, i, A, Lin, Uin, Din, Lout, Uout, u);
+    build_finish_rows<T, false>(row0, P.n, u, Dout, Udiag, sh_u, sh_d, sh_q, nsing);
 }
 
 // Persistent in-place kernel: tickets t = 0 .. nsweeps*nchunks-1 taken in
 // order from ctr; ticket t is chunk (t mod nchunks) in sweep (t / nchunks).
-template <typename T>
+template <typename T, typename AT>
 __global__ void __launch_bounds__(BUILD_THREADS)
-k_build_async(PatternView P, const double *__restrict__ A, T *L, T *U, T *D, T *Udiag,
+k_build_async(PatternView P, const AT *__restrict__ A, T *L, T *U, T *D, T *Udiag,
               int nsweeps, unsigned long long *nsing, unsigned long long *ticket) {
-    __shared__ double sh_u[BUILD_ROWS * BB];
-    __shared__ double sh_d[BUILD_ROWS * BB];
+    __shared__ double sh_u[BuildShared<T>::D];
+    __shared__ double sh_d[BuildShared<T>::D];
+    __shared__ __align__(16) float sh_q[BuildShared<T>::F];
     __shared__ unsigned long long s_t;
     const long long nchunks = (P.n + BUILD_ROWS - 1) / BUILD_ROWS;
     const long long total = nchunks * nsweeps;
@@ -211,37 +341,56 @@ k_build_async(PatternView P, const double *__restrict__ A, T *L, T *U, T *D, T *
         const int sweep = (int)(t / nchunks);
         const int row0 = (int)(t % nchunks) * BUILD_ROWS;
         const int i = row0 + (threadIdx.x >> 2);
-        if (i < P.n) build_row_products<T, true>(P, i, A, L, U, D, L, U, sh_u);
-        build_cta_invert<T, true>(row0, P.n, D, sweep == nsweeps - 1 ? Udiag : nullptr, sh_u,
-                                  sh_d, nsing);
+        typename BuildArith<T>::C u[4] = {0, 0, 0, 0};
+        if (i < P.n) build_row_products<T, true>(P, i, A, L, U, D, L, U, u);
+        build_finish_rows<T, true>(row0, P.n, u, D, sweep == nsweeps - 1 ? Udiag : nullptr,
+                                   sh_u, sh_d, sh_q, nsing);
     }
 }
 
-// X^0 = A: L^0 = strictly lower blocks of A (unscaled), U^0 = upper blocks,
-// Dinv^0 = inv(A_ii) (Sec. 6 setup: the initial guess is the matrix itself).
+// Once per build, one pass over the FP64 A:
+//  * the constant blocks (U_ij, i < j, with no product pair: U_ij = A_ij in
+//    every sweep) go into U[cur] and, for synchronous builds, U[other];
+//  * for FP32/BF16 factors every other block is stored as FP32 in A32, which
+//    the sweeps read instead of A (they compute in FP32; same values);
+//  * from A (init_from_a): X^0 = A, i.e. L^0 = strictly lower blocks of A
+//    (unscaled), U^0 = upper blocks, Dinv^0 = inv(A_ii), U_ii stored (Sec. 6
+//    setup: the initial guess of the factorisation is the matrix itself).
 template <typename T>
 __global__ void __launch_bounds__(BUILD_THREADS)
-k_build_init(PatternView P, const double *__restrict__ A, T *__restrict__ L, T *__restrict__ U,
-             T *__restrict__ D, T *__restrict__ Udiag, unsigned long long *nsing) {
-    __shared__ double sh_u[BUILD_ROWS * BB];
-    __shared__ double sh_d[BUILD_ROWS * BB];
+k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__ A32,
+                T *__restrict__ L, T *__restrict__ U, T *__restrict__ Uother, T *__restrict__ D,
+                T *__restrict__ Udiag, int init_from_a, unsigned long long *nsing) {
+    __shared__ double sh_u[BuildShared<T>::D];
+    __shared__ double sh_d[BuildShared<T>::D];
+    __shared__ __align__(16) float sh_q[BuildShared<T>::F];
     const int row0 = blockIdx.x * BUILD_ROWS;
     const int i = row0 + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    typename BuildArith<T>::C ud[4] = {0, 0, 0, 0};
     if (i < P.n) {
         const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1], dp = P.diagpos[i];
         const int lb = P.lrow[i], ub = P.urow[i];
         for (int p = p0; p < p1; p++) {
             double a[4];
             ld_row(A + (size_t)p * BB + q * BS, a);
+            const bool constant_u = p > dp && P.pair_ptr[p] == P.pair_ptr[p + 1];
+            if (constant_u) {
+                T *u = U + (size_t)(ub + p - dp - 1) * BB + q * BS;
+                st_row(u, a);
+                if (Uother) st_row(Uother + (size_t)(ub + p - dp - 1) * BB + q * BS, a);
+                continue;
+            }
+            if (A32) st_row(A32 + (size_t)p * BB + q * BS, a);
+            if (!init_from_a) continue;
             if (p < dp) st_row(L + (size_t)(lb + p - p0) * BB + q * BS, a);
             else if (p > dp) st_row(U + (size_t)(ub + p - dp - 1) * BB + q * BS, a);
             else {
-                double *u = sh_u + (threadIdx.x >> 2) * BB + q * BS;
-                u[0] = a[0]; u[1] = a[1]; u[2] = a[2]; u[3] = a[3];
+                using C = typename BuildArith<T>::C;
+                ud[0] = (C)a[0]; ud[1] = (C)a[1]; ud[2] = (C)a[2]; ud[3] = (C)a[3];
             }
         }
     }
-    build_cta_invert<T, false>(row0, P.n, D, Udiag, sh_u, sh_d, nsing);
+    if (init_from_a) build_finish_rows<T, false>(row0, P.n, ud, D, Udiag, sh_u, sh_d, sh_q, nsing);
 }
 
 // Export to A's layout in FP64: X[p] = L or U block, U_ii on the diagonal.
@@ -269,6 +418,44 @@ __global__ void k_export(PatternView P, const T *__restrict__ L, const T *__rest
     }
 }
 
+template <typename T, typename AT>
+static abilu_status sweeps_t(abilu_factors f, const AT *Asrc, int nsweeps, abilu_mode mode,
+                             cudaStream_t st) {
+    const PatternView &P = f->p->v;
+    const int grid = (P.n + BUILD_ROWS - 1) / BUILD_ROWS;
+    T **L = reinterpret_cast<T **>(f->L), **U = reinterpret_cast<T **>(f->U);
+    T **D = reinterpret_cast<T **>(f->D);
+    T *Ud = reinterpret_cast<T *>(f->Udiag);
+    if (mode == ABILU_SYNC) {
+        for (int s = 0; s < nsweeps; s++) {
+            const int c = f->cur, o = 1 - f->cur;
+            k_build_sync<T, AT><<<counted(grid), BUILD_THREADS, 0, st>>>(
+                P, Asrc, L[c], U[c], D[c], L[o], U[o], D[o], s == nsweeps - 1 ? Ud : nullptr,
+                f->ctr);
+            ABILU_LAUNCH_CHECK("k_build_sync");
+            f->cur = o;
+        }
+    } else {
+        static int per_sm = -1;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (per_sm < 0)
+            ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_async<T, AT>,
+                                                                     BUILD_THREADS, 0));
+        ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        // at most one CTA per chunk: more would sweep the same rows at once
+        int ctas = per_sm * sms;
+        if (ctas > grid) ctas = grid;
+        if (ctas < 1) ctas = 1;
+        ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, sizeof(unsigned long long), st));
+        const int c = f->cur;
+        k_build_async<T, AT><<<counted(ctas), BUILD_THREADS, 0, st>>>(P, Asrc, L[c], U[c], D[c], Ud,
+                                                                      nsweeps, f->ctr, f->ctr + 1);
+        ABILU_LAUNCH_CHECK("k_build_async");
+    }
+    return ABILU_OK;
+}
+
 template <typename T>
 static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st) {
@@ -277,38 +464,16 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
     T **L = reinterpret_cast<T **>(f->L), **U = reinterpret_cast<T **>(f->U);
     T **D = reinterpret_cast<T **>(f->D);
     T *Ud = reinterpret_cast<T *>(f->Udiag);
-    if (init == ABILU_INIT_FROM_A) {
-        k_build_init<T><<<counted(grid), BUILD_THREADS, 0, st>>>(P, A, L[f->cur], U[f->cur], D[f->cur], Ud,
-                                                        f->ctr);
-        ABILU_LAUNCH_CHECK("k_build_init");
-    }
+    constexpr bool narrow = sizeof(T) < 8;
+    float *A32 = narrow ? reinterpret_cast<float *>(f->A32) : nullptr;
+    const int c = f->cur;
+    k_build_prepare<T><<<counted(grid), BUILD_THREADS, 0, st>>>(
+        P, A, A32, L[c], U[c], mode == ABILU_SYNC ? U[1 - c] : nullptr, D[c], Ud,
+        init == ABILU_INIT_FROM_A ? 1 : 0, f->ctr);
+    ABILU_LAUNCH_CHECK("k_build_prepare");
     if (nsweeps == 0) return ABILU_OK;
-    if (mode == ABILU_SYNC) {
-        for (int s = 0; s < nsweeps; s++) {
-            const int c = f->cur, o = 1 - f->cur;
-            k_build_sync<T><<<counted(grid), BUILD_THREADS, 0, st>>>(
-                P, A, L[c], U[c], D[c], L[o], U[o], D[o], s == nsweeps - 1 ? Ud : nullptr, f->ctr);
-            ABILU_LAUNCH_CHECK("k_build_sync");
-            f->cur = o;
-        }
-    } else {
-        int dev;
-        cudaGetDevice(&dev);
-        int per_sm = 0, sms = 0;
-        ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_async<T>,
-                                                                 BUILD_THREADS, 0));
-        ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        // at most one CTA per chunk: more would sweep the same rows at once
-        int ctas = per_sm * sms;
-        if (ctas > grid) ctas = grid;
-        if (ctas < 1) ctas = 1;
-        ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, sizeof(unsigned long long), st));
-        const int c = f->cur;
-        k_build_async<T><<<counted(ctas), BUILD_THREADS, 0, st>>>(P, A, L[c], U[c], D[c], Ud, nsweeps,
-                                                         f->ctr, f->ctr + 1);
-        ABILU_LAUNCH_CHECK("k_build_async");
-    }
-    return ABILU_OK;
+    if constexpr (narrow) return sweeps_t<T, float>(f, A32, nsweeps, mode, st);
+    else return sweeps_t<T, double>(f, A, nsweeps, mode, st);
 }
 
 template <typename T>

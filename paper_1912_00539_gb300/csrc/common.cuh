@@ -65,6 +65,8 @@ struct abilu_factors_s {
     // factor storage; [cur] is the current iterate, [1-cur] the sync target
     void *L[2], *U[2], *D[2];
     void *Udiag;
+    void *A32;                 // FP32 copy of A's non-constant blocks (FP32/BF16 factors)
+    void *r32;                 // FP32 copy of the apply input (FP32/BF16 factors)
     int cur;
     // apply work vectors (VT = double for F64, float otherwise)
     void *y[2], *x[2];
@@ -174,6 +176,14 @@ __device__ __forceinline__ void st_row(__nv_bfloat16 *p, const double v[4]) {
 __device__ __forceinline__ void st_row(double *p, const float v[4]) {
     double w[4] = {v[0], v[1], v[2], v[3]};
     st_row(p, w);
+}
+__device__ __forceinline__ void st_row(__nv_bfloat16 *p, const float v[4]) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned *>(&a);
+    u.y = *reinterpret_cast<unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
 }
 
 // Quad helpers: the 4 threads of an aligned group of 4 lanes cooperate on one

@@ -26,8 +26,8 @@ namespace abilu {
 
 abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st);
-abilu_status apply_dispatch(abilu_factors f, const double *r, double *z, int nl, int nu,
-                            abilu_mode mode, cudaStream_t st, const int *skip);
+abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip);
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
                          double beta, double *y, cudaStream_t st, const int *skip);
 abilu_status ensure_krylov(abilu_factors f, int m);
@@ -100,11 +100,23 @@ __device__ __forceinline__ bool last_cta(SolveState *S) {
     return am_last;
 }
 
-// sum over CTAs in order of partials[c*stride + k]
-__device__ __forceinline__ double sum_partials(const double *partials, int stride, int k) {
-    double s = 0.0;
-    for (int c = 0; c < (int)gridDim.x; c++) s += __ldcg(partials + (size_t)c * stride + k);
-    return s;
+// In the last CTA: out[k] = sum over CTAs c of partials[c*stride + k0 + k],
+// k < kn <= TILE.  Thread t adds the partials of CTAs t, t+256, ... in that
+// order (independent loads, one latency round), then a fixed-order block
+// reduction: deterministic for a fixed grid.  Every thread of the CTA calls it.
+template <int K>
+__device__ __forceinline__ void reduce_partials(const double *partials, int stride, int k0,
+                                                int kn, double *sh_w, double *out) {
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = 0.0;
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
+        const double *p = partials + (size_t)c * stride + k0;
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            if (k < kn) v[k] += __ldcg(p + k);
+    }
+    block_sum<K>(v, sh_w, out, kn);
 }
 
 // ---------------------------------------------------------------- residual
@@ -119,7 +131,7 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
     double v[2] = {0.0, 0.0};
     const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
     for (int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2); i < P.n; i += rows_per_grid) {
-        // same arithmetic as the SpMV kernel: per block a 4-term dot, summed in row order
+        // same arithmetic as the SpMV kernel: one FMA chain over the row's blocks
         const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1];
         double s = 0.0;
         for (int p = p0; p < p1; p++) {
@@ -127,7 +139,10 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
             const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
             const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)j * BS);
             double2 a0 = __ldg(ap), a1 = __ldg(ap + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
-            s += a0.x * x0.x + a0.y * x0.y + a1.x * x1.x + a1.y * x1.y;
+            s = fma(a0.x, x0.x, s);
+            s = fma(a0.y, x0.y, s);
+            s = fma(a1.x, x1.x, s);
+            s = fma(a1.y, x1.y, s);
         }
         const size_t o = (size_t)i * BS + q;
         const double bi = b[o];
@@ -142,9 +157,10 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
         partials[blockIdx.x * 2 + 1] = sh_o[1];
     }
     if (!last_cta(S)) return;
+    reduce_partials<2>(partials, 2, 0, 2, sh_w, sh_o);
     if (threadIdx.x == 0) {
-        const double rr = sum_partials(partials, 2, 0);
-        if (init) S->bnorm = sqrt(sum_partials(partials, 2, 1));
+        const double rr = sh_o[0];
+        if (init) S->bnorm = sqrt(sh_o[1]);
         else S->restarts += 1;
         S->beta = sqrt(rr);
         S->converged = S->beta <= S->rtol * S->bnorm ? 1 : 0;
@@ -161,17 +177,21 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
     }
 }
 
-// v_out = v_in * S->hn_inv
+// v_out = v_in * S->hn_inv; with FP32/BF16 factors also v32 = (float) v_out,
+// the right-hand side the next preconditioner application reads
 __global__ void __launch_bounds__(RED_THREADS)
-k_scale(const double *vin, double *vout, long long nv2, SolveState *S) {
+k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *S) {
     if (*reinterpret_cast<volatile int *>(&S->done)) return;
     const double s = S->hn_inv;
     const double2 *a = reinterpret_cast<const double2 *>(vin);
     double2 *o = reinterpret_cast<double2 *>(vout);
+    float2 *o32 = reinterpret_cast<float2 *>(v32);
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
          e += (long long)gridDim.x * blockDim.x) {
         double2 t = a[e];
-        o[e] = make_double2(t.x * s, t.y * s);
+        t = make_double2(t.x * s, t.y * s);
+        o[e] = t;
+        if (v32) o32[e] = make_float2((float)t.x, (float)t.y);
     }
 }
 
@@ -195,7 +215,7 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
             for (int k = 0; k < TILE; k++)
                 if (k < kn) {
                     const double2 v = V2[(size_t)(k0 + k) * nv2 + e];
-                    acc[k] += v.x * wv.x + v.y * wv.y;
+                    acc[k] = fma(v.y, wv.y, fma(v.x, wv.x, acc[k]));
                 }
         }
         block_sum<TILE>(acc, sh_w, sh_o, kn);
@@ -203,8 +223,12 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
     }
     if (!last_cta(S)) return;
     double *h = pass == 0 ? S->h : S->h2;
-    for (int k = threadIdx.x; k < jp1; k += blockDim.x) h[k] = sum_partials(partials, MAXM + 2, k);
-    __syncthreads();
+    for (int k0 = 0; k0 < jp1; k0 += TILE) {
+        const int kn = jp1 - k0 < TILE ? jp1 - k0 : TILE;
+        reduce_partials<TILE>(partials, MAXM + 2, k0, kn, sh_w, sh_o);
+        if (threadIdx.x < kn) h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        __syncthreads();
+    }
     if (threadIdx.x == 0) S->counter = 0;
 }
 
@@ -232,14 +256,15 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
             t.y -= sh_h[k] * v.y;
         }
         w2[e] = t;
-        nrm[0] += t.x * t.x + t.y * t.y;
+        nrm[0] = fma(t.y, t.y, fma(t.x, t.x, nrm[0]));
     }
     if (!final_pass) return;
     block_sum<1>(nrm, sh_w, sh_o, 1);
     if (threadIdx.x == 0) partials[(size_t)blockIdx.x * (MAXM + 2) + MAXM + 1] = sh_o[0];
     if (!last_cta(S)) return;
+    reduce_partials<1>(partials, MAXM + 2, MAXM + 1, 1, sh_w, sh_o);
     if (threadIdx.x != 0) return;
-    const double hn = sqrt(sum_partials(partials, MAXM + 2, MAXM + 1));
+    const double hn = sqrt(sh_o[0]);
     double col[MAXM + 1];
     for (int i = 0; i <= j; i++) col[i] = S->h[i] + (pass == 1 ? S->h2[i] : 0.0);
     col[j + 1] = hn;
@@ -364,6 +389,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     const int nred = red_ctas();
     const abilu_mode mode = (abilu_mode)opts->mode;
     const int *skip = &SS->done;
+    float *v32 = reinterpret_cast<float *>(f->r32);  // NULL for FP64 factors
 
     if (opts->build) {
         s = build_dispatch(f, A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
@@ -372,7 +398,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
     k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 1);
-    k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, nv2, SS);
+    k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
     ABILU_LAUNCH_CHECK("fgmres init");
     cudaEvent_t ev[2];
     ABILU_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
@@ -387,7 +413,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     while (!h.converged && h.iters < opts->max_iters) {
         int j = 0;
         for (; j < m; j++) {
-            s = apply_dispatch(f, V + (size_t)j * nv, Z + (size_t)j * nv, opts->apply_sweeps_lower,
+            s = apply_dispatch(f, V + (size_t)j * nv, v32, Z + (size_t)j * nv, opts->apply_sweeps_lower,
                                opts->apply_sweeps_upper, mode, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
@@ -397,7 +423,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
                 k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, f->partials, 1);
                 k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, f->partials, 1, 1);
             }
-            k_scale<<<counted(nred), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, nv2, SS);
+            k_scale<<<counted(nred), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step"); break; }
             cudaEventRecord(ev[j & 1], st);
@@ -409,7 +435,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
         if (ret != ABILU_OK) break;
         k_xupdate<<<counted(nred), RED_THREADS, 0, st>>>(Z, nv2, x, SS);
         k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 0);
-        k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, nv2, SS);
+        k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres restart"); break; }
         e = cudaStreamSynchronize(st);

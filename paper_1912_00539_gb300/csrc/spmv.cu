@@ -8,7 +8,9 @@
 // 128-byte block as one fully used line), forms the 4-term dot product with
 // x_j, and writes y_i[q].  The first four blocks of a row are loaded before
 // any arithmetic so each thread keeps up to 8 independent 16-byte loads in
-// flight.  FP64 work is the minimum, 16 FMA per block.
+// flight.  FP64 work is the minimum, 16 FMA per block: one running FMA chain
+// per output entry (FP64 throughput on this GPU is ~1.2 TFLOP/s, so at
+// 0.25 flop per byte the FP64 pipe, not only HBM, bounds this kernel).
 #include "common.cuh"
 
 namespace abilu {
@@ -19,7 +21,6 @@ constexpr int SPMV_ROWS = SPMV_THREADS / 4;
 __device__ __forceinline__ double row_dot_blocks(const PatternView &P, const double *__restrict__ A,
                                                  const double *__restrict__ x, int i, int q) {
     const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1];
-    double acc[4];
     double2 a0[4], a1[4];
     int jj[4];
 #pragma unroll
@@ -40,8 +41,10 @@ __device__ __forceinline__ double row_dot_blocks(const PatternView &P, const dou
         if (jj[k] >= 0) {
             const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)jj[k] * BS);
             double2 x0 = __ldg(xp), x1 = __ldg(xp + 1);
-            acc[k] = a0[k].x * x0.x + a0[k].y * x0.y + a1[k].x * x1.x + a1[k].y * x1.y;
-            s += acc[k];
+            s = fma(a0[k].x, x0.x, s);
+            s = fma(a0[k].y, x0.y, s);
+            s = fma(a1[k].x, x1.x, s);
+            s = fma(a1[k].y, x1.y, s);
         }
     }
     for (int p = p0 + 4; p < p1; p++) {  // rows longer than four blocks
@@ -49,7 +52,10 @@ __device__ __forceinline__ double row_dot_blocks(const PatternView &P, const dou
         const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
         const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)j * BS);
         double2 b0 = __ldg(ap), b1 = __ldg(ap + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
-        s += b0.x * x0.x + b0.y * x0.y + b1.x * x1.x + b1.y * x1.y;
+        s = fma(b0.x, x0.x, s);
+        s = fma(b0.y, x0.y, s);
+        s = fma(b1.x, x1.x, s);
+        s = fma(b1.y, x1.y, s);
     }
     return s;
 }

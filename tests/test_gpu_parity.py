@@ -403,3 +403,19 @@ def test_full_size_512x512_parity(ab):
         xn = xs.cpu().numpy()
         r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, xn)
         assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", ["sync", "async"])
+def test_refined_fp32_inverse_is_fp32_accurate(ab, dsys, mode):
+    """FP32 factors: Dinv_i (FP32 adjugate + one error-free Newton step) equals
+    the FP64 inverse of the stored FP32 U_ii to a few FP32 ulps."""
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, "f32")
+    fac.build(dsys.A, 3, mode=mode)
+    X, D = fac.export()
+    X, D = X.cpu().numpy(), D.cpu().numpy()
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    Uii = X[rows == s.colind]
+    ref = np.linalg.inv(Uii)
+    err = np.abs(D - ref).max(axis=(1, 2)) / np.abs(ref).max(axis=(1, 2))
+    assert err.max() < 8 * 2.0 ** -24, err.max()
