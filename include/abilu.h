@@ -137,6 +137,36 @@ abilu_status abilu_apply(abilu_factors f, const double *r, double *z, int nsweep
                          int nsweeps_upper, abilu_mode mode, abilu_stream stream);
 
 /*
+ * abilu_apply_noalloc — the synchronous FP64 preconditioner application for
+ * callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is an interface for callers that cannot call cudaMalloc (code inside
+ * another library's allocator hooks or memory pool, frameworks that reserve
+ * all device memory up front, code that must not allocate while a CUDA graph
+ * is being built).  It allocates nothing: the factors come in as plain arrays
+ * and the sweep vectors live in a fixed __device__ array inside the library.
+ *
+ * Computes the same z as abilu_apply(..., ABILU_SYNC) on FP64 factors:
+ * nsweeps_lower Jacobi sweeps on L y = r from y = 0, then nsweeps_upper on
+ * U z = y from z = 0.  rowptr/colind: the pattern (device, as for
+ * abilu_pattern_create); X: double[nnzb][4][4] factors in A's pattern layout
+ * (L_ij at column < row, U_ij at column > row, the diagonal entry ignored), as
+ * abilu_factors_export writes them; Dinv: double[n][4][4] = inv(U_ii); r, z:
+ * double[n][4], distinct.  All device pointers, 16-byte aligned, caller-owned.
+ *
+ * Limit: n <= 65,536 cells (the fixed scratch is 3 vectors of that size,
+ * 6 MiB, held by every GPU that loads the library until the process exits);
+ * larger n returns ABILU_EINVAL without touching the device.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU
+ * (different streams or host threads) race on it; serialise them.  Asynchronous
+ * on `stream`; returns ABILU_EINVAL for bad arguments.
+ */
+abilu_status abilu_apply_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                                 const double *X, const double *Dinv, const double *r, double *z,
+                                 int nsweeps_lower, int nsweeps_upper, abilu_stream stream);
+
+/*
  * Block sparse matrix-vector product y = alpha * A x + beta * y (FP64), the
  * product FGMRES needs once per iteration (Sec. 6 setup).  x and y distinct.
  * beta == 0 does not read y.

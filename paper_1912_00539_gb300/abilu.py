@@ -31,7 +31,7 @@ INITS = {"a": 0, "previous": 1}
 EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_pattern_create", "abilu_pattern_destroy",
            "abilu_pattern_counts", "abilu_factors_create", "abilu_factors_destroy", "abilu_build",
            "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
-           "fgmres_default_opts", "fgmres_solve")
+           "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc")
 
 
 class FgmresOpts(C.Structure):
@@ -62,6 +62,8 @@ _lib.abilu_factors_destroy.restype = None
 _lib.abilu_build.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
 _lib.abilu_apply.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
 _lib.bsr_spmv.argtypes = [_vp, _vp, _f64, _vp, _f64, _vp, _vp]
+_lib.abilu_apply_noalloc.argtypes = [_i32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp]
+_lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
 _lib.fgmres_default_opts.argtypes = [C.POINTER(FgmresOpts)]
@@ -189,6 +191,23 @@ def bsr_spmv(pattern: Pattern, A, x, y, alpha=1.0, beta=0.0, stream=None):
     _check(_lib.bsr_spmv(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
                          float(alpha), _ptr(x, torch.float64, nv, "x"), float(beta),
                          _ptr(y, torch.float64, nv, "y"), _stream(stream)))
+
+
+NOALLOC_MAX_CELLS = 65536
+
+
+def apply_noalloc(rowptr, colind, X, Dinv, r, z, nsweeps_lower, nsweeps_upper, stream=None):
+    """abilu_apply_noalloc: synchronous FP64 application on factors given as
+    arrays (A's pattern layout), with no device allocation by the library."""
+    import torch
+    n = rowptr.numel() - 1
+    _check(_lib.abilu_apply_noalloc(n, _ptr(rowptr, torch.int32, what="rowptr"),
+                                    _ptr(colind, torch.int32, what="colind"),
+                                    _ptr(X, torch.float64, 16 * colind.numel(), "X"),
+                                    _ptr(Dinv, torch.float64, 16 * n, "Dinv"),
+                                    _ptr(r, torch.float64, 4 * n, "r"),
+                                    _ptr(z, torch.float64, 4 * n, "z"), int(nsweeps_lower),
+                                    int(nsweeps_upper), _stream(stream)))
 
 
 @dataclass
