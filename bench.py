@@ -40,6 +40,20 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(torch, value, device):
+    """Largest value over all ranks (the job's wall time is the slowest rank's)."""
+    if not torch.distributed.is_available() or not torch.distributed.is_initialized():
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, max_ms):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -166,17 +180,20 @@ def _events(torch, n):
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def kernel_rooflines(torch, ab, pat, A, fac, s, peak):
-    """Average duration of single launches of each hot kernel (CUDA events on
-    the launching stream, back-to-back launches after warm-up) and achieved
-    GB/s from the algorithmic bytes of one launch."""
+def kernel_rooflines(torch, ab, pat, A, fac, s, peak, mode="async"):
+    """Average duration of the hot kernels, each isolated as the difference of
+    two public calls timed with CUDA events on the launching stream
+    (back-to-back calls after warm-up), and achieved GB/s from the algorithmic
+    bytes of one launch (formulas in the design doc).  FP32 factors."""
     N, nnzb = s.n, s.nnzb
     E = (nnzb - N) // 2
     f, v = 4, 4   # FP32 factors, FP32 apply vectors
+    c = pat.counts()
+    nw, npairs = c["nwork"], c["npairs"]
     x = torch.randn(N, 4, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     z = torch.empty_like(x)
-    reps = 50
+    reps = 40
 
     def avg_us(fn):
         for _ in range(5):
@@ -192,17 +209,41 @@ def kernel_rooflines(torch, ab, pat, A, fac, s, peak):
 
     out = {}
     t = avg_us(lambda: ab.bsr_spmv(pat, A, x, y))
-    b = nnzb * (128 + 4) + 4 * (N + 1) + 2 * 32 * N
-    out["spmv_f64"] = {"us": t, "bytes": b, "launches_per_call": 1}
-    t = avg_us(lambda: fac.build(A, 1, "sync", init="previous"))
-    b = nnzb * 132 + 4 * (N + 1) + 2 * 16 * f * (nnzb + N)
-    out["build_sweep_f32"] = {"us": t, "bytes": b, "launches_per_call": 1}
-    # one lower and one upper sweep: apply(2, 2) runs one lower sweep kernel
-    # (with x^1 = Dinv y fused) and one upper sweep kernel
-    t = avg_us(lambda: fac.apply(x, z, 2, 2, "sync"))
+    out["spmv_f64"] = {"us": t, "bytes": nnzb * (128 + 4) + 4 * (N + 1) + 2 * 32 * N,
+                       "sweeps": 1}
+    # build: prepare pass + sweeps; the sweeps are the difference to 0 sweeps.
+    # One sweep's unique bytes over the work list: records, FP32 A rows, pair
+    # ranges and pairs, the pairs' L and U rows, Dinv read and written, L written
+    sweep_b = (nw * 16 + nw * 16 * f + 4 * (nnzb + 1) + npairs * 8 + 2 * npairs * 16 * f
+               + 2 * N * 16 * f + c["nl"] * 16 * f)
+    nb = BUILD_SWEEPS
+    t0 = avg_us(lambda: fac.build(A, 0, mode, init="previous"))
+    tb = avg_us(lambda: fac.build(A, nb, mode, init="previous"))
+    if mode == "async":   # one persistent launch runs all sweeps
+        out["build_sweeps_f32"] = {"us": tb - t0, "bytes": nb * sweep_b, "sweeps": nb}
+    else:
+        out["build_sweep_f32"] = {"us": (tb - t0) / nb, "bytes": sweep_b, "sweeps": 1}
+    # prepare (warm start): A read once, FP32 copy of the work blocks, constant
+    # U blocks (into both buffers for sync builds), index arrays
+    ncu_ = c["nu"] - (nw - c["nl"] - N)
+    out["build_prepare_f32"] = {"us": t0, "bytes": nnzb * 128 + 4 * (nnzb + 1) + 16 * (N + 1)
+                                + nw * 16 * f + (2 if mode == "sync" else 1) * ncu_ * 16 * f,
+                                "sweeps": 1}
     bl = E * (16 * f + 4) + 4 * (N + 1) + 3 * N * 4 * v
     bu = E * (16 * f + 4) + 16 * f * N + 4 * (N + 1) + 3 * N * 4 * v
-    out["lower+upper_sweep_f32"] = {"us": t, "bytes": bl + bu, "launches_per_call": 2}
+    na = APPLY_SWEEPS
+    t00 = avg_us(lambda: fac.apply(x, z, 0, 0, mode))
+    if mode == "async":
+        tl = avg_us(lambda: fac.apply(x, z, na, 0, mode)) - t00
+        tu = avg_us(lambda: fac.apply(x, z, 0, na, mode)) - t00
+        out["lower_sweeps_f32"] = {"us": tl, "bytes": na * bl, "sweeps": na}
+        out["upper_sweeps_f32"] = {"us": tu, "bytes": na * bu, "sweeps": na}
+    else:
+        t11 = avg_us(lambda: fac.apply(x, z, 1, 1, mode))
+        tl = avg_us(lambda: fac.apply(x, z, 2, 1, mode)) - t11
+        tu = avg_us(lambda: fac.apply(x, z, 1, 2, mode)) - t11
+        out["lower_sweep_f32"] = {"us": tl, "bytes": bl, "sweeps": 1}
+        out["upper_sweep_f32"] = {"us": tu, "bytes": bu, "sweeps": 1}
     for k in out.values():
         k["GBs"] = k["bytes"] / (k["us"] * 1e-6) / 1e9
         k["frac"] = k["GBs"] / peak
@@ -217,10 +258,13 @@ def run_kernels_only(args):
     s = _system()
     pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
     A = torch.from_numpy(s.vals).cuda()
-    fk = ab.Factors(pat, "f32")
-    fk.build(A, BUILD_SWEEPS, "sync")
-    kern = kernel_rooflines(torch, ab, pat, A, fk, s, peak)
-    print(json.dumps({k: {kk: round(vv, 3) for kk, vv in v.items()} for k, v in kern.items()}))
+    out = {}
+    for mode in ("async", "sync"):
+        fk = ab.Factors(pat, "f32")
+        fk.build(A, BUILD_SWEEPS, mode)
+        kern = kernel_rooflines(torch, ab, pat, A, fk, s, peak, mode)
+        out[mode] = {k: {kk: round(vv, 3) for kk, vv in v.items()} for k, v in kern.items()}
+    print(json.dumps(out))
     return 0
 
 
@@ -296,12 +340,8 @@ def run_gpu(args):
     launches = ab.kernel_launches() - l0
     clk = clocks.stop()
     step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(torch, evs[0].elapsed_time(evs[-1]), dev)
+    value = job_rate(args.steps, world, total_ms)
 
     # ---- end to end: A and b from pinned host memory, x back, every step
     hA = torch.from_numpy(s.vals).pin_memory()
@@ -329,29 +369,31 @@ def run_gpu(args):
         e2e_step()
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * args.steps / (e2e_ms * 1e-3), "unit": "solves/s",
+    e2e_ms = max_over_ranks(torch, e0.elapsed_time(e1), dev)
+    e2e = {"value": job_rate(args.steps, world, e2e_ms), "unit": "solves/s",
            "h2d_bytes_per_step": hA.numel() * 8 + hb.numel() * 8,
            "d2h_bytes_per_step": hx.numel() * 8}
 
     # ---- per-kernel rooflines (the dominant kernel by solve time share)
     fk = ab.Factors(pat, "f32")
-    fk.build(A, BUILD_SWEEPS, "sync")
-    kern = kernel_rooflines(torch, ab, pat, A, fk, s, peak)
+    fk.build(A, BUILD_SWEEPS, args.mode)
+    kern = kernel_rooflines(torch, ab, pat, A, fk, s, peak, args.mode)
     it = statistics.median(iters)
-    per_solve = {"spmv_f64": it + 2, "build_sweep_f32": BUILD_SWEEPS,
-                 "lower+upper_sweep_f32": it * (APPLY_SWEEPS - 1)}
+    # launches of each kernel per solve (it Arnoldi steps, 2 residuals)
+    if args.mode == "async":
+        per_solve = {"spmv_f64": it, "build_sweeps_f32": 1, "build_prepare_f32": 1,
+                     "lower_sweeps_f32": it, "upper_sweeps_f32": it}
+    else:
+        per_solve = {"spmv_f64": it, "build_sweep_f32": BUILD_SWEEPS, "build_prepare_f32": 1,
+                     "lower_sweep_f32": it * (APPLY_SWEEPS - 1),
+                     "upper_sweep_f32": it * (APPLY_SWEEPS - 1)}
     share = {k: kern[k]["us"] * per_solve[k] for k in kern}
     dom = max(share, key=share.get)
     dk = kern[dom]
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(dk["GBs"], 1), "peak": peak,
             "unit": "GB/s", "frac": round(dk["frac"], 4),
             "traffic": None, "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": dk["bytes"] / dk["launches_per_call"]}
+            "algorithmic_bytes_per_launch": dk["bytes"], "sweeps_per_launch": dk["sweeps"]}
     kernels = {k: {"us_per_call": round(v["us"], 2), "GBs": round(v["GBs"], 1),
                    "frac_of_measured_peak": round(v["frac"], 4),
                    "us_per_solve": round(share[k], 1)} for k, v in kern.items()}

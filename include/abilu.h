@@ -98,7 +98,9 @@ abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int32_t *rowptr
 void abilu_pattern_destroy(abilu_pattern p);
 
 /* Host-side counts of a pattern: n, nnzb, strictly-lower blocks, strictly-upper
- * blocks, product pairs, largest row length.  `out` is host int64_t[6]. */
+ * blocks, product pairs, largest row length, blocks a build sweep updates (all
+ * but the strictly-upper blocks without product pairs, which stay equal to A).
+ * `out` is host int64_t[7]. */
 abilu_status abilu_pattern_counts(abilu_pattern p, int64_t *out);
 
 /*

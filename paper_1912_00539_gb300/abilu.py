@@ -132,9 +132,9 @@ class Pattern:
         self.n, self.nnzb = n, nnzb
 
     def counts(self) -> dict:
-        out = (C.c_int64 * 6)()
+        out = (C.c_int64 * 7)()
         _check(_lib.abilu_pattern_counts(self.handle, out))
-        return dict(zip(("n", "nnzb", "nl", "nu", "npairs", "max_row"), list(out)))
+        return dict(zip(("n", "nnzb", "nl", "nu", "npairs", "max_row", "nwork"), list(out)))
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -247,3 +247,4 @@ def fgmres_solve(pattern: Pattern, A, factors: Factors, b, x, restart=30, max_it
     _check(st, allow=(OK, WARN_SINGULAR) if raise_on_noconv else (OK, WARN_SINGULAR, ENOCONV))
     return SolveResult(r.iters, r.restarts, r.rel_resid_est, r.rel_resid_true,
                        r.singular_blocks, st)
+

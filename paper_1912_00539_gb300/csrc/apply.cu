@@ -31,19 +31,34 @@ constexpr int APPLY_ROWS = APPLY_THREADS / 4;
 template <typename T> struct ApplyArith { using VT = float; };
 template <> struct ApplyArith<double> { using VT = double; };
 
+__device__ __forceinline__ double to_f64v(float v) { return to_f64(v); }
+__device__ __forceinline__ double to_f64v(double v) { return v; }
+
 __device__ __forceinline__ bool skipped(const int *skip) {
     return skip && *reinterpret_cast<const volatile int *>(skip);
-}
-
-// 4 unknowns of cell j as the compute type
-template <typename VT, typename YT>
-__device__ __forceinline__ void ld_cell(const YT *v, int j, VT out[4]) {
-    ld_row(v + (size_t)j * BS, out);
 }
 
 template <typename VT>
 __device__ __forceinline__ VT dot4(const VT a[4], const VT b[4]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
+}
+
+// s - sum over blocks l0..l1-1 of (row q of factor block l) . v[col[l]].
+// VOL: the vector is being updated in place by other threads.  (Prefetching
+// the row's blocks before the arithmetic was measured slower here: the extra
+// registers cost more occupancy than the shorter dependency chain gained.)
+template <bool VOL, typename T, typename VT>
+__device__ __forceinline__ VT row_sweep_sum(VT s, const T *__restrict__ F,
+                                            const int32_t *__restrict__ col, int l0, int l1,
+                                            const VT *v) {
+    const int q = threadIdx.x & 3;
+    for (int l = l0; l < l1; l++) {
+        VT a[4], b[4];
+        ld_row(F + (size_t)l * BB + q * BS, a);
+        ld_row_sel<VOL>(v + (size_t)col[l] * BS, b);
+        s -= dot4(a, b);
+    }
+    return s;
 }
 
 // x_i = Dinv_i t_i where thread q holds t_i[q]; returns x_i[q]
@@ -66,20 +81,12 @@ k_lower_sync(PatternView P, const T *__restrict__ L, const VT *__restrict__ r,
     if (skipped(skip)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
-    VT s = r[(size_t)i * BS + q];
-    const int l1 = P.lrow[i + 1];
-    for (int l = P.lrow[i]; l < l1; l++) {
-        const int j = P.lcol[l];
-        VT lr[4], yj[4];
-        ld_row(L + (size_t)l * BB + q * BS, lr);
-        ld_cell(yin, j, yj);
-        s -= dot4(lr, yj);
-    }
+    const VT s = row_sweep_sum<false>(r[(size_t)i * BS + q], L, P.lcol, P.lrow[i], P.lrow[i + 1], yin);
     yout[(size_t)i * BS + q] = s;
     if (x1 || z) {
         VT x = dinv_times<T, VT>(D, i, s);
         if (x1) x1[(size_t)i * BS + q] = x;
-        if (z) z[(size_t)i * BS + q] = (double)x;
+        if (z) z[(size_t)i * BS + q] = to_f64v(x);
     }
 }
 
@@ -94,7 +101,7 @@ k_diag_apply(PatternView P, const T *__restrict__ D, const VT *__restrict__ y,
     VT t = y[(size_t)i * BS + q];
     VT x = dinv_times<T, VT>(D, i, t);
     if (x1) x1[(size_t)i * BS + q] = x;
-    if (z) z[(size_t)i * BS + q] = (double)x;
+    if (z) z[(size_t)i * BS + q] = to_f64v(x);
 }
 
 template <typename T, typename VT>
@@ -105,18 +112,10 @@ k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
     if (skipped(skip)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
-    VT s = y[(size_t)i * BS + q];
-    const int u1 = P.urow[i + 1];
-    for (int u = P.urow[i]; u < u1; u++) {
-        const int j = P.ucol[u];
-        VT ur[4], xj[4];
-        ld_row(U + (size_t)u * BB + q * BS, ur);
-        ld_cell(xin, j, xj);
-        s -= dot4(ur, xj);
-    }
+    const VT s = row_sweep_sum<false>(y[(size_t)i * BS + q], U, P.ucol, P.urow[i], P.urow[i + 1], xin);
     VT x = dinv_times<T, VT>(D, i, s);
     if (xout) xout[(size_t)i * BS + q] = x;
-    if (z) z[(size_t)i * BS + q] = (double)x;
+    if (z) z[(size_t)i * BS + q] = to_f64v(x);
 }
 
 // ---------------------------------------------------------------- async
@@ -146,15 +145,8 @@ k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, 
         if (t >= total) break;
         const int i = (int)(t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
         if (i < P.n) {
-            VT s = r[(size_t)i * BS + q];
-            const int l1 = P.lrow[i + 1];
-            for (int l = P.lrow[i]; l < l1; l++) {
-                const int j = P.lcol[l];
-                VT lr[4], yj[4];
-                ld_row(L + (size_t)l * BB + q * BS, lr);
-                ld_row_volatile(y + (size_t)j * BS, yj);
-                s -= dot4(lr, yj);
-            }
+            const VT s = row_sweep_sum<true>(r[(size_t)i * BS + q], L, P.lcol, P.lrow[i],
+                                             P.lrow[i + 1], (const VT *)y);
             st_vol(y + (size_t)i * BS + q, s);
         }
     }
@@ -181,18 +173,11 @@ k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
         const bool last = t / nchunks == nsweeps - 1;
         const int i = (int)(nchunks - 1 - t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
         if (i < P.n) {  // quads of one row stay together: the shuffles below are quad-local
-            VT s = y[(size_t)i * BS + q];
-            const int u1 = P.urow[i + 1];
-            for (int u = P.urow[i]; u < u1; u++) {
-                const int j = P.ucol[u];
-                VT ur[4], xj[4];
-                ld_row(U + (size_t)u * BB + q * BS, ur);
-                ld_row_volatile(x + (size_t)j * BS, xj);
-                s -= dot4(ur, xj);
-            }
+            const VT s = row_sweep_sum<true>(y[(size_t)i * BS + q], U, P.ucol, P.urow[i],
+                                             P.urow[i + 1], (const VT *)x);
             VT xi = dinv_times<T, VT>(D, i, s);
             st_vol(x + (size_t)i * BS + q, xi);
-            if (last) z[(size_t)i * BS + q] = (double)xi;
+            if (last) z[(size_t)i * BS + q] = to_f64v(xi);
         }
     }
 }

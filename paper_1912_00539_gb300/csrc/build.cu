@@ -304,6 +304,108 @@ template <typename T> struct BuildShared {
     static constexpr int F = sizeof(T) == 8 ? 1 : BUILD_ROWS * 48;
 };
 
+// ---- block work items (FP32/BF16 factors)
+// The block-asynchronous iteration updates one block per step (Eq.
+// async_blockilu_fp: the update function ranges over the blocks), so a work
+// item here is one block of the pattern's work list, handled by one quad.  Its
+// dependency chain is short (work record -> A row, pair range, Dinv_j ->
+// pairs -> compute), and there are four times more of them in flight than
+// block rows, which is what hides memory latency on this GPU.
+constexpr int WORK_PER_CTA = BUILD_THREADS / 4;
+static_assert(WORK_PER_CTA == WORK_CHUNK, "work list chunks are sorted per CTA");
+
+template <typename T, bool VOL>
+__device__ __forceinline__ void build_block(const PatternView &P, int w,
+                                            const float *__restrict__ A32, const T *Lin,
+                                            const T *Uin, const T *Din, T *Lout, T *Uout, T *Dout,
+                                            T *Udiag, float *sh_q, unsigned long long *nsing) {
+    const int q = threadIdx.x & 3;
+    const int4 rec = P.work[w];
+    const int p = rec.x, j = rec.y, dst = rec.z, kind = rec.w;
+    float s[4], d[4];
+    ld_row(A32 + (size_t)p * BB + q * BS, s);
+    const int t0 = P.pair_ptr[p], t1 = P.pair_ptr[p + 1];
+    if (kind == WORK_L) ld_row_sel<VOL>(Din + (size_t)j * BB + q * BS, d);
+    for (int t = t0; t < t1; t++) {
+        const int2 pr = P.pairs[t];
+        float l[4], u[4];
+        ld_row_sel<VOL>(Lin + (size_t)pr.x * BB + q * BS, l);  // row q of L_ik
+        ld_row_sel<VOL>(Uin + (size_t)pr.y * BB + q * BS, u);  // row q of U_kj
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] += l[k] * qshfl(u[c], k);
+#pragma unroll
+        for (int c = 0; c < 4; c++) s[c] -= acc[c];
+    }
+    if (kind == WORK_L) {  // L_ij = S Dinv_j; row k of Dinv_j lives in thread k
+        float o[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            float d0 = qshfl(d[c], 0), d1 = qshfl(d[c], 1), d2 = qshfl(d[c], 2), d3 = qshfl(d[c], 3);
+            o[c] = s[0] * d0 + s[1] * d1 + s[2] * d2 + s[3] * d3;
+        }
+        st_row_sel<VOL>(Lout + (size_t)dst * BB + q * BS, o);
+    } else if (kind == WORK_U) {
+        st_row_sel<VOL>(Uout + (size_t)dst * BB + q * BS, s);
+    } else {  // U_ii = S, Dinv_i = inv(U_ii)
+        float x[4];
+        if (quad_inv4_refined(s, x, sh_q) && q == 0) atomicAdd(nsing, 1ull);
+        st_row_sel<VOL>(Dout + (size_t)dst * BB + q * BS, x);
+        if (Udiag) st_row_sel<false>(Udiag + (size_t)dst * BB + q * BS, s);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BUILD_THREADS)
+k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__restrict__ Lin,
+                    const T *__restrict__ Uin, const T *__restrict__ Din, T *__restrict__ Lout,
+                    T *__restrict__ Uout, T *__restrict__ Dout, T *__restrict__ Udiag,
+                    unsigned long long *nsing) {
+    __shared__ __align__(16) float sh_q[WORK_PER_CTA * 48];
+    const int w = blockIdx.x * WORK_PER_CTA + (threadIdx.x >> 2);
+    if (w >= P.nwork) return;  // whole quads leave together
+    build_block<T, false>(P, w, A32, Lin, Uin, Din, Lout, Uout, Dout, Udiag,
+                          sh_q + (threadIdx.x >> 2) * 48, nsing);
+}
+
+// In place.  Each warp takes tickets t = 0 .. nsweeps*nchunks-1 in order from
+// one counter (no CTA barrier, so warps never wait for each other); ticket t
+// is chunk (t mod nchunks) of sweep t / nchunks, a chunk being 32 consecutive
+// work blocks, done in 4 steps of 8 (one block per quad, consecutive blocks,
+// so a step stays within one kind of the kind-sorted list).
+constexpr int WARP_CHUNK = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(BUILD_THREADS, 5)
+k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T *D, T *Udiag,
+                     int nsweeps, int max_warps, unsigned long long *nsing,
+                     unsigned long long *ticket) {
+    __shared__ __align__(16) float sh_q[WORK_PER_CTA * 48];
+    // at most one warp per chunk: more would sweep the same blocks at once
+    if (blockIdx.x * (BUILD_THREADS / 32) + (threadIdx.x >> 5) >= max_warps) return;
+    const long long nchunks = (P.nwork + WARP_CHUNK - 1) / WARP_CHUNK;
+    const long long total = nchunks * nsweeps;
+    const int lane = threadIdx.x & 31;
+    float *myq = sh_q + (threadIdx.x >> 2) * 48;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(ticket, 1ull);
+        const long long t = (long long)__shfl_sync(0xffffffffu, tk, 0);
+        if (t >= total) break;
+        const bool last = t / nchunks == nsweeps - 1;
+        const int base = (int)(t % nchunks) * WARP_CHUNK + (lane >> 2);
+#pragma unroll 1
+        for (int k = 0; k < WARP_CHUNK / 8; k++) {
+            const int w = base + 8 * k;
+            if (w < P.nwork)
+                build_block<T, true>(P, w, A32, L, U, D, L, U, D, last ? Udiag : nullptr, myq, nsing);
+        }
+        __syncwarp();
+    }
+}
+
 template <typename T, typename AT>
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_sync(PatternView P, const AT *__restrict__ A, const T *__restrict__ Lin,
@@ -385,8 +487,11 @@ k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__
             if (p < dp) st_row(L + (size_t)(lb + p - p0) * BB + q * BS, a);
             else if (p > dp) st_row(U + (size_t)(ub + p - dp - 1) * BB + q * BS, a);
             else {
-                using C = typename BuildArith<T>::C;
-                ud[0] = (C)a[0]; ud[1] = (C)a[1]; ud[2] = (C)a[2]; ud[3] = (C)a[3];
+                if constexpr (sizeof(T) == 8) {
+                    ud[0] = a[0]; ud[1] = a[1]; ud[2] = a[2]; ud[3] = a[3];
+                } else {
+                    ud[0] = to_f32(a[0]); ud[1] = to_f32(a[1]); ud[2] = to_f32(a[2]); ud[3] = to_f32(a[3]);
+                }
             }
         }
     }
@@ -416,6 +521,46 @@ __global__ void k_export(PatternView P, const T *__restrict__ L, const T *__rest
         ld_row(D + (size_t)i * BB + q * BS, v);
         st_row(Dinv + (size_t)i * BB + q * BS, v);
     }
+}
+
+template <typename T>
+static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweeps,
+                                   abilu_mode mode, cudaStream_t st) {
+    const PatternView &P = f->p->v;
+    const int grid = (P.nwork + WORK_PER_CTA - 1) / WORK_PER_CTA;
+    T **L = reinterpret_cast<T **>(f->L), **U = reinterpret_cast<T **>(f->U);
+    T **D = reinterpret_cast<T **>(f->D);
+    T *Ud = reinterpret_cast<T *>(f->Udiag);
+    if (grid == 0) return ABILU_OK;
+    if (mode == ABILU_SYNC) {
+        for (int s = 0; s < nsweeps; s++) {
+            const int c = f->cur, o = 1 - f->cur;
+            k_build_blocks_sync<T><<<counted(grid), BUILD_THREADS, 0, st>>>(
+                P, A32, L[c], U[c], D[c], L[o], U[o], D[o], s == nsweeps - 1 ? Ud : nullptr, f->ctr);
+            ABILU_LAUNCH_CHECK("k_build_blocks_sync");
+            f->cur = o;
+        }
+    } else {
+        static int per_sm = -1;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (per_sm < 0)
+            ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_blocks_async<T>,
+                                                                     BUILD_THREADS, 0));
+        ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int wchunks = (P.nwork + WARP_CHUNK - 1) / WARP_CHUNK;
+        int warps = per_sm * sms * (BUILD_THREADS / 32);
+        if (warps > wchunks) warps = wchunks;
+        if (warps < 1) warps = 1;
+        const int ctas = (warps + BUILD_THREADS / 32 - 1) / (BUILD_THREADS / 32);
+        ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, sizeof(unsigned long long), st));
+        const int c = f->cur;
+        k_build_blocks_async<T><<<counted(ctas), BUILD_THREADS, 0, st>>>(P, A32, L[c], U[c], D[c], Ud,
+                                                                         nsweeps, warps, f->ctr,
+                                                                         f->ctr + 1);
+        ABILU_LAUNCH_CHECK("k_build_blocks_async");
+    }
+    return ABILU_OK;
 }
 
 template <typename T, typename AT>
@@ -472,7 +617,7 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
         init == ABILU_INIT_FROM_A ? 1 : 0, f->ctr);
     ABILU_LAUNCH_CHECK("k_build_prepare");
     if (nsweeps == 0) return ABILU_OK;
-    if constexpr (narrow) return sweeps_t<T, float>(f, A32, nsweeps, mode, st);
+    if constexpr (narrow) return block_sweeps_t<T>(f, A32, nsweeps, mode, st);
     else return sweeps_t<T, double>(f, A, nsweeps, mode, st);
 }
 

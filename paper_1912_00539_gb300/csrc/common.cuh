@@ -47,7 +47,15 @@ struct PatternView {
     const int32_t *lrow, *urow, *lcol, *ucol;
     const int32_t *pair_ptr;   // [nnzb+1] product pairs of block p
     const int2 *pairs;         // (lpos of L_ik, upos of U_kj)
+    // blocks a build sweep updates, in row-major order: every L and diagonal
+    // block and the U blocks with product pairs (the others equal A always).
+    // work[w] = {p, j, destination (lpos / i / upos), kind (WORK_L/D/U)}
+    int32_t nwork;
+    const int4 *work;
 };
+
+enum : int { WORK_L = 0, WORK_D = 1, WORK_U = 2 };
+constexpr int WORK_CHUNK = 64;  // work blocks per CTA of the build kernels (<= 64)
 
 }  // namespace abilu
 
@@ -85,6 +93,35 @@ struct abilu_factors_s {
 // ---------------------------------------------------------------- device helpers
 namespace abilu {
 
+// FP64 -> FP32, round to nearest even, with integer instructions.  On this GPU
+// the hardware conversion runs on the FP64 pipe (about 1/60 of the FP32 rate),
+// so conversions at every FP64/FP32 boundary would bound the FP32 kernels.
+// Results in the normal FP32 range are formed from the bits (23-bit mantissa
+// from the top of the 52-bit one, rounded on the 29 dropped bits); zeros,
+// subnormals, overflow, Inf and NaN take the hardware conversion.
+__device__ __forceinline__ float to_f32(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+    if (e < 1 || e > 253) return __double2float_rn(d);
+    const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1FFFFFFFu;
+    unsigned f = (hi & 0x80000000u) | ((unsigned)e << 23) | m23;
+    f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (m23 & 1u));
+    return __uint_as_float(f);
+}
+
+// FP32 -> FP64 (exact) with integer instructions; zeros, subnormals, Inf and
+// NaN take the hardware conversion.
+__device__ __forceinline__ double to_f64(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned ex = (u >> 23) & 0xFFu;
+    if (ex == 0u || ex == 0xFFu) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | ((ex + (1023u - 127u)) << 20) | ((u & 0x7FFFFFu) >> 3);
+    const unsigned lo = (u & 0x7u) << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 __device__ __forceinline__ void ld_row(const double *p, double v[4]) {
     double2 a = reinterpret_cast<const double2 *>(p)[0];
     double2 b = reinterpret_cast<const double2 *>(p)[1];
@@ -92,13 +129,13 @@ __device__ __forceinline__ void ld_row(const double *p, double v[4]) {
 }
 __device__ __forceinline__ void ld_row(const float *p, double v[4]) {
     float4 a = *reinterpret_cast<const float4 *>(p);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[0] = to_f64(a.x); v[1] = to_f64(a.y); v[2] = to_f64(a.z); v[3] = to_f64(a.w);
 }
 __device__ __forceinline__ void ld_row(const __nv_bfloat16 *p, double v[4]) {
     uint2 u = *reinterpret_cast<const uint2 *>(p);
     float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.x));
     float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&u.y));
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    v[0] = to_f64(a.x); v[1] = to_f64(a.y); v[2] = to_f64(b.x); v[3] = to_f64(b.y);
 }
 __device__ __forceinline__ void ld_row(const float *p, float v[4]) {
     float4 a = *reinterpret_cast<const float4 *>(p);
@@ -113,7 +150,7 @@ __device__ __forceinline__ void ld_row(const __nv_bfloat16 *p, float v[4]) {
 __device__ __forceinline__ void ld_row(const double *p, float v[4]) {
     double w[4];
     ld_row(p, w);
-    v[0] = (float)w[0]; v[1] = (float)w[1]; v[2] = (float)w[2]; v[3] = (float)w[3];
+    v[0] = to_f32(w[0]); v[1] = to_f32(w[1]); v[2] = to_f32(w[2]); v[3] = to_f32(w[3]);
 }
 
 // volatile (relaxed, uncached-in-L1) loads for data other threads may be
@@ -129,24 +166,24 @@ __device__ __forceinline__ void ld_row_volatile(const float *p, float v[4]) {
 __device__ __forceinline__ void ld_row_volatile(const float *p, double v[4]) {
     float w[4];
     ld_row_volatile(p, w);
-    v[0] = w[0]; v[1] = w[1]; v[2] = w[2]; v[3] = w[3];
+    v[0] = to_f64(w[0]); v[1] = to_f64(w[1]); v[2] = to_f64(w[2]); v[3] = to_f64(w[3]);
 }
-__device__ __forceinline__ void ld_row_volatile(const __nv_bfloat16 *p, double v[4]) {
+__device__ __forceinline__ void ld_row_volatile(const __nv_bfloat16 *p, float v[4]) {
     unsigned a, b;
     asm volatile("ld.volatile.global.v2.u32 {%0,%1}, [%2];" : "=r"(a), "=r"(b) : "l"(p));
     float2 x = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&a));
     float2 y = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&b));
     v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
 }
-__device__ __forceinline__ void ld_row_volatile(const __nv_bfloat16 *p, float v[4]) {
-    double w[4];
+__device__ __forceinline__ void ld_row_volatile(const __nv_bfloat16 *p, double v[4]) {
+    float w[4];
     ld_row_volatile(p, w);
-    v[0] = (float)w[0]; v[1] = (float)w[1]; v[2] = (float)w[2]; v[3] = (float)w[3];
+    v[0] = to_f64(w[0]); v[1] = to_f64(w[1]); v[2] = to_f64(w[2]); v[3] = to_f64(w[3]);
 }
 __device__ __forceinline__ void ld_row_volatile(const double *p, float v[4]) {
     double w[4];
     ld_row_volatile(p, w);
-    v[0] = (float)w[0]; v[1] = (float)w[1]; v[2] = (float)w[2]; v[3] = (float)w[3];
+    v[0] = to_f32(w[0]); v[1] = to_f32(w[1]); v[2] = to_f32(w[2]); v[3] = to_f32(w[3]);
 }
 
 template <bool VOL, typename T, typename C>
@@ -160,21 +197,21 @@ __device__ __forceinline__ void st_row(double *p, const double v[4]) {
     reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 __device__ __forceinline__ void st_row(float *p, const double v[4]) {
-    *reinterpret_cast<float4 *>(p) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+    *reinterpret_cast<float4 *>(p) = make_float4(to_f32(v[0]), to_f32(v[1]), to_f32(v[2]), to_f32(v[3]));
 }
 __device__ __forceinline__ void st_row(float *p, const float v[4]) {
     *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 __device__ __forceinline__ void st_row(__nv_bfloat16 *p, const double v[4]) {
-    __nv_bfloat162 a = __floats2bfloat162_rn((float)v[0], (float)v[1]);
-    __nv_bfloat162 b = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+    __nv_bfloat162 a = __floats2bfloat162_rn(to_f32(v[0]), to_f32(v[1]));
+    __nv_bfloat162 b = __floats2bfloat162_rn(to_f32(v[2]), to_f32(v[3]));
     uint2 u;
     u.x = *reinterpret_cast<unsigned *>(&a);
     u.y = *reinterpret_cast<unsigned *>(&b);
     *reinterpret_cast<uint2 *>(p) = u;
 }
 __device__ __forceinline__ void st_row(double *p, const float v[4]) {
-    double w[4] = {v[0], v[1], v[2], v[3]};
+    double w[4] = {to_f64(v[0]), to_f64(v[1]), to_f64(v[2]), to_f64(v[3])};
     st_row(p, w);
 }
 __device__ __forceinline__ void st_row(__nv_bfloat16 *p, const float v[4]) {

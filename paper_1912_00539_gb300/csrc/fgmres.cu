@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "reduce.cuh"
 
 namespace abilu {
 
@@ -34,8 +35,6 @@ abilu_status ensure_krylov(abilu_factors f, int m);
 int red_ctas();
 
 constexpr int MAXM = 64;
-constexpr int RED_THREADS = 256;
-constexpr int RED_WARPS = RED_THREADS / 32;
 constexpr int TILE = 8;   // Krylov vectors per pass of the dot kernel
 
 struct HostStatus {       // pinned, host-mapped mirror
@@ -67,26 +66,6 @@ __device__ __forceinline__ void publish(SolveState *S) {
     vh->beta = S->beta;
     vh->bnorm = S->bnorm;
     __threadfence_system();
-}
-
-// block-wide sum of K values per thread; result in sh_out[k] (valid after sync)
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double *sh_w, double *sh_out, int kn) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; k++)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; k++) sh_w[warp * K + k] = v[k];
-    __syncthreads();
-    if (threadIdx.x < kn) {
-        double s = 0.0;
-        for (int w = 0; w < RED_WARPS; w++) s += sh_w[w * K + threadIdx.x];
-        sh_out[threadIdx.x] = s;
-    }
-    __syncthreads();
 }
 
 // last-CTA election after this CTA stored its partials
@@ -191,8 +170,30 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
         double2 t = a[e];
         t = make_double2(t.x * s, t.y * s);
         o[e] = t;
-        if (v32) o32[e] = make_float2((float)t.x, (float)t.y);
+        if (v32) o32[e] = make_float2(to_f32(t.x), to_f32(t.y));
     }
+}
+
+// Partial dot products of K consecutive basis vectors with w for this CTA.
+// K is a compile-time width so no predicated-off FP64 FMA is issued.
+template <int K>
+__device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long long nv2,
+                                          int k0, const double2 *__restrict__ w2,
+                                          double *sh_w, double *sh_o, double *partials) {
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
+         e += (long long)gridDim.x * blockDim.x) {
+        const double2 wv = w2[e];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const double2 v = V2[(size_t)(k0 + k) * nv2 + e];
+            acc[k] = fma(v.y, wv.y, fma(v.x, wv.x, acc[k]));
+        }
+    }
+    block_sum<K>(acc, sh_w, sh_o, K);
+    if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
 }
 
 // h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2)
@@ -204,22 +205,16 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const double2 *V2 = reinterpret_cast<const double2 *>(V);
     for (int k0 = 0; k0 < jp1; k0 += TILE) {
-        const int kn = jp1 - k0 < TILE ? jp1 - k0 : TILE;
-        double acc[TILE];
-#pragma unroll
-        for (int k = 0; k < TILE; k++) acc[k] = 0.0;
-        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
-             e += (long long)gridDim.x * blockDim.x) {
-            const double2 wv = w2[e];
-#pragma unroll
-            for (int k = 0; k < TILE; k++)
-                if (k < kn) {
-                    const double2 v = V2[(size_t)(k0 + k) * nv2 + e];
-                    acc[k] = fma(v.y, wv.y, fma(v.x, wv.x, acc[k]));
-                }
+        switch (jp1 - k0 < TILE ? jp1 - k0 : TILE) {
+        case 1: dots_tile<1>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        case 2: dots_tile<2>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        case 3: dots_tile<3>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        case 4: dots_tile<4>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        case 5: dots_tile<5>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        case 6: dots_tile<6>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        case 7: dots_tile<7>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        default: dots_tile<8>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
         }
-        block_sum<TILE>(acc, sh_w, sh_o, kn);
-        if (threadIdx.x < kn) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
     }
     if (!last_cta(S)) return;
     double *h = pass == 0 ? S->h : S->h2;

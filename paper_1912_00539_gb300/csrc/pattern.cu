@@ -207,6 +207,48 @@ __global__ void k_pat_pairs(int n, const int32_t *__restrict__ rowptr,
     }
 }
 
+// FILL = false: count the row's work blocks; FILL = true: write them
+template <bool FILL>
+__global__ void k_pat_work(int n, const int32_t *__restrict__ rowptr,
+                           const int32_t *__restrict__ colind, const int32_t *__restrict__ diagpos,
+                           const int32_t *__restrict__ lrow, const int32_t *__restrict__ urow,
+                           const int32_t *__restrict__ pair_ptr, int32_t *__restrict__ wcnt,
+                           const int32_t *__restrict__ wptr, int4 *__restrict__ work) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p0 = rowptr[i], p1 = rowptr[i + 1], dp = diagpos[i];
+    int c = 0, out = FILL ? wptr[i] : 0;
+    for (int p = p0; p < p1; p++) {
+        if (p > dp && pair_ptr[p] == pair_ptr[p + 1]) continue;  // constant U block
+        if (FILL) {
+            int kind = p < dp ? WORK_L : (p == dp ? WORK_D : WORK_U);
+            int dst = p < dp ? lrow[i] + (p - p0) : (p == dp ? i : urow[i] + (p - dp - 1));
+            work[out + c] = make_int4(p, colind[p], dst, kind);
+        }
+        c++;
+    }
+    if (!FILL) wcnt[i] = c;
+}
+
+// Inside each chunk of `chunk` consecutive work blocks, put the diagonal
+// blocks first, then the L blocks, then the U blocks (stable).  The blocks of a
+// chunk are processed concurrently by one CTA, so the order inside a chunk
+// changes no result; grouping the kinds keeps the warps of a CTA on one code
+// path (the diagonal path also inverts U_ii).
+__global__ void k_pat_work_sort(int nwork, int chunk, int4 *work) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w0 = c * chunk;
+    if (w0 >= nwork) return;
+    const int w1 = w0 + chunk < nwork ? w0 + chunk : nwork;
+    int4 buf[64];
+    for (int w = w0; w < w1; w++) buf[w - w0] = work[w];
+    int out = w0;
+    const int order[3] = {WORK_D, WORK_L, WORK_U};
+    for (int o = 0; o < 3; o++)
+        for (int k = 0; k < w1 - w0; k++)
+            if (buf[k].w == order[o]) work[out++] = buf[k];
+}
+
 }  // namespace abilu
 
 using namespace abilu;
@@ -315,6 +357,28 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     k_pat_pairs<true><<<counted(gb), 256, 0, st>>>(n, d_rowptr, d_colind, diagpos, lrow, urow, nullptr,
                                           pair_ptr, pairs);
     TRY(cu(cudaGetLastError(), "k_pat_pairs fill"));
+    // work list of the build sweeps
+    int32_t *wcnt = lcnt, *wptr;  // lcnt is free again: reuse it for the counts
+    TRY(alloc((void **)&wptr, sizeof(int32_t) * (n + 1)));
+    k_pat_work<false><<<counted(gb), 256, 0, st>>>(n, d_rowptr, d_colind, diagpos, lrow, urow,
+                                                   pair_ptr, wcnt, nullptr, nullptr);
+    TRY(cu(cudaGetLastError(), "k_pat_work count"));
+    TRY(scan(wcnt, wptr, n, scratch, err, st));
+    int32_t nwork;
+    TRY(cu(cudaMemcpyAsync(&nwork, wptr + n, 4, cudaMemcpyDeviceToHost, st), "read nwork"));
+    TRY(cu(cudaStreamSynchronize(st), "sync"));
+    int4 *work;
+    TRY(alloc((void **)&work, sizeof(int4) * (nwork > 0 ? nwork : 1)));
+    k_pat_work<true><<<counted(gb), 256, 0, st>>>(n, d_rowptr, d_colind, diagpos, lrow, urow,
+                                                  pair_ptr, nullptr, wptr, work);
+    TRY(cu(cudaGetLastError(), "k_pat_work fill"));
+    {
+        const int chunks = (nwork + WORK_CHUNK - 1) / WORK_CHUNK;
+        if (chunks > 0) {
+            k_pat_work_sort<<<counted((chunks + 127) / 128), 128, 0, st>>>(nwork, WORK_CHUNK, work);
+            TRY(cu(cudaGetLastError(), "k_pat_work_sort"));
+        }
+    }
     TRY(cu(cudaStreamSynchronize(st), "sync"));
 #undef TRY
     p->v.n = n;
@@ -331,6 +395,8 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     p->v.ucol = ucol;
     p->v.pair_ptr = pair_ptr;
     p->v.pairs = pairs;
+    p->v.nwork = nwork;
+    p->v.work = work;
     p->max_row = (int)herr[2];
     *out = p;
     return ABILU_OK;
@@ -344,5 +410,6 @@ extern "C" abilu_status abilu_pattern_counts(abilu_pattern p, int64_t *out) {
     out[3] = p->v.nu;
     out[4] = p->v.npairs;
     out[5] = p->max_row;
+    out[6] = p->v.nwork;
     return ABILU_OK;
 }

@@ -92,6 +92,10 @@ def test_pattern_counts_exact(ab, dsys):
     assert c["nl"] == int(np.sum(rows > s.colind)) and c["nu"] == int(np.sum(rows < s.colind))
     assert c["npairs"] == npairs
     assert c["max_row"] == int(np.diff(s.rowptr).max())
+    # work list: every L and diagonal block plus the U blocks with a product pair
+    u_with_pairs = sum(1 for i in range(s.n) for j in s.colind[s.rowptr[i]:s.rowptr[i + 1]]
+                       if j > i and any(k < i and j in nbr[k] for k in nbr[i]))
+    assert c["nwork"] == c["nl"] + s.n + u_with_pairs
 
 
 @pytest.mark.parametrize("bad", ["unsorted", "no_diag", "col_range", "rowptr"])
@@ -419,3 +423,31 @@ def test_refined_fp32_inverse_is_fp32_accurate(ab, dsys, mode):
     ref = np.linalg.inv(Uii)
     err = np.abs(D - ref).max(axis=(1, 2)) / np.abs(ref).max(axis=(1, 2))
     assert err.max() < 8 * 2.0 ** -24, err.max()
+
+
+def test_fp64_to_fp32_rounding_is_exact(ab):
+    """FP32 factors from 0 sweeps hold float32(A) in every L, U and U_ii block;
+    the FP64->FP32 rounding (integer instructions on the GPU) must equal
+    numpy's round-to-nearest-even bit for bit, ties, subnormals and extremes
+    included."""
+    s = gen.small_system(12, 9, seed=21)
+    vals = s.vals.copy()
+    rng = np.random.default_rng(22)
+    special = np.array([1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24, -(1 + 2.0 ** -24), 1 - 2.0 ** -25,
+                        2.0 ** -130, -2.0 ** -140, 1e-300, 3.4e38, -3.3e38, 0.0, -0.0,
+                        1.5 * 2.0 ** -126, 2.0 ** 127 * (2 - 2.0 ** -23),
+                        np.nextafter(1.0, 2.0), 0.1, 1.0 / 3.0])
+    flat = vals.reshape(-1)
+    idx = rng.choice(flat.size, size=4000, replace=False)
+    flat[idx[:len(special)]] = special
+    # random doubles sitting exactly on float32 ties
+    t = rng.standard_normal(2000).astype(np.float32).astype(np.float64)
+    ulp = np.abs(np.spacing(t.astype(np.float32)).astype(np.float64))
+    flat[idx[len(special):len(special) + 2000]] = t + 0.5 * ulp
+    d = Dev(ab, gen.System("ties", s.rowptr, s.colind, vals, s.b, s.perm, s.cfl))
+    fac = ab.Factors(d.pat, "f32")
+    fac.build(d.A, 0, mode="sync")
+    X, _ = fac.export()
+    ref = vals.astype(np.float32).astype(np.float64)
+    got = X.cpu().numpy()
+    np.testing.assert_array_equal(got.view(np.int64), ref.view(np.int64))
