@@ -40,6 +40,16 @@ def _dist():
     return rank, world, local
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
+# kernel from the ncu captures summarised in profiles/ (same kernel code; set
+# an entry to None when its kernel changes until it is captured again)
+PROFILED_TRAFFIC = {
+    "spmv_f64": 295.449344e6 + 13.645312e6,          # profiles/k_spmv_inviscid_512x512.md
+    "build_sweeps_f32": 1.446059e9 + 505.616640e6,   # profiles/k_build_blocks_async_f32_...
+    "build_sweep_f32": 281.962496e6 + 66.468096e6,   # profiles/k_build_blocks_sync_f32_...
+}
+
+
 def max_over_ranks(torch, value, device):
     """Largest value over all ranks (the job's wall time is the slowest rank's)."""
     if not torch.distributed.is_available() or not torch.distributed.is_initialized():
@@ -392,7 +402,7 @@ def run_gpu(args):
     dk = kern[dom]
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(dk["GBs"], 1), "peak": peak,
             "unit": "GB/s", "frac": round(dk["frac"], 4),
-            "traffic": None, "peak_kind": peak_kind,
+            "traffic": PROFILED_TRAFFIC.get(dom), "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": dk["bytes"], "sweeps_per_launch": dk["sweeps"]}
     kernels = {k: {"us_per_call": round(v["us"], 2), "GBs": round(v["GBs"], 1),
                    "frac_of_measured_peak": round(v["frac"], 4),
