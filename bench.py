@@ -41,12 +41,13 @@ def _dist():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
-# kernel from the ncu captures summarised in profiles/ (same kernel code; set
-# an entry to None when its kernel changes until it is captured again)
+# kernel from one ncu --set full capture of that kernel on this workload (same
+# kernel code; set an entry to None when its kernel changes until it is
+# captured again)
 PROFILED_TRAFFIC = {
-    "spmv_f64": 295.449344e6 + 13.645312e6,          # profiles/k_spmv_inviscid_512x512.md
-    "build_sweeps_f32": 1.446059e9 + 505.616640e6,   # profiles/k_build_blocks_async_f32_...
-    "build_sweep_f32": 281.962496e6 + 66.468096e6,   # profiles/k_build_blocks_sync_f32_...
+    "spmv_f64": 295.449344e6 + 13.645312e6,          # k_spmv
+    "build_sweeps_f32": 1.446059e9 + 505.616640e6,   # k_build_blocks_async<float>, 6 sweeps
+    "build_sweep_f32": 281.962496e6 + 66.468096e6,   # k_build_blocks_sync<float>
 }
 
 
