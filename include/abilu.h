@@ -228,6 +228,43 @@ abilu_status fgmres_solve(abilu_pattern p, const double *A_vals, abilu_factors f
                           const double *b, double *x, const fgmres_opts *opts,
                           fgmres_result *res, abilu_stream stream);
 
+/*
+ * Batched solves: many independent systems of uneven size (for example one
+ * Jacobian per grid block or per request) handled by the same launches.  Each
+ * system is the problem above, solved by the same method; the batch runs every
+ * build sweep, triangular sweep and SpMV of all systems in one launch (the
+ * systems form one block-diagonal pattern, each system's rows padded to a
+ * multiple of 64 with identity rows), and FGMRES keeps a separate Krylov
+ * state, Hessenberg, Givens rotations and convergence test per system; the
+ * systems iterate in lockstep and a converged system stops contributing.
+ *
+ * abilu_batch_create: `n`, `nnzb` are HOST arrays [nsys]; `rowptr`, `colind`
+ * are HOST arrays [nsys] of DEVICE pointers to each system's pattern (as for
+ * abilu_pattern_create; copied).  Synchronises `stream`.  The batch owns the
+ * concatenated values, right-hand sides, solutions, factors (in `dtype`) and
+ * Krylov workspace.
+ * abilu_batch_set_system: copies system s's A values (device, double
+ * [nnzb_s][4][4]) and right-hand side (device, double[n_s][4]) into the batch;
+ * either may be NULL to keep the current one.  Asynchronous on `stream`.
+ * abilu_batch_solve: builds (if opts->build) and solves every system from
+ * x0 = 0 with the options of fgmres_solve; `res` is a HOST array [nsys].
+ * Synchronises `stream`.  ABILU_ENOCONV if any system did not converge.
+ * abilu_batch_get_solution: copies system s's solution (device, double
+ * [n_s][4]).  abilu_batch_counts: host int64_t[4] = systems, padded rows,
+ * blocks, 64-row chunks.
+ */
+typedef struct abilu_batch_s *abilu_batch;
+abilu_status abilu_batch_create(int32_t nsys, const int32_t *n, const int32_t *nnzb,
+                                const int32_t *const *rowptr, const int32_t *const *colind,
+                                abilu_dtype dtype, abilu_stream stream, abilu_batch *out);
+void abilu_batch_destroy(abilu_batch b);
+abilu_status abilu_batch_counts(abilu_batch b, int64_t *out);
+abilu_status abilu_batch_set_system(abilu_batch b, int32_t s, const double *A_vals,
+                                    const double *rhs, abilu_stream stream);
+abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts, fgmres_result *res,
+                               abilu_stream stream);
+abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x, abilu_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

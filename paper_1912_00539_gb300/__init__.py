@@ -3,5 +3,5 @@
 The computation lives in libabilu.so (hand-written sm_103a CUDA behind the C
 ABI of include/abilu.h); ``abilu`` is its thin Python binding.
 """
-from .abilu import (AbiluError, Factors, Pattern, SolveResult, bsr_spmv, default_opts,  # noqa: F401
-                    fgmres_solve, kernel_launches, version)
+from .abilu import (AbiluError, Batch, Factors, Pattern, SolveResult, bsr_spmv,  # noqa: F401
+                    default_opts, fgmres_solve, kernel_launches, version)

@@ -31,7 +31,9 @@ INITS = {"a": 0, "previous": 1}
 EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_pattern_create", "abilu_pattern_destroy",
            "abilu_pattern_counts", "abilu_factors_create", "abilu_factors_destroy", "abilu_build",
            "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
-           "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc")
+           "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc", "abilu_batch_create",
+           "abilu_batch_destroy", "abilu_batch_counts", "abilu_batch_set_system",
+           "abilu_batch_solve", "abilu_batch_get_solution")
 
 
 class FgmresOpts(C.Structure):
@@ -70,6 +72,17 @@ _lib.fgmres_default_opts.argtypes = [C.POINTER(FgmresOpts)]
 _lib.fgmres_default_opts.restype = None
 _lib.fgmres_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, C.POINTER(FgmresOpts),
                               C.POINTER(FgmresResult), _vp]
+_lib.abilu_batch_create.argtypes = [_i32, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_vp),
+                                   C.POINTER(_vp), C.c_int, _vp, C.POINTER(_vp)]
+_lib.abilu_batch_destroy.argtypes = [_vp]
+_lib.abilu_batch_destroy.restype = None
+_lib.abilu_batch_counts.argtypes = [_vp, C.POINTER(_i64)]
+_lib.abilu_batch_set_system.argtypes = [_vp, _i32, _vp, _vp, _vp]
+_lib.abilu_batch_solve.argtypes = [_vp, C.POINTER(FgmresOpts), C.POINTER(FgmresResult), _vp]
+_lib.abilu_batch_get_solution.argtypes = [_vp, _i32, _vp, _vp]
+for _nm in ("abilu_batch_create", "abilu_batch_counts", "abilu_batch_set_system",
+            "abilu_batch_solve", "abilu_batch_get_solution"):
+    getattr(_lib, _nm).restype = C.c_int
 for _nm in ("abilu_pattern_create", "abilu_pattern_counts", "abilu_factors_create", "abilu_build",
             "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
             "fgmres_solve"):
@@ -248,3 +261,64 @@ def fgmres_solve(pattern: Pattern, A, factors: Factors, b, x, restart=30, max_it
     return SolveResult(r.iters, r.restarts, r.rel_resid_est, r.rel_resid_true,
                        r.singular_blocks, st)
 
+
+def _opts(restart, max_iters, rtol, build_sweeps, apply_sweeps_lower, apply_sweeps_upper, mode,
+          build, init, reorth):
+    return FgmresOpts(int(restart), int(max_iters), float(rtol), int(build_sweeps),
+                      int(apply_sweeps_lower), int(apply_sweeps_upper), MODES[mode],
+                      int(bool(build)), INITS[init], int(bool(reorth)))
+
+
+class Batch:
+    """Many independent systems solved by the same launches (abilu_batch_*)."""
+
+    def __init__(self, patterns, dtype="f32", stream=None):
+        """patterns: list of (rowptr, colind) int32 CUDA tensors, one per system."""
+        import torch
+        nsys = len(patterns)
+        self.n = [int(rp.numel() - 1) for rp, _ in patterns]
+        self.nnzb = [int(ci.numel()) for _, ci in patterns]
+        n_arr = (C.c_int32 * nsys)(*self.n)
+        nz_arr = (C.c_int32 * nsys)(*self.nnzb)
+        rps = (C.c_void_p * nsys)(*[_ptr(rp, torch.int32, what="rowptr").value for rp, _ in patterns])
+        cis = (C.c_void_p * nsys)(*[_ptr(ci, torch.int32, what="colind").value for _, ci in patterns])
+        h = C.c_void_p()
+        _check(_lib.abilu_batch_create(nsys, n_arr, nz_arr, rps, cis, DTYPES[dtype],
+                                       _stream(stream), C.byref(h)))
+        self.handle = h
+        self.nsys = nsys
+        self.dtype = dtype
+
+    def counts(self) -> dict:
+        out = (C.c_int64 * 4)()
+        _check(_lib.abilu_batch_counts(self.handle, out))
+        return dict(zip(("nsys", "rows", "blocks", "chunks"), list(out)))
+
+    def set_system(self, s, A=None, b=None, stream=None):
+        import torch
+        pa = _ptr(A, torch.float64, 16 * self.nnzb[s], "A") if A is not None else None
+        pb = _ptr(b, torch.float64, 4 * self.n[s], "b") if b is not None else None
+        _check(_lib.abilu_batch_set_system(self.handle, int(s), pa, pb, _stream(stream)))
+
+    def solve(self, restart=30, max_iters=2500, rtol=1e-6, build_sweeps=1, apply_sweeps_lower=3,
+              apply_sweeps_upper=3, mode="async", build=True, init="a", reorth=False,
+              stream=None):
+        o = _opts(restart, max_iters, rtol, build_sweeps, apply_sweeps_lower, apply_sweeps_upper,
+                  mode, build, init, reorth)
+        res = (FgmresResult * self.nsys)()
+        st = _lib.abilu_batch_solve(self.handle, C.byref(o), res, _stream(stream))
+        _check(st, allow=(OK, WARN_SINGULAR, ENOCONV))
+        return [SolveResult(r.iters, r.restarts, r.rel_resid_est, r.rel_resid_true,
+                            r.singular_blocks, r.status) for r in res]
+
+    def solution(self, s, x, stream=None):
+        import torch
+        _check(_lib.abilu_batch_get_solution(self.handle, int(s),
+                                             _ptr(x, torch.float64, 4 * self.n[s], "x"),
+                                             _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.abilu_batch_destroy(h)
+            self.handle = None

@@ -1,0 +1,596 @@
+// Batched solve of many independent systems of uneven size in the same
+// launches.
+//
+// The systems are concatenated into one block-diagonal pattern (no block
+// couples two systems), each system's rows padded to a multiple of 64 with
+// identity rows.  Because the fixed-point map of Eq. (bilu), the triangular
+// sweeps and the SpMV never read across a block row's pattern, one build
+// sweep, one triangular sweep or one SpMV over the concatenation is exactly
+// that step for every system at once: the single-system kernels run
+// unchanged, one launch for the whole batch (the large systems load-balance
+// the small ones across the GPU).  The padding makes every 64-row chunk belong
+// to one system, so the Krylov kernels below give each CTA one chunk and keep a
+// separate FGMRES state per system: per-system dot products and norms (the
+// partials of a system's chunks summed in order by the last of them to finish),
+// per-system Hessenberg, Givens rotations and convergence.  The systems iterate
+// in lockstep; a system that has converged (or left its cycle) skips its
+// chunks in the Krylov kernels.  Padding rows have b = 0 and stay x = 0, so they
+// change no norm.
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "reduce.cuh"
+
+namespace abilu {
+
+abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
+                            abilu_init init, cudaStream_t st);
+abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip);
+abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
+                         double beta, double *y, cudaStream_t st, const int *skip);
+
+constexpr int BMAXM = 64;
+constexpr int CHUNK_ROWS = 64;           // rows per CTA = padding unit
+constexpr int CHUNK_VALS = CHUNK_ROWS * BS;
+constexpr int BTILE = 8;
+constexpr int PSTRIDE = BMAXM + 2;       // partials per chunk
+
+struct BState {
+    double H[BMAXM * BMAXM];   // R after rotations, H[i*BMAXM + j]
+    double cs[BMAXM], sn[BMAXM], g[BMAXM + 1], h[BMAXM + 1], h2[BMAXM + 1], y[BMAXM];
+    double bnorm, beta, hn_inv, est;
+    int done;        // out of the current cycle (converged estimate, breakdown, cycle end, max)
+    int finished;    // converged (true residual) or max_iters reached
+    int converged, iters, kdim, restarts, breakdown;
+    unsigned counter;
+};
+
+struct BConf {
+    double rtol;
+    int max_iters, m;
+};
+
+__device__ __forceinline__ bool last_cta_of(BState *St, int nck) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = atomicAdd(&St->counter, 1u) == (unsigned)(nck - 1);
+    __syncthreads();
+    if (am_last) __threadfence();
+    return am_last;
+}
+
+// sum over the system's chunks c0..c1-1 (in this order per thread, then a
+// fixed-order block reduction) of partials[c*PS + k0 + k], k < kn <= K
+template <int K, int PS>
+__device__ __forceinline__ void reduce_sys(const double *partials, int c0, int c1, int k0, int kn,
+                                           double *sh_w, double *out) {
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = 0.0;
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const double *p = partials + (size_t)c * PS + k0;
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            if (k < kn) v[k] += __ldcg(p + k);
+    }
+    block_sum<K>(v, sh_w, out, kn);
+}
+
+// r = b - A x for the chunk's rows (into r_out), ||r||^2 and ||b||^2 per system;
+// the system's last chunk sets beta, the convergence state and a new cycle
+__global__ void __launch_bounds__(RED_THREADS)
+k_b_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
+             const double *__restrict__ x, double *__restrict__ r_out, BState *S,
+             const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
+             double *partials, BConf cf, int init, int *hs_done, int *hs_fin) {
+    __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
+    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    BState *St = S + s;
+    if (!init && St->finished) return;  // whole system skips
+    const int i = chunk * CHUNK_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    double v[2] = {0.0, 0.0};
+    {
+        const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1];
+        double acc = 0.0;
+        for (int p = p0; p < p1; p++) {
+            const int j = __ldg(P.colind + p);
+            const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
+            const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)j * BS);
+            double2 a0 = __ldg(ap), a1 = __ldg(ap + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
+            acc = fma(a0.x, x0.x, acc);
+            acc = fma(a0.y, x0.y, acc);
+            acc = fma(a1.x, x1.x, acc);
+            acc = fma(a1.y, x1.y, acc);
+        }
+        const size_t o = (size_t)i * BS + q;
+        const double bi = b[o], ri = bi - acc;
+        r_out[o] = ri;
+        v[0] = ri * ri;
+        v[1] = bi * bi;
+    }
+    block_sum<2>(v, sh_w, sh_o, 2);
+    if (threadIdx.x == 0) {
+        partials[(size_t)chunk * 2 + 0] = sh_o[0];
+        partials[(size_t)chunk * 2 + 1] = sh_o[1];
+    }
+    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    if (!last_cta_of(St, c1 - c0)) return;
+    reduce_sys<2, 2>(partials, c0, c1, 0, 2, sh_w, sh_o);
+    if (threadIdx.x == 0) {
+        if (init) St->bnorm = sqrt(sh_o[1]);
+        else St->restarts += 1;
+        St->beta = sqrt(sh_o[0]);
+        St->converged = (St->beta <= cf.rtol * St->bnorm || St->bnorm == 0.0) ? 1 : 0;
+        St->finished = (St->converged || St->iters >= cf.max_iters) ? 1 : 0;
+        St->done = St->finished;
+        St->hn_inv = St->beta > 0.0 ? 1.0 / St->beta : 0.0;
+        St->kdim = 0;
+        St->breakdown = 0;
+        St->g[0] = St->beta;
+        for (int k = 1; k <= BMAXM; k++) St->g[k] = 0.0;
+        if (init) St->est = St->bnorm > 0.0 ? St->beta / St->bnorm : 0.0;
+        St->counter = 0;
+        reinterpret_cast<volatile int *>(hs_done)[s] = St->done;
+        reinterpret_cast<volatile int *>(hs_fin)[s] = St->finished;
+        __threadfence_system();
+    }
+}
+
+// v_out = v_in * hn_inv of the chunk's system (and the FP32 copy for the apply)
+__global__ void __launch_bounds__(RED_THREADS)
+k_b_scale(const double *vin, double *vout, float *v32, const BState *S,
+          const int *__restrict__ chunk_sys) {
+    const int chunk = blockIdx.x;
+    const BState *St = S + chunk_sys[chunk];
+    if (St->done) return;
+    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
+    const double t = vin[e] * St->hn_inv;
+    vout[e] = t;
+    if (v32) v32[e] = to_f32(t);
+}
+
+template <int K>
+__device__ __forceinline__ void b_dots_tile(const double *__restrict__ V, size_t nv, int k0,
+                                            double wv, size_t e, double *sh_w, double *sh_o,
+                                            double *partials, int chunk) {
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = V[(size_t)(k0 + k) * nv + e] * wv;
+    block_sum<K>(acc, sh_w, sh_o, K);
+    if (threadIdx.x < K) partials[(size_t)chunk * PSTRIDE + k0 + threadIdx.x] = sh_o[threadIdx.x];
+}
+
+// h[k] = <V_k, w>_s for k <= j, per system (pass 0 -> h, 1 -> h2)
+__global__ void __launch_bounds__(RED_THREADS)
+k_b_dots(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w, BState *S,
+         const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0, double *partials,
+         int pass) {
+    __shared__ double sh_w[RED_WARPS * BTILE], sh_o[BTILE];
+    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    BState *St = S + s;
+    if (St->done) return;
+    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
+    const double wv = w[e];
+    const int jp1 = j + 1;
+    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
+        switch (jp1 - k0 < BTILE ? jp1 - k0 : BTILE) {
+        case 1: b_dots_tile<1>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 2: b_dots_tile<2>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 3: b_dots_tile<3>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 4: b_dots_tile<4>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 5: b_dots_tile<5>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 6: b_dots_tile<6>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 7: b_dots_tile<7>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        default: b_dots_tile<8>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        }
+    }
+    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    if (!last_cta_of(St, c1 - c0)) return;
+    double *h = pass == 0 ? St->h : St->h2;
+    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
+        const int kn = jp1 - k0 < BTILE ? jp1 - k0 : BTILE;
+        reduce_sys<BTILE, PSTRIDE>(partials, c0, c1, k0, kn, sh_w, sh_o);
+        if (threadIdx.x < kn) h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) St->counter = 0;
+}
+
+// w -= sum_k h[k] V_k per system; on the final pass ||w||, and the system's last
+// chunk applies the Givens update of column j and the convergence test
+__global__ void __launch_bounds__(RED_THREADS)
+k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ w, BState *S,
+           const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
+           double *partials, BConf cf, int pass, int final_pass, int *hs_done) {
+    __shared__ double sh_h[BMAXM + 1];
+    __shared__ double sh_w[RED_WARPS], sh_o[1];
+    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    BState *St = S + s;
+    if (St->done) return;
+    const int jp1 = j + 1;
+    const double *hsrc = pass == 0 ? St->h : St->h2;
+    for (int k = threadIdx.x; k < jp1; k += blockDim.x) sh_h[k] = hsrc[k];
+    __syncthreads();
+    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
+    double t = w[e];
+    for (int k = 0; k < jp1; k++) t = fma(-sh_h[k], V[(size_t)k * nv + e], t);
+    w[e] = t;
+    if (!final_pass) return;
+    double nrm[1] = {t * t};
+    block_sum<1>(nrm, sh_w, sh_o, 1);
+    if (threadIdx.x == 0) partials[(size_t)chunk * PSTRIDE + BMAXM + 1] = sh_o[0];
+    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    if (!last_cta_of(St, c1 - c0)) return;
+    reduce_sys<1, PSTRIDE>(partials, c0, c1, BMAXM + 1, 1, sh_w, sh_o);
+    if (threadIdx.x != 0) return;
+    const double hn = sqrt(sh_o[0]);
+    double col[BMAXM + 1];
+    for (int i = 0; i <= j; i++) col[i] = St->h[i] + (pass == 1 ? St->h2[i] : 0.0);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; i++) {
+        const double a = col[i], c = col[i + 1];
+        col[i] = St->cs[i] * a + St->sn[i] * c;
+        col[i + 1] = -St->sn[i] * a + St->cs[i] * c;
+    }
+    const double a = col[j], c = col[j + 1];
+    const double d = sqrt(a * a + c * c);
+    double cs = 1.0, sn = 0.0;
+    if (d != 0.0) { cs = a / d; sn = c / d; }
+    St->cs[j] = cs;
+    St->sn[j] = sn;
+    col[j] = cs * a + sn * c;
+    for (int i = 0; i <= j; i++) St->H[i * BMAXM + j] = col[i];
+    const double gj = St->g[j];
+    St->g[j + 1] = -sn * gj;
+    St->g[j] = cs * gj;
+    St->iters += 1;
+    St->kdim = j + 1;
+    St->est = St->bnorm > 0.0 ? fabs(St->g[j + 1]) / St->bnorm : 0.0;
+    St->breakdown = hn == 0.0 ? 1 : 0;
+    St->done = (fabs(St->g[j + 1]) <= cf.rtol * St->bnorm || hn == 0.0 ||
+                St->iters >= cf.max_iters || j + 1 >= cf.m) ? 1 : 0;
+    St->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
+    St->counter = 0;
+    if (St->done) {
+        reinterpret_cast<volatile int *>(hs_done)[s] = 1;
+        __threadfence_system();
+    }
+}
+
+// y = R^{-1} g per system (one thread per system)
+__global__ void k_b_ysolve(BState *S, int nsys) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    BState *St = S + s;
+    const int kd = St->kdim;
+    for (int i = kd - 1; i >= 0; i--) {
+        double v = St->g[i];
+        for (int k = i + 1; k < kd; k++) v -= St->H[i * BMAXM + k] * St->y[k];
+        St->y[i] = v / St->H[i * BMAXM + i];
+    }
+}
+
+// x += Z y for the chunk's system
+__global__ void __launch_bounds__(RED_THREADS)
+k_b_xupdate(const double *__restrict__ Z, size_t nv, double *__restrict__ x, const BState *S,
+            const int *__restrict__ chunk_sys) {
+    const int chunk = blockIdx.x;
+    const BState *St = S + chunk_sys[chunk];
+    const int kd = St->kdim;
+    if (kd == 0) return;
+    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
+    double t = x[e];
+    for (int k = 0; k < kd; k++) t = fma(St->y[k], Z[(size_t)k * nv + e], t);
+    x[e] = t;
+}
+
+__global__ void k_b_init(BState *S, int nsys) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    S[s].iters = 0;
+    S[s].restarts = 0;
+    S[s].counter = 0;
+    S[s].finished = 0;
+    S[s].done = 0;
+}
+
+// ---- concatenation
+// rows of system s (padded): rowptr of the concatenation; the padding rows'
+// single (diagonal) block and their identity values
+__global__ void k_cat_rows(int row_off, int nnz_off, int n, int nnzb, int nrows_padded,
+                           const int32_t *__restrict__ rowptr, int32_t *__restrict__ rowptr_cat,
+                           int32_t *__restrict__ colind_cat, double *__restrict__ A_cat) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows_padded) return;
+    if (r < n) {
+        rowptr_cat[row_off + r] = nnz_off + rowptr[r];
+    } else {
+        const int p = nnz_off + nnzb + (r - n);
+        rowptr_cat[row_off + r] = p;
+        colind_cat[p] = row_off + r;
+        double *a = A_cat + (size_t)p * BB;
+        for (int k = 0; k < BB; k++) a[k] = (k % 5 == 0) ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_cat_cols(int row_off, int nnz_off, int nnzb, const int32_t *__restrict__ colind,
+                           int32_t *__restrict__ colind_cat) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnzb) colind_cat[nnz_off + p] = row_off + colind[p];
+}
+
+__global__ void k_fill_int(int *a, int n, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+}  // namespace abilu
+
+using namespace abilu;
+
+struct abilu_batch_s {
+    int nsys;
+    std::vector<int> n, nnzb, row_off, nnz_off, chunk0;
+    int rows, blocks, nchunks;
+    int32_t *rowptr, *colind;   // concatenation (device)
+    double *A, *b, *x;          // concatenation (device)
+    int *chunk_sys, *sys_chunk0;
+    BState *S;
+    double *partials;
+    double *krylov;
+    int krylov_m;
+    int *hs_done, *hs_fin;      // pinned, host-mapped
+    abilu_pattern pat;
+    abilu_factors fac;
+    std::vector<void *> allocs;
+};
+
+static void batch_free(abilu_batch b) {
+    if (!b) return;
+    if (b->fac) abilu_factors_destroy(b->fac);
+    if (b->pat) abilu_pattern_destroy(b->pat);
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->krylov) cudaFree(b->krylov);
+    if (b->hs_done) cudaFreeHost(b->hs_done);
+    if (b->hs_fin) cudaFreeHost(b->hs_fin);
+    delete b;
+}
+
+extern "C" void abilu_batch_destroy(abilu_batch b) { batch_free(b); }
+
+extern "C" abilu_status abilu_batch_create(int32_t nsys, const int32_t *n, const int32_t *nnzb,
+                                           const int32_t *const *rowptr,
+                                           const int32_t *const *colind, abilu_dtype dtype,
+                                           abilu_stream stream, abilu_batch *out) {
+    if (!out) return fail(ABILU_EINVAL, "batch_create: out is NULL");
+    *out = nullptr;
+    if (nsys < 1 || !n || !nnzb || !rowptr || !colind)
+        return fail(ABILU_EINVAL, "batch_create: need nsys >= 1 and the host arrays");
+    cudaStream_t st = S(stream);
+    abilu_batch b = new abilu_batch_s();
+    b->nsys = nsys;
+    b->pat = nullptr;
+    b->fac = nullptr;
+    b->krylov = nullptr;
+    b->krylov_m = 0;
+    b->hs_done = b->hs_fin = nullptr;
+    long long rows = 0, blocks = 0;
+    for (int s = 0; s < nsys; s++) {
+        if (n[s] < 1 || nnzb[s] < n[s] || !rowptr[s] || !colind[s]) {
+            batch_free(b);
+            return fail(ABILU_EINVAL, "batch_create: system %d has n=%d nnzb=%d or NULL arrays", s, n[s], nnzb[s]);
+        }
+        const int padded = (n[s] + CHUNK_ROWS - 1) / CHUNK_ROWS * CHUNK_ROWS;
+        b->n.push_back(n[s]);
+        b->nnzb.push_back(nnzb[s]);
+        b->row_off.push_back((int)rows);
+        b->nnz_off.push_back((int)blocks);
+        b->chunk0.push_back((int)(rows / CHUNK_ROWS));
+        rows += padded;
+        blocks += (long long)nnzb[s] + (padded - n[s]);
+    }
+    if (rows > 0x7fffffffLL / BB || blocks > 0x7fffffffLL / BB) {
+        batch_free(b);
+        return fail(ABILU_EINVAL, "batch_create: batch too large for 32-bit block indices");
+    }
+    b->chunk0.push_back((int)(rows / CHUNK_ROWS));
+    b->rows = (int)rows;
+    b->blocks = (int)blocks;
+    b->nchunks = (int)(rows / CHUNK_ROWS);
+    auto alloc = [&](void **p, size_t bytes) -> abilu_status {
+        cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "batch_create: cudaMalloc");
+        b->allocs.push_back(*p);
+        return ABILU_OK;
+    };
+#define TRY(x)                                                  \
+    do {                                                        \
+        abilu_status s_ = (x);                                  \
+        if (s_ != ABILU_OK) { batch_free(b); return s_; }       \
+    } while (0)
+    TRY(alloc((void **)&b->rowptr, sizeof(int32_t) * (rows + 1)));
+    TRY(alloc((void **)&b->colind, sizeof(int32_t) * blocks));
+    TRY(alloc((void **)&b->A, sizeof(double) * BB * blocks));
+    TRY(alloc((void **)&b->b, sizeof(double) * BS * rows));
+    TRY(alloc((void **)&b->x, sizeof(double) * BS * rows));
+    TRY(alloc((void **)&b->chunk_sys, sizeof(int) * b->nchunks));
+    TRY(alloc((void **)&b->sys_chunk0, sizeof(int) * (nsys + 1)));
+    TRY(alloc((void **)&b->S, sizeof(BState) * nsys));
+    TRY(alloc((void **)&b->partials, sizeof(double) * PSTRIDE * b->nchunks));
+    auto cu = [&](cudaError_t e, const char *w) -> abilu_status {
+        return e == cudaSuccess ? ABILU_OK : cuda_fail(e, w);
+    };
+    TRY(cu(cudaHostAlloc((void **)&b->hs_done, sizeof(int) * nsys, cudaHostAllocMapped), "hostalloc"));
+    TRY(cu(cudaHostAlloc((void **)&b->hs_fin, sizeof(int) * nsys, cudaHostAllocMapped), "hostalloc"));
+    TRY(cu(cudaMemsetAsync(b->A, 0, sizeof(double) * BB * blocks, st), "memset A"));
+    TRY(cu(cudaMemsetAsync(b->b, 0, sizeof(double) * BS * rows, st), "memset b"));
+    TRY(cu(cudaMemsetAsync(b->x, 0, sizeof(double) * BS * rows, st), "memset x"));
+    for (int s = 0; s < nsys; s++) {
+        const int padded = b->chunk0[s + 1] * CHUNK_ROWS - b->row_off[s];
+        k_cat_rows<<<counted((padded + 255) / 256), 256, 0, st>>>(
+            b->row_off[s], b->nnz_off[s], b->n[s], b->nnzb[s], padded, rowptr[s], b->rowptr,
+            b->colind, b->A);
+        k_cat_cols<<<counted((b->nnzb[s] + 255) / 256), 256, 0, st>>>(b->row_off[s], b->nnz_off[s],
+                                                                      b->nnzb[s], colind[s], b->colind);
+        const int nck = b->chunk0[s + 1] - b->chunk0[s];
+        k_fill_int<<<counted((nck + 255) / 256), 256, 0, st>>>(b->chunk_sys + b->chunk0[s], nck, s);
+        TRY(cu(cudaGetLastError(), "batch concatenation"));
+    }
+    const int32_t last = (int32_t)blocks;
+    TRY(cu(cudaMemcpyAsync(b->rowptr + rows, &last, sizeof last, cudaMemcpyHostToDevice, st), "rowptr end"));
+    TRY(cu(cudaMemcpyAsync(b->sys_chunk0, b->chunk0.data(), sizeof(int) * (nsys + 1),
+                           cudaMemcpyHostToDevice, st), "chunk table"));
+    TRY(cu(cudaStreamSynchronize(st), "sync"));
+    TRY(abilu_pattern_create(b->rows, b->blocks, b->rowptr, b->colind, stream, &b->pat));
+    TRY(abilu_factors_create(b->pat, dtype, &b->fac));
+#undef TRY
+    *out = b;
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_batch_counts(abilu_batch b, int64_t *out) {
+    if (!b || !out) return fail(ABILU_EINVAL, "batch_counts: NULL argument");
+    out[0] = b->nsys;
+    out[1] = b->rows;
+    out[2] = b->blocks;
+    out[3] = b->nchunks;
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_batch_set_system(abilu_batch b, int32_t s, const double *A_vals,
+                                               const double *rhs, abilu_stream stream) {
+    if (!b || s < 0 || s >= b->nsys) return fail(ABILU_EINVAL, "batch_set_system: bad batch or index");
+    cudaStream_t st = S(stream);
+    if (A_vals)
+        ABILU_CUDA(cudaMemcpyAsync(b->A + (size_t)b->nnz_off[s] * BB, A_vals,
+                                   sizeof(double) * BB * b->nnzb[s], cudaMemcpyDeviceToDevice, st));
+    if (rhs)
+        ABILU_CUDA(cudaMemcpyAsync(b->b + (size_t)b->row_off[s] * BS, rhs,
+                                   sizeof(double) * BS * b->n[s], cudaMemcpyDeviceToDevice, st));
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x,
+                                                 abilu_stream stream) {
+    if (!b || s < 0 || s >= b->nsys || !x) return fail(ABILU_EINVAL, "batch_get_solution: bad argument");
+    ABILU_CUDA(cudaMemcpyAsync(x, b->x + (size_t)b->row_off[s] * BS, sizeof(double) * BS * b->n[s],
+                               cudaMemcpyDeviceToDevice, S(stream)));
+    return ABILU_OK;
+}
+
+static bool all_set(const int *flags, int n) {
+    const volatile int *v = flags;
+    for (int s = 0; s < n; s++)
+        if (!v[s]) return false;
+    return true;
+}
+
+extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts,
+                                          fgmres_result *res, abilu_stream stream) {
+    if (!b || !opts || !res) return fail(ABILU_EINVAL, "batch_solve: NULL argument");
+    const int m = opts->restart;
+    if (m < 1 || m > BMAXM) return fail(ABILU_EINVAL, "batch_solve: restart must be in 1..%d", BMAXM);
+    if (opts->max_iters < 0 || !(opts->rtol >= 0.0) || opts->apply_sweeps_lower < 0 ||
+        opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 ||
+        (opts->mode != ABILU_SYNC && opts->mode != ABILU_ASYNC))
+        return fail(ABILU_EINVAL, "batch_solve: bad options");
+    cudaStream_t st = S(stream);
+    const PatternView &P = b->pat->v;
+    const size_t nv = (size_t)b->rows * BS;
+    if (!b->krylov || b->krylov_m < m) {
+        if (b->krylov) cudaFree(b->krylov);
+        b->krylov = nullptr;
+        ABILU_CUDA(cudaMalloc(&b->krylov, sizeof(double) * nv * (2 * (size_t)m + 2)));
+        b->krylov_m = m;
+    }
+    double *V = b->krylov, *Z = V + (size_t)(m + 1) * nv, *w = Z + (size_t)m * nv;
+    float *v32 = reinterpret_cast<float *>(b->fac->r32);
+    const abilu_mode mode = (abilu_mode)opts->mode;
+    const BConf cf = {opts->rtol, opts->max_iters, m};
+    const int nck = b->nchunks, nsys = b->nsys;
+    abilu_status s;
+    if (opts->build) {
+        ABILU_CUDA(cudaMemsetAsync(b->fac->ctr, 0, sizeof(unsigned long long), st));
+        s = build_dispatch(b->fac, b->A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
+        if (s != ABILU_OK) return s;
+    }
+    ABILU_CUDA(cudaMemsetAsync(b->x, 0, sizeof(double) * nv, st));
+    ABILU_CUDA(cudaMemsetAsync(b->S, 0, sizeof(BState) * nsys, st));
+    k_b_init<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
+    k_b_residual<<<counted(nck), RED_THREADS, 0, st>>>(P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
+                                                       b->sys_chunk0, b->partials, cf, 1,
+                                                       b->hs_done, b->hs_fin);
+    k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(V, V, v32, b->S, b->chunk_sys);
+    ABILU_LAUNCH_CHECK("batch init");
+    ABILU_CUDA(cudaStreamSynchronize(st));
+    cudaEvent_t ev[2];
+    ABILU_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    ABILU_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    abilu_status ret = ABILU_OK;
+    int cycles = 0;
+    while (!all_set(b->hs_fin, nsys) && cycles <= opts->max_iters) {
+        cycles++;
+        for (int j = 0; j < m; j++) {
+            s = apply_dispatch(b->fac, V + (size_t)j * nv, v32, Z + (size_t)j * nv,
+                               opts->apply_sweeps_lower, opts->apply_sweeps_upper, mode, st, nullptr);
+            if (s != ABILU_OK) { ret = s; break; }
+            if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, nullptr)) != ABILU_OK) { ret = s; break; }
+            k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
+                                                           b->partials, 0);
+            k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
+                                                             b->partials, cf, 0, !opts->reorth, b->hs_done);
+            if (opts->reorth) {
+                k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
+                                                               b->sys_chunk0, b->partials, 1);
+                k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
+                                                                 b->sys_chunk0, b->partials, cf, 1, 1,
+                                                                 b->hs_done);
+            }
+            k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, v32, b->S,
+                                                            b->chunk_sys);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { ret = cuda_fail(e, "batch step"); break; }
+            cudaEventRecord(ev[j & 1], st);
+            if (j >= 1) {  // look at step j-1 while step j runs
+                cudaEventSynchronize(ev[(j - 1) & 1]);
+                if (all_set(b->hs_done, nsys)) break;
+            }
+        }
+        if (ret != ABILU_OK) break;
+        k_b_ysolve<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
+        k_b_xupdate<<<counted(nck), RED_THREADS, 0, st>>>(Z, nv, b->x, b->S, b->chunk_sys);
+        k_b_residual<<<counted(nck), RED_THREADS, 0, st>>>(P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
+                                                           b->sys_chunk0, b->partials, cf, 0,
+                                                           b->hs_done, b->hs_fin);
+        k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(V, V, v32, b->S, b->chunk_sys);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "batch restart"); break; }
+    }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    std::vector<BState> hs(nsys);
+    ABILU_CUDA(cudaMemcpy(hs.data(), b->S, sizeof(BState) * nsys, cudaMemcpyDeviceToHost));
+    unsigned long long ns = 0;
+    ABILU_CUDA(cudaMemcpy(&ns, b->fac->ctr, sizeof ns, cudaMemcpyDeviceToHost));
+    int nconv = 0;
+    for (int q = 0; q < nsys; q++) {
+        res[q].iters = hs[q].iters;
+        res[q].restarts = hs[q].restarts;
+        res[q].rel_resid_est = hs[q].est;
+        res[q].rel_resid_true = hs[q].bnorm > 0.0 ? hs[q].beta / hs[q].bnorm : 0.0;
+        res[q].singular_blocks = (int64_t)ns;
+        res[q].status = hs[q].converged ? (ns ? ABILU_WARN_SINGULAR : ABILU_OK) : ABILU_ENOCONV;
+        nconv += hs[q].converged;
+    }
+    if (ret == ABILU_OK && nconv < nsys)
+        ret = fail(ABILU_ENOCONV, "batch_solve: %d of %d systems did not converge", nsys - nconv, nsys);
+    else if (ret == ABILU_OK && ns)
+        ret = fail(ABILU_WARN_SINGULAR, "batch_solve: %llu singular diagonal blocks replaced", ns);
+    return ret;
+}

@@ -1,0 +1,107 @@
+"""Batched solves: every system of a batch gets the result it gets alone.
+
+The batch runs the build, triangular sweeps and SpMV of all systems in the same
+launches over a padded block-diagonal concatenation and keeps a separate
+FGMRES state per system.  In synchronous mode each system's arithmetic is the
+single-system arithmetic except the order of the dot-product reductions, so
+iteration counts must agree and solutions agree to the solve tolerance.
+"""
+import numpy as np
+import pytest
+
+import abilu_inputs as gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ab():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1912_00539_gb300 as m
+    return m
+
+
+def _dev(s):
+    import torch
+    return (torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda(),
+            torch.from_numpy(np.ascontiguousarray(s.vals)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(s.b)).cuda())
+
+
+def _systems():
+    return [gen.small_system(5, 4, seed=31),                        # 40 cells (< one 64-row chunk)
+            gen.small_system(37, 11, seed=32),                      # 814 cells, ragged
+            gen.make_system(30, 20, 41, 42, 43, cfl=10.0),          # easy: converges early
+            gen.make_system(40, 40, 44, 45, 46, cfl=1e4),           # harder
+            gen.random_pattern_system(150, 400, seed=33),           # pattern with triangles
+            gen.workload("inviscid_64x64")]
+
+
+@pytest.mark.parametrize("dtype,mode", [("f64", "sync"), ("f32", "sync"), ("f32", "async")])
+def test_batch_matches_single_solves(ab, dtype, mode):
+    import torch
+    systems = _systems()
+    devs = [_dev(s) for s in systems]
+    batch = ab.Batch([(d[0], d[1]) for d in devs], dtype=dtype)
+    c = batch.counts()
+    assert c["nsys"] == len(systems) and c["rows"] % 64 == 0
+    assert c["rows"] == sum(-(-s.n // 64) * 64 for s in systems)
+    for k, d in enumerate(devs):
+        batch.set_system(k, d[2], d[3])
+    opts = dict(restart=30, rtol=1e-6, build_sweeps=4, apply_sweeps_lower=3,
+                apply_sweeps_upper=3, mode=mode)
+    res = batch.solve(**opts)
+    for k, (s, d) in enumerate(zip(systems, devs)):
+        x = torch.empty_like(d[3])
+        batch.solution(k, x)
+        xn = x.cpu().numpy()
+        r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, xn)
+        assert res[k].converged and res[k].rel_resid_true <= 1e-6, (k, res[k])
+        assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
+        # alone
+        pat = ab.Pattern(d[0], d[1])
+        fac = ab.Factors(pat, dtype)
+        xa = torch.zeros_like(d[3])
+        ra = ab.fgmres_solve(pat, d[2], fac, d[3], xa, **opts)
+        if mode == "sync":
+            assert res[k].iters == ra.iters, (k, res[k].iters, ra.iters)
+            scale = np.abs(xa.cpu().numpy()).max()
+            assert np.abs(xn - xa.cpu().numpy()).max() <= 1e-6 * scale
+        else:
+            assert abs(res[k].iters - ra.iters) <= max(2, ra.iters // 5), (k, res[k].iters, ra.iters)
+
+
+def test_batch_value_update_and_warm_start(ab):
+    """New values on the same patterns, factors warm-started (init=previous)."""
+    import torch
+    systems = _systems()[:3]
+    devs = [_dev(s) for s in systems]
+    batch = ab.Batch([(d[0], d[1]) for d in devs], dtype="f32")
+    for k, d in enumerate(devs):
+        batch.set_system(k, d[2], d[3])
+    batch.solve(build_sweeps=3, mode="sync")
+    rng = np.random.default_rng(7)
+    for k, s in enumerate(systems):
+        vals = s.vals * (1.0 + 0.01 * rng.standard_normal(s.vals.shape))
+        bnew = rng.standard_normal(s.b.shape)
+        batch.set_system(k, torch.from_numpy(vals).cuda(), torch.from_numpy(bnew).cuda())
+        systems[k] = gen.System(s.name, s.rowptr, s.colind, vals, bnew, s.perm, s.cfl)
+    res = batch.solve(build_sweeps=1, mode="sync", init="previous")
+    for k, s in enumerate(systems):
+        x = torch.empty((s.n, 4), dtype=torch.float64, device="cuda")
+        batch.solution(k, x)
+        r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
+        assert res[k].converged
+        assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
+
+
+def test_batch_rejects_bad_input(ab):
+    import torch
+    s = gen.small_system(3, 3, seed=34)
+    rp = torch.from_numpy(s.rowptr).cuda()
+    ci = torch.from_numpy(s.colind.copy()).cuda()
+    ci[0], ci[1] = int(s.colind[1]), int(s.colind[0])   # unsorted row
+    with pytest.raises(ab.AbiluError):
+        ab.Batch([(rp, ci)])
