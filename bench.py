@@ -291,14 +291,165 @@ def run_profile_solves(args):
     x = torch.zeros_like(b)
     fac = ab.Factors(pat, args.dtype)
     for _ in range(args.warmup + args.profile_solves):
-        x.zero_()
         r = ab.fgmres_solve(pat, A, fac, b, x, restart=RESTART, rtol=RTOL,
                             build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=APPLY_SWEEPS,
-                            apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode, raise_on_noconv=True)
+                            apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode, raise_on_noconv=True,
+                            zero_guess=True)
     torch.cuda.synchronize()
     print(json.dumps({"solves": args.warmup + args.profile_solves, "iters": r.iters,
                       "rel_resid_true": r.rel_resid_true}))
     return 0
+
+
+def run_batched(args, nsys=64, steps=3):
+    """64 uneven systems (2k-200k cells, aspect 1/8-8, CFL 10-1e4), FP32
+    factors, FGMRES(30) to 1e-6: the batch solved in the same launches vs the
+    same systems solved one after another through the single-system API."""
+    import torch
+    import abilu_inputs as gen
+    import paper_1912_00539_gb300 as ab
+    t0 = time.perf_counter()
+    systems = gen.batch_systems(nsys)
+    tgen = time.perf_counter() - t0
+    dev = [(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda(),
+            torch.from_numpy(s.vals).cuda(), torch.from_numpy(s.b).cuda()) for s in systems]
+    batch = ab.Batch([(d[0], d[1]) for d in dev], dtype="f32")
+    for k, d in enumerate(dev):
+        batch.set_system(k, d[2], d[3])
+    cells = sum(s.n for s in systems)
+    from paper_1912_00539_gb300 import autotune
+    t0 = time.perf_counter()
+    choice = autotune.tune_batch(batch, cells, restart=RESTART, rtol=RTOL)
+    ttune = time.perf_counter() - t0
+    opts = dict(restart=RESTART, rtol=RTOL, build_sweeps=choice.build_sweeps,
+                apply_sweeps_lower=choice.apply_sweeps, apply_sweeps_upper=choice.apply_sweeps,
+                mode=choice.mode)
+    res = batch.solve(**opts)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch, 2)
+    e0.record()
+    for _ in range(steps):
+        res = batch.solve(**opts)
+    e1.record()
+    torch.cuda.synchronize()
+    tb = e0.elapsed_time(e1) / steps
+    pats = [ab.Pattern(d[0], d[1]) for d in dev]
+    facs = [ab.Factors(p, "f32") for p in pats]
+    xs = [torch.zeros_like(d[3]) for d in dev]
+
+    def one_by_one():
+        out = []
+        for d, p, f, x in zip(dev, pats, facs, xs):
+            x.zero_()
+            out.append(ab.fgmres_solve(p, d[2], f, d[3], x, **opts))
+        return out
+
+    r1 = one_by_one()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        r1 = one_by_one()
+    e1.record()
+    torch.cuda.synchronize()
+    t1 = e0.elapsed_time(e1) / steps
+    return {"workload": f"batch of {nsys} systems, {cells} cells", "cells": cells,
+            "autotuned": {"build_sweeps": choice.build_sweeps, "apply_sweeps": choice.apply_sweeps,
+                          "mode": choice.mode, "tuning_s": round(ttune, 1)},
+            "batch_ms": round(tb, 3), "batch_systems_per_s": round(nsys / (tb * 1e-3), 1),
+            "one_by_one_ms": round(t1, 3), "one_by_one_systems_per_s": round(nsys / (t1 * 1e-3), 1),
+            "converged": sum(r.converged for r in res), "iters_max": max(r.iters for r in res),
+            "iters_min": min(r.iters for r in res),
+            "iters_one_by_one_max": max(r.iters for r in r1), "generation_s": round(tgen, 1)}
+
+
+def _r(v):
+    """Round for the report without zeroing small magnitudes."""
+    return float(f"{v:.4g}") if isinstance(v, float) else v
+
+
+def run_serving(args, n_requests=48):
+    """Poisson stream of requests (4k-1M cells, 5 value updates each, CFL x4 per
+    update), FP32 factors, served with concurrent slots; against plain FP64
+    ABILU served one request at a time on the same GPU."""
+    import torch  # noqa: F401
+    import abilu_inputs as gen
+    from paper_1912_00539_gb300 import serving
+    t0 = time.perf_counter()
+    stream = gen.serving_stream(rate_hz=1.0, n_requests=n_requests, seed=5)
+    tgen = time.perf_counter() - t0
+    unit = [serving.Request(r.rid, r.arrival, r.system.rowptr, r.system.colind,
+                            [(v, b) for v, b, _ in r.updates]) for r in stream]
+
+    def at_rate(rate):
+        return [serving.Request(r.rid, r.arrival / rate, r.rowptr, r.colind, r.updates)
+                for r in unit]
+
+    budget = 0.5 * torch.cuda.get_device_properties(0).total_memory
+    cfg = dict(build_sweeps=args.batch_build_sweeps, apply_sweeps=args.batch_apply_sweeps)
+    # warm-up (library kernels, allocator)
+    serving.Server(budget, slots=2, dtype="f32", mode=args.mode, **cfg).run(at_rate(1e6)[:2])
+    # capacity: everything queued at t=0, one slot
+    res, wall = serving.Server(budget, slots=1, dtype="f32", mode=args.mode, **cfg).run(at_rate(1e6))
+    cap = serving.summarize(res, wall)
+    cap_req_rate = cap["requests"] / cap["wall_s"]
+    out = {"workload": f"{n_requests} requests, 4k-1M cells, 5 updates each",
+           "cells": int(sum(r.n for r in unit)), "generation_s": round(tgen, 1),
+           "single_slot_capacity_solves_per_s": round(cap["solves_per_s"], 1)}
+    for frac in (0.5, 1.0):
+        res, wall = serving.Server(budget, slots=8, dtype="f32", mode=args.mode,
+                                   **cfg).run(at_rate(frac * cap_req_rate))
+        out[f"f32_rate_{frac}x"] = {k: ({kk: _r(vv) for kk, vv in v.items()} if isinstance(v, dict)
+                                        else _r(v)) for k, v in serving.summarize(res, wall).items()}
+    res, wall = serving.Server(budget, slots=1, dtype="f64", mode="sync",
+                               **cfg).run(at_rate(1.0 * cap_req_rate))
+    out["f64_one_at_a_time_rate_1.0x"] = {k: ({kk: _r(vv) for kk, vv in v.items()}
+                                               if isinstance(v, dict) else _r(v))
+                                           for k, v in serving.summarize(res, wall).items()}
+    return out
+
+
+def run_viscous(args):
+    """Viscous-like anisotropic grid (1024x256, CFL 1e4, wall-normal coupling
+    x100): RCM vs wall-normal line ordering, FP32 factors, 8 build and 6+6
+    apply sweeps, FGMRES(50) to 1e-6; iterations against the FP64 oracle."""
+    import torch
+    import abilu_inputs as gen
+    import oracle
+    import paper_1912_00539_gb300 as ab
+    out = {}
+    for order in ("rcm", "line"):
+        name = f"viscous_1024x256_{order}"
+        s = gen.workload(name)
+        st = gen.SOLVER_SETTINGS[name]
+        pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+        A = torch.from_numpy(s.vals).cuda()
+        b = torch.from_numpy(s.b).cuda()
+        Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, st["build_sweeps"])
+        _, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, st["apply_sweeps"],
+                              st["apply_sweeps"], restart=st["restart"], rtol=st["rtol"])
+        row = {"oracle_f64_iters": ro.iters}
+        for dt, md in (("f32", "sync"), ("f32", "async"), ("f64", "sync")):
+            fac = ab.Factors(pat, dt)
+            x = torch.zeros_like(b)
+
+            def solve():
+                x.zero_()
+                return ab.fgmres_solve(pat, A, fac, b, x, restart=st["restart"], rtol=st["rtol"],
+                                       build_sweeps=st["build_sweeps"],
+                                       apply_sweeps_lower=st["apply_sweeps"],
+                                       apply_sweeps_upper=st["apply_sweeps"], mode=md)
+            r = solve()
+            torch.cuda.synchronize()
+            e0, e1 = _events(torch, 2)
+            e0.record()
+            for _ in range(5):
+                r = solve()
+            e1.record()
+            torch.cuda.synchronize()
+            row[f"{dt}_{md}"] = {"iters": r.iters, "rel_resid_true": r.rel_resid_true,
+                                 "solves_per_s": round(5 / (e0.elapsed_time(e1) * 1e-3), 1)}
+        out[order] = row
+    return out
 
 
 def run_gpu(args):
@@ -322,11 +473,10 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     def solve():
-        x.zero_()
         return ab.fgmres_solve(pat, A, fac, b, x, restart=RESTART, rtol=RTOL,
                                build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=APPLY_SWEEPS,
                                apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode,
-                               raise_on_noconv=True)
+                               raise_on_noconv=True, zero_guess=True)
 
     for _ in range(args.warmup):
         res = solve()
@@ -365,10 +515,10 @@ def run_gpu(args):
     def e2e_step():
         dA.copy_(hA, non_blocking=True)
         db.copy_(hb, non_blocking=True)
-        dx.zero_()
         ab.fgmres_solve(pat, dA, fac, db, dx, restart=RESTART, rtol=RTOL,
                         build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=APPLY_SWEEPS,
-                        apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode, raise_on_noconv=True)
+                        apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode, raise_on_noconv=True,
+                        zero_guess=True)
         hx.copy_(dx, non_blocking=True)
 
     for _ in range(2):
@@ -418,11 +568,10 @@ def run_gpu(args):
             xv = torch.zeros_like(b)
 
             def sv():
-                xv.zero_()
                 return ab.fgmres_solve(pat, A, fv, b, xv, restart=RESTART, rtol=RTOL,
                                        build_sweeps=BUILD_SWEEPS,
                                        apply_sweeps_lower=APPLY_SWEEPS,
-                                       apply_sweeps_upper=APPLY_SWEEPS, mode=md)
+                                       apply_sweeps_upper=APPLY_SWEEPS, mode=md, zero_guess=True)
             r = sv()
             sv()
             torch.cuda.synchronize()
@@ -478,6 +627,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
     ap.add_argument("--profile-solves", type=int, default=0)
+    ap.add_argument("--batched", action="store_true", help="only the batched workload")
+    ap.add_argument("--serving", action="store_true", help="only the serving workload")
+    ap.add_argument("--viscous", action="store_true", help="only the viscous-like workload")
+    ap.add_argument("--batch-build-sweeps", type=int, default=4)
+    ap.add_argument("--batch-apply-sweeps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -485,6 +639,15 @@ def main():
         return run_kernels_only(args)
     if args.profile_solves:
         return run_profile_solves(args)
+    if args.batched:
+        print(json.dumps(run_batched(args)))
+        return 0
+    if args.serving:
+        print(json.dumps(run_serving(args)))
+        return 0
+    if args.viscous:
+        print(json.dumps(run_viscous(args)))
+        return 0
     return run_gpu(args)
 
 

@@ -183,6 +183,23 @@ abilu_status bsr_spmv(abilu_pattern p, const double *A_vals, double alpha, const
  */
 abilu_status abilu_factors_export(abilu_factors f, double *X, double *Dinv, abilu_stream stream);
 
+/*
+ * Diagnostics of the current factors against A (Sec. 6.2, the quantities the
+ * paper tracks over pseudo-time steps), evaluated in FP64 from the stored
+ * factors; `out` is host double[4]:
+ *   out[0] = ||x - h(x)||_1, the ILU fixed-point residual over all entries of
+ *            L and U, h being the map of Eq. (blockH) with inv(U_jj) recomputed
+ *            from the stored U_jj (the paper plots its ratio to the value at
+ *            the initial guess: call this after a 0-sweep build for that);
+ *   out[1] = max |(LU)_ij - A_ij| over the blocks of S_B (0 at the fixed point);
+ *   out[2] = ||L - I||_inf, the max-norm of the Jacobi iteration matrix of the
+ *            lower block triangular solve (unit diagonal blocks);
+ *   out[3] = ||D_U^{-1}(U - D_U)||_inf for the upper solve, D_U = block diagonal.
+ * Synchronises `stream`.
+ */
+abilu_status abilu_factors_diagnostics(abilu_factors f, const double *A_vals, double *out,
+                                       abilu_stream stream);
+
 /* Synchronises `stream`, then returns in *singular_blocks (host) how many
  * singular diagonal blocks the builds since the last call replaced, and resets
  * the count. */
@@ -199,6 +216,7 @@ typedef struct {
     int32_t build;              /* 1: build the factors from A inside the solve; 0: use them as they are */
     int32_t init;               /* abilu_init for that build */
     int32_t reorth;             /* 0: one classical Gram-Schmidt pass; 1: two passes (CGS2) */
+    int32_t zero_guess;         /* 1: start from x0 = 0 (x is overwritten; r0 = b, no SpMV) */
 } fgmres_opts;
 
 typedef struct {
@@ -211,7 +229,8 @@ typedef struct {
 } fgmres_result;
 
 /* Defaults: restart 30, max_iters 2500, rtol 1e-6, 1 build / 3+3 apply sweeps
- * (the paper's choice, Sec. 6.1), ABILU_ASYNC, build from A, reorth 0. */
+ * (the paper's choice, Sec. 6.1), ABILU_ASYNC, build from A, reorth 0,
+ * zero_guess 0 (x holds x0). */
 void fgmres_default_opts(fgmres_opts *opts);
 
 /*

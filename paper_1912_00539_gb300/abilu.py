@@ -31,6 +31,7 @@ INITS = {"a": 0, "previous": 1}
 EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_pattern_create", "abilu_pattern_destroy",
            "abilu_pattern_counts", "abilu_factors_create", "abilu_factors_destroy", "abilu_build",
            "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
+           "abilu_factors_diagnostics",
            "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc", "abilu_batch_create",
            "abilu_batch_destroy", "abilu_batch_counts", "abilu_batch_set_system",
            "abilu_batch_solve", "abilu_batch_get_solution")
@@ -40,7 +41,7 @@ class FgmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
                 ("build_sweeps", C.c_int32), ("apply_sweeps_lower", C.c_int32),
                 ("apply_sweeps_upper", C.c_int32), ("mode", C.c_int32), ("build", C.c_int32),
-                ("init", C.c_int32), ("reorth", C.c_int32)]
+                ("init", C.c_int32), ("reorth", C.c_int32), ("zero_guess", C.c_int32)]
 
 
 class FgmresResult(C.Structure):
@@ -68,6 +69,8 @@ _lib.abilu_apply_noalloc.argtypes = [_i32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int
 _lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
+_lib.abilu_factors_diagnostics.argtypes = [_vp, _vp, C.POINTER(_f64), _vp]
+_lib.abilu_factors_diagnostics.restype = C.c_int
 _lib.fgmres_default_opts.argtypes = [C.POINTER(FgmresOpts)]
 _lib.fgmres_default_opts.restype = None
 _lib.fgmres_solve.argtypes = [_vp, _vp, _vp, _vp, _vp, C.POINTER(FgmresOpts),
@@ -85,6 +88,7 @@ for _nm in ("abilu_batch_create", "abilu_batch_counts", "abilu_batch_set_system"
     getattr(_lib, _nm).restype = C.c_int
 for _nm in ("abilu_pattern_create", "abilu_pattern_counts", "abilu_factors_create", "abilu_build",
             "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
+           "abilu_factors_diagnostics",
             "fgmres_solve"):
     getattr(_lib, _nm).restype = C.c_int
 
@@ -186,6 +190,16 @@ class Factors:
                                          _ptr(D, torch.float64), _stream(stream)))
         return X, D
 
+    def diagnostics(self, A, stream=None) -> dict:
+        """ILU fixed-point residual, LU defect and Jacobi-matrix norms (FP64)."""
+        import torch
+        out = (C.c_double * 4)()
+        _check(_lib.abilu_factors_diagnostics(self.handle,
+                                              _ptr(A, torch.float64, 16 * self.pattern.nnzb, "A"),
+                                              out, _stream(stream)))
+        return dict(zip(("ilu_residual_l1", "lu_defect_max", "jacobi_norm_L", "jacobi_norm_U"),
+                        list(out)))
+
     def singular_blocks(self, stream=None) -> int:
         v = C.c_int64()
         _check(_lib.abilu_factors_status(self.handle, C.byref(v), _stream(stream)))
@@ -246,11 +260,11 @@ def default_opts() -> FgmresOpts:
 def fgmres_solve(pattern: Pattern, A, factors: Factors, b, x, restart=30, max_iters=2500,
                  rtol=1e-6, build_sweeps=1, apply_sweeps_lower=3, apply_sweeps_upper=3,
                  mode="async", build=True, init="a", reorth=False, stream=None,
-                 raise_on_noconv=False) -> SolveResult:
+                 raise_on_noconv=False, zero_guess=False) -> SolveResult:
     import torch
     o = FgmresOpts(int(restart), int(max_iters), float(rtol), int(build_sweeps),
                    int(apply_sweeps_lower), int(apply_sweeps_upper), MODES[mode], int(bool(build)),
-                   INITS[init], int(bool(reorth)))
+                   INITS[init], int(bool(reorth)), int(bool(zero_guess)))
     r = FgmresResult()
     nv = 4 * pattern.n
     st = _lib.fgmres_solve(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
@@ -266,7 +280,7 @@ def _opts(restart, max_iters, rtol, build_sweeps, apply_sweeps_lower, apply_swee
           build, init, reorth):
     return FgmresOpts(int(restart), int(max_iters), float(rtol), int(build_sweeps),
                       int(apply_sweeps_lower), int(apply_sweeps_upper), MODES[mode],
-                      int(bool(build)), INITS[init], int(bool(reorth)))
+                      int(bool(build)), INITS[init], int(bool(reorth)), 1)
 
 
 class Batch:

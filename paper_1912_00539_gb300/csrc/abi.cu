@@ -9,10 +9,10 @@ namespace abilu {
 abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st);
 abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
-                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip);
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
 abilu_status export_dispatch(abilu_factors f, double *X, double *Dinv, cudaStream_t st);
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
-                         double beta, double *y, cudaStream_t st, const int *skip);
+                         double beta, double *y, cudaStream_t st, Skip skip);
 size_t solve_state_bytes();
 size_t host_status_bytes();
 int max_restart();
@@ -133,7 +133,7 @@ extern "C" abilu_status abilu_apply(abilu_factors f, const double *r, double *z,
     if (!aligned16(r) || !aligned16(z)) return fail(ABILU_EINVAL, "apply: vectors must be 16-byte aligned");
     if (nl < 0 || nu < 0) return fail(ABILU_EINVAL, "apply: negative sweep count");
     if (mode != ABILU_SYNC && mode != ABILU_ASYNC) return fail(ABILU_EINVAL, "apply: bad mode");
-    return apply_dispatch(f, r, nullptr, z, nl, nu, mode, S(stream), nullptr);
+    return apply_dispatch(f, r, nullptr, z, nl, nu, mode, S(stream), Skip{});
 }
 
 extern "C" abilu_status bsr_spmv(abilu_pattern p, const double *A, double alpha, const double *x,
@@ -142,7 +142,7 @@ extern "C" abilu_status bsr_spmv(abilu_pattern p, const double *A, double alpha,
     if (x == y) return fail(ABILU_EINVAL, "spmv: x and y must be distinct");
     if (!aligned16(A) || !aligned16(x) || !aligned16(y))
         return fail(ABILU_EINVAL, "spmv: pointers must be 16-byte aligned");
-    return spmv_launch(p->v, A, alpha, x, beta, y, S(stream), nullptr);
+    return spmv_launch(p->v, A, alpha, x, beta, y, S(stream), Skip{});
 }
 
 extern "C" abilu_status abilu_factors_export(abilu_factors f, double *X, double *Dinv,

@@ -34,9 +34,7 @@ template <> struct ApplyArith<double> { using VT = double; };
 __device__ __forceinline__ double to_f64v(float v) { return to_f64(v); }
 __device__ __forceinline__ double to_f64v(double v) { return v; }
 
-__device__ __forceinline__ bool skipped(const int *skip) {
-    return skip && *reinterpret_cast<const volatile int *>(skip);
-}
+static_assert(APPLY_ROWS == SKIP_CHUNK_ROWS, "one CTA (or ticket) per 64-row chunk");
 
 template <typename VT>
 __device__ __forceinline__ VT dot4(const VT a[4], const VT b[4]) {
@@ -77,8 +75,8 @@ template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_lower_sync(PatternView P, const T *__restrict__ L, const VT *__restrict__ r,
              const VT *__restrict__ yin, VT *__restrict__ yout, const T *__restrict__ D,
-             VT *__restrict__ x1, double *__restrict__ z, const int *skip) {
-    if (skipped(skip)) return;
+             VT *__restrict__ x1, double *__restrict__ z, Skip skip) {
+    if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     const VT s = row_sweep_sum<false>(r[(size_t)i * BS + q], L, P.lcol, P.lrow[i], P.lrow[i + 1], yin);
@@ -94,8 +92,8 @@ k_lower_sync(PatternView P, const T *__restrict__ L, const VT *__restrict__ r,
 template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_diag_apply(PatternView P, const T *__restrict__ D, const VT *__restrict__ y,
-             VT *__restrict__ x1, double *__restrict__ z, const int *skip) {
-    if (skipped(skip)) return;
+             VT *__restrict__ x1, double *__restrict__ z, Skip skip) {
+    if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     VT t = y[(size_t)i * BS + q];
@@ -108,8 +106,8 @@ template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
              const VT *__restrict__ y, const VT *__restrict__ xin, VT *__restrict__ xout,
-             double *__restrict__ z, const int *skip) {
-    if (skipped(skip)) return;
+             double *__restrict__ z, Skip skip) {
+    if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     const VT s = row_sweep_sum<false>(y[(size_t)i * BS + q], U, P.ucol, P.urow[i], P.urow[i + 1], xin);
@@ -131,8 +129,8 @@ template <> __device__ __forceinline__ void st_vol<double>(double *p, double v) 
 template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, VT *y,
-              int nsweeps, unsigned long long *ticket, const int *skip) {
-    if (skipped(skip)) return;
+              int nsweeps, unsigned long long *ticket, Skip skip) {
+    if (skip_all(skip)) return;
     __shared__ unsigned long long s_t;
     const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
     const long long total = nchunks * nsweeps;
@@ -143,8 +141,9 @@ k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, 
         const long long t = (long long)s_t;
         __syncthreads();
         if (t >= total) break;
-        const int i = (int)(t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
-        if (i < P.n) {
+        const int chunk = (int)(t % nchunks);
+        const int i = chunk * APPLY_ROWS + (threadIdx.x >> 2);
+        if (i < P.n && !skip_chunk(skip, chunk)) {
             const VT s = row_sweep_sum<true>(r[(size_t)i * BS + q], L, P.lcol, P.lrow[i],
                                              P.lrow[i + 1], (const VT *)y);
             st_vol(y + (size_t)i * BS + q, s);
@@ -158,8 +157,8 @@ template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
               const VT *__restrict__ y, VT *x, double *__restrict__ z, int nsweeps,
-              unsigned long long *ticket, const int *skip) {
-    if (skipped(skip)) return;
+              unsigned long long *ticket, Skip skip) {
+    if (skip_all(skip)) return;
     __shared__ unsigned long long s_t;
     const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
     const long long total = nchunks * nsweeps;
@@ -171,8 +170,9 @@ k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
         __syncthreads();
         if (t >= total) break;
         const bool last = t / nchunks == nsweeps - 1;
-        const int i = (int)(nchunks - 1 - t % nchunks) * APPLY_ROWS + (threadIdx.x >> 2);
-        if (i < P.n) {  // quads of one row stay together: the shuffles below are quad-local
+        const int chunk = (int)(nchunks - 1 - t % nchunks);
+        const int i = chunk * APPLY_ROWS + (threadIdx.x >> 2);
+        if (i < P.n && !skip_chunk(skip, chunk)) {  // quads of a row stay together
             const VT s = row_sweep_sum<true>(y[(size_t)i * BS + q], U, P.ucol, P.urow[i],
                                              P.urow[i + 1], (const VT *)x);
             VT xi = dinv_times<T, VT>(D, i, s);
@@ -193,6 +193,15 @@ k_to_f32(const double *__restrict__ r, float *__restrict__ r32, long long n4) {
     st_row(r32 + e, v);
 }
 
+// v = 0 (n values) unless the launch is skipped: the zero initial guess of the
+// in-place sweeps, as a kernel so that a skipped FGMRES step costs no memset
+template <typename VT>
+__global__ void k_zero(VT *v, long long n, Skip skip) {
+    if (skip_all(skip)) return;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) v[e] = (VT)0;
+}
+
 template <typename K>
 static int resident_ctas(K kernel, int threads) {
     int dev = 0, per_sm = 0, sms = 0;
@@ -203,9 +212,20 @@ static int resident_ctas(K kernel, int threads) {
     return c > 0 ? c : 1;
 }
 
+// resident CTAs of the persistent kernels, looked up once (before any stream
+// capture: see apply_warm)
+template <typename T, typename VT> static int lower_async_ctas() {
+    static int c = resident_ctas(k_lower_async<T, VT>, APPLY_THREADS);
+    return c;
+}
+template <typename T, typename VT> static int upper_async_ctas() {
+    static int c = resident_ctas(k_upper_async<T, VT>, APPLY_THREADS);
+    return c;
+}
+
 template <typename T>
 static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_in, double *z,
-                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip) {
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip) {
     using VT = typename ApplyArith<T>::VT;
     const PatternView &P = f->p->v;
     const int c = f->cur;
@@ -235,25 +255,28 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
 
     if (mode == ABILU_ASYNC) {
         const long long nchunks = grid;
-        ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
+        const long long n4 = (long long)P.n * BS;
+        const int zgrid = (int)((n4 + 255) / 256);
+        k_zero<VT><<<counted(zgrid), 256, 0, st>>>(y[0], n4, skip);
         if (nl > 0) {
-            ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, 8, st));
-            static int ctas_l = resident_ctas(k_lower_async<T, VT>, APPLY_THREADS);
+            k_zero<unsigned long long><<<counted(1), 32, 0, st>>>(f->ctr + 1, 1, skip);
+            const int ctas_l = lower_async_ctas<T, VT>();
             int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
             k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl, f->ctr + 1, skip);
             ABILU_LAUNCH_CHECK("k_lower_async");
         }
         if (nu > 0) {
-            ABILU_CUDA(cudaMemsetAsync(x[0], 0, vbytes, st));
-            ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, 8, st));
-            static int ctas_u = resident_ctas(k_upper_async<T, VT>, APPLY_THREADS);
+            k_zero<VT><<<counted(zgrid), 256, 0, st>>>(x[0], n4, skip);
+            k_zero<unsigned long long><<<counted(1), 32, 0, st>>>(f->ctr + 1, 1, skip);
+            const int ctas_u = upper_async_ctas<T, VT>();
             int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
             k_upper_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, U, D, y[0], x[0], z, nu,
                                                                        f->ctr + 1, skip);
             ABILU_LAUNCH_CHECK("k_upper_async");
         } else {
-            ABILU_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)P.n * BS, st));
+            k_zero<double><<<counted(zgrid), 256, 0, st>>>(z, n4, skip);
         }
+        ABILU_LAUNCH_CHECK("apply async");
         return ABILU_OK;
     }
 
@@ -294,8 +317,21 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
     return ABILU_OK;
 }
 
+// Performs the one-time occupancy lookups of the apply kernels of a dtype, so
+// that later calls make no such API call (needed inside stream capture).
+void apply_warm(abilu_dtype dt) {
+    switch (dt) {
+    case ABILU_F64: lower_async_ctas<double, double>(); upper_async_ctas<double, double>(); break;
+    case ABILU_F32: lower_async_ctas<float, float>(); upper_async_ctas<float, float>(); break;
+    case ABILU_BF16:
+        lower_async_ctas<__nv_bfloat16, float>();
+        upper_async_ctas<__nv_bfloat16, float>();
+        break;
+    }
+}
+
 abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
-                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip) {
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip) {
     switch (f->dtype) {
     case ABILU_F64: return apply_t<double>(f, r, r32, z, nl, nu, mode, st, skip);
     case ABILU_F32: return apply_t<float>(f, r, r32, z, nl, nu, mode, st, skip);

@@ -16,6 +16,7 @@
 // in lockstep; a system that has converged (or left its cycle) skips its
 // chunks in the Krylov kernels.  Padding rows have b = 0 and stay x = 0, so they
 // change no norm.
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -28,9 +29,10 @@ namespace abilu {
 abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st);
 abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
-                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip);
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
-                         double beta, double *y, cudaStream_t st, const int *skip);
+                         double beta, double *y, cudaStream_t st, Skip skip);
+void apply_warm(abilu_dtype dt);
 
 constexpr int BMAXM = 64;
 constexpr int CHUNK_ROWS = 64;           // rows per CTA = padding unit
@@ -86,7 +88,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_b_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
              const double *__restrict__ x, double *__restrict__ r_out, BState *S,
              const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
-             double *partials, BConf cf, int init, int *hs_done, int *hs_fin) {
+             double *partials, BConf cf, int init, int *hs_done, int *hs_fin, int *sys_done,
+             int *bflag) {
     __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
     const int chunk = blockIdx.x, s = chunk_sys[chunk];
     BState *St = S + s;
@@ -94,7 +97,8 @@ k_b_residual(PatternView P, const double *__restrict__ A, const double *__restri
     const int i = chunk * CHUNK_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     double v[2] = {0.0, 0.0};
     {
-        const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1];
+        // a solve starts from x = 0, where r = b needs no product
+        const int p0 = P.rowptr[i], p1 = init ? p0 : P.rowptr[i + 1];
         double acc = 0.0;
         for (int p = p0; p < p1; p++) {
             const int j = __ldg(P.colind + p);
@@ -134,9 +138,23 @@ k_b_residual(PatternView P, const double *__restrict__ A, const double *__restri
         for (int k = 1; k <= BMAXM; k++) St->g[k] = 0.0;
         if (init) St->est = St->bnorm > 0.0 ? St->beta / St->bnorm : 0.0;
         St->counter = 0;
+        sys_done[s] = St->done;
+        if (!St->done) {  // active in the coming cycle (bflag was reset to {1, 0})
+            bflag[0] = 0;
+            atomicAdd(bflag + 1, 1);
+        }
         reinterpret_cast<volatile int *>(hs_done)[s] = St->done;
         reinterpret_cast<volatile int *>(hs_fin)[s] = St->finished;
         __threadfence_system();
+    }
+}
+
+// bflag = {all systems done with the cycle, systems still active}; reset
+// before the residual kernel that starts a cycle
+__global__ void k_b_flags_reset(int *bflag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        bflag[0] = 1;
+        bflag[1] = 0;
     }
 }
 
@@ -205,7 +223,8 @@ k_b_dots(const double *__restrict__ V, size_t nv, int j, const double *__restric
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ w, BState *S,
            const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
-           double *partials, BConf cf, int pass, int final_pass, int *hs_done) {
+           double *partials, BConf cf, int pass, int final_pass, int *hs_done, int *sys_done,
+           int *bflag) {
     __shared__ double sh_h[BMAXM + 1];
     __shared__ double sh_w[RED_WARPS], sh_o[1];
     const int chunk = blockIdx.x, s = chunk_sys[chunk];
@@ -256,6 +275,8 @@ k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ 
     St->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
     St->counter = 0;
     if (St->done) {
+        sys_done[s] = 1;
+        if (atomicSub(bflag + 1, 1) == 1) bflag[0] = 1;  // the last active system left
         reinterpret_cast<volatile int *>(hs_done)[s] = 1;
         __threadfence_system();
     }
@@ -344,6 +365,14 @@ struct abilu_batch_s {
     double *krylov;
     int krylov_m;
     int *hs_done, *hs_fin;      // pinned, host-mapped
+    int *sys_done, *bflag;      // device: per-system cycle exit; {all done, active count}
+    cudaGraphExec_t graph;      // one restart cycle, captured on first use
+    int gkey[6];
+    long long g_fixed, g_step;  // kernels per replay outside the steps; per step run
+    cudaStream_t cap_stream;    // capture happens here: the caller's stream may be the
+                                // legacy default stream, which cannot be captured
+    cudaStream_t body_stream;   // capture of the conditional step bodies
+    int no_graph;               // 1: host-driven cycles (ABILU_NO_GRAPH set or capture failed)
     abilu_pattern pat;
     abilu_factors fac;
     std::vector<void *> allocs;
@@ -355,6 +384,9 @@ static void batch_free(abilu_batch b) {
     if (b->pat) abilu_pattern_destroy(b->pat);
     for (void *p : b->allocs) cudaFree(p);
     if (b->krylov) cudaFree(b->krylov);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->body_stream) cudaStreamDestroy(b->body_stream);
     if (b->hs_done) cudaFreeHost(b->hs_done);
     if (b->hs_fin) cudaFreeHost(b->hs_fin);
     delete b;
@@ -378,6 +410,10 @@ extern "C" abilu_status abilu_batch_create(int32_t nsys, const int32_t *n, const
     b->krylov = nullptr;
     b->krylov_m = 0;
     b->hs_done = b->hs_fin = nullptr;
+    b->graph = nullptr;
+    b->cap_stream = nullptr;
+    b->body_stream = nullptr;
+    b->no_graph = getenv("ABILU_NO_GRAPH") != nullptr;
     long long rows = 0, blocks = 0;
     for (int s = 0; s < nsys; s++) {
         if (n[s] < 1 || nnzb[s] < n[s] || !rowptr[s] || !colind[s]) {
@@ -421,9 +457,13 @@ extern "C" abilu_status abilu_batch_create(int32_t nsys, const int32_t *n, const
     TRY(alloc((void **)&b->sys_chunk0, sizeof(int) * (nsys + 1)));
     TRY(alloc((void **)&b->S, sizeof(BState) * nsys));
     TRY(alloc((void **)&b->partials, sizeof(double) * PSTRIDE * b->nchunks));
+    TRY(alloc((void **)&b->sys_done, sizeof(int) * nsys));
+    TRY(alloc((void **)&b->bflag, sizeof(int) * 4));
     auto cu = [&](cudaError_t e, const char *w) -> abilu_status {
         return e == cudaSuccess ? ABILU_OK : cuda_fail(e, w);
     };
+    TRY(cu(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream"));
+    TRY(cu(cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking), "stream"));
     TRY(cu(cudaHostAlloc((void **)&b->hs_done, sizeof(int) * nsys, cudaHostAllocMapped), "hostalloc"));
     TRY(cu(cudaHostAlloc((void **)&b->hs_fin, sizeof(int) * nsys, cudaHostAllocMapped), "hostalloc"));
     TRY(cu(cudaMemsetAsync(b->A, 0, sizeof(double) * BB * blocks, st), "memset A"));
@@ -489,6 +529,128 @@ static bool all_set(const int *flags, int n) {
     return true;
 }
 
+// One Arnoldi step j of every active system.  Every kernel skips the chunks of
+// systems that have left the cycle (and returns at once when all have).
+static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const BConf &cf, int j,
+                                 cudaStream_t st) {
+    const PatternView &P = b->pat->v;
+    const int m = cf.m, nck = b->nchunks;
+    const size_t nv = (size_t)b->rows * BS;
+    double *V = b->krylov, *Z = V + (size_t)(m + 1) * nv, *w = Z + (size_t)m * nv;
+    float *v32 = reinterpret_cast<float *>(b->fac->r32);
+    const Skip skip{b->bflag, b->chunk_sys, b->sys_done};
+    abilu_status s = apply_dispatch(b->fac, V + (size_t)j * nv, v32, Z + (size_t)j * nv,
+                                    opts->apply_sweeps_lower, opts->apply_sweeps_upper,
+                                    (abilu_mode)opts->mode, st, skip);
+    if (s != ABILU_OK) return s;
+    if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
+    k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
+                                                   b->partials, 0);
+    k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
+                                                     b->partials, cf, 0, !opts->reorth, b->hs_done,
+                                                     b->sys_done, b->bflag);
+    if (opts->reorth) {
+        k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
+                                                       b->sys_chunk0, b->partials, 1);
+        k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
+                                                         b->sys_chunk0, b->partials, cf, 1, 1,
+                                                         b->hs_done, b->sys_done, b->bflag);
+    }
+    k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, v32, b->S,
+                                                    b->chunk_sys);
+    ABILU_LAUNCH_CHECK("batch step");
+    return ABILU_OK;
+}
+
+// End of a cycle: x += Z y per system, true residual, new v_0, new cycle flags.
+static abilu_status enqueue_restart(abilu_batch b, const BConf &cf, cudaStream_t st) {
+    const PatternView &P = b->pat->v;
+    const int m = cf.m, nck = b->nchunks, nsys = b->nsys;
+    const size_t nv = (size_t)b->rows * BS;
+    double *V = b->krylov, *Z = V + (size_t)(m + 1) * nv;
+    float *v32 = reinterpret_cast<float *>(b->fac->r32);
+    k_b_ysolve<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
+    k_b_xupdate<<<counted(nck), RED_THREADS, 0, st>>>(Z, nv, b->x, b->S, b->chunk_sys);
+    k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
+    k_b_residual<<<counted(nck), RED_THREADS, 0, st>>>(P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
+                                                       b->sys_chunk0, b->partials, cf, 0, b->hs_done,
+                                                       b->hs_fin, b->sys_done, b->bflag);
+    k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(V, V, v32, b->S, b->chunk_sys);
+    ABILU_LAUNCH_CHECK("batch restart");
+    return ABILU_OK;
+}
+
+// condition of the IF node around an Arnoldi step: run it unless every system
+// has left the cycle; bflag[2] counts the steps that ran
+__global__ void k_b_set_cond(cudaGraphConditionalHandle h, int *bflag) {
+    const int run = *reinterpret_cast<const volatile int *>(bflag) == 0;
+    cudaGraphSetConditional(h, run ? 1u : 0u);
+    if (run) bflag[2]++;
+}
+
+// Capture one restart cycle as a graph: each of the m steps is the body of an
+// IF node whose condition a one-thread kernel sets from the device flag, so
+// the steps after every system has converged cost a condition check, not a
+// launch of their kernels; then the restart.
+static abilu_status capture_cycle(abilu_batch b, const fgmres_opts *opts, const BConf &cf,
+                                  cudaGraph_t *out) {
+    cudaStream_t cs = b->cap_stream, bs = b->body_stream;
+    *out = nullptr;
+    const unsigned long long l0 = launches();
+    unsigned long long in_steps = 0;
+    ABILU_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    abilu_status st = ABILU_OK;
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < cf.m && st == ABILU_OK && e == cudaSuccess; j++) {
+        cudaStreamCaptureStatus cstat;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamGetCaptureInfo(cs, &cstat, nullptr, &g, nullptr, nullptr, nullptr);
+        if (e != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+        if (e != cudaSuccess) break;
+        k_b_set_cond<<<counted(1), 1, 0, cs>>>(h, b->bflag);
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        e = cudaStreamGetCaptureInfo(cs, &cstat, nullptr, &g, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) break;
+        cudaGraphNodeParams prm = {};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = h;
+        prm.conditional.type = cudaGraphCondTypeIf;
+        prm.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &prm);
+        if (e != cudaSuccess) break;
+        e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) break;
+        e = cudaStreamBeginCaptureToGraph(bs, prm.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        const unsigned long long s0 = launches();
+        st = enqueue_step(b, opts, cf, j, bs);
+        in_steps += launches() - s0;
+        cudaGraph_t body;
+        cudaError_t e2 = cudaStreamEndCapture(bs, &body);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (st == ABILU_OK && e == cudaSuccess) st = enqueue_restart(b, cf, cs);
+    cudaGraph_t g = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(cs, &g);
+    const long long captured = (long long)(launches() - l0);
+    note_launches(-captured);   // captured, not launched: replays are counted
+    b->g_step = cf.m ? (long long)in_steps / cf.m : 0;
+    b->g_fixed = captured - (long long)in_steps;
+    if (st != ABILU_OK || e != cudaSuccess || e3 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (st != ABILU_OK) return st;
+        return cuda_fail(e != cudaSuccess ? e : e3, "batch_solve: conditional graph capture");
+    }
+    *out = g;
+    return ABILU_OK;
+}
+
 extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts,
                                           fgmres_result *res, abilu_stream stream) {
     if (!b || !opts || !res) return fail(ABILU_EINVAL, "batch_solve: NULL argument");
@@ -504,76 +666,86 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
     if (!b->krylov || b->krylov_m < m) {
         if (b->krylov) cudaFree(b->krylov);
         b->krylov = nullptr;
+        if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
         ABILU_CUDA(cudaMalloc(&b->krylov, sizeof(double) * nv * (2 * (size_t)m + 2)));
         b->krylov_m = m;
     }
-    double *V = b->krylov, *Z = V + (size_t)(m + 1) * nv, *w = Z + (size_t)m * nv;
+    double *V = b->krylov;
     float *v32 = reinterpret_cast<float *>(b->fac->r32);
-    const abilu_mode mode = (abilu_mode)opts->mode;
     const BConf cf = {opts->rtol, opts->max_iters, m};
     const int nck = b->nchunks, nsys = b->nsys;
     abilu_status s;
     if (opts->build) {
         ABILU_CUDA(cudaMemsetAsync(b->fac->ctr, 0, sizeof(unsigned long long), st));
-        s = build_dispatch(b->fac, b->A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
+        s = build_dispatch(b->fac, b->A, opts->build_sweeps, (abilu_mode)opts->mode,
+                           (abilu_init)opts->init, st);
         if (s != ABILU_OK) return s;
     }
     ABILU_CUDA(cudaMemsetAsync(b->x, 0, sizeof(double) * nv, st));
     ABILU_CUDA(cudaMemsetAsync(b->S, 0, sizeof(BState) * nsys, st));
     k_b_init<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
+    k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
     k_b_residual<<<counted(nck), RED_THREADS, 0, st>>>(P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
-                                                       b->sys_chunk0, b->partials, cf, 1,
-                                                       b->hs_done, b->hs_fin);
+                                                       b->sys_chunk0, b->partials, cf, 1, b->hs_done,
+                                                       b->hs_fin, b->sys_done, b->bflag);
     k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(V, V, v32, b->S, b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch init");
+    // the cycle graph: captured once per (restart, sweeps, mode, reorth, factor
+    // buffer), replayed for every cycle of every later solve
+    const int key[6] = {m, opts->apply_sweeps_lower, opts->apply_sweeps_upper, opts->mode,
+                        opts->reorth, (int)b->fac->cur};
+    if (b->graph && memcmp(key, b->gkey, sizeof key) != 0) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (!b->graph && !b->no_graph) {
+        apply_warm(b->fac->dtype);
+        cudaGraph_t g = nullptr;
+        if (capture_cycle(b, opts, cf, &g) == ABILU_OK &&
+            cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess) {
+            memcpy(b->gkey, key, sizeof key);
+        } else {
+            b->graph = nullptr;
+            b->no_graph = 1;   // this runtime cannot: use the host-driven loop
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
+    ABILU_CUDA(cudaMemsetAsync(b->bflag + 2, 0, sizeof(int), st));
     ABILU_CUDA(cudaStreamSynchronize(st));
-    cudaEvent_t ev[2];
-    ABILU_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    ABILU_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     abilu_status ret = ABILU_OK;
-    int cycles = 0;
+    int cycles = 0, replays = 0;
     while (!all_set(b->hs_fin, nsys) && cycles <= opts->max_iters) {
         cycles++;
-        for (int j = 0; j < m; j++) {
-            s = apply_dispatch(b->fac, V + (size_t)j * nv, v32, Z + (size_t)j * nv,
-                               opts->apply_sweeps_lower, opts->apply_sweeps_upper, mode, st, nullptr);
-            if (s != ABILU_OK) { ret = s; break; }
-            if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, nullptr)) != ABILU_OK) { ret = s; break; }
-            k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
-                                                           b->partials, 0);
-            k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
-                                                             b->partials, cf, 0, !opts->reorth, b->hs_done);
-            if (opts->reorth) {
-                k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
-                                                               b->sys_chunk0, b->partials, 1);
-                k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
-                                                                 b->sys_chunk0, b->partials, cf, 1, 1,
-                                                                 b->hs_done);
+        cudaError_t e = cudaSuccess;
+        if (b->graph) {
+            e = cudaGraphLaunch(b->graph, st);
+            replays++;
+        } else {  // host-driven: look at step j-1 while step j runs
+            cudaEvent_t ev[2];
+            cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+            for (int j = 0; j < m; j++) {
+                if ((ret = enqueue_step(b, opts, cf, j, st)) != ABILU_OK) break;
+                cudaEventRecord(ev[j & 1], st);
+                if (j >= 1) {
+                    cudaEventSynchronize(ev[(j - 1) & 1]);
+                    if (all_set(b->hs_done, nsys)) break;
+                }
             }
-            k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, v32, b->S,
-                                                            b->chunk_sys);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) { ret = cuda_fail(e, "batch step"); break; }
-            cudaEventRecord(ev[j & 1], st);
-            if (j >= 1) {  // look at step j-1 while step j runs
-                cudaEventSynchronize(ev[(j - 1) & 1]);
-                if (all_set(b->hs_done, nsys)) break;
-            }
+            cudaEventDestroy(ev[0]);
+            cudaEventDestroy(ev[1]);
+            if (ret != ABILU_OK) break;
+            if ((ret = enqueue_restart(b, cf, st)) != ABILU_OK) break;
         }
-        if (ret != ABILU_OK) break;
-        k_b_ysolve<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
-        k_b_xupdate<<<counted(nck), RED_THREADS, 0, st>>>(Z, nv, b->x, b->S, b->chunk_sys);
-        k_b_residual<<<counted(nck), RED_THREADS, 0, st>>>(P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
-                                                           b->sys_chunk0, b->partials, cf, 0,
-                                                           b->hs_done, b->hs_fin);
-        k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(V, V, v32, b->S, b->chunk_sys);
-        cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) { ret = cuda_fail(e, "batch restart"); break; }
+        if (e != cudaSuccess) { ret = cuda_fail(e, "batch cycle"); break; }
     }
-    cudaStreamSynchronize(st);
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
+    if (replays) {
+        int steps = 0;
+        ABILU_CUDA(cudaMemcpy(&steps, b->bflag + 2, sizeof steps, cudaMemcpyDeviceToHost));
+        note_launches(replays * b->g_fixed + (long long)steps * b->g_step);
+    }
     std::vector<BState> hs(nsys);
     ABILU_CUDA(cudaMemcpy(hs.data(), b->S, sizeof(BState) * nsys, cudaMemcpyDeviceToHost));
     unsigned long long ns = 0;

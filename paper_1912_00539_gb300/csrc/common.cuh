@@ -33,6 +33,8 @@ inline cudaStream_t S(abilu_stream s) { return reinterpret_cast<cudaStream_t>(s)
 // Host-side count of kernel launches made by the library (every launch site
 // wraps its grid size in counted()); read through abilu_kernel_launches().
 void note_launch();
+void note_launches(long long delta);   // graph replays; captures taken back
+unsigned long long launches();
 template <typename G> inline G counted(G grid) { note_launch(); return grid; }
 
 // Device view of an analysed pattern.  Positions: "p" indexes A's blocks,
@@ -92,6 +94,23 @@ struct abilu_factors_s {
 
 // ---------------------------------------------------------------- device helpers
 namespace abilu {
+
+// Early exit of the row kernels.  `flag`: the whole launch returns when *flag
+// is nonzero (an FGMRES cycle that has ended).  `chunk_sys`/`sys_done`: in a
+// batch, the 64-row chunk c belongs to system chunk_sys[c], whose rows are
+// skipped while sys_done[that system] is nonzero.
+constexpr int SKIP_CHUNK_ROWS = 64;
+struct Skip {
+    const int *flag;
+    const int *chunk_sys;
+    const int *sys_done;
+};
+__device__ __forceinline__ bool skip_all(const Skip &s) {
+    return s.flag && *reinterpret_cast<const volatile int *>(s.flag);
+}
+__device__ __forceinline__ bool skip_chunk(const Skip &s, int chunk) {
+    return s.chunk_sys && reinterpret_cast<const volatile int *>(s.sys_done)[s.chunk_sys[chunk]];
+}
 
 // FP64 -> FP32, round to nearest even, with integer instructions.  On this GPU
 // the hardware conversion runs on the FP64 pipe (about 1/60 of the FP32 rate),

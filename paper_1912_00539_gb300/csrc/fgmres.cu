@@ -28,9 +28,9 @@ namespace abilu {
 abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st);
 abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
-                            int nl, int nu, abilu_mode mode, cudaStream_t st, const int *skip);
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
-                         double beta, double *y, cudaStream_t st, const int *skip);
+                         double beta, double *y, cudaStream_t st, Skip skip);
 abilu_status ensure_krylov(abilu_factors f, int m);
 int red_ctas();
 
@@ -104,14 +104,14 @@ __device__ __forceinline__ void reduce_partials(const double *partials, int stri
 __global__ void __launch_bounds__(RED_THREADS)
 k_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
            const double *__restrict__ x, double *__restrict__ r_out, SolveState *S,
-           double *partials, int init) {
+           double *partials, int init, int x_is_zero) {
     __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
     const int q = threadIdx.x & 3;
     double v[2] = {0.0, 0.0};
     const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
     for (int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2); i < P.n; i += rows_per_grid) {
         // same arithmetic as the SpMV kernel: one FMA chain over the row's blocks
-        const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1];
+        const int p0 = P.rowptr[i], p1 = x_is_zero ? p0 : P.rowptr[i + 1];  // x = 0: r = b
         double s = 0.0;
         for (int p = p0; p < p1; p++) {
             const int j = __ldg(P.colind + p);
@@ -342,6 +342,7 @@ extern "C" void fgmres_default_opts(fgmres_opts *o) {
     o->build = 1;
     o->init = ABILU_INIT_FROM_A;
     o->reorth = 0;
+    o->zero_guess = 0;
 }
 
 namespace abilu {
@@ -383,7 +384,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     HostStatus *hs = reinterpret_cast<HostStatus *>(f->host_status);
     const int nred = red_ctas();
     const abilu_mode mode = (abilu_mode)opts->mode;
-    const int *skip = &SS->done;
+    const Skip skip{&SS->done, nullptr, nullptr};
     float *v32 = reinterpret_cast<float *>(f->r32);  // NULL for FP64 factors
 
     if (opts->build) {
@@ -392,7 +393,9 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     }
     ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
-    k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 1);
+    if (opts->zero_guess) ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
+    k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 1,
+                                                      opts->zero_guess ? 1 : 0);
     k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
     ABILU_LAUNCH_CHECK("fgmres init");
     cudaEvent_t ev[2];
@@ -429,7 +432,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
         }
         if (ret != ABILU_OK) break;
         k_xupdate<<<counted(nred), RED_THREADS, 0, st>>>(Z, nv2, x, SS);
-        k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 0);
+        k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 0, 0);
         k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres restart"); break; }

@@ -34,6 +34,9 @@ const char *last_error() { return g_msg; }
 
 static unsigned long long g_launches = 0;
 void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+void note_launches(long long d) {
+    __atomic_add_fetch(&g_launches, (unsigned long long)d, __ATOMIC_RELAXED);
+}
 unsigned long long launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 // ------------------------------------------------------------------ scan

@@ -62,8 +62,8 @@ __device__ __forceinline__ double row_dot_blocks(const PatternView &P, const dou
 
 __global__ void __launch_bounds__(SPMV_THREADS)
 k_spmv(PatternView P, const double *__restrict__ A, double alpha, const double *__restrict__ x,
-       double beta, double *__restrict__ y, const int *skip) {
-    if (skip && *reinterpret_cast<const volatile int *>(skip)) return;
+       double beta, double *__restrict__ y, Skip skip) {
+    if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * SPMV_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     const double s = row_dot_blocks(P, A, x, i, q);
@@ -72,7 +72,8 @@ k_spmv(PatternView P, const double *__restrict__ A, double alpha, const double *
 }
 
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
-                         double beta, double *y, cudaStream_t st, const int *skip) {
+                         double beta, double *y, cudaStream_t st, Skip skip) {
+    static_assert(SPMV_ROWS == SKIP_CHUNK_ROWS, "one CTA per 64-row chunk");
     const int grid = (P.n + SPMV_ROWS - 1) / SPMV_ROWS;
     k_spmv<<<counted(grid), SPMV_THREADS, 0, st>>>(P, A, alpha, x, beta, y, skip);
     ABILU_LAUNCH_CHECK("k_spmv");

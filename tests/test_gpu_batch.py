@@ -105,3 +105,47 @@ def test_batch_rejects_bad_input(ab):
     ci[0], ci[1] = int(s.colind[1]), int(s.colind[0])   # unsorted row
     with pytest.raises(ab.AbiluError):
         ab.Batch([(rp, ci)])
+
+
+@pytest.mark.parametrize("mode", ["sync", "async"])
+def test_graph_and_host_driven_cycles_agree(ab, mode, monkeypatch):
+    """The replayed cycle graph (conditional steps) and the host-driven loop run
+    the same kernels on the same data; in sync mode the results are identical."""
+    import torch
+    systems = _systems()[:4]
+    devs = [_dev(s) for s in systems]
+    out = {}
+    for graph in (True, False):
+        if graph:
+            monkeypatch.delenv("ABILU_NO_GRAPH", raising=False)
+        else:
+            monkeypatch.setenv("ABILU_NO_GRAPH", "1")
+        batch = ab.Batch([(d[0], d[1]) for d in devs], dtype="f32")
+        for k, d in enumerate(devs):
+            batch.set_system(k, d[2], d[3])
+        opts = dict(restart=10, rtol=1e-6, build_sweeps=4, apply_sweeps_lower=3,
+                    apply_sweeps_upper=3, mode=mode)
+        runs = []
+        for rep in range(2):                  # second solve replays the captured graph
+            l0 = ab.kernel_launches()
+            res = batch.solve(**opts)
+            torch.cuda.synchronize()
+            launches = ab.kernel_launches() - l0
+            xs = []
+            for k, d in enumerate(devs):
+                x = torch.empty_like(d[3])
+                batch.solution(k, x)
+                xs.append(x.cpu().numpy())
+            runs.append((res, xs, launches))
+        out[graph] = runs
+        del batch
+    for graph, runs in out.items():
+        for res, xs, launches in runs:
+            assert all(r.converged for r in res)
+            # at least init + one cycle of every step's kernels
+            assert launches >= 10, launches
+    if mode == "sync":
+        for (rg, xg, _), (rh, xh, _) in zip(out[True], out[False]):
+            assert [r.iters for r in rg] == [r.iters for r in rh]
+            for a, b in zip(xg, xh):
+                np.testing.assert_array_equal(a, b)

@@ -451,3 +451,37 @@ def test_fp64_to_fp32_rounding_is_exact(ab):
     ref = vals.astype(np.float32).astype(np.float64)
     got = X.cpu().numpy()
     np.testing.assert_array_equal(got.view(np.int64), ref.view(np.int64))
+
+
+def test_zero_guess_equals_explicit_zero_start(ab):
+    """zero_guess overwrites x and starts from r0 = b; in synchronous mode the
+    result is bit for bit that of an explicit x0 = 0 (A 0 = 0 exactly)."""
+    import torch
+    d = Dev(ab, gen.small_system(20, 15, seed=12))
+    fac = ab.Factors(d.pat, "f32")
+    x0 = d.vec()
+    r0 = ab.fgmres_solve(d.pat, d.A, fac, d.b, x0, build_sweeps=3, mode="sync")
+    x1 = d.vec(np.full((d.s.n, 4), 7.0))
+    r1 = ab.fgmres_solve(d.pat, d.A, fac, d.b, x1, build_sweeps=3, mode="sync", zero_guess=True)
+    assert r0.iters == r1.iters
+    assert torch.equal(x0, x1)
+
+
+@pytest.mark.parametrize("dtype,nsweeps", [("f64", 0), ("f64", 3), ("f32", 3)])
+def test_diagnostics_match_oracle(ab, dsys, dtype, nsweeps):
+    """GPU diagnostics (Sec. 6.2 quantities) equal the oracle's evaluated on the
+    same (exported) factors."""
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, dtype)
+    fac.build(dsys.A, nsweeps, mode="sync")
+    X, D = fac.export()
+    Xn, Dn = X.cpu().numpy(), D.cpu().numpy()
+    g = fac.diagnostics(dsys.A)
+    r_ref = oracle.ilu_residual_l1(s.rowptr, s.colind, s.vals, Xn)
+    d_ref = oracle.lu_defect_max(s.rowptr, s.colind, s.vals, Xn)
+    ln, un = oracle.jacobi_norms(s.rowptr, s.colind, Xn, Dn)
+    scale = np.abs(s.vals).max()
+    assert abs(g["ilu_residual_l1"] - r_ref) <= 1e-9 * max(r_ref, 1.0) + 1e-9 * scale
+    assert abs(g["lu_defect_max"] - d_ref) <= 1e-11 * scale
+    assert abs(g["jacobi_norm_L"] - ln) <= 1e-12 * max(ln, 1.0)
+    assert abs(g["jacobi_norm_U"] - un) <= 1e-10 * max(un, 1.0)

@@ -92,3 +92,14 @@ def test_batch_specs_ranges():
     cells = np.array([2 * s["nx"] * s["ny"] for s in specs])
     assert len(specs) == 64 and cells.min() >= 1500 and cells.max() <= 230000
     assert all(10 <= s["cfl"] <= 1e4 for s in specs)
+
+
+def test_serving_footprint_model():
+    import __graft_entry__ as g
+    g._build_ext().build()              # the package loads the CUDA library (no GPU call here)
+    from paper_1912_00539_gb300.serving import footprint_bytes as fb
+    small, big = fb(1000, 4000), fb(100000, 400000)
+    assert 90 * small < big < 110 * small
+    assert fb(1000, 4000, "f64") > fb(1000, 4000, "f32") > fb(1000, 4000, "bf16")
+    # 512x512 grid: a couple of GB
+    assert 1e9 < fb(524288, 2095104) < 4e9
