@@ -9,10 +9,14 @@
 // (Algorithm 5; backward row order for U), chunks of rows handed out in order
 // by a ticket counter.
 //
-// Sync-mode shortcuts that do not change the result: from y^0 = 0 the first
-// lower sweep gives y^1 = b exactly, so it is not run (the second sweep reads b
-// as y^1); and x^1 = Dinv_i y_i needs only row i, so it is fused into the last
-// lower sweep.  The last upper sweep writes the FP64 output directly.  With
+// Shortcuts that do not change the result: from y^0 = 0 the first lower sweep
+// gives y^1 = b exactly, so it is not run (the second sweep reads b as y^1);
+// and x^1 = Dinv_i y_i needs only row i, so it is fused into the last lower
+// sweep.  The last upper sweep writes the FP64 output directly.  In ASYNC mode
+// the same first updates are taken: y = b and x^1 = Dinv y are the first
+// update of every unknown with every read seeing the zero initial guess, one
+// of the orders an asynchronous sweep may run in, and the in-place sweeps then
+// perform the remaining n_L - 1 and n_U - 1 updates of each unknown.  With
 // FP32/BF16 factors the FP64 right-hand side is converted to FP32 once per
 // application (FGMRES hands over the FP32 copy it already wrote).
 //
@@ -27,6 +31,10 @@ namespace abilu {
 
 constexpr int APPLY_THREADS = 256;
 constexpr int APPLY_ROWS = APPLY_THREADS / 4;
+// The in-place sweeps are bound by the latency of their dependent loads, so
+// the FP32 ones keep 8 CTAs (64 warps) resident per SM: 32 registers a thread
+// (FP64 ones, with twice the registers per value, 6).
+template <typename VT> constexpr int async_min_ctas() { return sizeof(VT) == 4 ? 8 : 6; }
 
 template <typename T> struct ApplyArith { using VT = float; };
 template <> struct ApplyArith<double> { using VT = double; };
@@ -125,11 +133,14 @@ template <> __device__ __forceinline__ void st_vol<double>(double *p, double v) 
     asm volatile("st.volatile.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
 }
 
-// In-place lower sweeps over all nsweeps, y must hold 0 on entry.
+// In-place lower sweeps (nsweeps more updates of every row); y holds the first
+// update (y = b) on entry.  The last update of a row also forms x^1 = Dinv y
+// (into x1, or into z as FP64 when it is the final upper result).
 template <typename T, typename VT>
-__global__ void __launch_bounds__(APPLY_THREADS)
+__global__ void __launch_bounds__(APPLY_THREADS, async_min_ctas<VT>())
 k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, VT *y,
-              int nsweeps, unsigned long long *ticket, Skip skip) {
+              int nsweeps, const T *__restrict__ D, VT *__restrict__ x1, double *__restrict__ z,
+              unsigned long long *ticket, Skip skip) {
     if (skip_all(skip)) return;
     __shared__ unsigned long long s_t;
     const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
@@ -141,18 +152,47 @@ k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, 
         const long long t = (long long)s_t;
         __syncthreads();
         if (t >= total) break;
+        const bool last = t / nchunks == nsweeps - 1;
         const int chunk = (int)(t % nchunks);
         const int i = chunk * APPLY_ROWS + (threadIdx.x >> 2);
-        if (i < P.n && !skip_chunk(skip, chunk)) {
+        if (i < P.n && !skip_chunk(skip, chunk)) {  // quads of a row stay together
             const VT s = row_sweep_sum<true>(r[(size_t)i * BS + q], L, P.lcol, P.lrow[i],
                                              P.lrow[i + 1], (const VT *)y);
             st_vol(y + (size_t)i * BS + q, s);
+            if (last && (x1 || z)) {
+                const VT x = dinv_times<T, VT>(D, i, s);
+                if (x1) x1[(size_t)i * BS + q] = x;
+                if (z) z[(size_t)i * BS + q] = to_f64v(x);
+            }
         }
     }
 }
 
-// In-place upper sweeps, chunks in backward order; x must hold 0 on entry.
-// The last sweep of each chunk also writes the FP64 result z.
+// First update of the asynchronous application: y = b, and when no further
+// lower sweep runs also x^1 = Dinv b (into x1 or z); resets the two ticket
+// counters of the in-place kernels that follow.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(APPLY_THREADS)
+k_async_start(PatternView P, const T *__restrict__ D, const VT *__restrict__ r,
+              VT *__restrict__ y, VT *__restrict__ x1, double *__restrict__ z,
+              unsigned long long *tickets, Skip skip) {
+    if (skip_all(skip)) return;
+    if (blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0ull;
+    if (skip_chunk(skip, blockIdx.x)) return;
+    const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    if (i >= P.n) return;
+    const VT b = r[(size_t)i * BS + q];
+    y[(size_t)i * BS + q] = b;
+    if (x1 || z) {
+        const VT x = dinv_times<T, VT>(D, i, b);
+        if (x1) x1[(size_t)i * BS + q] = x;
+        if (z) z[(size_t)i * BS + q] = to_f64v(x);
+    }
+}
+
+// In-place upper sweeps (nsweeps more updates of every row), chunks in
+// backward order; x holds x^1 on entry.  The last sweep of each chunk also
+// writes the FP64 result z.
 template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
@@ -256,27 +296,31 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
     if (mode == ABILU_ASYNC) {
         const long long nchunks = grid;
         const long long n4 = (long long)P.n * BS;
-        const int zgrid = (int)((n4 + 255) / 256);
-        k_zero<VT><<<counted(zgrid), 256, 0, st>>>(y[0], n4, skip);
-        if (nl > 0) {
-            k_zero<unsigned long long><<<counted(1), 32, 0, st>>>(f->ctr + 1, 1, skip);
+        if (nl == 0 || nu == 0) {  // y = 0, or no upper update: z = x^0 = 0
+            k_zero<double><<<counted((int)((n4 + 255) / 256)), 256, 0, st>>>(z, n4, skip);
+            ABILU_LAUNCH_CHECK("apply async");
+            return ABILU_OK;
+        }
+        unsigned long long *tk = f->ctr + 2;   // [0] lower, [1] upper tickets
+        VT *x1 = nu >= 2 ? x[0] : nullptr;
+        double *z1 = nu == 1 ? z : nullptr;
+        k_async_start<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
+            P, D, rv, y[0], nl == 1 ? x1 : nullptr, nl == 1 ? z1 : nullptr, tk, skip);
+        ABILU_LAUNCH_CHECK("k_async_start");
+        if (nl >= 2) {
             const int ctas_l = lower_async_ctas<T, VT>();
             int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
-            k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl, f->ctr + 1, skip);
+            k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl - 1, D, x1,
+                                                                       z1, tk, skip);
             ABILU_LAUNCH_CHECK("k_lower_async");
         }
-        if (nu > 0) {
-            k_zero<VT><<<counted(zgrid), 256, 0, st>>>(x[0], n4, skip);
-            k_zero<unsigned long long><<<counted(1), 32, 0, st>>>(f->ctr + 1, 1, skip);
+        if (nu >= 2) {
             const int ctas_u = upper_async_ctas<T, VT>();
             int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
-            k_upper_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, U, D, y[0], x[0], z, nu,
-                                                                       f->ctr + 1, skip);
+            k_upper_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, U, D, y[0], x[0], z, nu - 1,
+                                                                       tk + 1, skip);
             ABILU_LAUNCH_CHECK("k_upper_async");
-        } else {
-            k_zero<double><<<counted(zgrid), 256, 0, st>>>(z, n4, skip);
         }
-        ABILU_LAUNCH_CHECK("apply async");
         return ABILU_OK;
     }
 

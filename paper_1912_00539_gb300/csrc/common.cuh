@@ -98,7 +98,10 @@ namespace abilu {
 // Early exit of the row kernels.  `flag`: the whole launch returns when *flag
 // is nonzero (an FGMRES cycle that has ended).  `chunk_sys`/`sys_done`: in a
 // batch, the 64-row chunk c belongs to system chunk_sys[c], whose rows are
-// skipped while sys_done[that system] is nonzero.
+// skipped while sys_done[that system] is nonzero.  The flags are written only
+// by earlier kernels of the stream, so they are read with ordinary (L1-cached)
+// loads: a volatile load from every warp of a large grid queues on the one L2
+// line that holds the flag.
 constexpr int SKIP_CHUNK_ROWS = 64;
 struct Skip {
     const int *flag;
@@ -106,10 +109,10 @@ struct Skip {
     const int *sys_done;
 };
 __device__ __forceinline__ bool skip_all(const Skip &s) {
-    return s.flag && *reinterpret_cast<const volatile int *>(s.flag);
+    return s.flag && *s.flag;
 }
 __device__ __forceinline__ bool skip_chunk(const Skip &s, int chunk) {
-    return s.chunk_sys && reinterpret_cast<const volatile int *>(s.sys_done)[s.chunk_sys[chunk]];
+    return s.chunk_sys && s.sys_done[s.chunk_sys[chunk]];
 }
 
 // FP64 -> FP32, round to nearest even, with integer instructions.  On this GPU

@@ -160,7 +160,7 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
 // the right-hand side the next preconditioner application reads
 __global__ void __launch_bounds__(RED_THREADS)
 k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *S) {
-    if (*reinterpret_cast<volatile int *>(&S->done)) return;
+    if (S->done) return;   // set by an earlier kernel: a plain load
     const double s = S->hn_inv;
     const double2 *a = reinterpret_cast<const double2 *>(vin);
     double2 *o = reinterpret_cast<double2 *>(vout);
@@ -200,7 +200,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
 __global__ void __launch_bounds__(RED_THREADS)
 k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
        SolveState *S, double *partials, int pass) {
-    if (*reinterpret_cast<volatile int *>(&S->done)) return;
+    if (S->done) return;   // set by an earlier kernel: a plain load
     __shared__ double sh_w[RED_WARPS * TILE], sh_o[TILE];
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const double2 *V2 = reinterpret_cast<const double2 *>(V);
@@ -232,7 +232,7 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
 __global__ void __launch_bounds__(RED_THREADS)
 k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict__ w,
          SolveState *S, double *partials, int pass, int final_pass) {
-    if (*reinterpret_cast<volatile int *>(&S->done)) return;
+    if (S->done) return;   // set by an earlier kernel: a plain load
     __shared__ double sh_h[MAXM + 1];
     __shared__ double sh_w[RED_WARPS], sh_o[1];
     const int jp1 = j + 1;

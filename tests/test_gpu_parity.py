@@ -287,6 +287,31 @@ def test_async_apply_exact_with_enough_sweeps(ab, dsys):
     assert _rel(z.cpu().numpy(), z_ref) < 1e-12
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_async_apply_first_updates(ab, dsys, dtype):
+    """The asynchronous application starts with the first update of every
+    unknown read from the zero guesses (y = r, x^1 = Dinv r): with one sweep
+    per factor it is that update exactly, the synchronous result bit for bit;
+    with no lower or no upper sweep the result is zero.  Against the oracle's
+    sweeps on the exported factors: z = Dinv r."""
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, dtype)
+    fac.build(dsys.A, 2, mode="sync")
+    r = np.random.default_rng(17).standard_normal((s.n, 4))
+    za, zs = dsys.vec(), dsys.vec()
+    fac.apply(dsys.vec(r), za, 1, 1, mode="async")
+    fac.apply(dsys.vec(r), zs, 1, 1, mode="sync")
+    np.testing.assert_array_equal(za.cpu().numpy(), zs.cpu().numpy())
+    if dtype == "f64":
+        X, D = fac.export()
+        z_ref = oracle.apply(s.rowptr, s.colind, X.cpu().numpy(), D.cpu().numpy(), r, 1, 1)
+        assert _rel(za.cpu().numpy(), z_ref) < 1e-14
+    for nl, nu in ((0, 2), (2, 0)):
+        z = dsys.vec(np.ones((s.n, 4)))
+        fac.apply(dsys.vec(r), z, nl, nu, mode="async")
+        assert not z.cpu().numpy().any()
+
+
 # ------------------------------------------------------------------- FGMRES
 
 @pytest.mark.parametrize("dtype,mode", [("f64", "sync"), ("f32", "sync"), ("f32", "async"),
