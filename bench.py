@@ -394,7 +394,7 @@ def run_serving(args, n_requests=48):
     out = {"workload": f"{n_requests} requests, 4k-1M cells, 5 updates each",
            "cells": int(sum(r.n for r in unit)), "generation_s": round(tgen, 1),
            "single_slot_capacity_solves_per_s": round(cap["solves_per_s"], 1)}
-    for frac in (0.5, 1.0):
+    for frac in (0.25, 0.5, 1.0, 1.5):
         res, wall = serving.Server(budget, slots=8, dtype="f32", mode=args.mode,
                                    **cfg).run(at_rate(frac * cap_req_rate))
         out[f"f32_rate_{frac}x"] = {k: ({kk: _r(vv) for kk, vv in v.items()} if isinstance(v, dict)
