@@ -73,14 +73,21 @@ __device__ __forceinline__ bool inv4_adj(const double *a, double *r) {
 // Inverse of a 4x4 FP32 block accurate to FP32 rounding without FP64
 // instructions (FP64 and FP64<->FP32 conversions share this GPU's slow FP64
 // pipe).  The quad holding the block (thread q owns row q) computes
-//   X0 = adj(U)/det(U) in FP32 (every thread forms the minors; thread q its row),
+//   X0 = adj(U)/det(U) in FP32 (thread q: row q of adj(U), the cofactors of
+//        column q),
 //   R  = I - U X0 with error-free products and sums (TwoProd by FMA, TwoSum),
 //   X1 = X0 + X0 R  (one Newton step),
 // so X1 carries an error of about (cond(U) u)^2 + u, u = 2^-24: the FP32
 // rounding of the exact inverse for every block with cond(U) << 1/sqrt(u).
-// det == 0 or non-finite: singular, replaced by the identity (modified
-// iteration, Sec. 4.2); all four threads reach the same decision.
-// `sh` is this quad's 48-float scratch (U, X0, R), shared within the warp.
+// Thread q's cofactors are the 3x3 minors of the other three columns, taken
+// in the cyclic order q+1, q+2, q+3 (an even permutation of their natural
+// order, so every minor keeps its sign): the same instructions in all four
+// threads, no branch on q.  det(U) is thread 0's expansion along column 0,
+// shared by the quad, so all four threads reach the same singular decision
+// (det == 0 or non-finite: replaced by the identity, modified iteration,
+// Sec. 4.2).  `sh` is this quad's scratch of QUAD_SCRATCH floats (U, X0, R);
+// the stride of 52 floats puts the 8 quads of a warp on distinct banks.
+constexpr int QUAD_SCRATCH = 52;
 __device__ __forceinline__ bool quad_inv4_refined(const float u_row[4], float x_row[4],
                                                   float *sh) {
     const int q = threadIdx.x & 3;
@@ -88,19 +95,28 @@ __device__ __forceinline__ bool quad_inv4_refined(const float u_row[4], float x_
     float *shU = sh, *shX = sh + 16, *shR = sh + 32;
     reinterpret_cast<float4 *>(shU)[q] = make_float4(u_row[0], u_row[1], u_row[2], u_row[3]);
     __syncwarp(m);
-    float a[16];
+    const int k0 = (q + 1) & 3, k1 = (q + 2) & 3, k2 = (q + 3) & 3;
+    float b0[4], b1[4], b2[4], cq[4];   // columns k0, k1, k2 and q of U
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        float4 t = reinterpret_cast<const float4 *>(shU)[k];
-        a[4 * k] = t.x; a[4 * k + 1] = t.y; a[4 * k + 2] = t.z; a[4 * k + 3] = t.w;
+    for (int r = 0; r < 4; r++) {
+        b0[r] = shU[4 * r + k0];
+        b1[r] = shU[4 * r + k1];
+        b2[r] = shU[4 * r + k2];
+        cq[r] = shU[4 * r + q];
     }
-    float s0 = a[0] * a[5] - a[4] * a[1], s1 = a[0] * a[6] - a[4] * a[2];
-    float s2 = a[0] * a[7] - a[4] * a[3], s3 = a[1] * a[6] - a[5] * a[2];
-    float s4 = a[1] * a[7] - a[5] * a[3], s5 = a[2] * a[7] - a[6] * a[3];
-    float c5 = a[10] * a[15] - a[14] * a[11], c4 = a[9] * a[15] - a[13] * a[11];
-    float c3 = a[9] * a[14] - a[13] * a[10], c2 = a[8] * a[15] - a[12] * a[11];
-    float c1 = a[8] * a[14] - a[12] * a[10], c0 = a[8] * a[13] - a[12] * a[9];
-    float det = s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
+    // 2x2 minors of columns (k1, k2), rows (a, b)
+    const float m01 = b1[0] * b2[1] - b2[0] * b1[1], m02 = b1[0] * b2[2] - b2[0] * b1[2];
+    const float m03 = b1[0] * b2[3] - b2[0] * b1[3], m12 = b1[1] * b2[2] - b2[1] * b1[2];
+    const float m13 = b1[1] * b2[3] - b2[1] * b1[3], m23 = b1[2] * b2[3] - b2[2] * b1[3];
+    // minor of (row r, column q), then cofactor sign (-1)^(r+q)
+    const float sg = (q & 1) ? -1.0f : 1.0f;
+    float x0[4];
+    x0[0] = sg * (b0[1] * m23 - b0[2] * m13 + b0[3] * m12);
+    x0[1] = -sg * (b0[0] * m23 - b0[2] * m03 + b0[3] * m02);
+    x0[2] = sg * (b0[0] * m13 - b0[1] * m03 + b0[3] * m01);
+    x0[3] = -sg * (b0[0] * m12 - b0[1] * m02 + b0[2] * m01);
+    const float det_q = cq[0] * x0[0] + cq[1] * x0[1] + cq[2] * x0[2] + cq[3] * x0[3];
+    const float det = __shfl_sync(m, det_q, (threadIdx.x & 31) & ~3);
     if (det == 0.0f || !isfinite(det)) {
 #pragma unroll
         for (int c = 0; c < 4; c++) x_row[c] = (c == q) ? 1.0f : 0.0f;
@@ -108,21 +124,6 @@ __device__ __forceinline__ bool quad_inv4_refined(const float u_row[4], float x_
         return true;
     }
     const float id = 1.0f / det;
-    // row q of adj(U): the cofactors of column q of U
-    float x0[4];
-    if (q == 0) {
-        x0[0] = a[5] * c5 - a[6] * c4 + a[7] * c3;   x0[1] = -a[1] * c5 + a[2] * c4 - a[3] * c3;
-        x0[2] = a[13] * s5 - a[14] * s4 + a[15] * s3; x0[3] = -a[9] * s5 + a[10] * s4 - a[11] * s3;
-    } else if (q == 1) {
-        x0[0] = -a[4] * c5 + a[6] * c2 - a[7] * c1;   x0[1] = a[0] * c5 - a[2] * c2 + a[3] * c1;
-        x0[2] = -a[12] * s5 + a[14] * s2 - a[15] * s1; x0[3] = a[8] * s5 - a[10] * s2 + a[11] * s1;
-    } else if (q == 2) {
-        x0[0] = a[4] * c4 - a[5] * c2 + a[7] * c0;    x0[1] = -a[0] * c4 + a[1] * c2 - a[3] * c0;
-        x0[2] = a[12] * s4 - a[13] * s2 + a[15] * s0; x0[3] = -a[8] * s4 + a[9] * s2 - a[11] * s0;
-    } else {
-        x0[0] = -a[4] * c3 + a[5] * c1 - a[6] * c0;   x0[1] = a[0] * c3 - a[1] * c1 + a[2] * c0;
-        x0[2] = -a[12] * s3 + a[13] * s1 - a[14] * s0; x0[3] = a[8] * s3 - a[9] * s1 + a[10] * s0;
-    }
 #pragma unroll
     for (int c = 0; c < 4; c++) x0[c] *= id;
     reinterpret_cast<float4 *>(shX)[q] = make_float4(x0[0], x0[1], x0[2], x0[3]);
@@ -284,7 +285,7 @@ __device__ __forceinline__ void build_finish_rows(int row0, int n, const typenam
     if constexpr (sizeof(T) < 8) {
         if (i < n) {
             float d[4];
-            if (quad_inv4_refined(u, d, sh_q + (threadIdx.x >> 2) * 48) && q == 0)
+            if (quad_inv4_refined(u, d, sh_q + (threadIdx.x >> 2) * QUAD_SCRATCH) && q == 0)
                 atomicAdd(nsing, 1ull);
             st_row_sel<VOL>(Dout + (size_t)i * BB + q * BS, d);
             if (Udiag) st_row_sel<false>(Udiag + (size_t)i * BB + q * BS, u);
@@ -301,18 +302,32 @@ __device__ __forceinline__ void build_finish_rows(int row0, int n, const typenam
 // shared memory of the build kernels: FP64 inversion scratch or FP32 quad scratch
 template <typename T> struct BuildShared {
     static constexpr int D = sizeof(T) == 8 ? BUILD_ROWS * BB : 1;
-    static constexpr int F = sizeof(T) == 8 ? 1 : BUILD_ROWS * 48;
+    static constexpr int F = sizeof(T) == 8 ? 1 : BUILD_ROWS * QUAD_SCRATCH;
 };
 
 // ---- block work items (FP32/BF16 factors)
 // The block-asynchronous iteration updates one block per step (Eq.
 // async_blockilu_fp: the update function ranges over the blocks), so a work
 // item here is one block of the pattern's work list, handled by one quad.  Its
-// dependency chain is short (work record -> A row, pair range, Dinv_j ->
-// pairs -> compute), and there are four times more of them in flight than
-// block rows, which is what hides memory latency on this GPU.
+// dependency chain is two loads deep: the 32-byte record and the item's FP32 A
+// row (stored at the item's index) are read together, then Dinv_j or the rows
+// of L_ik and U_kj that the record's inline pairs name (a third level only for
+// blocks with more than two pairs).  There are four times more items in
+// flight than block rows, which is what hides memory latency on this GPU.
 constexpr int WORK_PER_CTA = BUILD_THREADS / 4;
 static_assert(WORK_PER_CTA == WORK_CHUNK, "work list chunks are sorted per CTA");
+static_assert(sizeof(WorkItem) == 32, "work records are two 16-byte loads");
+
+// s -= L_ik U_kj for the quad's block (thread q: row q); u's row k lives in thread k
+__device__ __forceinline__ void sub_product(float s[4], const float l[4], const float u[4]) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[c] += l[k] * qshfl(u[c], k);
+#pragma unroll
+    for (int c = 0; c < 4; c++) s[c] -= acc[c];
+}
 
 template <typename T, bool VOL>
 __device__ __forceinline__ void build_block(const PatternView &P, int w,
@@ -320,24 +335,27 @@ __device__ __forceinline__ void build_block(const PatternView &P, int w,
                                             const T *Uin, const T *Din, T *Lout, T *Uout, T *Dout,
                                             T *Udiag, float *sh_q, unsigned long long *nsing) {
     const int q = threadIdx.x & 3;
-    const int4 rec = P.work[w];
-    const int p = rec.x, j = rec.y, dst = rec.z, kind = rec.w;
+    const WorkItem it = P.work[w];
     float s[4], d[4];
-    ld_row(A32 + (size_t)p * BB + q * BS, s);
-    const int t0 = P.pair_ptr[p], t1 = P.pair_ptr[p + 1];
-    if (kind == WORK_L) ld_row_sel<VOL>(Din + (size_t)j * BB + q * BS, d);
-    for (int t = t0; t < t1; t++) {
-        const int2 pr = P.pairs[t];
-        float l[4], u[4];
-        ld_row_sel<VOL>(Lin + (size_t)pr.x * BB + q * BS, l);  // row q of L_ik
-        ld_row_sel<VOL>(Uin + (size_t)pr.y * BB + q * BS, u);  // row q of U_kj
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-#pragma unroll
-            for (int c = 0; c < 4; c++) acc[c] += l[k] * qshfl(u[c], k);
-#pragma unroll
-        for (int c = 0; c < 4; c++) s[c] -= acc[c];
+    ld_row(A32 + (size_t)w * BB + q * BS, s);
+    const int kind = it.kind_np & 3, np = it.kind_np >> 2, dst = it.dst;
+    if (kind == WORK_L) ld_row_sel<VOL>(Din + (size_t)it.j * BB + q * BS, d);
+    if (np > 0) {  // products in pair order (ascending k)
+        float l0[4], u0[4], l1[4], u1[4];
+        ld_row_sel<VOL>(Lin + (size_t)it.pr[0].x * BB + q * BS, l0);  // row q of L_ik
+        ld_row_sel<VOL>(Uin + (size_t)it.pr[0].y * BB + q * BS, u0);  // row q of U_kj
+        if (np > 1) {
+            ld_row_sel<VOL>(Lin + (size_t)it.pr[1].x * BB + q * BS, l1);
+            ld_row_sel<VOL>(Uin + (size_t)it.pr[1].y * BB + q * BS, u1);
+        }
+        sub_product(s, l0, u0);
+        if (np > 1) sub_product(s, l1, u1);
+        for (int t = 2; t < np; t++) {
+            const int2 pr = P.pairs[it.t0 + t];
+            ld_row_sel<VOL>(Lin + (size_t)pr.x * BB + q * BS, l0);
+            ld_row_sel<VOL>(Uin + (size_t)pr.y * BB + q * BS, u0);
+            sub_product(s, l0, u0);
+        }
     }
     if (kind == WORK_L) {  // L_ij = S Dinv_j; row k of Dinv_j lives in thread k
         float o[4];
@@ -358,16 +376,16 @@ __device__ __forceinline__ void build_block(const PatternView &P, int w,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BUILD_THREADS)
+__global__ void __launch_bounds__(BUILD_THREADS, 6)   // 40 registers: measured fastest
 k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__restrict__ Lin,
                     const T *__restrict__ Uin, const T *__restrict__ Din, T *__restrict__ Lout,
                     T *__restrict__ Uout, T *__restrict__ Dout, T *__restrict__ Udiag,
                     unsigned long long *nsing) {
-    __shared__ __align__(16) float sh_q[WORK_PER_CTA * 48];
+    __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
     const int w = blockIdx.x * WORK_PER_CTA + (threadIdx.x >> 2);
     if (w >= P.nwork) return;  // whole quads leave together
     build_block<T, false>(P, w, A32, Lin, Uin, Din, Lout, Uout, Dout, Udiag,
-                          sh_q + (threadIdx.x >> 2) * 48, nsing);
+                          sh_q + (threadIdx.x >> 2) * QUAD_SCRATCH, nsing);
 }
 
 // In place.  Each warp takes tickets t = 0 .. nsweeps*nchunks-1 in order from
@@ -378,17 +396,17 @@ k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__res
 constexpr int WARP_CHUNK = 32;
 
 template <typename T>
-__global__ void __launch_bounds__(BUILD_THREADS, 5)
+__global__ void __launch_bounds__(BUILD_THREADS, 5)   // 48 registers: measured fastest (4, 6 slower)
 k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T *D, T *Udiag,
                      int nsweeps, int max_warps, unsigned long long *nsing,
                      unsigned long long *ticket) {
-    __shared__ __align__(16) float sh_q[WORK_PER_CTA * 48];
+    __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
     // at most one warp per chunk: more would sweep the same blocks at once
     if (blockIdx.x * (BUILD_THREADS / 32) + (threadIdx.x >> 5) >= max_warps) return;
     const long long nchunks = (P.nwork + WARP_CHUNK - 1) / WARP_CHUNK;
     const long long total = nchunks * nsweeps;
     const int lane = threadIdx.x & 31;
-    float *myq = sh_q + (threadIdx.x >> 2) * 48;
+    float *myq = sh_q + (threadIdx.x >> 2) * QUAD_SCRATCH;
     for (;;) {
         unsigned long long tk = 0;
         if (lane == 0) tk = atomicAdd(ticket, 1ull);
@@ -482,7 +500,7 @@ k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__
                 if (Uother) st_row(Uother + (size_t)(ub + p - dp - 1) * BB + q * BS, a);
                 continue;
             }
-            if (A32) st_row(A32 + (size_t)p * BB + q * BS, a);
+            if (A32) st_row(A32 + (size_t)P.wpos[p] * BB + q * BS, a);  // work order
             if (!init_from_a) continue;
             if (p < dp) st_row(L + (size_t)(lb + p - p0) * BB + q * BS, a);
             else if (p > dp) st_row(U + (size_t)(ub + p - dp - 1) * BB + q * BS, a);

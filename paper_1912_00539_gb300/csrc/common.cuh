@@ -51,12 +51,24 @@ struct PatternView {
     const int2 *pairs;         // (lpos of L_ik, upos of U_kj)
     // blocks a build sweep updates, in row-major order: every L and diagonal
     // block and the U blocks with product pairs (the others equal A always).
-    // work[w] = {p, j, destination (lpos / i / upos), kind (WORK_L/D/U)}
+    // The FP32 copy of A that the sweeps read is stored in this order, so a
+    // work item's A row is at its index w; wpos[p] = w (-1: constant block).
     int32_t nwork;
-    const int4 *work;
+    const struct WorkItem *work;
+    const int32_t *wpos;
 };
 
 enum : int { WORK_L = 0, WORK_D = 1, WORK_U = 2 };
+
+// One work item of the build sweeps, 32 bytes: everything its loads depend
+// on, so a sweep reads the record, its FP32 A row (at the item's index) and
+// the rows the pairs name without a further lookup.  kind_np = kind | (number
+// of product pairs << 2); pairs t0 .. t0+np-1 of the pair list, the first two
+// repeated inline.
+struct __align__(16) WorkItem {
+    int32_t j, dst, kind_np, t0;
+    int2 pr[2];
+};
 constexpr int WORK_CHUNK = 64;  // work blocks per CTA of the build kernels (<= 64)
 
 }  // namespace abilu

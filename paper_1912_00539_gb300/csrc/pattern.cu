@@ -252,6 +252,27 @@ __global__ void k_pat_work_sort(int nwork, int chunk, int4 *work) {
             if (buf[k].w == order[o]) work[out++] = buf[k];
 }
 
+// After the sort: the 32-byte records the sweeps read (pair range and the
+// first two pairs inline) and wpos[p] = w, where the FP32 copy of A_p goes.
+__global__ void k_pat_work_items(int nwork, const int4 *__restrict__ work,
+                                 const int32_t *__restrict__ pair_ptr,
+                                 const int2 *__restrict__ pairs, int32_t *__restrict__ wpos,
+                                 WorkItem *__restrict__ items) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwork) return;
+    const int4 r = work[w];
+    const int t0 = pair_ptr[r.x], np = pair_ptr[r.x + 1] - t0;
+    WorkItem it;
+    it.j = r.y;
+    it.dst = r.z;
+    it.kind_np = r.w | (np << 2);
+    it.t0 = t0;
+    it.pr[0] = np > 0 ? pairs[t0] : make_int2(0, 0);
+    it.pr[1] = np > 1 ? pairs[t0 + 1] : make_int2(0, 0);
+    items[w] = it;
+    wpos[r.x] = w;
+}
+
 }  // namespace abilu
 
 using namespace abilu;
@@ -382,6 +403,16 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
             TRY(cu(cudaGetLastError(), "k_pat_work_sort"));
         }
     }
+    int32_t *wpos;
+    WorkItem *items;
+    TRY(alloc((void **)&wpos, sizeof(int32_t) * nnzb));
+    TRY(alloc((void **)&items, sizeof(WorkItem) * (nwork > 0 ? nwork : 1)));
+    TRY(cu(cudaMemsetAsync(wpos, 0xFF, sizeof(int32_t) * nnzb, st), "memset wpos"));
+    if (nwork > 0) {
+        k_pat_work_items<<<counted((nwork + 255) / 256), 256, 0, st>>>(nwork, work, pair_ptr, pairs,
+                                                                       wpos, items);
+        TRY(cu(cudaGetLastError(), "k_pat_work_items"));
+    }
     TRY(cu(cudaStreamSynchronize(st), "sync"));
 #undef TRY
     p->v.n = n;
@@ -399,7 +430,8 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     p->v.pair_ptr = pair_ptr;
     p->v.pairs = pairs;
     p->v.nwork = nwork;
-    p->v.work = work;
+    p->v.work = items;
+    p->v.wpos = wpos;
     p->max_row = (int)herr[2];
     *out = p;
     return ABILU_OK;
