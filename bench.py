@@ -237,11 +237,17 @@ def kernel_rooflines(torch, ab, pat, A, fac, s, peak, mode="async"):
     # prepare (warm start): A read once, FP32 copy of the work blocks, constant
     # U blocks (into both buffers for sync builds), index arrays
     ncu_ = c["nu"] - (nw - c["nl"] - N)
+    # plus, after the sweeps, the Dinv-scaled upper blocks (FP32 factors): U and
+    # Dinv read, Us written
     out["build_prepare_f32"] = {"us": t0, "bytes": nnzb * 128 + 4 * (nnzb + 1) + 16 * (N + 1)
-                                + nw * 16 * f + (2 if mode == "sync" else 1) * ncu_ * 16 * f,
+                                + nw * 16 * f + (2 if mode == "sync" else 1) * ncu_ * 16 * f
+                                + 2 * c["nu"] * 16 * f + N * 16 * f + 4 * (N + 1),
                                 "sweeps": 1}
+    # a sweep reads its factor blocks and column indices, the right-hand side and
+    # the gathered neighbour values, and writes its vector; the upper sweeps run
+    # on Us = Dinv U with right-hand side Dinv y, so no Dinv read
     bl = E * (16 * f + 4) + 4 * (N + 1) + 3 * N * 4 * v
-    bu = E * (16 * f + 4) + 16 * f * N + 4 * (N + 1) + 3 * N * 4 * v
+    bu = E * (16 * f + 4) + 4 * (N + 1) + 3 * N * 4 * v
     # both modes take the first update of each factor without a sweep (y = r,
     # x^1 = Dinv y); the sweeps are the difference to one update per factor
     na = APPLY_SWEEPS

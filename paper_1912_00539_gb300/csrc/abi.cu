@@ -81,7 +81,8 @@ extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype,
     const bool narrow = dtype != ABILU_F64;
     const size_t ba = narrow ? rnd(sizeof(float) * BB * (size_t)v.nnzb) : 0;
     const size_t br = narrow ? rnd(sizeof(float) * BS * (size_t)v.n) : 0;
-    const size_t total = 2 * bl + 2 * bu + 3 * bd + 4 * bv + bc + bs + bp + ba + br;
+    const size_t bus = dtype == ABILU_F32 ? bu : 0;   // Dinv-scaled upper blocks
+    const size_t total = 2 * bl + 2 * bu + 3 * bd + 4 * bv + bc + bs + bp + ba + br + bus;
     abilu_factors f = new abilu_factors_s();
     memset(f, 0, sizeof *f);
     f->p = p;
@@ -106,6 +107,7 @@ extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype,
     f->partials = reinterpret_cast<double *>(m); m += bp;
     f->A32 = narrow ? m : nullptr; m += ba;
     f->r32 = narrow ? m : nullptr; m += br;
+    f->Us = bus ? m : nullptr; m += bus;
     e = cudaMemset(f->mem, 0, total);
     if (e == cudaSuccess) e = cudaHostAlloc(&f->host_status, host_status_bytes(), cudaHostAllocMapped);
     if (e != cudaSuccess) { factors_free(f); return cuda_fail(e, "factors_create"); }

@@ -18,13 +18,19 @@
 // of the orders an asynchronous sweep may run in, and the in-place sweeps then
 // perform the remaining n_L - 1 and n_U - 1 updates of each unknown.  With
 // FP32/BF16 factors the FP64 right-hand side is converted to FP32 once per
-// application (FGMRES hands over the FP32 copy it already wrote).
+// application (FGMRES hands over the FP32 copy it already wrote).  With FP32
+// factors the upper sweeps run on the Dinv-scaled blocks Us_ij = Dinv_i U_ij
+// formed once per build: x_i = yh_i - sum_{j>i} Us_ij x_j with yh = Dinv y (formed where
+// x^1 = Dinv y is formed), the same iteration without re-reading Dinv in every
+// sweep.
 //
 // Thread mapping: a quad per block row, thread q computes unknown q of the
 // row: it reads row q of each factor block (one 16-byte load for FP32, 32 for
 // FP64, 8 for BF16; contiguous across the quad) and the neighbour's 4 unknowns
 // (one vector load, shared by the quad).  FP32 and BF16 factors run in FP32;
 // FP64 factors in FP64.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace abilu {
@@ -88,7 +94,7 @@ k_lower_sync(PatternView P, const T *__restrict__ L, const VT *__restrict__ r,
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     const VT s = row_sweep_sum<false>(r[(size_t)i * BS + q], L, P.lcol, P.lrow[i], P.lrow[i + 1], yin);
-    yout[(size_t)i * BS + q] = s;
+    if (yout) yout[(size_t)i * BS + q] = s;
     if (x1 || z) {
         VT x = dinv_times<T, VT>(D, i, s);
         if (x1) x1[(size_t)i * BS + q] = x;
@@ -110,7 +116,8 @@ k_diag_apply(PatternView P, const T *__restrict__ D, const VT *__restrict__ y,
     if (z) z[(size_t)i * BS + q] = to_f64v(x);
 }
 
-template <typename T, typename VT>
+// SCALED: U holds Us = Dinv U and y holds yh = Dinv y, so x = the row sum
+template <typename T, typename VT, bool SCALED>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
              const VT *__restrict__ y, const VT *__restrict__ xin, VT *__restrict__ xout,
@@ -119,7 +126,9 @@ k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     const VT s = row_sweep_sum<false>(y[(size_t)i * BS + q], U, P.ucol, P.urow[i], P.urow[i + 1], xin);
-    VT x = dinv_times<T, VT>(D, i, s);
+    VT x;
+    if constexpr (SCALED) x = s;
+    else x = dinv_times<T, VT>(D, i, s);
     if (xout) xout[(size_t)i * BS + q] = x;
     if (z) z[(size_t)i * BS + q] = to_f64v(x);
 }
@@ -135,12 +144,13 @@ template <> __device__ __forceinline__ void st_vol<double>(double *p, double v) 
 
 // In-place lower sweeps (nsweeps more updates of every row); y holds the first
 // update (y = b) on entry.  The last update of a row also forms x^1 = Dinv y
-// (into x1, or into z as FP64 when it is the final upper result).
+// (into x1, or into z as FP64 when it is the final upper result; with scaled
+// upper blocks also into yh, the upper sweeps' right-hand side).
 template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS, async_min_ctas<VT>())
 k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, VT *y,
-              int nsweeps, const T *__restrict__ D, VT *__restrict__ x1, double *__restrict__ z,
-              unsigned long long *ticket, Skip skip) {
+              int nsweeps, const T *__restrict__ D, VT *__restrict__ x1, VT *__restrict__ yh,
+              double *__restrict__ z, unsigned long long *ticket, Skip skip) {
     if (skip_all(skip)) return;
     __shared__ unsigned long long s_t;
     const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
@@ -162,6 +172,7 @@ k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, 
             if (last && (x1 || z)) {
                 const VT x = dinv_times<T, VT>(D, i, s);
                 if (x1) x1[(size_t)i * BS + q] = x;
+                if (yh) yh[(size_t)i * BS + q] = x;
                 if (z) z[(size_t)i * BS + q] = to_f64v(x);
             }
         }
@@ -174,7 +185,7 @@ k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, 
 template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_async_start(PatternView P, const T *__restrict__ D, const VT *__restrict__ r,
-              VT *__restrict__ y, VT *__restrict__ x1, double *__restrict__ z,
+              VT *__restrict__ y, VT *__restrict__ x1, VT *__restrict__ yh, double *__restrict__ z,
               unsigned long long *tickets, Skip skip) {
     if (skip_all(skip)) return;
     if (blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0ull;
@@ -186,6 +197,7 @@ k_async_start(PatternView P, const T *__restrict__ D, const VT *__restrict__ r,
     if (x1 || z) {
         const VT x = dinv_times<T, VT>(D, i, b);
         if (x1) x1[(size_t)i * BS + q] = x;
+        if (yh) yh[(size_t)i * BS + q] = x;
         if (z) z[(size_t)i * BS + q] = to_f64v(x);
     }
 }
@@ -193,7 +205,7 @@ k_async_start(PatternView P, const T *__restrict__ D, const VT *__restrict__ r,
 // In-place upper sweeps (nsweeps more updates of every row), chunks in
 // backward order; x holds x^1 on entry.  The last sweep of each chunk also
 // writes the FP64 result z.
-template <typename T, typename VT>
+template <typename T, typename VT, bool SCALED>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
               const VT *__restrict__ y, VT *x, double *__restrict__ z, int nsweeps,
@@ -215,7 +227,9 @@ k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
         if (i < P.n && !skip_chunk(skip, chunk)) {  // quads of a row stay together
             const VT s = row_sweep_sum<true>(y[(size_t)i * BS + q], U, P.ucol, P.urow[i],
                                              P.urow[i + 1], (const VT *)x);
-            VT xi = dinv_times<T, VT>(D, i, s);
+            VT xi;
+            if constexpr (SCALED) xi = s;
+            else xi = dinv_times<T, VT>(D, i, s);
             st_vol(x + (size_t)i * BS + q, xi);
             if (last) z[(size_t)i * BS + q] = to_f64v(xi);
         }
@@ -259,7 +273,7 @@ template <typename T, typename VT> static int lower_async_ctas() {
     return c;
 }
 template <typename T, typename VT> static int upper_async_ctas() {
-    static int c = resident_ctas(k_upper_async<T, VT>, APPLY_THREADS);
+    static int c = resident_ctas(k_upper_async<T, VT, std::is_same<T, float>::value>, APPLY_THREADS);
     return c;
 }
 
@@ -274,7 +288,6 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
     const T *D = reinterpret_cast<const T *>(f->D[c]);
     VT *y[2] = {reinterpret_cast<VT *>(f->y[0]), reinterpret_cast<VT *>(f->y[1])};
     VT *x[2] = {reinterpret_cast<VT *>(f->x[0]), reinterpret_cast<VT *>(f->x[1])};
-    const size_t vbytes = sizeof(VT) * (size_t)P.n * BS;
     const int grid = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
 
     // right-hand side in the compute type
@@ -293,69 +306,78 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
         }
     }
 
+    // FP32 factors: upper sweeps on Us = Dinv U with right-hand side yh = Dinv y
+    // (BF16 would round Dinv U to 8 bits and save no bytes)
+    constexpr bool SC = std::is_same<T, float>::value;
+    const T *UU = SC ? reinterpret_cast<const T *>(f->Us) : U;
+    const long long n4 = (long long)P.n * BS;
+    if (nl == 0 || nu == 0) {  // y = 0, or no upper update: z = x^0 = 0
+        k_zero<double><<<counted((int)((n4 + 255) / 256)), 256, 0, st>>>(z, n4, skip);
+        ABILU_LAUNCH_CHECK("apply");
+        return ABILU_OK;
+    }
+
     if (mode == ABILU_ASYNC) {
         const long long nchunks = grid;
-        const long long n4 = (long long)P.n * BS;
-        if (nl == 0 || nu == 0) {  // y = 0, or no upper update: z = x^0 = 0
-            k_zero<double><<<counted((int)((n4 + 255) / 256)), 256, 0, st>>>(z, n4, skip);
-            ABILU_LAUNCH_CHECK("apply async");
-            return ABILU_OK;
-        }
         unsigned long long *tk = f->ctr + 2;   // [0] lower, [1] upper tickets
-        VT *x1 = nu >= 2 ? x[0] : nullptr;
+        VT *x1 = nu >= 2 ? x[0] : nullptr;     // x^1, updated in place by the upper sweeps
+        VT *yh = SC && nu >= 2 ? y[1] : nullptr;
         double *z1 = nu == 1 ? z : nullptr;
         k_async_start<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
-            P, D, rv, y[0], nl == 1 ? x1 : nullptr, nl == 1 ? z1 : nullptr, tk, skip);
+            P, D, rv, y[0], nl == 1 ? x1 : nullptr, nl == 1 ? yh : nullptr, nl == 1 ? z1 : nullptr,
+            tk, skip);
         ABILU_LAUNCH_CHECK("k_async_start");
         if (nl >= 2) {
             const int ctas_l = lower_async_ctas<T, VT>();
             int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
             k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl - 1, D, x1,
-                                                                       z1, tk, skip);
+                                                                       yh, z1, tk, skip);
             ABILU_LAUNCH_CHECK("k_lower_async");
         }
         if (nu >= 2) {
             const int ctas_u = upper_async_ctas<T, VT>();
             int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
-            k_upper_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, U, D, y[0], x[0], z, nu - 1,
-                                                                       tk + 1, skip);
+            k_upper_async<T, VT, SC><<<counted(g), APPLY_THREADS, 0, st>>>(
+                P, UU, D, SC ? y[1] : y[0], x[0], z, nu - 1, tk + 1, skip);
             ABILU_LAUNCH_CHECK("k_upper_async");
         }
         return ABILU_OK;
     }
 
-    // ---- synchronous: y^1 = r (the first sweep from y = 0), y^s in y[s & 1]
-    const VT *yfin;
-    bool x1_done = false;
-    if (nl == 0) {
-        ABILU_CUDA(cudaMemsetAsync(y[0], 0, vbytes, st));
-        yfin = y[0];
-    } else {
-        yfin = rv;
-        for (int s = 2; s <= nl; s++) {
-            const bool fuse = (s == nl) && nu >= 1;
-            VT *x1 = fuse && nu >= 2 ? x[1] : nullptr;
-            double *zz = fuse && nu == 1 ? z : nullptr;
-            k_lower_sync<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, L, rv, yfin, y[s & 1], D,
-                                                                         x1, zz, skip);
-            ABILU_LAUNCH_CHECK("k_lower_sync");
-            yfin = y[s & 1];
-            x1_done = fuse;
-        }
-    }
-    if (nu == 0) {
-        ABILU_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)P.n * BS, st));
-        return ABILU_OK;
-    }
-    if (!x1_done) {
-        k_diag_apply<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
-            P, D, yfin, nu >= 2 ? x[1] : nullptr, nu == 1 ? z : nullptr, skip);
+    // ---- synchronous: y^1 = r (the first sweep from y = 0), y^s in y[s & 1];
+    // x^1 = Dinv y^{n_L} fused into the last lower sweep.  Scaled: that sweep
+    // writes only yh = x^1 (in place of y^{n_L}), and the first upper sweep
+    // reads x^1 from it.
+    const VT *yfin;     // the upper sweeps' right-hand side (y, or yh when scaled)
+    const VT *xfirst;   // x^1
+    if (nl == 1) {      // no lower sweep runs: x^1 = Dinv r
+        VT *x1 = nu >= 2 ? (SC ? y[0] : x[1]) : nullptr;
+        k_diag_apply<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, D, rv, x1,
+                                                                     nu == 1 ? z : nullptr, skip);
         ABILU_LAUNCH_CHECK("k_diag_apply");
+        yfin = SC ? y[0] : rv;
+        xfirst = x1;
+    } else {
+        const VT *yprev = rv;
+        VT *x1 = nullptr;
+        for (int s = 2; s <= nl; s++) {
+            const bool last = s == nl;
+            VT *yout = y[s & 1];
+            if (last) x1 = nu >= 2 ? (SC ? yout : x[1]) : nullptr;
+            k_lower_sync<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
+                P, L, rv, yprev, (last && SC) ? nullptr : yout, D, last ? x1 : nullptr,
+                (last && nu == 1) ? z : nullptr, skip);
+            ABILU_LAUNCH_CHECK("k_lower_sync");
+            yprev = yout;
+        }
+        yfin = yprev;   // y^{n_L}, or yh when scaled (written as x1 into the same buffer)
+        xfirst = x1;
     }
     for (int s = 2; s <= nu; s++) {  // x^s in x[s & 1], the last one to z
         const bool last = s == nu;
-        k_upper_sync<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
-            P, U, D, yfin, x[(s - 1) & 1], last ? nullptr : x[s & 1], last ? z : nullptr, skip);
+        const VT *xin = s == 2 ? xfirst : x[(s - 1) & 1];
+        k_upper_sync<T, VT, SC><<<counted(grid), APPLY_THREADS, 0, st>>>(
+            P, UU, D, yfin, xin, last ? nullptr : x[s & 1], last ? z : nullptr, skip);
         ABILU_LAUNCH_CHECK("k_upper_sync");
     }
     return ABILU_OK;

@@ -516,6 +516,29 @@ k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__
     if (init_from_a) build_finish_rows<T, false>(row0, P.n, ud, D, Udiag, sh_u, sh_d, sh_q, nsing);
 }
 
+// Us_ij = Dinv_i U_ij for every strictly upper block (FP32 factors), once per
+// build: the upper sweeps then read x_i = Dinv_i y_i - sum_j Us_ij x_j
+// (the same iteration as x_i = Dinv_i (y_i - sum_j U_ij x_j), Sec. 4.1) and
+// no longer re-read Dinv_i in every sweep.  A quad per block row, thread q
+// forms row q: sum_k Dinv_i[q][k] U_ij[k][:] with U's rows from the quad.
+template <typename T>
+__global__ void __launch_bounds__(BUILD_THREADS)
+k_scale_upper(PatternView P, const T *__restrict__ U, const T *__restrict__ D, T *__restrict__ Us) {
+    const int i = blockIdx.x * BUILD_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    if (i >= P.n) return;
+    float d[4];
+    ld_row(D + (size_t)i * BB + q * BS, d);
+    for (int l = P.urow[i]; l < P.urow[i + 1]; l++) {
+        float u[4], o[4] = {0.f, 0.f, 0.f, 0.f};
+        ld_row(U + (size_t)l * BB + q * BS, u);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) o[c] += d[k] * qshfl(u[c], k);
+        st_row(Us + (size_t)l * BB + q * BS, o);
+    }
+}
+
 // Export to A's layout in FP64: X[p] = L or U block, U_ii on the diagonal.
 template <typename T>
 __global__ void k_export(PatternView P, const T *__restrict__ L, const T *__restrict__ U,
@@ -634,9 +657,23 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
         P, A, A32, L[c], U[c], mode == ABILU_SYNC ? U[1 - c] : nullptr, D[c], Ud,
         init == ABILU_INIT_FROM_A ? 1 : 0, f->ctr);
     ABILU_LAUNCH_CHECK("k_build_prepare");
-    if (nsweeps == 0) return ABILU_OK;
-    if constexpr (narrow) return block_sweeps_t<T>(f, A32, nsweeps, mode, st);
-    else return sweeps_t<T, double>(f, A, nsweeps, mode, st);
+    if constexpr (narrow) {
+        if (nsweeps > 0) {
+            abilu_status s = block_sweeps_t<T>(f, A32, nsweeps, mode, st);
+            if (s != ABILU_OK) return s;
+        }
+        const int cf = f->cur;
+        if (f->Us && P.nu > 0) {
+            k_scale_upper<T><<<counted(grid), BUILD_THREADS, 0, st>>>(
+                P, reinterpret_cast<const T *>(f->U[cf]), reinterpret_cast<const T *>(f->D[cf]),
+                reinterpret_cast<T *>(f->Us));
+            ABILU_LAUNCH_CHECK("k_scale_upper");
+        }
+        return ABILU_OK;
+    } else {
+        if (nsweeps == 0) return ABILU_OK;
+        return sweeps_t<T, double>(f, A, nsweeps, mode, st);
+    }
 }
 
 template <typename T>

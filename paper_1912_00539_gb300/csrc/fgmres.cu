@@ -35,7 +35,7 @@ abilu_status ensure_krylov(abilu_factors f, int m);
 int red_ctas();
 
 constexpr int MAXM = 64;
-constexpr int TILE = 8;   // Krylov vectors per pass of the dot kernel
+constexpr int TILE = 6;   // Krylov vectors per pass of the dot kernel (64 registers)
 
 struct HostStatus {       // pinned, host-mapped mirror
     int done, iters, converged, kdim, restarts, breakdown;
@@ -183,8 +183,28 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; k++) acc[k] = 0.0;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
-         e += (long long)gridDim.x * blockDim.x) {
+    const long long st = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // narrow tiles: two grid strides per iteration, twice the loads in flight
+    // with the same accumulation order (e, e + st, e + 2 st, ...); wide tiles
+    // already have K + 1 loads in flight (and the registers to match)
+    if constexpr (K <= 4) {
+        for (; e + st < nv2; e += 2 * st) {
+            const double2 wa = w2[e], wb = w2[e + st];
+            double2 va[K], vb[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                va[k] = V2[(size_t)(k0 + k) * nv2 + e];
+                vb[k] = V2[(size_t)(k0 + k) * nv2 + e + st];
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                acc[k] = fma(va[k].y, wa.y, fma(va[k].x, wa.x, acc[k]));
+                acc[k] = fma(vb[k].y, wb.y, fma(vb[k].x, wb.x, acc[k]));
+            }
+        }
+    }
+    for (; e < nv2; e += st) {
         const double2 wv = w2[e];
 #pragma unroll
         for (int k = 0; k < K; k++) {
@@ -196,8 +216,10 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
     if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
 }
 
-// h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2)
-__global__ void __launch_bounds__(RED_THREADS)
+// h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2).  The grid is
+// 4 CTAs per SM and all of them must be resident at once (one wave), so the
+// kernel is held to 64 registers.
+__global__ void __launch_bounds__(RED_THREADS, 4)
 k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
        SolveState *S, double *partials, int pass) {
     if (S->done) return;   // set by an earlier kernel: a plain load
@@ -211,9 +233,7 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
         case 3: dots_tile<3>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
         case 4: dots_tile<4>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
         case 5: dots_tile<5>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        case 6: dots_tile<6>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        case 7: dots_tile<7>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        default: dots_tile<8>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+        default: dots_tile<6>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
         }
     }
     if (!last_cta(S)) return;
@@ -242,8 +262,23 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
     double2 *w2 = reinterpret_cast<double2 *>(w);
     const double2 *V2 = reinterpret_cast<const double2 *>(V);
     double nrm[1] = {0.0};
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
-         e += (long long)gridDim.x * blockDim.x) {
+    const long long st = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; e + st < nv2; e += 2 * st) {  // two grid strides per iteration
+        double2 ta = w2[e], tb = w2[e + st];
+        for (int k = 0; k < jp1; k++) {
+            const double2 va = V2[(size_t)k * nv2 + e], vb = V2[(size_t)k * nv2 + e + st];
+            ta.x -= sh_h[k] * va.x;
+            ta.y -= sh_h[k] * va.y;
+            tb.x -= sh_h[k] * vb.x;
+            tb.y -= sh_h[k] * vb.y;
+        }
+        w2[e] = ta;
+        w2[e + st] = tb;
+        nrm[0] = fma(ta.y, ta.y, fma(ta.x, ta.x, nrm[0]));
+        nrm[0] = fma(tb.y, tb.y, fma(tb.x, tb.x, nrm[0]));
+    }
+    if (e < nv2) {
         double2 t = w2[e];
         for (int k = 0; k < jp1; k++) {
             const double2 v = V2[(size_t)k * nv2 + e];

@@ -60,6 +60,12 @@ __device__ __forceinline__ double row_dot_blocks(const PatternView &P, const dou
     return s;
 }
 
+// PLAIN: y = A x (alpha = 1, beta = 0, decided on the host), the form FGMRES
+// uses: no FP64 instruction beyond the 16 FMA per block (a compare and a
+// multiply per output would add ~12% to this FP64-pipe-bound kernel).
+// Otherwise y = alpha A x + beta y, and beta == 0 never reads y (which may
+// hold NaN).
+template <bool PLAIN>
 __global__ void __launch_bounds__(SPMV_THREADS)
 k_spmv(PatternView P, const double *__restrict__ A, double alpha, const double *__restrict__ x,
        double beta, double *__restrict__ y, Skip skip) {
@@ -68,14 +74,18 @@ k_spmv(PatternView P, const double *__restrict__ A, double alpha, const double *
     if (i >= P.n) return;
     const double s = row_dot_blocks(P, A, x, i, q);
     const size_t o = (size_t)i * BS + q;
-    y[o] = beta == 0.0 ? alpha * s : alpha * s + beta * y[o];
+    if constexpr (PLAIN) y[o] = s;
+    else y[o] = beta == 0.0 ? alpha * s : alpha * s + beta * y[o];
 }
 
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
                          double beta, double *y, cudaStream_t st, Skip skip) {
     static_assert(SPMV_ROWS == SKIP_CHUNK_ROWS, "one CTA per 64-row chunk");
     const int grid = (P.n + SPMV_ROWS - 1) / SPMV_ROWS;
-    k_spmv<<<counted(grid), SPMV_THREADS, 0, st>>>(P, A, alpha, x, beta, y, skip);
+    if (alpha == 1.0 && beta == 0.0)
+        k_spmv<true><<<counted(grid), SPMV_THREADS, 0, st>>>(P, A, alpha, x, beta, y, skip);
+    else
+        k_spmv<false><<<counted(grid), SPMV_THREADS, 0, st>>>(P, A, alpha, x, beta, y, skip);
     ABILU_LAUNCH_CHECK("k_spmv");
     return ABILU_OK;
 }

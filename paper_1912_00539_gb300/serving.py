@@ -66,14 +66,16 @@ class RequestResult:
 
 
 def footprint_bytes(n: int, nnzb: int, dtype: str = "f32", restart: int = 30) -> int:
-    """Device bytes one request holds: A, b, x, pattern arrays, factors (two
-    iterates, inverses, U_ii, FP32 copy of A), sweep vectors and the Krylov
-    basis (V: restart+1 vectors, Z: restart, w)."""
+    """Device bytes one request holds: A, b, x, pattern arrays (including the
+    build's work list and records), factors (two iterates, inverses, U_ii, and
+    for FP32/BF16 the FP32 copy of A, for FP32 the Dinv-scaled upper blocks), sweep
+    vectors and the Krylov basis (V: restart+1 vectors, Z: restart, w)."""
     f = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
     vec = 32 * n
     a = 128 * nnzb
-    pattern = 4 * (2 * nnzb + 7 * n) + 8 * nnzb + 16 * nnzb + 8 * nnzb
-    factors = 2 * 16 * f * nnzb + 3 * 16 * f * n + (64 * nnzb + 16 * n if f < 8 else 0) + 4 * vec
+    pattern = 4 * (2 * nnzb + 7 * n) + 8 * nnzb + 16 * nnzb + 8 * nnzb + 4 * nnzb + 32 * nnzb
+    narrow = (64 * nnzb + 16 * n if f < 8 else 0) + (8 * f * nnzb if f == 4 else 0)
+    factors = 2 * 16 * f * nnzb + 3 * 16 * f * n + narrow + 4 * vec
     krylov = (2 * restart + 2) * vec
     return a + 2 * vec + pattern + factors + krylov
 
