@@ -37,10 +37,10 @@ namespace abilu {
 
 constexpr int APPLY_THREADS = 256;
 constexpr int APPLY_ROWS = APPLY_THREADS / 4;
-// The in-place sweeps are bound by the latency of their dependent loads, so
-// the FP32 ones keep 8 CTAs (64 warps) resident per SM: 32 registers a thread
-// (FP64 ones, with twice the registers per value, 6).
-template <typename VT> constexpr int async_min_ctas() { return sizeof(VT) == 4 ? 8 : 6; }
+// The sweeps are bound by the latency of their dependent loads, so the FP32
+// ones keep 8 CTAs (64 warps) resident per SM: 32 registers a thread (FP64
+// ones, with twice the registers per value, 6).
+template <typename VT> constexpr int sweep_min_ctas() { return sizeof(VT) == 4 ? 8 : 6; }
 
 template <typename T> struct ApplyArith { using VT = float; };
 template <> struct ApplyArith<double> { using VT = double; };
@@ -118,7 +118,7 @@ k_diag_apply(PatternView P, const T *__restrict__ D, const VT *__restrict__ y,
 
 // SCALED: U holds Us = Dinv U and y holds yh = Dinv y, so x = the row sum
 template <typename T, typename VT, bool SCALED>
-__global__ void __launch_bounds__(APPLY_THREADS)
+__global__ void __launch_bounds__(APPLY_THREADS, sweep_min_ctas<VT>())
 k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
              const VT *__restrict__ y, const VT *__restrict__ xin, VT *__restrict__ xout,
              double *__restrict__ z, Skip skip) {
@@ -147,7 +147,7 @@ template <> __device__ __forceinline__ void st_vol<double>(double *p, double v) 
 // (into x1, or into z as FP64 when it is the final upper result; with scaled
 // upper blocks also into yh, the upper sweeps' right-hand side).
 template <typename T, typename VT>
-__global__ void __launch_bounds__(APPLY_THREADS, async_min_ctas<VT>())
+__global__ void __launch_bounds__(APPLY_THREADS, sweep_min_ctas<VT>())
 k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, VT *y,
               int nsweeps, const T *__restrict__ D, VT *__restrict__ x1, VT *__restrict__ yh,
               double *__restrict__ z, unsigned long long *ticket, Skip skip) {

@@ -23,6 +23,7 @@
 
 #include "common.cuh"
 #include "reduce.cuh"
+#include "spmv.cuh"
 
 namespace abilu {
 
@@ -98,18 +99,7 @@ k_b_residual(PatternView P, const double *__restrict__ A, const double *__restri
     double v[2] = {0.0, 0.0};
     {
         // a solve starts from x = 0, where r = b needs no product
-        const int p0 = P.rowptr[i], p1 = init ? p0 : P.rowptr[i + 1];
-        double acc = 0.0;
-        for (int p = p0; p < p1; p++) {
-            const int j = __ldg(P.colind + p);
-            const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
-            const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)j * BS);
-            double2 a0 = __ldg(ap), a1 = __ldg(ap + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
-            acc = fma(a0.x, x0.x, acc);
-            acc = fma(a0.y, x0.y, acc);
-            acc = fma(a1.x, x1.x, acc);
-            acc = fma(a1.y, x1.y, acc);
-        }
+        const double acc = init ? 0.0 : row_dot_blocks(P, A, x, i, q);
         const size_t o = (size_t)i * BS + q;
         const double bi = b[o], ri = bi - acc;
         r_out[o] = ri;

@@ -477,7 +477,7 @@ k_build_async(PatternView P, const AT *__restrict__ A, T *L, T *U, T *D, T *Udia
 //    (unscaled), U^0 = upper blocks, Dinv^0 = inv(A_ii), U_ii stored (Sec. 6
 //    setup: the initial guess of the factorisation is the matrix itself).
 template <typename T>
-__global__ void __launch_bounds__(BUILD_THREADS)
+__global__ void __launch_bounds__(BUILD_THREADS, sizeof(T) == 8 ? 3 : 4)
 k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__ A32,
                 T *__restrict__ L, T *__restrict__ U, T *__restrict__ Uother, T *__restrict__ D,
                 T *__restrict__ Udiag, int init_from_a, unsigned long long *nsing) {
@@ -490,25 +490,36 @@ k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__
     if (i < P.n) {
         const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1], dp = P.diagpos[i];
         const int lb = P.lrow[i], ub = P.urow[i];
-        for (int p = p0; p < p1; p++) {
-            double a[4];
-            ld_row(A + (size_t)p * BB + q * BS, a);
-            const bool constant_u = p > dp && P.pair_ptr[p] == P.pair_ptr[p + 1];
-            if (constant_u) {
-                T *u = U + (size_t)(ub + p - dp - 1) * BB + q * BS;
-                st_row(u, a);
-                if (Uother) st_row(Uother + (size_t)(ub + p - dp - 1) * BB + q * BS, a);
-                continue;
+        // four blocks of the row at a time, every load issued before any store
+        for (int pb = p0; pb < p1; pb += 4) {
+            double a[4][4];
+            int wp[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (pb + k < p1) {
+                    ld_row(A + (size_t)(pb + k) * BB + q * BS, a[k]);
+                    wp[k] = P.wpos[pb + k];
+                }
             }
-            if (A32) st_row(A32 + (size_t)P.wpos[p] * BB + q * BS, a);  // work order
-            if (!init_from_a) continue;
-            if (p < dp) st_row(L + (size_t)(lb + p - p0) * BB + q * BS, a);
-            else if (p > dp) st_row(U + (size_t)(ub + p - dp - 1) * BB + q * BS, a);
-            else {
-                if constexpr (sizeof(T) == 8) {
-                    ud[0] = a[0]; ud[1] = a[1]; ud[2] = a[2]; ud[3] = a[3];
-                } else {
-                    ud[0] = to_f32(a[0]); ud[1] = to_f32(a[1]); ud[2] = to_f32(a[2]); ud[3] = to_f32(a[3]);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int p = pb + k;
+                if (p >= p1) break;
+                if (p > dp && wp[k] < 0) {  // not a work item: a constant U block
+                    st_row(U + (size_t)(ub + p - dp - 1) * BB + q * BS, a[k]);
+                    if (Uother) st_row(Uother + (size_t)(ub + p - dp - 1) * BB + q * BS, a[k]);
+                    continue;
+                }
+                if (A32) st_row(A32 + (size_t)wp[k] * BB + q * BS, a[k]);  // work order
+                if (!init_from_a) continue;
+                if (p < dp) st_row(L + (size_t)(lb + p - p0) * BB + q * BS, a[k]);
+                else if (p > dp) st_row(U + (size_t)(ub + p - dp - 1) * BB + q * BS, a[k]);
+                else {
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        if constexpr (sizeof(T) == 8) ud[c] = a[k][c];
+                        else ud[c] = to_f32(a[k][c]);
+                    }
                 }
             }
         }

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "reduce.cuh"
+#include "spmv.cuh"
 
 namespace abilu {
 
@@ -101,28 +102,21 @@ __device__ __forceinline__ void reduce_partials(const double *partials, int stri
 // ---------------------------------------------------------------- residual
 // r = b - A x into r_out (= V_0 unnormalised), ||r||^2 and (init) ||b||^2.
 // The last CTA sets beta, the convergence flag and starts the next cycle.
-__global__ void __launch_bounds__(RED_THREADS)
+// Launched with 3 CTAs per SM (its registers allow 3 resident: one wave).
+__global__ void __launch_bounds__(RED_THREADS, 3)
 k_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
            const double *__restrict__ x, double *__restrict__ r_out, SolveState *S,
            double *partials, int init, int x_is_zero) {
+    // a restart after a cycle in which no step ran (the initial guess had
+    // already converged) would recompute the same residual: keep the state
+    if (!init && S->kdim == 0) return;
     __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
     const int q = threadIdx.x & 3;
     double v[2] = {0.0, 0.0};
     const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
     for (int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2); i < P.n; i += rows_per_grid) {
-        // same arithmetic as the SpMV kernel: one FMA chain over the row's blocks
-        const int p0 = P.rowptr[i], p1 = x_is_zero ? p0 : P.rowptr[i + 1];  // x = 0: r = b
-        double s = 0.0;
-        for (int p = p0; p < p1; p++) {
-            const int j = __ldg(P.colind + p);
-            const double2 *ap = reinterpret_cast<const double2 *>(A + (size_t)p * BB + q * BS);
-            const double2 *xp = reinterpret_cast<const double2 *>(x + (size_t)j * BS);
-            double2 a0 = __ldg(ap), a1 = __ldg(ap + 1), x0 = __ldg(xp), x1 = __ldg(xp + 1);
-            s = fma(a0.x, x0.x, s);
-            s = fma(a0.y, x0.y, s);
-            s = fma(a1.x, x1.x, s);
-            s = fma(a1.y, x1.y, s);
-        }
+        // the SpMV kernel's arithmetic (x = 0: r = b, no product)
+        const double s = x_is_zero ? 0.0 : row_dot_blocks(P, A, x, i, q);
         const size_t o = (size_t)i * BS + q;
         const double bi = b[o];
         const double ri = bi - s;
@@ -418,6 +412,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     SolveState *SS = reinterpret_cast<SolveState *>(f->scal);
     HostStatus *hs = reinterpret_cast<HostStatus *>(f->host_status);
     const int nred = red_ctas();
+    const int nres = nred / 4 * 3;   // k_residual: 3 CTAs per SM
     const abilu_mode mode = (abilu_mode)opts->mode;
     const Skip skip{&SS->done, nullptr, nullptr};
     float *v32 = reinterpret_cast<float *>(f->r32);  // NULL for FP64 factors
@@ -429,21 +424,19 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
     if (opts->zero_guess) ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
-    k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 1,
+    k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 1,
                                                       opts->zero_guess ? 1 : 0);
     k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
     ABILU_LAUNCH_CHECK("fgmres init");
     cudaEvent_t ev[2];
     ABILU_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     ABILU_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    ABILU_CUDA(cudaStreamSynchronize(st));
-    HostStatus h = read_status(hs);
+    // No wait for the initial residual: the first cycle is enqueued at once,
+    // and its kernels return at once if the initial guess already converged
+    // (the device flag is set).  The host reads the status one step behind.
+    HostStatus h = {};
     abilu_status ret = ABILU_OK;
-    if (h.bnorm == 0.0) {  // b = 0: the solution is x = 0
-        ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
-        h.converged = 1;
-    }
-    while (!h.converged && h.iters < opts->max_iters) {
+    for (bool first = true; first || (!h.converged && h.iters < opts->max_iters); first = false) {
         int j = 0;
         for (; j < m; j++) {
             s = apply_dispatch(f, V + (size_t)j * nv, v32, Z + (size_t)j * nv, opts->apply_sweeps_lower,
@@ -467,7 +460,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
         }
         if (ret != ABILU_OK) break;
         k_xupdate<<<counted(nred), RED_THREADS, 0, st>>>(Z, nv2, x, SS);
-        k_residual<<<counted(nred), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 0, 0);
+        k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 0, 0);
         k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres restart"); break; }
@@ -475,6 +468,8 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres sync"); break; }
         h = read_status(hs);
     }
+    if (ret == ABILU_OK && h.bnorm == 0.0)  // b = 0: the solution is x = 0
+        ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
     cudaStreamSynchronize(st);
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
