@@ -284,6 +284,17 @@ abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts, fgmres_re
                                abilu_stream stream);
 abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x, abilu_stream stream);
 
+/*
+ * abilu_to_f32 — out[i] = in[i] rounded to FP32, round to nearest even, for
+ * i < n: the conversion FGMRES uses to hand the normalised Krylov vector to
+ * FP32/BF16 preconditioners, done with integer instructions only (this GPU's
+ * hardware FP64->FP32 conversion runs on its FP64 pipe).  A utility outside
+ * the paper's method; it gives IEEE results for every input (subnormal
+ * results, overflow to Inf, quiet NaN).  in: double[n], out: float[n], device,
+ * caller-owned, 8- and 4-byte aligned.  n >= 0.  Asynchronous on `stream`.
+ */
+abilu_status abilu_to_f32(const double *in, float *out, int64_t n, abilu_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

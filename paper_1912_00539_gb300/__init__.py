@@ -4,4 +4,4 @@ The computation lives in libabilu.so (hand-written sm_103a CUDA behind the C
 ABI of include/abilu.h); ``abilu`` is its thin Python binding.
 """
 from .abilu import (AbiluError, Batch, Factors, Pattern, SolveResult, bsr_spmv,  # noqa: F401
-                    default_opts, fgmres_solve, kernel_launches, version)
+                    default_opts, fgmres_solve, kernel_launches, to_f32, version)

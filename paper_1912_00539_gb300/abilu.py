@@ -34,7 +34,7 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_factors_diagnostics",
            "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc", "abilu_batch_create",
            "abilu_batch_destroy", "abilu_batch_counts", "abilu_batch_set_system",
-           "abilu_batch_solve", "abilu_batch_get_solution")
+           "abilu_batch_solve", "abilu_batch_get_solution", "abilu_to_f32")
 
 
 class FgmresOpts(C.Structure):
@@ -66,6 +66,7 @@ _lib.abilu_build.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
 _lib.abilu_apply.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
 _lib.bsr_spmv.argtypes = [_vp, _vp, _f64, _vp, _f64, _vp, _vp]
 _lib.abilu_apply_noalloc.argtypes = [_i32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp]
+_lib.abilu_to_f32.argtypes = [_vp, _vp, _i64, _vp]
 _lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
@@ -84,7 +85,7 @@ _lib.abilu_batch_set_system.argtypes = [_vp, _i32, _vp, _vp, _vp]
 _lib.abilu_batch_solve.argtypes = [_vp, C.POINTER(FgmresOpts), C.POINTER(FgmresResult), _vp]
 _lib.abilu_batch_get_solution.argtypes = [_vp, _i32, _vp, _vp]
 for _nm in ("abilu_batch_create", "abilu_batch_counts", "abilu_batch_set_system",
-            "abilu_batch_solve", "abilu_batch_get_solution"):
+            "abilu_batch_solve", "abilu_batch_get_solution", "abilu_to_f32"):
     getattr(_lib, _nm).restype = C.c_int
 for _nm in ("abilu_pattern_create", "abilu_pattern_counts", "abilu_factors_create", "abilu_build",
             "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
@@ -218,6 +219,14 @@ def bsr_spmv(pattern: Pattern, A, x, y, alpha=1.0, beta=0.0, stream=None):
     _check(_lib.bsr_spmv(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
                          float(alpha), _ptr(x, torch.float64, nv, "x"), float(beta),
                          _ptr(y, torch.float64, nv, "y"), _stream(stream)))
+
+
+def to_f32(x, out, stream=None):
+    """abilu_to_f32: FP64 -> FP32 round to nearest even with integer
+    instructions (the conversion of the FGMRES normalisation)."""
+    import torch
+    _check(_lib.abilu_to_f32(_ptr(x, torch.float64, what="x"),
+                             _ptr(out, torch.float32, x.numel(), "out"), x.numel(), _stream(stream)))
 
 
 NOALLOC_MAX_CELLS = 65536

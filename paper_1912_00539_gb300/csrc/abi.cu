@@ -166,3 +166,21 @@ extern "C" abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_
     *singular_blocks = (int64_t)v;
     return ABILU_OK;
 }
+
+namespace abilu {
+__global__ void k_to_f32_int(const double *__restrict__ in, float *__restrict__ out, long long n) {
+    const long long st = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += st)
+        out[e] = to_f32_int(in[e]);
+}
+}  // namespace abilu
+
+extern "C" abilu_status abilu_to_f32(const double *in, float *out, int64_t n, abilu_stream stream) {
+    if (n < 0 || (n > 0 && (!in || !out))) return fail(ABILU_EINVAL, "to_f32: bad argument");
+    if (n == 0) return ABILU_OK;
+    const long long blocks = (n + 255) / 256;
+    const int grid = (int)(blocks < red_ctas() ? blocks : red_ctas());
+    k_to_f32_int<<<counted(grid), 256, 0, S(stream)>>>(in, out, n);
+    ABILU_LAUNCH_CHECK("k_to_f32_int");
+    return ABILU_OK;
+}

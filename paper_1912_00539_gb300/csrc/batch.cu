@@ -158,7 +158,7 @@ k_b_scale(const double *vin, double *vout, float *v32, const BState *S,
     const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
     const double t = vin[e] * St->hn_inv;
     vout[e] = t;
-    if (v32) v32[e] = to_f32(t);
+    if (v32) v32[e] = to_f32_int(t);
 }
 
 template <int K>

@@ -147,6 +147,37 @@ __device__ __forceinline__ float to_f32(double d) {
     return __uint_as_float(f);
 }
 
+// to_f32 with every case in integer instructions, for kernels bound by the
+// FP64 pipe (the Krylov normalisation): the hardware fallback above is issued
+// there, predicated off, for every element and takes FP64-pipe cycles.
+// Subnormal results shift the 53-bit significand right and round to nearest
+// even (2^23 is the smallest normal); |d| < 2^-150 gives +-0; overflow Inf; NaN
+// a quiet NaN with the top payload bits.  (Where the FP64 pipe is idle the
+// shorter to_f32 is faster: fewer registers.)
+__device__ __forceinline__ float to_f32_int(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int ed = (int)((hi >> 20) & 0x7FFu);
+    const int e = ed - 1023 + 127;
+    const unsigned m23 = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1FFFFFFFu;
+    if (e >= 1 && e <= 254) {
+        unsigned f = sign | ((unsigned)e << 23) | m23;
+        f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (m23 & 1u));
+        return __uint_as_float(f);
+    }
+    if (ed == 0x7FF) return __uint_as_float(sign | 0x7F800000u | ((m23 | rem) ? (0x400000u | m23) : 0u));
+    if (e > 254) return __uint_as_float(sign | 0x7F800000u);
+    if (e < -23) return __uint_as_float(sign);
+    const unsigned long long M = (1ull << 52) | (b & 0xFFFFFFFFFFFFFull);
+    const int sh = 926 - ed;  // 30 .. 53
+    const unsigned long long half = 1ull << (sh - 1), drop = M & ((1ull << sh) - 1ull);
+    unsigned long long q = M >> sh;
+    q += (drop > half) | ((drop == half) & (q & 1ull));
+    return __uint_as_float(sign | (unsigned)q);
+}
+
 // FP32 -> FP64 (exact) with integer instructions; zeros, subnormals, Inf and
 // NaN take the hardware conversion.
 __device__ __forceinline__ double to_f64(float x) {

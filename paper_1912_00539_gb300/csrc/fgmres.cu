@@ -164,7 +164,7 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
         double2 t = a[e];
         t = make_double2(t.x * s, t.y * s);
         o[e] = t;
-        if (v32) o32[e] = make_float2(to_f32(t.x), to_f32(t.y));
+        if (v32) o32[e] = make_float2(to_f32_int(t.x), to_f32_int(t.y));
     }
 }
 

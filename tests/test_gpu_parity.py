@@ -462,20 +462,54 @@ def test_fp64_to_fp32_rounding_is_exact(ab):
                         2.0 ** -130, -2.0 ** -140, 1e-300, 3.4e38, -3.3e38, 0.0, -0.0,
                         1.5 * 2.0 ** -126, 2.0 ** 127 * (2 - 2.0 ** -23),
                         np.nextafter(1.0, 2.0), 0.1, 1.0 / 3.0])
+    # the bottom of the subnormal range (ties at 2^-150 and 3 * 2^-150), a
+    # subnormal that rounds up into the smallest normal, overflow, Inf, NaN
+    special = np.concatenate([special, [
+        2.0 ** -150, 2.0 ** -150 * (1 + 2.0 ** -20), 3 * 2.0 ** -150, 2.0 ** -151,
+        2.0 ** -126 * (1 - 2.0 ** -25), -2.0 ** -126 * (1 - 2.0 ** -30),
+        3.5e38, -1e39, 2.0 ** 128 * (1 - 2.0 ** -25), np.inf, -np.inf, np.nan]])
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    offdiag = np.flatnonzero(rows != s.colind)          # non-finite values stay off U_ii
+    entries = (offdiag[:, None] * 16 + np.arange(16)).reshape(-1)
+    idx = rng.choice(entries, size=len(special) + 16 + 900, replace=False)
     flat = vals.reshape(-1)
-    idx = rng.choice(flat.size, size=4000, replace=False)
     flat[idx[:len(special)]] = special
     # random doubles sitting exactly on float32 ties
-    t = rng.standard_normal(2000).astype(np.float32).astype(np.float64)
+    t = rng.standard_normal(900).astype(np.float32).astype(np.float64)
     ulp = np.abs(np.spacing(t.astype(np.float32)).astype(np.float64))
-    flat[idx[len(special):len(special) + 2000]] = t + 0.5 * ulp
+    flat[idx[len(special):len(special) + 900]] = t + 0.5 * ulp
     d = Dev(ab, gen.System("ties", s.rowptr, s.colind, vals, s.b, s.perm, s.cfl))
     fac = ab.Factors(d.pat, "f32")
     fac.build(d.A, 0, mode="sync")
     X, _ = fac.export()
-    ref = vals.astype(np.float32).astype(np.float64)
+    with np.errstate(over="ignore"):
+        ref = vals.astype(np.float32).astype(np.float64)
     got = X.cpu().numpy()
     np.testing.assert_array_equal(got.view(np.int64), ref.view(np.int64))
+
+
+def test_integer_fp32_conversion_is_exact(ab):
+    """abilu_to_f32 (the integer-only conversion of the FGMRES normalisation)
+    equals numpy's FP64 -> FP32 round to nearest even bit for bit: normal
+    values, ties, subnormal results and their rounding into the smallest
+    normal, the bottom of the subnormal range, overflow, Inf, NaN, zeros."""
+    import torch
+    rng = np.random.default_rng(23)
+    x = rng.standard_normal(200000) * 10.0 ** rng.uniform(-48, 40, 200000)
+    t = rng.standard_normal(20000).astype(np.float32).astype(np.float64)
+    ties = t + 0.5 * np.abs(np.spacing(t.astype(np.float32)).astype(np.float64))
+    sub = rng.integers(1, 2 ** 23, 20000) * 2.0 ** -149 + rng.choice([0.5, 0.25, 0.75], 20000) * 2.0 ** -149
+    special = np.array([0.0, -0.0, 2.0 ** -150, 3 * 2.0 ** -150, 2.0 ** -151, 2.0 ** -1074,
+                        2.0 ** -126 * (1 - 2.0 ** -25), 2.0 ** -126 * (1 - 2.0 ** -24),
+                        3.4028234663852886e38, 2.0 ** 128 * (1 - 2.0 ** -25), 2.0 ** 128 * (1 - 2.0 ** -24),
+                        1e39, -1e300, np.inf, -np.inf, np.nan, 1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24])
+    allv = np.concatenate([x, ties, sub, -sub, special])
+    d = torch.from_numpy(allv).cuda()
+    out = torch.empty(allv.size, dtype=torch.float32, device="cuda")
+    ab.to_f32(d, out)
+    with np.errstate(over="ignore"):
+        ref = allv.astype(np.float32)
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
 
 
 def test_zero_guess_equals_explicit_zero_start(ab):
