@@ -106,8 +106,11 @@ abilu_status abilu_pattern_counts(abilu_pattern p, int64_t *out);
 /*
  * Factor storage for one pattern: L (strictly lower blocks), U (strictly upper
  * blocks), inv(U_ii) and U_ii, in `dtype`, plus the work vectors of the
- * triangular sweeps.  The inversions and the build arithmetic are FP64 in every
- * dtype; only storage (and, for F32/BF16, the apply sweeps) is narrower.
+ * triangular sweeps.  F64: build arithmetic and 4x4 inversions in FP64.
+ * F32/BF16: the build sweeps compute in FP32 from an FP32 copy of A, and each
+ * inversion is an FP32 adjugate refined by one error-free Newton step (the
+ * FP32 rounding of the exact inverse for cond(U_ii) << 4000); the apply
+ * sweeps run in FP32.  F32 also keeps inv(U_ii) U_ij for the upper sweeps.
  */
 abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype, abilu_factors *out);
 void abilu_factors_destroy(abilu_factors f);
@@ -118,9 +121,10 @@ void abilu_factors_destroy(abilu_factors f);
  *   L_ij = (A_ij - sum_{k<j} L_ik U_kj) U_jj^-1  (i > j),
  * over every block of S_B at once.  ABILU_SYNC: x^{n+1} = h(x^n) (Eq.
  * seq_blockilu_fp), deterministic and bit-reproducible; ABILU_ASYNC: in-place
- * updates reading whatever values are current, work items = block rows taken
- * in chunks from a queue, no barrier between sweeps (Algorithm 4 with blocks,
- * Eq. async_blockilu_fp).  `A_vals` double[nnzb][4][4] on the device.
+ * updates reading whatever values are current, work items (single blocks for
+ * FP32/BF16 factors, block rows for FP64) taken in chunks from a queue, no
+ * barrier between sweeps (Algorithm 4 with blocks, Eq. async_blockilu_fp).
+ * `A_vals` double[nnzb][4][4] on the device.
  * nsweeps >= 0 (0 leaves X^0).  Singular diagonal blocks met during the build
  * are counted on the device; read them with abilu_factors_status.
  */
@@ -202,7 +206,9 @@ abilu_status abilu_factors_diagnostics(abilu_factors f, const double *A_vals, do
 
 /* Synchronises `stream`, then returns in *singular_blocks (host) how many
  * singular diagonal blocks the builds since the last call replaced, and resets
- * the count. */
+ * the count.  Returns ABILU_ETIMEOUT (and resets it) if a bounded wait inside
+ * an asynchronous application's staged pipeline ran out since the last call
+ * (the results of that application are then invalid; never expected). */
 abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_blocks, abilu_stream stream);
 
 typedef struct {

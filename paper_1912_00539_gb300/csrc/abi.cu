@@ -75,7 +75,7 @@ extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype,
     const size_t bu = rnd(esz * BB * (size_t)(v.nu > 0 ? v.nu : 1));
     const size_t bd = rnd(esz * BB * (size_t)v.n);
     const size_t bv = rnd(vt * BS * (size_t)v.n);
-    const size_t bc = rnd(sizeof(unsigned long long) * 4);
+    const size_t bc = rnd(sizeof(unsigned long long) * 8);   // counters, tickets, error word
     const size_t bs = rnd(solve_state_bytes());
     const size_t bp = rnd(sizeof(double) * MAXM_PARTIAL_STRIDE * (size_t)red_ctas());
     const bool narrow = dtype != ABILU_F64;
@@ -159,11 +159,15 @@ extern "C" abilu_status abilu_factors_export(abilu_factors f, double *X, double 
 extern "C" abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_blocks,
                                              abilu_stream stream) {
     if (!f || !singular_blocks) return fail(ABILU_EINVAL, "factors_status: NULL argument");
-    unsigned long long v = 0;
-    ABILU_CUDA(cudaMemcpyAsync(&v, f->ctr, sizeof v, cudaMemcpyDeviceToHost, S(stream)));
+    unsigned long long cv[5] = {0, 0, 0, 0, 0};
+    ABILU_CUDA(cudaMemcpyAsync(cv, f->ctr, sizeof cv, cudaMemcpyDeviceToHost, S(stream)));
     ABILU_CUDA(cudaStreamSynchronize(S(stream)));
-    ABILU_CUDA(cudaMemsetAsync(f->ctr, 0, sizeof v, S(stream)));
-    *singular_blocks = (int64_t)v;
+    ABILU_CUDA(cudaMemsetAsync(f->ctr, 0, sizeof cv[0], S(stream)));
+    *singular_blocks = (int64_t)cv[0];
+    if (cv[4]) {  // a staged sweep's bounded wait ran out since the last check
+        ABILU_CUDA(cudaMemsetAsync(f->ctr + 4, 0, sizeof cv[4], S(stream)));
+        return fail(ABILU_ETIMEOUT, "factors_status: %llu pipeline waits timed out", cv[4]);
+    }
     return ABILU_OK;
 }
 

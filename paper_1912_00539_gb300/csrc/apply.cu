@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "pipe.cuh"
 
 namespace abilu {
 
@@ -236,6 +237,146 @@ k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
     }
 }
 
+// ---------------------------------------------------------------- async, staged
+// The in-place sweeps with factors in FP32/BF16, as a warp-specialised
+// pipeline: a producer warp takes the next ticket (chunk, sweep), and copies
+// the chunk's read-only data -- its rows' factor blocks and column indices
+// (contiguous in the compact L/U arrays), its row pointers and right-hand side
+// -- into one of two shared-memory stages with bulk asynchronous copies, while
+// the 8 consumer warps (a quad per row) sweep the chunk staged before it.  The
+// in-place vector itself is never staged: every neighbour value is read from
+// global memory at the moment of the update, as in the unstaged kernels, so
+// the iteration is the same asynchronous iteration (Algorithm 5); only the
+// latency of the ticket, the row pointers and the factor rows leaves the
+// critical path.  A chunk with more than PIPE_CAP factor blocks is read from
+// global memory instead.  Lower (UPPER = false): y_i = b_i - sum L_ij y_j,
+// the last update of a row also forms x^1 = Dinv_i y_i into x1 / yh / z.
+// Upper: x_i = rhs_i - sum Us_ij x_j (SCALED) or Dinv_i (rhs_i - sum U_ij x_j),
+// chunks in backward order, the last update writes z.
+constexpr int PIPE_CONSUMERS = 8;                          // warps
+constexpr int PIPE_THREADS = (PIPE_CONSUMERS + 1) * 32;    // + the producer warp
+constexpr int PIPE_CAP = 160;                              // factor blocks per stage
+constexpr int PIPE_ROWP = 68;                              // row pointers copied per chunk
+
+template <typename T> struct __align__(128) PipeStage {   // every field 16-byte aligned
+    T F[PIPE_CAP * BB];
+    int32_t col[PIPE_CAP + 8];
+    float rhs[APPLY_ROWS * BS];
+    int32_t rowp[PIPE_ROWP];
+    long long ticket;     // -1: no more work
+    int32_t fb, cb, staged, pad;
+};
+
+template <bool UPPER, bool SCALED, typename T>
+__global__ void __launch_bounds__(PIPE_THREADS, 7)   // 7 x 288 threads per SM: 32 registers
+k_tri_async_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
+                   const float *__restrict__ rhs, float *v, int nsweeps,
+                   float *__restrict__ x1, float *__restrict__ yh, double *__restrict__ z,
+                   unsigned long long *ticket, unsigned long long *err, Skip skip) {
+    if (skip_all(skip)) return;
+    __shared__ __align__(128) PipeStage<T> st[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
+    const int32_t *rowp = UPPER ? P.urow : P.lrow;
+    const int32_t *colg = UPPER ? P.ucol : P.lcol;
+    const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
+    const long long total = nchunks * nsweeps;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], PIPE_CONSUMERS);
+        mbar_init(&empty[1], PIPE_CONSUMERS);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == PIPE_CONSUMERS) {  // ---- producer (one lane)
+        if (lane != 0) return;
+        for (int k = 0;; k++) {
+            const int s = k & 1, u = k >> 1;
+            if (u >= 1 && !mbar_wait(&empty[s], (u - 1) & 1, err)) return;
+            PipeStage<T> &S = st[s];
+            const long long t = (long long)atomicAdd(ticket, 1ull);
+            if (t >= total) {
+                S.ticket = -1;
+                mbar_arrive(&full[s]);
+                return;
+            }
+            const int c = (int)(t % nchunks);
+            const int chunk = UPPER ? (int)(nchunks - 1 - c) : c;
+            const int i0 = chunk * APPLY_ROWS, i1 = min(i0 + APPLY_ROWS, P.n);
+            const int fb = rowp[i0], fe = rowp[i1];
+            const bool staged = fe - fb <= PIPE_CAP;
+            const int cb = fb & ~3, ce = (fe + 3) & ~3;
+            S.ticket = t;
+            S.fb = fb;
+            S.cb = cb;
+            S.staged = staged;
+            unsigned bytes = 0;
+            const bool run = !skip_chunk(skip, chunk);
+            if (run) {
+                bytes = PIPE_ROWP * 4 + (unsigned)(i1 - i0) * 16;
+                if (staged) bytes += (unsigned)(fe - fb) * BB * sizeof(T) + (unsigned)(ce - cb) * 4;
+            }
+            mbar_arrive_tx(&full[s], bytes);
+            if (run) {
+                bulk_g2s(S.rowp, rowp + i0, PIPE_ROWP * 4, &full[s]);
+                bulk_g2s(S.rhs, rhs + (size_t)i0 * BS, (unsigned)(i1 - i0) * 16, &full[s]);
+                if (staged) {
+                    if (fe > fb) bulk_g2s(S.F, F + (size_t)fb * BB, (unsigned)(fe - fb) * BB * sizeof(T), &full[s]);
+                    if (ce > cb) bulk_g2s(S.col, colg + cb, (unsigned)(ce - cb) * 4, &full[s]);
+                }
+            }
+        }
+    }
+
+    // ---- consumers: a quad per row of the staged chunk
+    const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+    for (int k = 0;; k++) {
+        const int s = k & 1, u = k >> 1;
+        if (!mbar_wait(&full[s], u & 1, err)) return;
+        const PipeStage<T> &S = st[s];
+        const long long t = S.ticket;
+        if (t < 0) return;
+        const int c = (int)(t % nchunks);
+        const int chunk = UPPER ? (int)(nchunks - 1 - c) : c;
+        const bool last = t / nchunks == nsweeps - 1;
+        const int i = chunk * APPLY_ROWS + r;
+        if (i < P.n && !skip_chunk(skip, chunk)) {
+            const int l0 = S.rowp[r], l1 = S.rowp[r + 1];
+            float acc = S.rhs[r * BS + q];
+            for (int l = l0; l < l1; l++) {
+                float a[4], b[4];
+                int j;
+                if (S.staged) {
+                    ld_row(S.F + (size_t)(l - S.fb) * BB + q * BS, a);
+                    j = S.col[l - S.cb];
+                } else {
+                    ld_row(F + (size_t)l * BB + q * BS, a);
+                    j = colg[l];
+                }
+                ld_row_volatile(v + (size_t)j * BS, b);
+                acc -= dot4(a, b);
+            }
+            float xi = acc;
+            if constexpr (UPPER && !SCALED) xi = dinv_times<T, float>(D, i, acc);
+            st_vol(v + (size_t)i * BS + q, xi);
+            if (last) {
+                if constexpr (UPPER) {
+                    z[(size_t)i * BS + q] = to_f64v(xi);
+                } else if (x1 || yh || z) {
+                    const float x = dinv_times<T, float>(D, i, acc);
+                    if (x1) x1[(size_t)i * BS + q] = x;
+                    if (yh) yh[(size_t)i * BS + q] = x;
+                    if (z) z[(size_t)i * BS + q] = to_f64v(x);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
 // r32 = (float) r, once per application (the sweeps then read 16-byte FP32
 // rows and do no FP64 conversions on the slow FP64 pipe)
 __global__ void __launch_bounds__(APPLY_THREADS)
@@ -276,6 +417,11 @@ template <typename T, typename VT> static int upper_async_ctas() {
     static int c = resident_ctas(k_upper_async<T, VT, std::is_same<T, float>::value>, APPLY_THREADS);
     return c;
 }
+template <bool UPPER, bool SCALED, typename T> static int staged_ctas() {
+    static int c = resident_ctas(k_tri_async_staged<UPPER, SCALED, T>, PIPE_THREADS);
+    return c;
+}
+
 
 template <typename T>
 static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_in, double *z,
@@ -327,19 +473,34 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             P, D, rv, y[0], nl == 1 ? x1 : nullptr, nl == 1 ? yh : nullptr, nl == 1 ? z1 : nullptr,
             tk, skip);
         ABILU_LAUNCH_CHECK("k_async_start");
+        unsigned long long *err = f->ctr + 4;
         if (nl >= 2) {
-            const int ctas_l = lower_async_ctas<T, VT>();
-            int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
-            k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl - 1, D, x1,
-                                                                       yh, z1, tk, skip);
-            ABILU_LAUNCH_CHECK("k_lower_async");
+            if constexpr (sizeof(VT) == 4) {  // staged pipeline (FP32/BF16 factors)
+                const int c = staged_ctas<false, false, T>();
+                const int g = (int)(c < nchunks ? c : nchunks);
+                k_tri_async_staged<false, false, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+                    P, L, D, rv, y[0], nl - 1, x1, yh, z1, tk, err, skip);
+            } else {
+                const int ctas_l = lower_async_ctas<T, VT>();
+                const int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
+                k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl - 1, D,
+                                                                           x1, yh, z1, tk, skip);
+            }
+            ABILU_LAUNCH_CHECK("lower async");
         }
         if (nu >= 2) {
-            const int ctas_u = upper_async_ctas<T, VT>();
-            int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
-            k_upper_async<T, VT, SC><<<counted(g), APPLY_THREADS, 0, st>>>(
-                P, UU, D, SC ? y[1] : y[0], x[0], z, nu - 1, tk + 1, skip);
-            ABILU_LAUNCH_CHECK("k_upper_async");
+            if constexpr (sizeof(VT) == 4) {
+                const int c = staged_ctas<true, SC, T>();
+                const int g = (int)(c < nchunks ? c : nchunks);
+                k_tri_async_staged<true, SC, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+                    P, UU, D, SC ? y[1] : y[0], x[0], nu - 1, nullptr, nullptr, z, tk + 1, err, skip);
+            } else {
+                const int ctas_u = upper_async_ctas<T, VT>();
+                const int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
+                k_upper_async<T, VT, SC><<<counted(g), APPLY_THREADS, 0, st>>>(
+                    P, UU, D, SC ? y[1] : y[0], x[0], z, nu - 1, tk + 1, skip);
+            }
+            ABILU_LAUNCH_CHECK("upper async");
         }
         return ABILU_OK;
     }
@@ -388,10 +549,13 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
 void apply_warm(abilu_dtype dt) {
     switch (dt) {
     case ABILU_F64: lower_async_ctas<double, double>(); upper_async_ctas<double, double>(); break;
-    case ABILU_F32: lower_async_ctas<float, float>(); upper_async_ctas<float, float>(); break;
+    case ABILU_F32:
+        staged_ctas<false, false, float>();
+        staged_ctas<true, true, float>();
+        break;
     case ABILU_BF16:
-        lower_async_ctas<__nv_bfloat16, float>();
-        upper_async_ctas<__nv_bfloat16, float>();
+        staged_ctas<false, false, __nv_bfloat16>();
+        staged_ctas<true, false, __nv_bfloat16>();
         break;
     }
 }

@@ -738,8 +738,13 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
     }
     std::vector<BState> hs(nsys);
     ABILU_CUDA(cudaMemcpy(hs.data(), b->S, sizeof(BState) * nsys, cudaMemcpyDeviceToHost));
-    unsigned long long ns = 0;
-    ABILU_CUDA(cudaMemcpy(&ns, b->fac->ctr, sizeof ns, cudaMemcpyDeviceToHost));
+    unsigned long long cv[5] = {0, 0, 0, 0, 0};
+    ABILU_CUDA(cudaMemcpy(cv, b->fac->ctr, sizeof cv, cudaMemcpyDeviceToHost));
+    const unsigned long long ns = cv[0];
+    if (cv[4] && ret == ABILU_OK) {  // a staged sweep's bounded wait ran out: results invalid
+        cudaMemset(b->fac->ctr + 4, 0, sizeof(unsigned long long));
+        ret = fail(ABILU_ETIMEOUT, "batch_solve: %llu pipeline waits timed out", cv[4]);
+    }
     int nconv = 0;
     for (int q = 0; q < nsys; q++) {
         res[q].iters = hs[q].iters;

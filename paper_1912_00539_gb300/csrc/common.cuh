@@ -94,8 +94,8 @@ struct abilu_factors_s {
     int cur;
     // apply work vectors (VT = double for F64, float otherwise)
     void *y[2], *x[2];
-    // device counters: [0] singular blocks, [1] async ticket counter,
-    // [2..3] spare
+    // device counters: [0] singular blocks, [1] build tickets, [2] lower and
+    // [3] upper apply tickets, [4] timed-out pipeline waits, [5..7] spare
     unsigned long long *ctr;
     // FGMRES workspace (grown on demand)
     double *krylov;            // V (m+1 vectors) then Z (m vectors)

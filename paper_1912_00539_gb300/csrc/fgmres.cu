@@ -478,9 +478,14 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     res->restarts = h.restarts;
     res->rel_resid_est = h.est;
     res->rel_resid_true = h.bnorm > 0.0 ? h.beta / h.bnorm : 0.0;
-    unsigned long long ns = 0;
-    cudaMemcpy(&ns, f->ctr, sizeof ns, cudaMemcpyDeviceToHost);
+    unsigned long long cv[5] = {0, 0, 0, 0, 0};
+    cudaMemcpy(cv, f->ctr, sizeof cv, cudaMemcpyDeviceToHost);
+    const unsigned long long ns = cv[0];
     res->singular_blocks = (int64_t)ns;
+    if (cv[4] && ret == ABILU_OK) {  // a staged sweep's bounded wait ran out: results invalid
+        cudaMemset(f->ctr + 4, 0, sizeof(unsigned long long));
+        ret = fail(ABILU_ETIMEOUT, "fgmres_solve: %llu pipeline waits timed out", cv[4]);
+    }
     if (ret == ABILU_OK) {
         if (!h.converged) ret = fail(ABILU_ENOCONV, "fgmres_solve: %d iterations, relative residual %.3e > rtol %.3e", h.iters, res->rel_resid_true, opts->rtol);
         else if (ns > 0) ret = fail(ABILU_WARN_SINGULAR, "fgmres_solve: %llu singular diagonal blocks replaced", ns);

@@ -327,8 +327,9 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     TRY(alloc((void **)&diagpos, sizeof(int32_t) * n));
     TRY(alloc((void **)&lcnt, sizeof(int32_t) * n));
     TRY(alloc((void **)&ucnt, sizeof(int32_t) * n));
-    TRY(alloc((void **)&lrow, sizeof(int32_t) * (n + 1)));
-    TRY(alloc((void **)&urow, sizeof(int32_t) * (n + 1)));
+    // +68 entries: a sweep copies rowptr windows of 68 entries per 64-row chunk
+    TRY(alloc((void **)&lrow, sizeof(int32_t) * (n + 1 + 68)));
+    TRY(alloc((void **)&urow, sizeof(int32_t) * (n + 1 + 68)));
     TRY(alloc((void **)&pair_cnt, sizeof(int32_t) * nnzb));
     TRY(alloc((void **)&pair_ptr, sizeof(int32_t) * (nnzb + 1)));
     TRY(alloc((void **)&scratch, sizeof(long long) * ntiles));
@@ -361,8 +362,10 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     TRY(cu(cudaMemcpyAsync(&nl_nu[1], urow + n, 4, cudaMemcpyDeviceToHost, st), "read nu"));
     TRY(cu(cudaStreamSynchronize(st), "sync"));
     int32_t *lcol, *ucol;
-    TRY(alloc((void **)&lcol, sizeof(int32_t) * (nl_nu[0] + 1)));
-    TRY(alloc((void **)&ucol, sizeof(int32_t) * (nl_nu[1] + 1)));
+    // padded to whole 16-byte groups (+16 bytes): the sweeps copy index ranges
+    // rounded out to 16-byte boundaries with bulk asynchronous copies
+    TRY(alloc((void **)&lcol, sizeof(int32_t) * ((nl_nu[0] + 3) / 4 * 4 + 4)));
+    TRY(alloc((void **)&ucol, sizeof(int32_t) * ((nl_nu[1] + 3) / 4 * 4 + 4)));
     k_pat_cols<<<counted(gb), 256, 0, st>>>(n, d_rowptr, d_colind, diagpos, lrow, urow, lcol, ucol);
     k_pat_pairs<false><<<counted(gb), 256, 0, st>>>(n, d_rowptr, d_colind, diagpos, lrow, urow, pair_cnt,
                                            nullptr, nullptr);
