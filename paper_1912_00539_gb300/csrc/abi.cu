@@ -82,7 +82,8 @@ extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype,
     const size_t ba = narrow ? rnd(sizeof(float) * BB * (size_t)v.nnzb) : 0;
     const size_t br = narrow ? rnd(sizeof(float) * BS * (size_t)v.n) : 0;
     const size_t bus = dtype == ABILU_F32 ? bu : 0;   // Dinv-scaled upper blocks
-    const size_t total = 2 * bl + 2 * bu + 3 * bd + 4 * bv + bc + bs + bp + ba + br + bus;
+    const size_t bcd = rnd(sizeof(int) * ((size_t)(v.nwork + 31) / 32 + 1));
+    const size_t total = 2 * bl + 2 * bu + 3 * bd + 4 * bv + bc + bs + bp + ba + br + bus + bcd;
     abilu_factors f = new abilu_factors_s();
     memset(f, 0, sizeof *f);
     f->p = p;
@@ -108,6 +109,7 @@ extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype,
     f->A32 = narrow ? m : nullptr; m += ba;
     f->r32 = narrow ? m : nullptr; m += br;
     f->Us = bus ? m : nullptr; m += bus;
+    f->chunk_done = reinterpret_cast<int *>(m); m += bcd;
     e = cudaMemset(f->mem, 0, total);
     if (e == cudaSuccess) e = cudaHostAlloc(&f->host_status, host_status_bytes(), cudaHostAllocMapped);
     if (e != cudaSuccess) { factors_free(f); return cuda_fail(e, "factors_create"); }

@@ -24,6 +24,7 @@
 // into chunks handed out by a ticket counter across all sweeps, so no barrier
 // separates sweeps (Algorithm 4 with blocks, Eq. async_blockilu_fp).
 #include "common.cuh"
+#include "pipe.cuh"
 
 namespace abilu {
 
@@ -393,13 +394,22 @@ k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__res
 // is chunk (t mod nchunks) of sweep t / nchunks, a chunk being 32 consecutive
 // work blocks, done in 4 steps of 8 (one block per quad, consecutive blocks,
 // so a step stays within one kind of the kind-sorted list).
+//
+// ORDERED (with `done`): the sweeps of one chunk run in order.  Tickets of
+// the same chunk in consecutive sweeps are nchunks apart, so when chunks are
+// few against warps one warp could still be updating chunk c in sweep s while
+// another takes it in sweep s + 1, and the older update's Dinv could land
+// after the newer U_ii.  Then a warp first waits (bounded; a timeout is
+// counted in *err and the warp stops) until done[c] records s completed
+// sweeps, and publishes s + 1 after its writes.  A wait points only to a
+// smaller ticket, held by a resident warp, so every wait ends.
 constexpr int WARP_CHUNK = 32;
 
-template <typename T>
+template <typename T, bool ORDERED>
 __global__ void __launch_bounds__(BUILD_THREADS, 5)   // 48 registers: measured fastest (4, 6 slower)
 k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T *D, T *Udiag,
                      int nsweeps, int max_warps, unsigned long long *nsing,
-                     unsigned long long *ticket) {
+                     unsigned long long *ticket, unsigned long long *err, int *done) {
     __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
     // at most one warp per chunk: more would sweep the same blocks at once
     if (blockIdx.x * (BUILD_THREADS / 32) + (threadIdx.x >> 5) >= max_warps) return;
@@ -412,15 +422,29 @@ k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T
         if (lane == 0) tk = atomicAdd(ticket, 1ull);
         const long long t = (long long)__shfl_sync(0xffffffffu, tk, 0);
         if (t >= total) break;
-        const bool last = t / nchunks == nsweeps - 1;
-        const int base = (int)(t % nchunks) * WARP_CHUNK + (lane >> 2);
+        const int sweep = (int)(t / nchunks), chunk = (int)(t % nchunks);
+        const bool last = sweep == nsweeps - 1;
+        const int base = chunk * WARP_CHUNK + (lane >> 2);
+        if constexpr (ORDERED) {  // wait for this chunk's previous sweep
+            int ok = 1;
+            if (lane == 0) {
+                unsigned it = 0;
+                while (*reinterpret_cast<volatile int *>(done + chunk) < sweep && ++it < PIPE_WAIT_LIMIT) {}
+                ok = it < PIPE_WAIT_LIMIT;
+                if (!ok) atomicAdd(err, 1ull);
+                __threadfence();
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) return;
+        }
 #pragma unroll 1
         for (int k = 0; k < WARP_CHUNK / 8; k++) {
             const int w = base + 8 * k;
             if (w < P.nwork)
                 build_block<T, true>(P, w, A32, L, U, D, L, U, D, last ? Udiag : nullptr, myq, nsing);
         }
+        if constexpr (ORDERED) __threadfence();   // this lane's factor writes, before the flag
         __syncwarp();
+        if (ORDERED && lane == 0) *reinterpret_cast<volatile int *>(done + chunk) = sweep + 1;
     }
 }
 
@@ -596,9 +620,9 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
         static int per_sm = -1;
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
-        if (per_sm < 0)
-            ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_blocks_async<T>,
-                                                                     BUILD_THREADS, 0));
+        if (per_sm < 0)   // the ordered variant is held to the same occupancy
+            ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, k_build_blocks_async<T, false>, BUILD_THREADS, 0));
         ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const int wchunks = (P.nwork + WARP_CHUNK - 1) / WARP_CHUNK;
         int warps = per_sm * sms * (BUILD_THREADS / 32);
@@ -606,10 +630,21 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
         if (warps < 1) warps = 1;
         const int ctas = (warps + BUILD_THREADS / 32 - 1) / (BUILD_THREADS / 32);
         ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, sizeof(unsigned long long), st));
+        // fewer than 4 chunks per warp: keep each chunk's sweeps in order (see
+        // the kernel); with more, an overlap needs one warp stalled for the
+        // time the others take to process several chunks each
+        int *done = nullptr;
+        if ((long long)wchunks < 4LL * warps) {
+            done = f->chunk_done;
+            ABILU_CUDA(cudaMemsetAsync(done, 0, sizeof(int) * (size_t)wchunks, st));
+        }
         const int c = f->cur;
-        k_build_blocks_async<T><<<counted(ctas), BUILD_THREADS, 0, st>>>(P, A32, L[c], U[c], D[c], Ud,
-                                                                         nsweeps, warps, f->ctr,
-                                                                         f->ctr + 1);
+        if (done)
+            k_build_blocks_async<T, true><<<counted(ctas), BUILD_THREADS, 0, st>>>(
+                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done);
+        else
+            k_build_blocks_async<T, false><<<counted(ctas), BUILD_THREADS, 0, st>>>(
+                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done);
         ABILU_LAUNCH_CHECK("k_build_blocks_async");
     }
     return ABILU_OK;

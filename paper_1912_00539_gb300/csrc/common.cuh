@@ -89,6 +89,7 @@ struct abilu_factors_s {
     void *Udiag;
     void *A32;                 // FP32 copy of A's non-constant blocks (FP32/BF16 factors)
     void *r32;                 // FP32 copy of the apply input (FP32/BF16 factors)
+    int *chunk_done;           // per 32-block chunk: completed sweeps (ordered async builds)
     void *Us;                  // Dinv_i U_ij for every strictly upper block (FP32
                                // factors): the matrix of the upper sweeps, formed per build
     int cur;
