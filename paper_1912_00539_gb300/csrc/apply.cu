@@ -237,22 +237,24 @@ k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
     }
 }
 
-// ---------------------------------------------------------------- async, staged
-// The in-place sweeps with factors in FP32/BF16, as a warp-specialised
-// pipeline: a producer warp takes the next ticket (chunk, sweep), and copies
-// the chunk's read-only data -- its rows' factor blocks and column indices
-// (contiguous in the compact L/U arrays), its row pointers and right-hand side
-// -- into one of two shared-memory stages with bulk asynchronous copies, while
-// the 8 consumer warps (a quad per row) sweep the chunk staged before it.  The
-// in-place vector itself is never staged: every neighbour value is read from
-// global memory at the moment of the update, as in the unstaged kernels, so
-// the iteration is the same asynchronous iteration (Algorithm 5); only the
-// latency of the ticket, the row pointers and the factor rows leaves the
-// critical path.  A chunk with more than PIPE_CAP factor blocks is read from
-// global memory instead.  Lower (UPPER = false): y_i = b_i - sum L_ij y_j,
-// the last update of a row also forms x^1 = Dinv_i y_i into x1 / yh / z.
-// Upper: x_i = rhs_i - sum Us_ij x_j (SCALED) or Dinv_i (rhs_i - sum U_ij x_j),
-// chunks in backward order, the last update writes z.
+// ---------------------------------------------------------------- staged sweeps
+// The sweeps with factors in FP32/BF16, as a warp-specialised pipeline: a
+// producer warp picks the next chunk of 64 rows (ASYNC: the next ticket
+// (chunk, sweep) from the queue; SYNC: this CTA's next chunk in a static
+// round-robin) and copies the chunk's read-only data -- its rows' factor
+// blocks and column indices (contiguous in the compact L/U arrays), its row
+// pointers and right-hand side -- into one of two shared-memory stages with
+// bulk asynchronous copies, while 8 consumer warps (a quad per row) sweep the
+// chunk staged before it.  The swept vector is never staged: neighbour values
+// are read from global memory at the moment of the update (ASYNC: in place,
+// volatile, Algorithm 5; SYNC: from the previous iterate `vin`, written to
+// `v`), so each mode computes exactly what its unstaged form computes; only
+// the latency of the ticket, the row pointers and the factor rows leaves the
+// critical path.  A chunk with more than PIPE_CAP factor blocks reads them
+// from global memory.  Lower (UPPER = false): y_i = b_i - sum L_ij y_j; the
+// last update of a row also forms x^1 = Dinv_i y_i into x1 / yh / z.  Upper:
+// x_i = rhs_i - sum Us_ij x_j (SCALED) or Dinv_i (rhs_i - sum U_ij x_j),
+// ASYNC chunks in backward order; the last update writes z.
 constexpr int PIPE_CONSUMERS = 8;                          // warps
 constexpr int PIPE_THREADS = (PIPE_CONSUMERS + 1) * 32;    // + the producer warp
 constexpr int PIPE_CAP = 160;                              // factor blocks per stage
@@ -267,19 +269,19 @@ template <typename T> struct __align__(128) PipeStage {   // every field 16-byte
     int32_t fb, cb, staged, pad;
 };
 
-template <bool UPPER, bool SCALED, typename T>
+template <bool UPPER, bool SCALED, bool SYNC, typename T>
 __global__ void __launch_bounds__(PIPE_THREADS, 7)   // 7 x 288 threads per SM: 32 registers
-k_tri_async_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
-                   const float *__restrict__ rhs, float *v, int nsweeps,
-                   float *__restrict__ x1, float *__restrict__ yh, double *__restrict__ z,
-                   unsigned long long *ticket, unsigned long long *err, Skip skip) {
+k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
+             const float *__restrict__ rhs, const float *vin, float *v, int nsweeps, int sync_last,
+             float *__restrict__ x1, float *__restrict__ yh, double *__restrict__ z,
+             unsigned long long *ticket, unsigned long long *err, Skip skip) {
     if (skip_all(skip)) return;
     __shared__ __align__(128) PipeStage<T> st[2];
     __shared__ __align__(8) uint64_t full[2], empty[2];
     const int32_t *rowp = UPPER ? P.urow : P.lrow;
     const int32_t *colg = UPPER ? P.ucol : P.lcol;
     const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
-    const long long total = nchunks * nsweeps;
+    const long long total = SYNC ? nchunks : nchunks * nsweeps;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         mbar_init(&full[0], 1);
@@ -296,14 +298,15 @@ k_tri_async_staged(PatternView P, const T *__restrict__ F, const T *__restrict__
             const int s = k & 1, u = k >> 1;
             if (u >= 1 && !mbar_wait(&empty[s], (u - 1) & 1, err)) return;
             PipeStage<T> &S = st[s];
-            const long long t = (long long)atomicAdd(ticket, 1ull);
+            const long long t = SYNC ? (long long)blockIdx.x + (long long)k * gridDim.x
+                                     : (long long)atomicAdd(ticket, 1ull);
             if (t >= total) {
                 S.ticket = -1;
                 mbar_arrive(&full[s]);
                 return;
             }
             const int c = (int)(t % nchunks);
-            const int chunk = UPPER ? (int)(nchunks - 1 - c) : c;
+            const int chunk = (UPPER && !SYNC) ? (int)(nchunks - 1 - c) : c;
             const int i0 = chunk * APPLY_ROWS, i1 = min(i0 + APPLY_ROWS, P.n);
             const int fb = rowp[i0], fe = rowp[i1];
             const bool staged = fe - fb <= PIPE_CAP;
@@ -339,8 +342,8 @@ k_tri_async_staged(PatternView P, const T *__restrict__ F, const T *__restrict__
         const long long t = S.ticket;
         if (t < 0) return;
         const int c = (int)(t % nchunks);
-        const int chunk = UPPER ? (int)(nchunks - 1 - c) : c;
-        const bool last = t / nchunks == nsweeps - 1;
+        const int chunk = (UPPER && !SYNC) ? (int)(nchunks - 1 - c) : c;
+        const bool last = SYNC ? sync_last != 0 : t / nchunks == nsweeps - 1;
         const int i = chunk * APPLY_ROWS + r;
         if (i < P.n && !skip_chunk(skip, chunk)) {
             const int l0 = S.rowp[r], l1 = S.rowp[r + 1];
@@ -355,15 +358,20 @@ k_tri_async_staged(PatternView P, const T *__restrict__ F, const T *__restrict__
                     ld_row(F + (size_t)l * BB + q * BS, a);
                     j = colg[l];
                 }
-                ld_row_volatile(v + (size_t)j * BS, b);
+                if constexpr (SYNC) ld_row(vin + (size_t)j * BS, b);
+                else ld_row_volatile(v + (size_t)j * BS, b);
                 acc -= dot4(a, b);
             }
             float xi = acc;
             if constexpr (UPPER && !SCALED) xi = dinv_times<T, float>(D, i, acc);
-            st_vol(v + (size_t)i * BS + q, xi);
+            if constexpr (SYNC) {
+                if (v) v[(size_t)i * BS + q] = xi;
+            } else {
+                st_vol(v + (size_t)i * BS + q, xi);
+            }
             if (last) {
                 if constexpr (UPPER) {
-                    z[(size_t)i * BS + q] = to_f64v(xi);
+                    if (z) z[(size_t)i * BS + q] = to_f64v(xi);
                 } else if (x1 || yh || z) {
                     const float x = dinv_times<T, float>(D, i, acc);
                     if (x1) x1[(size_t)i * BS + q] = x;
@@ -417,8 +425,8 @@ template <typename T, typename VT> static int upper_async_ctas() {
     static int c = resident_ctas(k_upper_async<T, VT, std::is_same<T, float>::value>, APPLY_THREADS);
     return c;
 }
-template <bool UPPER, bool SCALED, typename T> static int staged_ctas() {
-    static int c = resident_ctas(k_tri_async_staged<UPPER, SCALED, T>, PIPE_THREADS);
+template <bool UPPER, bool SCALED, bool SYNC, typename T> static int staged_ctas() {
+    static int c = resident_ctas(k_tri_staged<UPPER, SCALED, SYNC, T>, PIPE_THREADS);
     return c;
 }
 
@@ -476,10 +484,10 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
         unsigned long long *err = f->ctr + 4;
         if (nl >= 2) {
             if constexpr (sizeof(VT) == 4) {  // staged pipeline (FP32/BF16 factors)
-                const int c = staged_ctas<false, false, T>();
+                const int c = staged_ctas<false, false, false, T>();
                 const int g = (int)(c < nchunks ? c : nchunks);
-                k_tri_async_staged<false, false, T><<<counted(g), PIPE_THREADS, 0, st>>>(
-                    P, L, D, rv, y[0], nl - 1, x1, yh, z1, tk, err, skip);
+                k_tri_staged<false, false, false, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+                    P, L, D, rv, nullptr, y[0], nl - 1, 0, x1, yh, z1, tk, err, skip);
             } else {
                 const int ctas_l = lower_async_ctas<T, VT>();
                 const int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
@@ -490,10 +498,11 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
         }
         if (nu >= 2) {
             if constexpr (sizeof(VT) == 4) {
-                const int c = staged_ctas<true, SC, T>();
+                const int c = staged_ctas<true, SC, false, T>();
                 const int g = (int)(c < nchunks ? c : nchunks);
-                k_tri_async_staged<true, SC, T><<<counted(g), PIPE_THREADS, 0, st>>>(
-                    P, UU, D, SC ? y[1] : y[0], x[0], nu - 1, nullptr, nullptr, z, tk + 1, err, skip);
+                k_tri_staged<true, SC, false, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+                    P, UU, D, SC ? y[1] : y[0], nullptr, x[0], nu - 1, 0, nullptr, nullptr, z, tk + 1,
+                    err, skip);
             } else {
                 const int ctas_u = upper_async_ctas<T, VT>();
                 const int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
@@ -525,10 +534,11 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             const bool last = s == nl;
             VT *yout = y[s & 1];
             if (last) x1 = nu >= 2 ? (SC ? yout : x[1]) : nullptr;
+            // (the staged form was measured slower for this sweep: 19.3 vs 17.1 us)
             k_lower_sync<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
                 P, L, rv, yprev, (last && SC) ? nullptr : yout, D, last ? x1 : nullptr,
                 (last && nu == 1) ? z : nullptr, skip);
-            ABILU_LAUNCH_CHECK("k_lower_sync");
+            ABILU_LAUNCH_CHECK("lower sync");
             yprev = yout;
         }
         yfin = yprev;   // y^{n_L}, or yh when scaled (written as x1 into the same buffer)
@@ -537,9 +547,17 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
     for (int s = 2; s <= nu; s++) {  // x^s in x[s & 1], the last one to z
         const bool last = s == nu;
         const VT *xin = s == 2 ? xfirst : x[(s - 1) & 1];
-        k_upper_sync<T, VT, SC><<<counted(grid), APPLY_THREADS, 0, st>>>(
-            P, UU, D, yfin, xin, last ? nullptr : x[s & 1], last ? z : nullptr, skip);
-        ABILU_LAUNCH_CHECK("k_upper_sync");
+        if constexpr (sizeof(VT) == 4) {
+            const int c = staged_ctas<true, SC, true, T>();
+            const int g = c < grid ? c : grid;
+            k_tri_staged<true, SC, true, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+                P, UU, D, yfin, xin, last ? nullptr : x[s & 1], 1, last ? 1 : 0, nullptr, nullptr,
+                last ? z : nullptr, nullptr, f->ctr + 4, skip);
+        } else {
+            k_upper_sync<T, VT, SC><<<counted(grid), APPLY_THREADS, 0, st>>>(
+                P, UU, D, yfin, xin, last ? nullptr : x[s & 1], last ? z : nullptr, skip);
+        }
+        ABILU_LAUNCH_CHECK("upper sync");
     }
     return ABILU_OK;
 }
@@ -550,12 +568,14 @@ void apply_warm(abilu_dtype dt) {
     switch (dt) {
     case ABILU_F64: lower_async_ctas<double, double>(); upper_async_ctas<double, double>(); break;
     case ABILU_F32:
-        staged_ctas<false, false, float>();
-        staged_ctas<true, true, float>();
+        staged_ctas<false, false, false, float>();
+        staged_ctas<true, true, false, float>();
+        staged_ctas<true, true, true, float>();
         break;
     case ABILU_BF16:
-        staged_ctas<false, false, __nv_bfloat16>();
-        staged_ctas<true, false, __nv_bfloat16>();
+        staged_ctas<false, false, false, __nv_bfloat16>();
+        staged_ctas<true, false, false, __nv_bfloat16>();
+        staged_ctas<true, false, true, __nv_bfloat16>();
         break;
     }
 }
