@@ -45,9 +45,10 @@ def _dist():
 # kernel code; set an entry to None when its kernel changes until it is
 # captured again)
 PROFILED_TRAFFIC = {
-    "spmv_f64": 295.449344e6 + 13.645312e6,          # k_spmv
-    "build_sweeps_f32": 1.446059e9 + 505.616640e6,   # k_build_blocks_async<float>, 6 sweeps
-    "build_sweep_f32": 281.962496e6 + 66.468096e6,   # k_build_blocks_sync<float>
+    "spmv_f64": 295.446016e6 + 15.301120e6,          # k_spmv<1>
+    "build_sweeps_f32": 1.352304e9 + 509.246208e6,   # k_build_blocks_async<float, 0>, 6 sweeps
+    "lower_sweeps_f32": 133.483264e6 + 10.764032e6,  # k_tri_staged lower, 3 sweeps
+    "upper_sweeps_f32": 79.600128e6 + 3.838720e6,    # k_tri_staged upper (scaled), 3 sweeps
 }
 
 
@@ -223,9 +224,10 @@ def kernel_rooflines(torch, ab, pat, A, fac, s, peak, mode="async"):
     out["spmv_f64"] = {"us": t, "bytes": nnzb * (128 + 4) + 4 * (N + 1) + 2 * 32 * N,
                        "sweeps": 1}
     # build: prepare pass + sweeps; the sweeps are the difference to 0 sweeps.
-    # One sweep's unique bytes over the work list: records, FP32 A rows, pair
-    # ranges and pairs, the pairs' L and U rows, Dinv read and written, L written
-    sweep_b = (nw * 16 + nw * 16 * f + 4 * (nnzb + 1) + npairs * 8 + 2 * npairs * 16 * f
+    # One sweep's unique bytes over the work list: the 32-byte records, FP32 A
+    # rows, the pair list (counted whole, though the first two pairs of a block
+    # sit in its record), the pairs' L and U rows, Dinv read and written, L written
+    sweep_b = (nw * 32 + nw * 16 * f + npairs * 8 + 2 * npairs * 16 * f
                + 2 * N * 16 * f + c["nl"] * 16 * f)
     nb = BUILD_SWEEPS
     t0 = avg_us(lambda: fac.build(A, 0, mode, init="previous"))
