@@ -400,6 +400,32 @@ def serving_stream(rate_hz: float, n_requests: int, seed=5, cells_lo=4000,
     return out
 
 
+@dataclass
+class SemilinearCase:
+    """A steady model problem r(w) = A w + kappa w|w| - f for the pseudo-time
+    continuation driver: `system` carries A (the generator's Jacobian-shaped
+    matrix with a small mass term) on its pattern, `w_star` the manufactured
+    solution (f = A w* + kappa w*|w*| is formed by whoever evaluates A, not
+    here), `shift_scale` s_i = the mean diagonal entry of A_ii (the pseudo-time
+    shift of row i is s_i / CFL), `kappa` the nonlinearity."""
+    system: System
+    w_star: np.ndarray
+    shift_scale: np.ndarray
+    kappa: float
+
+
+def semilinear_case(nx, ny, seed=7, kappa=0.5, cfl_base=1.0e4, order="rcm") -> SemilinearCase:
+    """Seeded model problem on an nx x ny triangulated quad grid (three grid,
+    value and solution seeds derived from ``seed``)."""
+    s = make_system(nx, ny, 2000 + 3 * seed, 2001 + 3 * seed, 2002 + 3 * seed, cfl_base,
+                    order=order, name=f"semilinear{nx}x{ny}_s{seed}")
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    diag = s.vals[rows == s.colind]                      # [n][4][4], in row order
+    scale = np.einsum("nii->n", diag) / BS
+    w_star = np.random.default_rng(2003 + 3 * seed).standard_normal((s.n, BS))
+    return SemilinearCase(s, np.ascontiguousarray(w_star), np.ascontiguousarray(scale), float(kappa))
+
+
 def random_pattern_system(n: int, extra_edges: int, seed: int, cfl: float = 10.0,
                           structure: str = "general") -> System:
     """Small system on a random symmetric block pattern (with triangles).

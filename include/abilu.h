@@ -291,6 +291,18 @@ abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts, fgmres_re
 abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x, abilu_stream stream);
 
 /*
+ * abilu_add_block_diagonal — A_out = A_in + diag(d_i) on every diagonal block:
+ * A_out[diag of row i][c][c] = A_in[...][c][c] + d[i][c], every other entry
+ * copied.  The pseudo-time matrix M_tau + dr/dw of Sec. 2 (Eq. pseudotimestep)
+ * is assembled this way each step, the shift being V_i / dtau_i (and any
+ * diagonal part of the Jacobian that changes with the state).  A_in, A_out:
+ * double[nnzb][4][4] in the pattern's layout (they may be the same array);
+ * d: double[n][4].  Device pointers, caller-owned.  Asynchronous on `stream`.
+ */
+abilu_status abilu_add_block_diagonal(abilu_pattern p, const double *A_in, double *A_out,
+                                      const double *d, abilu_stream stream);
+
+/*
  * abilu_to_f32 — out[i] = in[i] rounded to FP32, round to nearest even, for
  * i < n: the conversion FGMRES uses to hand the normalised Krylov vector to
  * FP32/BF16 preconditioners, done with integer instructions only (this GPU's

@@ -34,7 +34,8 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_factors_diagnostics",
            "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc", "abilu_batch_create",
            "abilu_batch_destroy", "abilu_batch_counts", "abilu_batch_set_system",
-           "abilu_batch_solve", "abilu_batch_get_solution", "abilu_to_f32")
+           "abilu_batch_solve", "abilu_batch_get_solution", "abilu_add_block_diagonal",
+           "abilu_to_f32")
 
 
 class FgmresOpts(C.Structure):
@@ -67,6 +68,7 @@ _lib.abilu_apply.argtypes = [_vp, _vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
 _lib.bsr_spmv.argtypes = [_vp, _vp, _f64, _vp, _f64, _vp, _vp]
 _lib.abilu_apply_noalloc.argtypes = [_i32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp]
 _lib.abilu_to_f32.argtypes = [_vp, _vp, _i64, _vp]
+_lib.abilu_add_block_diagonal.argtypes = [_vp, _vp, _vp, _vp, _vp]
 _lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
@@ -85,7 +87,8 @@ _lib.abilu_batch_set_system.argtypes = [_vp, _i32, _vp, _vp, _vp]
 _lib.abilu_batch_solve.argtypes = [_vp, C.POINTER(FgmresOpts), C.POINTER(FgmresResult), _vp]
 _lib.abilu_batch_get_solution.argtypes = [_vp, _i32, _vp, _vp]
 for _nm in ("abilu_batch_create", "abilu_batch_counts", "abilu_batch_set_system",
-            "abilu_batch_solve", "abilu_batch_get_solution", "abilu_to_f32"):
+            "abilu_batch_solve", "abilu_batch_get_solution", "abilu_add_block_diagonal",
+           "abilu_to_f32"):
     getattr(_lib, _nm).restype = C.c_int
 for _nm in ("abilu_pattern_create", "abilu_pattern_counts", "abilu_factors_create", "abilu_build",
             "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
@@ -219,6 +222,16 @@ def bsr_spmv(pattern: Pattern, A, x, y, alpha=1.0, beta=0.0, stream=None):
     _check(_lib.bsr_spmv(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
                          float(alpha), _ptr(x, torch.float64, nv, "x"), float(beta),
                          _ptr(y, torch.float64, nv, "y"), _stream(stream)))
+
+
+def add_block_diagonal(pattern: Pattern, A_in, A_out, d, stream=None):
+    """abilu_add_block_diagonal: A_out = A_in + diag(d_i) on the diagonal blocks
+    (the pseudo-time shift of Sec. 2); A_in and A_out may be the same tensor."""
+    import torch
+    nb = 16 * pattern.nnzb
+    _check(_lib.abilu_add_block_diagonal(pattern.handle, _ptr(A_in, torch.float64, nb, "A_in"),
+                                         _ptr(A_out, torch.float64, nb, "A_out"),
+                                         _ptr(d, torch.float64, 4 * pattern.n, "d"), _stream(stream)))
 
 
 def to_f32(x, out, stream=None):

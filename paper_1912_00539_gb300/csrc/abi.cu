@@ -190,3 +190,31 @@ extern "C" abilu_status abilu_to_f32(const double *in, float *out, int64_t n, ab
     ABILU_LAUNCH_CHECK("k_to_f32_int");
     return ABILU_OK;
 }
+
+namespace abilu {
+// one thread per (block, row q): the row of 4 values, plus d on the diagonal
+__global__ void k_add_block_diagonal(PatternView P, const double *__restrict__ Ain,
+                                     double *Aout, const double *__restrict__ d) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p = e >> 2;
+    const int q = (int)(e & 3);
+    if (p >= P.nnzb) return;
+    double v[4];
+    ld_row(Ain + (size_t)p * BB + q * BS, v);
+    // p is a diagonal block iff p == diagpos[row of p]; rows are found from
+    // the column: a diagonal block has colind[p] = i and diagpos[i] = p
+    const int j = P.colind[p];
+    if (P.diagpos[j] == p) v[q] += d[(size_t)j * BS + q];
+    st_row(Aout + (size_t)p * BB + q * BS, v);
+}
+}  // namespace abilu
+
+extern "C" abilu_status abilu_add_block_diagonal(abilu_pattern p, const double *A_in, double *A_out,
+                                                 const double *d, abilu_stream stream) {
+    if (!p || !A_in || !A_out || !d) return fail(ABILU_EINVAL, "add_block_diagonal: NULL argument");
+    const long long threads = (long long)p->v.nnzb * 4;
+    k_add_block_diagonal<<<counted((int)((threads + 255) / 256)), 256, 0, S(stream)>>>(p->v, A_in,
+                                                                                      A_out, d);
+    ABILU_LAUNCH_CHECK("k_add_block_diagonal");
+    return ABILU_OK;
+}
