@@ -462,6 +462,7 @@ def run_viscous(args):
     """Viscous-like anisotropic grid (1024x256, CFL 1e4, wall-normal coupling
     x100): RCM vs wall-normal line ordering, FP32 factors, 8 build and 6+6
     apply sweeps, FGMRES(50) to 1e-6; iterations against the FP64 oracle."""
+    import numpy as np
     import torch
     import abilu_inputs as gen
     import oracle
@@ -499,6 +500,45 @@ def run_viscous(args):
             row[f"{dt}_{md}"] = {"iters": r.iters, "rel_resid_true": r.rel_resid_true,
                                  "solves_per_s": round(5 / (e0.elapsed_time(e1) * 1e-3), 1)}
         out[order] = row
+    # the library's orderings of the same grid (from its natural numbering):
+    # RCM, one-way dissection, lines found from the block norms, and the
+    # hybrid line-RCM / line-1WD orderings of the graph of lines and cells
+    s0 = gen.make_system(1024, 256, 301, 302, 303, 1.0e4, order="natural", wall_normal_scale=100.0)
+    st = gen.SOLVER_SETTINGS["viscous_1024x256_rcm"]
+    lib = {}
+    for kind in ("rcm", "1wd", "line", "line-rcm", "line-1wd"):
+        t0 = time.perf_counter()
+        perm, line_of = ab.order(s0.rowptr, s0.colind, kind, vals=s0.vals, line_threshold=10.0)
+        t_order = time.perf_counter() - t0
+        ro, co, src = ab.permute_pattern(s0.rowptr, s0.colind, perm)
+        pat = ab.Pattern(torch.from_numpy(ro).cuda(), torch.from_numpy(co).cuda())
+        A0 = torch.from_numpy(s0.vals).cuda()
+        A = torch.empty_like(A0)
+        ab.gather_blocks(torch.from_numpy(src).cuda(), A0, A)
+        b = torch.from_numpy(np.ascontiguousarray(s0.b[perm])).cuda()
+        row = {"lines": int(line_of.max() + 1), "order_s": round(t_order, 3)}
+        for dt, md in (("f32", "sync"), ("f32", "async")):
+            fac = ab.Factors(pat, dt)
+            x = torch.zeros_like(b)
+
+            def solve():
+                x.zero_()
+                return ab.fgmres_solve(pat, A, fac, b, x, restart=st["restart"], rtol=st["rtol"],
+                                       build_sweeps=st["build_sweeps"],
+                                       apply_sweeps_lower=st["apply_sweeps"],
+                                       apply_sweeps_upper=st["apply_sweeps"], mode=md)
+            r = solve()
+            torch.cuda.synchronize()
+            e0, e1 = _events(torch, 2)
+            e0.record()
+            for _ in range(5):
+                r = solve()
+            e1.record()
+            torch.cuda.synchronize()
+            row[f"{dt}_{md}"] = {"iters": r.iters, "rel_resid_true": _r(r.rel_resid_true),
+                                 "solves_per_s": round(5 / (e0.elapsed_time(e1) * 1e-3), 1)}
+        lib[kind] = row
+    out["library_orderings"] = lib
     return out
 
 

@@ -291,6 +291,61 @@ abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts, fgmres_re
 abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x, abilu_stream stream);
 
 /*
+ * Orderings of the cell graph (Sec. 5), host code on host arrays.  `kind`:
+ *   ABILU_ORDER_RCM       reverse Cuthill-McKee (pseudo-peripheral start,
+ *                         neighbours by increasing degree), per component;
+ *   ABILU_ORDER_1WD       one-way dissection: level sets of a rooted level
+ *                         structure every delta = sqrt((3 w + 13) / 2) levels
+ *                         (w = mean level width) are separators, the blocks
+ *                         between them are numbered first (each by RCM), the
+ *                         separators last;
+ *   ABILU_ORDER_LINE      lines of strongly coupled cells (Sec. 5.1) made
+ *                         contiguous, each at the position of its first cell;
+ *   ABILU_ORDER_LINE_RCM, ABILU_ORDER_LINE_1WD  the graph of lines and
+ *                         single cells (Sec. 5.2) ordered by RCM / 1WD, every
+ *                         line expanded in place.
+ * Lines: a cell is anisotropic when its strongest coupling exceeds its
+ * weakest by more than `line_threshold` (> 1); from the most anisotropic free
+ * cell a line grows at both ends to the strongest-coupled free neighbour while
+ * that coupling exceeds `line_threshold` times the end cell's weakest coupling
+ * and is at least the neighbour's strongest coupling / `line_threshold`; a
+ * cell with no weak coupling (a side boundary) is measured against the line's
+ * last anisotropic cell, at most two such cells in a row.
+ * Couplings: `weights` double[nnzb] per block (e.g. geometric), else the
+ * Frobenius norms of `vals` double[nnzb][4][4]; one of them is required for
+ * the line kinds, both may be NULL otherwise.  rowptr int32[n+1], colind
+ * int32[nnzb] (the block pattern; symmetrised internally).  Output perm
+ * int32[n]: perm[k] = the old index of the cell numbered k; line_of (may be
+ * NULL) int32[n]: each old cell's line index, -1 for cells in no line.  All
+ * pointers are HOST pointers; no device work.  ABILU_EINVAL on bad input.
+ */
+typedef enum {
+    ABILU_ORDER_RCM = 0,
+    ABILU_ORDER_1WD = 1,
+    ABILU_ORDER_LINE = 2,
+    ABILU_ORDER_LINE_RCM = 3,
+    ABILU_ORDER_LINE_1WD = 4
+} abilu_ordering;
+abilu_status abilu_order(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                         const double *weights, const double *vals, int32_t kind,
+                         double line_threshold, int32_t *perm, int32_t *line_of);
+
+/*
+ * The pattern renumbered by perm (as abilu_order returns it): row k of the
+ * result is old row perm[k] with its columns renumbered and sorted.  HOST
+ * arrays: rowptr_out int32[n+1], colind_out int32[nnzb], src_out int32[nnzb]
+ * (the old position of each new block, for abilu_gather_blocks).
+ */
+abilu_status abilu_permute_pattern(int32_t n, const int32_t *rowptr, const int32_t *colind,
+                                   const int32_t *perm, int32_t *rowptr_out, int32_t *colind_out,
+                                   int32_t *src_out);
+
+/* vals_out[p] = vals_in[src[p]] for p < nnzb (4x4 FP64 blocks), on the device:
+ * the block values in a renumbered pattern.  Device pointers, distinct arrays. */
+abilu_status abilu_gather_blocks(int64_t nnzb, const int32_t *src, const double *vals_in,
+                                 double *vals_out, abilu_stream stream);
+
+/*
  * abilu_add_block_diagonal — A_out = A_in + diag(d_i) on every diagonal block:
  * A_out[diag of row i][c][c] = A_in[...][c][c] + d[i][c], every other entry
  * copied.  The pseudo-time matrix M_tau + dr/dw of Sec. 2 (Eq. pseudotimestep)

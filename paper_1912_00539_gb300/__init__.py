@@ -4,5 +4,5 @@ The computation lives in libabilu.so (hand-written sm_103a CUDA behind the C
 ABI of include/abilu.h); ``abilu`` is its thin Python binding.
 """
 from .abilu import (AbiluError, Batch, Factors, Pattern, SolveResult,  # noqa: F401
-                    add_block_diagonal, bsr_spmv, default_opts, fgmres_solve, kernel_launches,
-                    to_f32, version)
+                    add_block_diagonal, bsr_spmv, default_opts, fgmres_solve, gather_blocks,
+                    kernel_launches, order, permute_pattern, to_f32, version)

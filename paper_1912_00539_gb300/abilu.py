@@ -34,7 +34,8 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_factors_diagnostics",
            "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc", "abilu_batch_create",
            "abilu_batch_destroy", "abilu_batch_counts", "abilu_batch_set_system",
-           "abilu_batch_solve", "abilu_batch_get_solution", "abilu_add_block_diagonal",
+           "abilu_batch_solve", "abilu_batch_get_solution", "abilu_order",
+           "abilu_permute_pattern", "abilu_gather_blocks", "abilu_add_block_diagonal",
            "abilu_to_f32")
 
 
@@ -69,6 +70,9 @@ _lib.bsr_spmv.argtypes = [_vp, _vp, _f64, _vp, _f64, _vp, _vp]
 _lib.abilu_apply_noalloc.argtypes = [_i32, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp]
 _lib.abilu_to_f32.argtypes = [_vp, _vp, _i64, _vp]
 _lib.abilu_add_block_diagonal.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.abilu_order.argtypes = [_i32, _vp, _vp, _vp, _vp, _i32, _f64, _vp, _vp]
+_lib.abilu_permute_pattern.argtypes = [_i32, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.abilu_gather_blocks.argtypes = [_i64, _vp, _vp, _vp, _vp]
 _lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
@@ -87,7 +91,8 @@ _lib.abilu_batch_set_system.argtypes = [_vp, _i32, _vp, _vp, _vp]
 _lib.abilu_batch_solve.argtypes = [_vp, C.POINTER(FgmresOpts), C.POINTER(FgmresResult), _vp]
 _lib.abilu_batch_get_solution.argtypes = [_vp, _i32, _vp, _vp]
 for _nm in ("abilu_batch_create", "abilu_batch_counts", "abilu_batch_set_system",
-            "abilu_batch_solve", "abilu_batch_get_solution", "abilu_add_block_diagonal",
+            "abilu_batch_solve", "abilu_batch_get_solution", "abilu_order",
+           "abilu_permute_pattern", "abilu_gather_blocks", "abilu_add_block_diagonal",
            "abilu_to_f32"):
     getattr(_lib, _nm).restype = C.c_int
 for _nm in ("abilu_pattern_create", "abilu_pattern_counts", "abilu_factors_create", "abilu_build",
@@ -222,6 +227,58 @@ def bsr_spmv(pattern: Pattern, A, x, y, alpha=1.0, beta=0.0, stream=None):
     _check(_lib.bsr_spmv(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
                          float(alpha), _ptr(x, torch.float64, nv, "x"), float(beta),
                          _ptr(y, torch.float64, nv, "y"), _stream(stream)))
+
+
+ORDERINGS = {"rcm": 0, "1wd": 1, "line": 2, "line-rcm": 3, "line-1wd": 4}
+
+
+def _host(a, dtype):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, C.c_void_p(a.ctypes.data)
+
+
+def order(rowptr, colind, kind="rcm", weights=None, vals=None, line_threshold=10.0):
+    """abilu_order on host (numpy) arrays: returns (perm, line_of), perm[k] =
+    the old index of the cell numbered k, line_of[c] = the line of old cell c
+    (-1: none)."""
+    import numpy as np
+    n = len(rowptr) - 1
+    rp, prp = _host(rowptr, np.int32)
+    ci, pci = _host(colind, np.int32)
+    w, pw = _host(weights, np.float64) if weights is not None else (None, None)
+    v, pv = _host(vals, np.float64) if vals is not None else (None, None)
+    perm = np.empty(n, np.int32)
+    line_of = np.empty(n, np.int32)
+    _check(_lib.abilu_order(n, prp, pci, pw, pv, ORDERINGS[kind], float(line_threshold),
+                            C.c_void_p(perm.ctypes.data), C.c_void_p(line_of.ctypes.data)))
+    return perm, line_of
+
+
+def permute_pattern(rowptr, colind, perm):
+    """abilu_permute_pattern on host arrays: (rowptr, colind, src) of the
+    pattern renumbered by perm; src[p] = the old position of new block p."""
+    import numpy as np
+    n = len(rowptr) - 1
+    rp, prp = _host(rowptr, np.int32)
+    ci, pci = _host(colind, np.int32)
+    pm, ppm = _host(perm, np.int32)
+    ro = np.empty(n + 1, np.int32)
+    co = np.empty(len(colind), np.int32)
+    src = np.empty(len(colind), np.int32)
+    _check(_lib.abilu_permute_pattern(n, prp, pci, ppm, C.c_void_p(ro.ctypes.data),
+                                      C.c_void_p(co.ctypes.data), C.c_void_p(src.ctypes.data)))
+    return ro, co, src
+
+
+def gather_blocks(src, vals_in, vals_out, stream=None):
+    """abilu_gather_blocks: vals_out[p] = vals_in[src[p]] on the device."""
+    import torch
+    nnzb = src.numel()
+    _check(_lib.abilu_gather_blocks(nnzb, _ptr(src, torch.int32, what="src"),
+                                    _ptr(vals_in, torch.float64, what="vals_in"),
+                                    _ptr(vals_out, torch.float64, 16 * nnzb, "vals_out"),
+                                    _stream(stream)))
 
 
 def add_block_diagonal(pattern: Pattern, A_in, A_out, d, stream=None):
