@@ -73,8 +73,16 @@ def _load():
         lib.orc_lu_defect_max.argtypes = [i32, _PI, _PI, _PD, _PD]
         lib.orc_lu_defect_max.restype = f64
         lib.orc_jacobi_norms.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
+        lib.orc_silu0_seq.argtypes = [i32, _PI, _PI, _PD, _PD]
+        lib.orc_silu0_seq.restype = C.c_int
+        lib.orc_silu_sync_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD]
+        lib.orc_silu_sync_sweep.restype = C.c_int
+        lib.orc_silu_lower_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
+        lib.orc_silu_upper_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
+        lib.orc_silu_apply.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, C.c_int, C.c_int, _PD]
         for nm in ("orc_lower_sweep", "orc_upper_sweep", "orc_lower_solve", "orc_upper_solve",
-                   "orc_apply", "orc_spmv", "orc_jacobi_norms"):
+                   "orc_apply", "orc_spmv", "orc_jacobi_norms", "orc_silu_lower_sweep",
+                   "orc_silu_upper_sweep", "orc_silu_apply"):
             getattr(lib, nm).restype = None
         _lib = lib
     return _lib
@@ -236,11 +244,15 @@ class FgmresResult:
 
 def fgmres(rowptr, colind, A, X, Dinv, b, n_lower, n_upper, restart=30, max_iters=2500,
            rtol=1e-6, x0=None):
-    """FGMRES(restart) with the block ILU preconditioner (X, Dinv) -> (x, result)."""
+    """FGMRES(restart) with the block ILU preconditioner (X, Dinv) -> (x, result);
+    Dinv=None: X holds scalar ILU factors (silu_*)."""
     n, keep, prp, pci = _pattern(rowptr, colind)
     A, pA = _d(A)
     X, pX = _d(X)
-    Dinv, pD = _d(Dinv)
+    if Dinv is None:
+        pD = None
+    else:
+        Dinv, pD = _d(Dinv)
     b, pb = _d(b)
     x = np.zeros((n, 4)) if x0 is None else np.array(x0, np.float64)
     res = _Res()
@@ -274,3 +286,63 @@ def jacobi_norms(rowptr, colind, X, Dinv):
     ln, un = C.c_double(), C.c_double()
     _load().orc_jacobi_norms(n, prp, pci, pX, pD, C.byref(ln), C.byref(un))
     return ln.value, un.value
+
+
+# ---------------------------------------------------------- scalar ILU(0)
+# Factors in A's block layout: blocks left of the diagonal hold L entries,
+# right of it U entries; a diagonal block holds its strictly lower L entries
+# (unit diagonal implied) and the rest of U.
+
+def silu0_seq(rowptr, colind, A):
+    """Sequential scalar ILU(0) on the scalar pattern -> (X, replaced pivots)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X = np.empty_like(A)
+    ns = _load().orc_silu0_seq(n, prp, pci, pA, X.ctypes.data_as(_PD))
+    return X, ns
+
+
+def silu_sync(rowptr, colind, A, nsweeps, X0=None):
+    """nsweeps Chow-Patel Jacobi-type sweeps from X0 (default A) -> (X, replaced pivots)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X = np.array(A if X0 is None else X0, np.float64)
+    Y = np.empty_like(X)
+    total = 0
+    for _ in range(nsweeps):
+        total += _load().orc_silu_sync_sweep(n, prp, pci, pA, X.ctypes.data_as(_PD),
+                                             Y.ctypes.data_as(_PD))
+        X, Y = Y, X
+    return X, total
+
+
+def silu_lower_sweep(rowptr, colind, X, r, y_in):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    r, pr = _d(r)
+    y_in, py = _d(y_in)
+    out = np.empty((n, 4))
+    _load().orc_silu_lower_sweep(n, prp, pci, pX, pr, py, out.ctypes.data_as(_PD))
+    return out
+
+
+def silu_upper_sweep(rowptr, colind, X, y, x_in):
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    y, py = _d(y)
+    x_in, px = _d(x_in)
+    out = np.empty((n, 4))
+    _load().orc_silu_upper_sweep(n, prp, pci, pX, py, px, out.ctypes.data_as(_PD))
+    return out
+
+
+def silu_apply(rowptr, colind, X, r, n_lower, n_upper):
+    """z ~= (LU)^{-1} r with scalar factors (negative sweep counts: exact)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    X, pX = _d(X)
+    r, pr = _d(r)
+    z = np.empty((n, 4))
+    work = np.empty(2 * n * 4)
+    _load().orc_silu_apply(n, prp, pci, pX, pr, z.ctypes.data_as(_PD), int(n_lower),
+                           int(n_upper), work.ctypes.data_as(_PD))
+    return z

@@ -435,12 +435,16 @@ typedef struct {
  * Right-preconditioned flexible GMRES(m) (Saad's FGMRES, used by the paper
  * through PETSc, Sec. 2 / Sec. 6 setup), with modified Gram-Schmidt and Givens
  * rotations.  The preconditioner is the block ILU given by (X, Dinv), applied
- * with n_lower / n_upper Jacobi sweeps (negative: exact).  x holds x0 on entry
+ * with n_lower / n_upper Jacobi sweeps (negative: exact); with Dinv == NULL it
+ * is the scalar ILU held in X (orc_silu_apply).  x holds x0 on entry
  * and the solution on exit.  Stops when the Givens residual estimate drops to
  * rtol*||b||, confirmed at the end of the cycle by the explicit residual; an
  * unconfirmed estimate restarts.  Stops at max_iters Arnoldi steps.
  * hist (may be NULL, max_iters+1 entries) receives |g_{j+1}| / ||b|| per step.
  */
+void orc_silu_apply(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *X,
+                    const double *r, double *z, int n_lower, int n_upper, double *work);
+
 int orc_fgmres(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
                const double *X, const double *Dinv, int n_lower, int n_upper,
                const double *b, double *x, int m, int max_iters, double rtol,
@@ -488,7 +492,8 @@ int orc_fgmres(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *
         int kdim = 0;
         for (int j = 0; j < m; j++) {
             double *vj = V + (long)j * nv, *zj = Z + (long)j * nv;
-            orc_apply(n, rowptr, colind, X, Dinv, vj, zj, n_lower, n_upper, work);
+            if (Dinv) orc_apply(n, rowptr, colind, X, Dinv, vj, zj, n_lower, n_upper, work);
+            else orc_silu_apply(n, rowptr, colind, X, vj, zj, n_lower, n_upper, work);
             orc_spmv(n, rowptr, colind, A, zj, w);
             for (int i = 0; i <= j; i++) { /* modified Gram-Schmidt */
                 double hij = dot(nv, w, V + (long)i * nv);
@@ -631,4 +636,213 @@ void orc_jacobi_norms(idx_t n, const idx_t *rowptr, const idx_t *colind,
     }
     *lnorm = ln;
     *unorm = un;
+}
+
+/* ------------------------------------------------ scalar ILU(0) (Chow-Patel) */
+
+/*
+ * The scalar variant the paper compares against (Sec. 3.2, Eq.
+ * scalarilu_fp_detail, Algorithm 3): ILU(0) of A taken entry by entry on the
+ * scalar pattern S = every entry of every block of S_B,
+ *   L_ij = (A_ij - sum_{k<j} L_ik U_kj) / U_jj   (i > j),
+ *   U_ij =  A_ij - sum_{k<i} L_ik U_kj           (i <= j),
+ * sums over k with (i,k) and (k,j) in S, ascending k, in a local accumulator.
+ * L has a unit diagonal.  The factors are returned in A's block layout: blocks
+ * left of the diagonal hold L entries, blocks right of it U entries, and a
+ * diagonal block holds its strictly lower entries of L and the rest of U.
+ * A zero pivot U_jj is replaced by 1 ("modified Jacobi-type iteration" of
+ * Chow and Patel, Sec. 3.2) and counted.
+ *
+ * The oracle works on the plain scalar CSR expansion of the block pattern:
+ * scalar row 4I+a holds the columns 4J+b of every block (I,J), ascending.
+ */
+typedef struct {
+    idx_t ns;       /* scalar rows */
+    long *ptr;      /* [ns+1] */
+    idx_t *col;     /* [nnz] scalar columns, ascending per row */
+    long *bpos;     /* [nnz] index into the block values: 16*p + 4*a + b */
+    long *dpos;     /* [ns] position of the diagonal entry in the scalar row */
+} scsr;
+
+static void scsr_free(scsr *s) { free(s->ptr); free(s->col); free(s->bpos); free(s->dpos); }
+
+static int scsr_from_blocks(idx_t n, const idx_t *rowptr, const idx_t *colind, scsr *s)
+{
+    s->ns = n * BS;
+    long nnz = (long)rowptr[n] * BB;
+    s->ptr = malloc(sizeof(long) * ((size_t)s->ns + 1));
+    s->col = malloc(sizeof(idx_t) * (size_t)nnz);
+    s->bpos = malloc(sizeof(long) * (size_t)nnz);
+    s->dpos = malloc(sizeof(long) * (size_t)s->ns);
+    if (!s->ptr || !s->col || !s->bpos || !s->dpos) { scsr_free(s); return -1; }
+    long o = 0;
+    for (idx_t I = 0; I < n; I++)
+        for (int a = 0; a < BS; a++) {
+            idx_t i = I * BS + a;
+            s->ptr[i] = o;
+            s->dpos[i] = -1;
+            for (idx_t p = rowptr[I]; p < rowptr[I + 1]; p++)
+                for (int b = 0; b < BS; b++) {
+                    idx_t j = colind[p] * BS + b;
+                    s->col[o] = j;
+                    s->bpos[o] = (long)p * BB + a * BS + b;
+                    if (j == i) s->dpos[i] = o;
+                    o++;
+                }
+        }
+    s->ptr[s->ns] = o;
+    return 0;
+}
+
+/* position of scalar entry (i, j) in the expansion, or -1 */
+static long scsr_find(const scsr *s, idx_t i, idx_t j)
+{
+    long lo = s->ptr[i], hi = s->ptr[i + 1];
+    while (lo < hi) {
+        long mid = (lo + hi) / 2;
+        if (s->col[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < s->ptr[i + 1] && s->col[lo] == j) ? lo : -1;
+}
+
+/* A_ij - sum_{k < min(i,j)} L_ik U_kj for the entry at position o of row i,
+ * reading the factors from F (block layout) */
+static double silu_residual(const scsr *s, const double *A, const double *F, idx_t i, long o)
+{
+    idx_t j = s->col[o];
+    idx_t kmax = i < j ? i : j;
+    double acc = A[s->bpos[o]];
+    for (long q = s->ptr[i]; q < s->ptr[i + 1] && s->col[q] < kmax; q++) {
+        idx_t k = s->col[q];
+        long r = scsr_find(s, k, j);
+        if (r >= 0) acc -= F[s->bpos[q]] * F[s->bpos[r]];
+    }
+    return acc;
+}
+
+/* the pivot U_jj as used by an L update: 1 if zero or non-finite (counted) */
+static double silu_pivot(const scsr *s, const double *F, idx_t j, int *nsing)
+{
+    double u = F[s->bpos[s->dpos[j]]];
+    if (u == 0.0 || !isfinite(u)) { (*nsing)++; return 1.0; }
+    return u;
+}
+
+/* Sequential scalar ILU(0): every entry once, scalar rows in order, columns
+ * ascending (the Gaussian-elimination order, Algorithm 3 with one thread).
+ * Returns the number of replaced pivots (or -1: out of memory). */
+int orc_silu0_seq(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A, double *X)
+{
+    scsr s;
+    if (scsr_from_blocks(n, rowptr, colind, &s)) return -1;
+    int nsing = 0;
+    memcpy(X, A, sizeof(double) * (size_t)rowptr[n] * BB);
+    for (idx_t i = 0; i < s.ns; i++)
+        for (long o = s.ptr[i]; o < s.ptr[i + 1]; o++) {
+            idx_t j = s.col[o];
+            double v = silu_residual(&s, A, X, i, o);
+            X[s.bpos[o]] = j < i ? v / silu_pivot(&s, X, j, &nsing) : v;
+        }
+    scsr_free(&s);
+    return nsing;
+}
+
+/* One synchronous (Jacobi-type) sweep of Eq. (scalarilu_fp): every entry of
+ * Xout from Xin.  The initial guess of the iteration is A itself (Sec. 6
+ * setup: L^0 = strictly lower part of A unscaled, U^0 = the rest). */
+int orc_silu_sync_sweep(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+                        const double *Xin, double *Xout)
+{
+    scsr s;
+    if (scsr_from_blocks(n, rowptr, colind, &s)) return -1;
+    int nsing = 0;
+    for (idx_t i = 0; i < s.ns; i++)
+        for (long o = s.ptr[i]; o < s.ptr[i + 1]; o++) {
+            idx_t j = s.col[o];
+            double v = silu_residual(&s, A, Xin, i, o);
+            Xout[s.bpos[o]] = j < i ? v / silu_pivot(&s, Xin, j, &nsing) : v;
+        }
+    scsr_free(&s);
+    return nsing;
+}
+
+/* One Jacobi sweep of the scalar lower solve (unit diagonal, Algorithm 2):
+ * y_out_i = r_i - sum_{j<i} L_ij y_in_j */
+void orc_silu_lower_sweep(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *X,
+                          const double *r, const double *y_in, double *y_out)
+{
+    scsr s;
+    if (scsr_from_blocks(n, rowptr, colind, &s)) return;
+    for (idx_t i = 0; i < s.ns; i++) {
+        double acc = r[i];
+        for (long o = s.ptr[i]; o < s.ptr[i + 1] && s.col[o] < i; o++)
+            acc -= X[s.bpos[o]] * y_in[s.col[o]];
+        y_out[i] = acc;
+    }
+    scsr_free(&s);
+}
+
+/* One Jacobi sweep of the scalar upper solve (Algorithm 2, backward):
+ * x_out_i = (y_i - sum_{j>i} U_ij x_in_j) / U_ii (a zero U_ii taken as 1) */
+void orc_silu_upper_sweep(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *X,
+                          const double *y, const double *x_in, double *x_out)
+{
+    scsr s;
+    if (scsr_from_blocks(n, rowptr, colind, &s)) return;
+    for (idx_t i = 0; i < s.ns; i++) {
+        double acc = y[i];
+        for (long o = s.dpos[i] + 1; o < s.ptr[i + 1]; o++)
+            acc -= X[s.bpos[o]] * x_in[s.col[o]];
+        double u = X[s.bpos[s.dpos[i]]];
+        if (u == 0.0 || !isfinite(u)) u = 1.0;
+        x_out[i] = acc / u;
+    }
+    scsr_free(&s);
+}
+
+/* z ~= (L U)^{-1} r: n_lower Jacobi sweeps on L y = r from y = 0, then n_upper
+ * on U z = y from z = 0 (n_lower/n_upper < 0: exact substitution).
+ * work: 2 * n * 4 doubles. */
+void orc_silu_apply(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *X,
+                    const double *r, double *z, int n_lower, int n_upper, double *work)
+{
+    long nv = (long)n * BS;
+    double *y = work, *t = work + nv;
+    if (n_lower < 0) {  /* forward substitution: the Jacobi sweep run in row order in place */
+        scsr s;
+        if (scsr_from_blocks(n, rowptr, colind, &s)) return;
+        for (idx_t i = 0; i < s.ns; i++) {
+            double acc = r[i];
+            for (long o = s.ptr[i]; o < s.ptr[i + 1] && s.col[o] < i; o++)
+                acc -= X[s.bpos[o]] * y[s.col[o]];
+            y[i] = acc;
+        }
+        scsr_free(&s);
+    } else {
+        memset(y, 0, sizeof(double) * nv);
+        for (int k = 0; k < n_lower; k++) {
+            orc_silu_lower_sweep(n, rowptr, colind, X, r, y, t);
+            memcpy(y, t, sizeof(double) * nv);
+        }
+    }
+    if (n_upper < 0) {  /* back substitution */
+        scsr s;
+        if (scsr_from_blocks(n, rowptr, colind, &s)) return;
+        for (idx_t i = s.ns - 1; i >= 0; i--) {
+            double acc = y[i];
+            for (long o = s.dpos[i] + 1; o < s.ptr[i + 1]; o++)
+                acc -= X[s.bpos[o]] * z[s.col[o]];
+            double u = X[s.bpos[s.dpos[i]]];
+            if (u == 0.0 || !isfinite(u)) u = 1.0;
+            z[i] = acc / u;
+        }
+        scsr_free(&s);
+    } else {
+        memset(z, 0, sizeof(double) * nv);
+        for (int k = 0; k < n_upper; k++) {
+            orc_silu_upper_sweep(n, rowptr, colind, X, y, z, t);
+            memcpy(z, t, sizeof(double) * nv);
+        }
+    }
 }

@@ -92,3 +92,34 @@ def lu_solve_dense(L, U, r):
     """(LU)^{-1} r with numpy.linalg.solve on the dense factors."""
     M = blocks_to_dense(L) @ blocks_to_dense(U)
     return np.linalg.solve(M, np.asarray(r).reshape(-1)).reshape(-1, 4)
+
+
+def scalar_mask(rowptr, colind):
+    """The scalar pattern S: every entry of every block of the block pattern."""
+    return np.kron(block_mask(rowptr, colind), np.ones((4, 4), bool))
+
+
+def silu0_ikj(rowptr, colind, vals):
+    """Scalar ILU(0) by masked IKJ elimination (Saad, Algorithm 10.4) on the
+    dense scalar matrix -> dense (L, U), L unit lower triangular."""
+    mask = scalar_mask(rowptr, colind)
+    W = to_dense(rowptr, colind, vals).copy()
+    n = W.shape[0]
+    for i in range(1, n):
+        for k in range(i):
+            if not mask[i, k]:
+                continue
+            W[i, k] = W[i, k] / W[k, k]
+            for j in range(k + 1, n):
+                if mask[i, j]:
+                    W[i, j] = W[i, j] - W[i, k] * W[k, j]
+    L = np.tril(W, -1) + np.eye(n)
+    U = np.triu(W)
+    return L, U
+
+
+def scalar_factors_dense(rowptr, colind, X):
+    """Dense (L, U) of scalar factors held in A's block layout."""
+    D = to_dense(rowptr, colind, X)
+    n = D.shape[0]
+    return np.tril(D, -1) + np.eye(n), np.triu(D)
