@@ -116,6 +116,20 @@ abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype, abilu_fact
 void abilu_factors_destroy(abilu_factors f);
 
 /*
+ * Factors of the scalar variant the paper compares against: Chow and Patel's
+ * asynchronous ILU(0) taken entry by entry on the scalar pattern (every entry
+ * of every block), Sec. 3.2, Eq. (scalarilu_fp_detail), Algorithm 3, applied
+ * by scalar triangular sweeps (Algorithm 2).  abilu_build, abilu_apply,
+ * fgmres_solve and abilu_factors_export take such a handle like a block one
+ * (sync/async sweeps, zero guesses, X^0 = A); a zero pivot is replaced by 1 and
+ * counted.  Export writes X in A's layout with each diagonal block holding its
+ * strictly lower L entries (unit diagonal implied) and the rest of U; Dinv is
+ * not written.  Diagnostics and batches are block-only.  dtype: ABILU_F64 only
+ * (ABILU_EINVAL otherwise).
+ */
+abilu_status abilu_factors_create_scalar(abilu_pattern p, abilu_dtype dtype, abilu_factors *out);
+
+/*
  * Build the preconditioner: `nsweeps` fixed-point sweeps of Eq. (bilu),
  *   U_ij = A_ij - sum_{k<i} L_ik U_kj            (i <= j),
  *   L_ij = (A_ij - sum_{k<j} L_ik U_kj) U_jj^-1  (i > j),

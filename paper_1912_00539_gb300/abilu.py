@@ -29,7 +29,8 @@ INITS = {"a": 0, "previous": 1}
 
 # every symbol the header declares
 EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_pattern_create", "abilu_pattern_destroy",
-           "abilu_pattern_counts", "abilu_factors_create", "abilu_factors_destroy", "abilu_build",
+           "abilu_pattern_counts", "abilu_factors_create", "abilu_factors_destroy",
+           "abilu_factors_create_scalar", "abilu_build",
            "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
            "abilu_factors_diagnostics",
            "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc", "abilu_batch_create",
@@ -62,6 +63,7 @@ _lib.abilu_pattern_destroy.argtypes = [_vp]
 _lib.abilu_pattern_destroy.restype = None
 _lib.abilu_pattern_counts.argtypes = [_vp, C.POINTER(_i64)]
 _lib.abilu_factors_create.argtypes = [_vp, C.c_int, C.POINTER(_vp)]
+_lib.abilu_factors_create_scalar.argtypes = [_vp, C.c_int, C.POINTER(_vp)]
 _lib.abilu_factors_destroy.argtypes = [_vp]
 _lib.abilu_factors_destroy.restype = None
 _lib.abilu_build.argtypes = [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp]
@@ -172,12 +174,15 @@ class Pattern:
 class Factors:
     """Factor storage of one pattern (abilu_factors_create)."""
 
-    def __init__(self, pattern: Pattern, dtype: str = "f32"):
+    def __init__(self, pattern: Pattern, dtype: str = "f32", scalar: bool = False):
+        """scalar=True: the scalar ILU(0) variant (abilu_factors_create_scalar, FP64)."""
         h = C.c_void_p()
-        _check(_lib.abilu_factors_create(pattern.handle, DTYPES[dtype], C.byref(h)))
+        create = _lib.abilu_factors_create_scalar if scalar else _lib.abilu_factors_create
+        _check(create(pattern.handle, DTYPES[dtype], C.byref(h)))
         self.handle = h
         self.pattern = pattern
         self.dtype = dtype
+        self.scalar = bool(scalar)
 
     def build(self, A, nsweeps, mode="sync", init="a", stream=None):
         import torch

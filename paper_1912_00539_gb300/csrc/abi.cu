@@ -58,6 +58,16 @@ static void factors_free(abilu_factors f) {
 
 extern "C" void abilu_factors_destroy(abilu_factors f) { factors_free(f); }
 
+extern "C" abilu_status abilu_factors_create_scalar(abilu_pattern p, abilu_dtype dtype,
+                                                    abilu_factors *out) {
+    if (!out) return fail(ABILU_EINVAL, "factors_create_scalar: out is NULL");
+    *out = nullptr;
+    if (dtype != ABILU_F64) return fail(ABILU_EINVAL, "factors_create_scalar: FP64 factors only");
+    abilu_status s = abilu_factors_create(p, dtype, out);
+    if (s == ABILU_OK) (*out)->scalar = 1;
+    return s;
+}
+
 extern "C" abilu_status abilu_factors_create(abilu_pattern p, abilu_dtype dtype, abilu_factors *out) {
     if (!p || !out) return fail(ABILU_EINVAL, "factors_create: NULL argument");
     *out = nullptr;

@@ -580,8 +580,12 @@ void apply_warm(abilu_dtype dt) {
     }
 }
 
+abilu_status scalar_apply(abilu_factors f, const double *r, double *z, int nl, int nu,
+                          abilu_mode mode, cudaStream_t st, Skip skip);
+
 abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
                             int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip) {
+    if (f->scalar) return scalar_apply(f, r, z, nl, nu, mode, st, skip);
     switch (f->dtype) {
     case ABILU_F64: return apply_t<double>(f, r, r32, z, nl, nu, mode, st, skip);
     case ABILU_F32: return apply_t<float>(f, r, r32, z, nl, nu, mode, st, skip);

@@ -733,8 +733,13 @@ static abilu_status export_t(abilu_factors f, double *X, double *Dinv, cudaStrea
     return ABILU_OK;
 }
 
+abilu_status scalar_build(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
+                          abilu_init init, cudaStream_t st);
+abilu_status scalar_export(abilu_factors f, double *X, cudaStream_t st);
+
 abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st) {
+    if (f->scalar) return scalar_build(f, A, nsweeps, mode, init, st);
     switch (f->dtype) {
     case ABILU_F64: return build_t<double>(f, A, nsweeps, mode, init, st);
     case ABILU_F32: return build_t<float>(f, A, nsweeps, mode, init, st);
@@ -744,6 +749,7 @@ abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu
 }
 
 abilu_status export_dispatch(abilu_factors f, double *X, double *Dinv, cudaStream_t st) {
+    if (f->scalar) return scalar_export(f, X, st);   // no Dinv: scalar pivots
     switch (f->dtype) {
     case ABILU_F64: return export_t<double>(f, X, Dinv, st);
     case ABILU_F32: return export_t<float>(f, X, Dinv, st);

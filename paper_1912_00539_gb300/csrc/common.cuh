@@ -83,6 +83,7 @@ struct abilu_pattern_s {
 struct abilu_factors_s {
     abilu_pattern p;
     abilu_dtype dtype;
+    int scalar;                // 1: scalar ILU(0) (Chow-Patel) factors in the block layout
     size_t esz;                // bytes per stored scalar
     // factor storage; [cur] is the current iterate, [1-cur] the sync target
     void *L[2], *U[2], *D[2];

@@ -163,6 +163,7 @@ using namespace abilu;
 extern "C" abilu_status abilu_factors_diagnostics(abilu_factors f, const double *A_vals,
                                                   double *out, abilu_stream stream) {
     if (!f || !A_vals || !out) return fail(ABILU_EINVAL, "factors_diagnostics: NULL argument");
+    if (f->scalar) return fail(ABILU_EINVAL, "factors_diagnostics: block factors only");
     switch (f->dtype) {
     case ABILU_F64: return diag_t<double>(f, A_vals, out, S(stream));
     case ABILU_F32: return diag_t<float>(f, A_vals, out, S(stream));
