@@ -434,6 +434,35 @@ def test_full_size_512x512_parity(ab):
         assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
 
 
+@pytest.mark.slow
+def test_full_size_512x512_fp32_build_sweeps(ab):
+    """FP32 factors at 512x512 (the benchmark's launch configuration of the
+    block work-item sweeps): 3 synchronous sweeps match the oracle's 3 FP64
+    sweeps within the FP32 storage tolerance;
+    6 asynchronous sweeps leave an ILU fixed-point residual no larger than 6
+    synchronous ones (they read newer values); 24 sweeps of either mode reach
+    sequential BILU(0) (the unique fixed point, Sec. 4.2) within the FP32
+    storage tolerance."""
+    s = gen.workload("inviscid_512x512")
+    d = Dev(ab, s)
+    f32 = ab.Factors(d.pat, "f32")
+    f32.build(d.A, 3, mode="sync")
+    X, D = f32.export()
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 3)
+    assert _rel(X.cpu().numpy(), Xo) < 1e-4 and _rel(D.cpu().numpy(), Do) < 1e-4
+    Xo6, _, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 6)
+    r_sync = oracle.ilu_residual_l1(s.rowptr, s.colind, s.vals, Xo6)
+    f32.build(d.A, 6, mode="async")
+    X, _ = f32.export()
+    r_async = oracle.ilu_residual_l1(s.rowptr, s.colind, s.vals, X.cpu().numpy())
+    assert r_async <= r_sync, (r_async, r_sync)
+    Xs, Ds, _ = oracle.bilu0_seq(s.rowptr, s.colind, s.vals)
+    for mode in ("sync", "async"):
+        f32.build(d.A, 24, mode=mode)
+        X, D = f32.export()
+        assert _rel(X.cpu().numpy(), Xs) < 1e-4 and _rel(D.cpu().numpy(), Ds) < 1e-4, mode
+
+
 @pytest.mark.parametrize("mode", ["sync", "async"])
 def test_refined_fp32_inverse_is_fp32_accurate(ab, dsys, mode):
     """FP32 factors: Dinv_i (FP32 adjugate + one error-free Newton step) equals
