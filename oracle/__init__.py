@@ -45,6 +45,16 @@ class _Res(C.Structure):
                 ("rel_resid_est", C.c_double), ("rel_resid_true", C.c_double)]
 
 
+class _MgLevel(C.Structure):
+    _fields_ = [("n", C.c_int32), ("rowptr", _PI), ("colind", _PI), ("A", _PD), ("X", _PD),
+                ("Dinv", _PD), ("agg", _PI)]
+
+
+class _Mg(C.Structure):
+    _fields_ = [("nlevels", C.c_int), ("lv", C.POINTER(_MgLevel)), ("n_lower", C.c_int),
+                ("n_upper", C.c_int), ("pre", C.c_int), ("post", C.c_int), ("coarse", C.c_int)]
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -80,6 +90,17 @@ def _load():
         lib.orc_silu_lower_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
         lib.orc_silu_upper_sweep.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, _PD]
         lib.orc_silu_apply.argtypes = [i32, _PI, _PI, _PD, _PD, _PD, C.c_int, C.c_int, _PD]
+        lib.orc_mg_aggregate.argtypes = [i32, _PI, _PI, _PD, f64, _PI]
+        lib.orc_mg_aggregate.restype = i32
+        lib.orc_galerkin_pattern.argtypes = [i32, _PI, _PI, _PI, i32, _PI, _PI]
+        lib.orc_galerkin_pattern.restype = C.c_long
+        lib.orc_galerkin_values.argtypes = [i32, _PI, _PI, _PD, _PI, i32, _PI, _PI, _PD]
+        lib.orc_galerkin_values.restype = None
+        lib.orc_mg_vcycle.argtypes = [C.POINTER(_Mg), _PD, _PD]
+        lib.orc_mg_vcycle.restype = C.c_int
+        lib.orc_fgmres_mg.argtypes = [C.POINTER(_Mg), _PD, _PD, C.c_int, C.c_int, f64,
+                                      C.POINTER(_Res), _PD]
+        lib.orc_fgmres_mg.restype = C.c_int
         for nm in ("orc_lower_sweep", "orc_upper_sweep", "orc_lower_solve", "orc_upper_solve",
                    "orc_apply", "orc_spmv", "orc_jacobi_norms", "orc_silu_lower_sweep",
                    "orc_silu_upper_sweep", "orc_silu_apply"):
@@ -346,3 +367,116 @@ def silu_apply(rowptr, colind, X, r, n_lower, n_upper):
     _load().orc_silu_apply(n, prp, pci, pX, pr, z.ctypes.data_as(_PD), int(n_lower),
                            int(n_upper), work.ctypes.data_as(_PD))
     return z
+
+
+# ------------------------------------------------- multigrid smoother (f4)
+# Block ILU sweeps as the smoother of an aggregation multigrid V-cycle: the
+# paper names this as future work without fixing a cycle; the cycle here is the
+# one the library implements (see abilu_oracle.c, "multigrid smoother").
+
+def mg_aggregate(rowptr, colind, A, theta):
+    """Greedy strong-coupling aggregation -> (agg int32[n], number of aggregates)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    agg = np.empty(n, np.int32)
+    nc = _load().orc_mg_aggregate(n, prp, pci, pA, float(theta), agg.ctypes.data_as(_PI))
+    if nc < 0:
+        raise MemoryError("orc_mg_aggregate")
+    return agg, int(nc)
+
+
+def galerkin(rowptr, colind, A, agg, nc):
+    """A_c = P^T A P for piecewise-constant P -> (rowptr_c, colind_c, Ac)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    agg, pg = _i(agg)
+    rpc = np.empty(nc + 1, np.int32)
+    cic = np.empty(max(len(keep[1]), 1), np.int32)
+    nnz = _load().orc_galerkin_pattern(n, prp, pci, pg, int(nc), rpc.ctypes.data_as(_PI),
+                                       cic.ctypes.data_as(_PI))
+    if nnz < 0:
+        raise MemoryError("orc_galerkin_pattern")
+    cic = np.ascontiguousarray(cic[:nnz])
+    Ac = np.empty((nnz, 4, 4))
+    _load().orc_galerkin_values(n, prp, pci, pA, pg, int(nc), rpc.ctypes.data_as(_PI),
+                                cic.ctypes.data_as(_PI), Ac.ctypes.data_as(_PD))
+    return rpc, cic, Ac
+
+
+@dataclass
+class MgLevel:
+    rowptr: np.ndarray
+    colind: np.ndarray
+    A: np.ndarray
+    X: np.ndarray
+    Dinv: np.ndarray
+    agg: np.ndarray | None    # each cell's aggregate on the next level (None: coarsest)
+
+
+def mg_hierarchy(rowptr, colind, A, theta=0.25, max_levels=10, min_coarse=512,
+                 build_sweeps=4):
+    """Levels of the cycle: coarsen while fewer than max_levels levels exist and
+    the last has more than min_coarse cells, stopping when aggregation no longer
+    reduces the cell count; every level's block ILU from build_sweeps
+    synchronous sweeps (from X^0 = A)."""
+    rp = np.ascontiguousarray(rowptr, np.int32)
+    ci = np.ascontiguousarray(colind, np.int32)
+    Av = np.ascontiguousarray(A, np.float64)
+    mats = [(rp, ci, Av)]
+    aggs = []
+    while len(mats) < max_levels and len(mats[-1][0]) - 1 > min_coarse:
+        r, c, a = mats[-1]
+        agg, nc = mg_aggregate(r, c, a, theta)
+        if nc >= len(r) - 1:
+            break
+        aggs.append(agg)
+        mats.append(galerkin(r, c, a, agg, nc))
+    levels = []
+    for k, (r, c, a) in enumerate(mats):
+        X, D, _ = bilu_sync(r, c, a, build_sweeps)
+        levels.append(MgLevel(r, c, a, X, D, aggs[k] if k < len(aggs) else None))
+    return levels
+
+
+def _mg_struct(levels, n_lower, n_upper, pre, post, coarse):
+    arr = (_MgLevel * len(levels))()
+    keep = []
+    for k, L in enumerate(levels):
+        rp, prp = _i(L.rowptr)
+        ci, pci = _i(L.colind)
+        A, pA = _d(L.A)
+        X, pX = _d(L.X)
+        D, pD = _d(L.Dinv)
+        if L.agg is not None:
+            ag, pg = _i(L.agg)
+            keep.append(ag)
+        else:
+            pg = None
+        keep += [rp, ci, A, X, D]
+        arr[k] = _MgLevel(len(rp) - 1, prp, pci, pA, pX, pD, pg)
+    mg = _Mg(len(levels), arr, int(n_lower), int(n_upper), int(pre), int(post), int(coarse))
+    return mg, (arr, keep)
+
+
+def mg_vcycle(levels, r, n_lower, n_upper, pre=1, post=1, coarse=2):
+    """z = one V-cycle applied to r, from zero (the multigrid preconditioner)."""
+    mg, keep = _mg_struct(levels, n_lower, n_upper, pre, post, coarse)
+    r, pr = _d(r)
+    z = np.empty((len(levels[0].rowptr) - 1, 4))
+    if _load().orc_mg_vcycle(C.byref(mg), pr, z.ctypes.data_as(_PD)) != 0:
+        raise MemoryError("orc_mg_vcycle")
+    return z
+
+
+def fgmres_mg(levels, b, n_lower, n_upper, pre=1, post=1, coarse=2, restart=30,
+              max_iters=2500, rtol=1e-6):
+    """FGMRES(restart) right-preconditioned by one V-cycle -> (x, result)."""
+    mg, keep = _mg_struct(levels, n_lower, n_upper, pre, post, coarse)
+    b, pb = _d(b)
+    x = np.zeros((len(levels[0].rowptr) - 1, 4))
+    res = _Res()
+    hist = np.full(max_iters + 1, np.nan)
+    _load().orc_fgmres_mg(C.byref(mg), pb, x.ctypes.data_as(_PD), int(restart), int(max_iters),
+                          float(rtol), C.byref(res), hist.ctypes.data_as(_PD))
+    return x, FgmresResult(res.iters, res.restarts, bool(res.converged), res.rel_resid_est,
+                           res.rel_resid_true, hist[: res.iters + 1])

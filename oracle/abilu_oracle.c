@@ -434,9 +434,10 @@ typedef struct {
 /*
  * Right-preconditioned flexible GMRES(m) (Saad's FGMRES, used by the paper
  * through PETSc, Sec. 2 / Sec. 6 setup), with modified Gram-Schmidt and Givens
- * rotations.  The preconditioner is the block ILU given by (X, Dinv), applied
- * with n_lower / n_upper Jacobi sweeps (negative: exact); with Dinv == NULL it
- * is the scalar ILU held in X (orc_silu_apply).  x holds x0 on entry
+ * rotations.  orc_fgmres_pc takes the preconditioner as a callback; in
+ * orc_fgmres it is the block ILU given by (X, Dinv), applied with n_lower /
+ * n_upper Jacobi sweeps (negative: exact), or with Dinv == NULL the scalar ILU
+ * held in X (orc_silu_apply).  x holds x0 on entry
  * and the solution on exit.  Stops when the Givens residual estimate drops to
  * rtol*||b||, confirmed at the end of the cycle by the explicit residual; an
  * unconfirmed estimate restarts.  Stops at max_iters Arnoldi steps.
@@ -445,23 +446,25 @@ typedef struct {
 void orc_silu_apply(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *X,
                     const double *r, double *z, int n_lower, int n_upper, double *work);
 
-int orc_fgmres(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
-               const double *X, const double *Dinv, int n_lower, int n_upper,
-               const double *b, double *x, int m, int max_iters, double rtol,
-               orc_fgmres_result *res, double *hist)
+/* A right preconditioner z = M^{-1} r as a callback (FGMRES allows it to vary
+ * from one application to the next). */
+typedef void (*orc_precond)(void *ctx, const double *r, double *z);
+
+int orc_fgmres_pc(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+                  orc_precond pc, void *ctx, const double *b, double *x, int m,
+                  int max_iters, double rtol, orc_fgmres_result *res, double *hist)
 {
     long nv = (long)n * BS;
     double *V = calloc((size_t)(m + 1) * nv, sizeof(double));
     double *Z = calloc((size_t)m * nv, sizeof(double));
     double *w = calloc((size_t)nv, sizeof(double));
-    double *work = calloc((size_t)2 * nv, sizeof(double));
     double *H = calloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
     double *cs = calloc((size_t)m, sizeof(double));
     double *sn = calloc((size_t)m, sizeof(double));
     double *g = calloc((size_t)m + 1, sizeof(double));
     double *yv = calloc((size_t)m, sizeof(double));
-    if (!V || !Z || !w || !work || !H || !cs || !sn || !g || !yv) {
-        free(V); free(Z); free(w); free(work); free(H); free(cs); free(sn); free(g); free(yv);
+    if (!V || !Z || !w || !H || !cs || !sn || !g || !yv) {
+        free(V); free(Z); free(w); free(H); free(cs); free(sn); free(g); free(yv);
         return -1;
     }
     memset(res, 0, sizeof *res);
@@ -492,8 +495,7 @@ int orc_fgmres(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *
         int kdim = 0;
         for (int j = 0; j < m; j++) {
             double *vj = V + (long)j * nv, *zj = Z + (long)j * nv;
-            if (Dinv) orc_apply(n, rowptr, colind, X, Dinv, vj, zj, n_lower, n_upper, work);
-            else orc_silu_apply(n, rowptr, colind, X, vj, zj, n_lower, n_upper, work);
+            pc(ctx, vj, zj);
             orc_spmv(n, rowptr, colind, A, zj, w);
             for (int i = 0; i <= j; i++) { /* modified Gram-Schmidt */
                 double hij = dot(nv, w, V + (long)i * nv);
@@ -552,8 +554,40 @@ int orc_fgmres(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *
         }
     }
 done:
-    free(V); free(Z); free(w); free(work); free(H); free(cs); free(sn); free(g); free(yv);
+    free(V); free(Z); free(w); free(H); free(cs); free(sn); free(g); free(yv);
     return res->converged ? 0 : 1;
+}
+
+/* the block (or, with Dinv == NULL, scalar) ILU preconditioner of orc_fgmres */
+typedef struct {
+    idx_t n;
+    const idx_t *rowptr, *colind;
+    const double *X, *Dinv;
+    int n_lower, n_upper;
+    double *work;
+} ilu_pc_ctx;
+
+static void ilu_pc(void *p, const double *r, double *z)
+{
+    const ilu_pc_ctx *c = p;
+    if (c->Dinv)
+        orc_apply(c->n, c->rowptr, c->colind, c->X, c->Dinv, r, z, c->n_lower, c->n_upper, c->work);
+    else
+        orc_silu_apply(c->n, c->rowptr, c->colind, c->X, r, z, c->n_lower, c->n_upper, c->work);
+}
+
+int orc_fgmres(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+               const double *X, const double *Dinv, int n_lower, int n_upper,
+               const double *b, double *x, int m, int max_iters, double rtol,
+               orc_fgmres_result *res, double *hist)
+{
+    ilu_pc_ctx c = {n, rowptr, colind, X, Dinv, n_lower, n_upper, NULL};
+    c.work = calloc((size_t)2 * n * BS, sizeof(double));
+    if (!c.work)
+        return -1;
+    int rc = orc_fgmres_pc(n, rowptr, colind, A, ilu_pc, &c, b, x, m, max_iters, rtol, res, hist);
+    free(c.work);
+    return rc;
 }
 
 /* ------------------------------------------------------------ diagnostics */
@@ -845,4 +879,275 @@ void orc_silu_apply(idx_t n, const idx_t *rowptr, const idx_t *colind, const dou
             memcpy(z, t, sizeof(double) * nv);
         }
     }
+}
+
+/* ------------------------------------------------------ multigrid smoother */
+/*
+ * Block ILU sweeps as the smoother of an aggregation multigrid cycle.  The
+ * paper's closing section names asynchronous block ILU as a fine-grain
+ * parallel multigrid smoother (and the study of its smoothing property) as
+ * future work; it fixes no cycle, so this is the plain statement of the one
+ * the library runs: unsmoothed aggregation (piecewise-constant transfer
+ * between a cell and its aggregate), Galerkin coarse operators, and on every
+ * level the smoother x += M^{-1} (b - A x) with M = L U the block ILU of that
+ * level's matrix applied by triangular sweeps.
+ */
+
+/* squared Frobenius norm of a block, entries summed in storage order */
+static double blk_norm2(const double *a)
+{
+    double s = 0.0;
+    for (int e = 0; e < BB; e++)
+        s += a[e] * a[e];
+    return s;
+}
+
+/*
+ * Greedy aggregation by strong couplings.  In row i, column j != i is a strong
+ * coupling when ||A_ij||^2 > 0 and ||A_ij||^2 >= theta^2 * max_{k != i}
+ * ||A_ik||^2 (Frobenius norms, compared squared).
+ *   Pass 1, i ascending: a cell that is not yet placed, has at least one
+ *     strong coupling, and none of whose strong neighbours is placed, roots a
+ *     new aggregate made of itself and its strong neighbours.
+ *   Pass 2, i ascending: a cell left over joins the pass-1 aggregate of its
+ *     strongest neighbour (largest norm, the lowest column on ties) that pass
+ *     1 placed; with no such neighbour it becomes an aggregate of its own.
+ * Aggregates are numbered in the order they are made.  agg[n] receives each
+ * cell's aggregate; returns the number of aggregates (-1: out of memory).
+ */
+idx_t orc_mg_aggregate(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+                       double theta, idx_t *agg)
+{
+    double *w = malloc(sizeof(double) * (size_t)(rowptr[n] > 0 ? rowptr[n] : 1));
+    double *rmax = malloc(sizeof(double) * (size_t)n);
+    idx_t *agg1 = malloc(sizeof(idx_t) * (size_t)n);
+    if (!w || !rmax || !agg1) {
+        free(w); free(rmax); free(agg1);
+        return -1;
+    }
+    const double t2 = theta * theta;
+    for (idx_t i = 0; i < n; i++) {
+        rmax[i] = 0.0;
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            w[p] = blk_norm2(A + p * BB);
+            if (colind[p] != i && w[p] > rmax[i])
+                rmax[i] = w[p];
+        }
+        agg[i] = -1;
+    }
+#define STRONG(i, p) (colind[p] != (i) && w[p] > 0.0 && w[p] >= t2 * rmax[i])
+    idx_t nc = 0;
+    for (idx_t i = 0; i < n; i++) {
+        if (agg[i] >= 0)
+            continue;
+        int nstrong = 0, free_nbrs = 1;
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++)
+            if (STRONG(i, p)) {
+                nstrong++;
+                if (agg[colind[p]] >= 0)
+                    free_nbrs = 0;
+            }
+        if (nstrong == 0 || !free_nbrs)
+            continue;
+        agg[i] = nc;
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++)
+            if (STRONG(i, p))
+                agg[colind[p]] = nc;
+        nc++;
+    }
+#undef STRONG
+    memcpy(agg1, agg, sizeof(idx_t) * (size_t)n);
+    for (idx_t i = 0; i < n; i++) {
+        if (agg1[i] >= 0)
+            continue;
+        long best = -1;
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            if (j == i || agg1[j] < 0)
+                continue;
+            if (best < 0 || w[p] > w[best])
+                best = p;
+        }
+        agg[i] = best >= 0 ? agg1[colind[best]] : nc++;
+    }
+    free(w); free(rmax); free(agg1);
+    return nc;
+}
+
+/*
+ * Pattern of the Galerkin coarse operator A_c = P^T A P, P the
+ * piecewise-constant prolongation (P_{i,I} = I_4 when agg[i] = I): block (I,J)
+ * is present when some block (i,j) of A has agg[i] = I and agg[j] = J.
+ * rowptr_c[nc+1], colind_c (capacity rowptr[n]) sorted per row.  Returns the
+ * number of coarse blocks (-1: out of memory).
+ */
+long orc_galerkin_pattern(idx_t n, const idx_t *rowptr, const idx_t *colind, const idx_t *agg,
+                          idx_t nc, idx_t *rowptr_c, idx_t *colind_c)
+{
+    /* cells of each aggregate, by counting sort */
+    idx_t *mptr = calloc((size_t)nc + 1, sizeof(idx_t));
+    idx_t *mem = malloc(sizeof(idx_t) * (size_t)n);
+    idx_t *mark = malloc(sizeof(idx_t) * (size_t)(nc > 0 ? nc : 1));
+    if (!mptr || !mem || !mark) {
+        free(mptr); free(mem); free(mark);
+        return -1;
+    }
+    for (idx_t i = 0; i < n; i++)
+        mptr[agg[i] + 1]++;
+    for (idx_t I = 0; I < nc; I++)
+        mptr[I + 1] += mptr[I];
+    {
+        idx_t *pos = malloc(sizeof(idx_t) * (size_t)(nc > 0 ? nc : 1));
+        if (!pos) {
+            free(mptr); free(mem); free(mark);
+            return -1;
+        }
+        memcpy(pos, mptr, sizeof(idx_t) * (size_t)nc);
+        for (idx_t i = 0; i < n; i++)
+            mem[pos[agg[i]]++] = i;
+        free(pos);
+    }
+    for (idx_t I = 0; I < nc; I++)
+        mark[I] = -1;
+    long nnz = 0;
+    rowptr_c[0] = 0;
+    for (idx_t I = 0; I < nc; I++) {
+        long start = nnz;
+        for (idx_t m = mptr[I]; m < mptr[I + 1]; m++) {
+            idx_t i = mem[m];
+            for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+                idx_t J = agg[colind[p]];
+                if (mark[J] != I) {
+                    mark[J] = I;
+                    colind_c[nnz++] = J;
+                }
+            }
+        }
+        /* insertion sort of the row's columns */
+        for (long a = start + 1; a < nnz; a++) {
+            idx_t v = colind_c[a];
+            long b = a - 1;
+            while (b >= start && colind_c[b] > v) {
+                colind_c[b + 1] = colind_c[b];
+                b--;
+            }
+            colind_c[b + 1] = v;
+        }
+        rowptr_c[I + 1] = (idx_t)nnz;
+    }
+    free(mptr); free(mem); free(mark);
+    return nnz;
+}
+
+/*
+ * Values of A_c = P^T A P: every block of A, in ascending position, is added
+ * entry by entry to coarse block (agg[i], agg[j]).
+ */
+void orc_galerkin_values(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+                         const idx_t *agg, idx_t nc, const idx_t *rowptr_c,
+                         const idx_t *colind_c, double *Ac)
+{
+    memset(Ac, 0, sizeof(double) * (size_t)rowptr_c[nc] * BB);
+    for (idx_t i = 0; i < n; i++)
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            long c = find_block(rowptr_c, colind_c, agg[i], agg[colind[p]]);
+            for (int e = 0; e < BB; e++)
+                Ac[c * BB + e] += A[p * BB + e];
+        }
+}
+
+/* one level of the hierarchy: its matrix, its block ILU factors and (except on
+ * the coarsest level) each cell's aggregate on the next level */
+typedef struct {
+    idx_t n;
+    const idx_t *rowptr, *colind;
+    const double *A, *X, *Dinv;
+    const idx_t *agg;
+} orc_mg_level;
+
+typedef struct {
+    int nlevels;
+    const orc_mg_level *lv;
+    int n_lower, n_upper;      /* triangular sweeps per smoothing step (negative: exact) */
+    int pre, post, coarse;     /* smoothing steps: before / after the coarse correction, coarsest level */
+} orc_mg;
+
+/* `steps` smoothing steps x += M^{-1} (b - A x) on level l */
+static void mg_smooth(const orc_mg_level *L, int n_lower, int n_upper, int steps,
+                      const double *b, double *x, double *r, double *z, double *work)
+{
+    long nv = (long)L->n * BS;
+    for (int s = 0; s < steps; s++) {
+        orc_spmv(L->n, L->rowptr, L->colind, L->A, x, r);
+        for (long k = 0; k < nv; k++)
+            r[k] = b[k] - r[k];
+        orc_apply(L->n, L->rowptr, L->colind, L->X, L->Dinv, r, z, n_lower, n_upper, work);
+        for (long k = 0; k < nv; k++)
+            x[k] += z[k];
+    }
+}
+
+/* x = V-cycle on level l applied to b, from x = 0 */
+static int mg_vcycle_level(const orc_mg *mg, int l, const double *b, double *x)
+{
+    const orc_mg_level *L = mg->lv + l;
+    long nv = (long)L->n * BS;
+    double *r = malloc(sizeof(double) * (size_t)nv);
+    double *z = malloc(sizeof(double) * (size_t)nv);
+    double *work = malloc(sizeof(double) * (size_t)(2 * nv));
+    if (!r || !z || !work) {
+        free(r); free(z); free(work);
+        return -1;
+    }
+    memset(x, 0, sizeof(double) * (size_t)nv);
+    int rc = 0;
+    if (l == mg->nlevels - 1) {
+        mg_smooth(L, mg->n_lower, mg->n_upper, mg->coarse, b, x, r, z, work);
+    } else {
+        const orc_mg_level *Lc = mg->lv + l + 1;
+        long nvc = (long)Lc->n * BS;
+        double *bc = calloc((size_t)nvc, sizeof(double));
+        double *xc = malloc(sizeof(double) * (size_t)nvc);
+        if (!bc || !xc) {
+            free(bc); free(xc); free(r); free(z); free(work);
+            return -1;
+        }
+        mg_smooth(L, mg->n_lower, mg->n_upper, mg->pre, b, x, r, z, work);
+        /* restriction of the residual: b_c = P^T (b - A x), cells in ascending order */
+        orc_spmv(L->n, L->rowptr, L->colind, L->A, x, r);
+        for (long k = 0; k < nv; k++)
+            r[k] = b[k] - r[k];
+        for (idx_t i = 0; i < L->n; i++)
+            for (int c = 0; c < BS; c++)
+                bc[(long)L->agg[i] * BS + c] += r[(long)i * BS + c];
+        rc = mg_vcycle_level(mg, l + 1, bc, xc);
+        /* prolongation of the correction: x_i += x_c[agg(i)] */
+        for (idx_t i = 0; i < L->n; i++)
+            for (int c = 0; c < BS; c++)
+                x[(long)i * BS + c] += xc[(long)L->agg[i] * BS + c];
+        mg_smooth(L, mg->n_lower, mg->n_upper, mg->post, b, x, r, z, work);
+        free(bc); free(xc);
+    }
+    free(r); free(z); free(work);
+    return rc;
+}
+
+/* z = one V-cycle applied to r (the multigrid preconditioner); 0 on success */
+int orc_mg_vcycle(const orc_mg *mg, const double *r, double *z)
+{
+    return mg_vcycle_level(mg, 0, r, z);
+}
+
+static void mg_pc(void *p, const double *r, double *z)
+{
+    orc_mg_vcycle((const orc_mg *)p, r, z);
+}
+
+/* FGMRES(m) on level 0's matrix, right-preconditioned by one V-cycle */
+int orc_fgmres_mg(const orc_mg *mg, const double *b, double *x, int m, int max_iters,
+                  double rtol, orc_fgmres_result *res, double *hist)
+{
+    const orc_mg_level *L = mg->lv;
+    return orc_fgmres_pc(L->n, L->rowptr, L->colind, L->A, mg_pc, (void *)mg, b, x, m, max_iters,
+                         rtol, res, hist);
 }
