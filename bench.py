@@ -593,6 +593,105 @@ def run_viscous(args):
     return out
 
 
+def run_multigrid(args):
+    """Block ILU sweeps as a multigrid smoother (the paper's future work):
+    FGMRES preconditioned by an aggregation V-cycle against the single-level
+    block ILU preconditioner on the 512x512 and viscous-like grids: levels,
+    iterations (with the FP64 oracle's), solves/s, the time of one V-cycle,
+    and the convergence factor of the V-cycle used as a stationary iteration
+    x += V(b - A x) with synchronous and asynchronous smoothing sweeps."""
+    import numpy as np
+    import torch
+    import abilu_inputs as gen
+    import oracle
+    import paper_1912_00539_gb300 as ab
+    out = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch, 2)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / reps
+
+    for name in ("inviscid_512x512", "viscous_1024x256_rcm"):
+        s = gen.workload(name)
+        st = gen.SOLVER_SETTINGS[name]
+        pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+        A = torch.from_numpy(s.vals).cuda()
+        b = torch.from_numpy(np.ascontiguousarray(s.b)).cuda()
+        x = torch.zeros_like(b)
+        row = {}
+        fac = ab.Factors(pat, "f32")
+
+        def plain():
+            x.zero_()
+            return ab.fgmres_solve(pat, A, fac, b, x, restart=st["restart"], rtol=st["rtol"],
+                                   build_sweeps=st["build_sweeps"],
+                                   apply_sweeps_lower=st["apply_sweeps"],
+                                   apply_sweeps_upper=st["apply_sweeps"], mode="async")
+        r, ms = timed(plain, 5)
+        row["abilu_f32_async"] = {"iters": r.iters, "rel_resid_true": _r(r.rel_resid_true),
+                                  "ms": round(ms, 3), "solves_per_s": round(1e3 / ms, 1)}
+        nb = st["build_sweeps"]
+        lv = oracle.mg_hierarchy(s.rowptr, s.colind, s.vals, build_sweeps=nb)
+        _, ro = oracle.fgmres_mg(lv, s.b, 2, 2, pre=1, post=1, coarse=2, restart=st["restart"],
+                                 rtol=st["rtol"], max_iters=300)
+        row["oracle_mg_f64_2+2_iters"] = ro.iters
+        for md in ("sync", "async"):
+            for sw in (1, 2):
+                mg = ab.Multigrid(pat, A, factor_dtype="f32", build_sweeps=nb,
+                                  apply_sweeps_lower=sw, apply_sweeps_upper=sw, mode=md)
+
+                def solve():
+                    x.zero_()
+                    return ab.fgmres_solve_mg(mg, A, b, x, restart=st["restart"], rtol=st["rtol"],
+                                              max_iters=300)
+                r, ms = timed(solve, 5)
+                rr = torch.empty_like(b)
+                z = torch.empty_like(b)
+                _, ms_cycle = timed(lambda: mg.apply(b, z), 20)
+                # V-cycle as a stationary iteration: residual reduction per cycle
+                x.zero_()
+                bnorm = float(torch.linalg.vector_norm(b))
+                for _ in range(10):
+                    rr.copy_(b)
+                    ab.bsr_spmv(pat, A, x, rr, alpha=-1.0, beta=1.0)
+                    mg.apply(rr, z)
+                    x.add_(z)
+                rr.copy_(b)
+                ab.bsr_spmv(pat, A, x, rr, alpha=-1.0, beta=1.0)
+                rho = (float(torch.linalg.vector_norm(rr)) / bnorm) ** 0.1
+                row[f"mg_f32_{md}_{sw}+{sw}"] = {
+                    "levels": mg.nlevels, "cells": mg.cells, "iters": r.iters,
+                    "rel_resid_true": _r(r.rel_resid_true), "ms": round(ms, 3),
+                    "solves_per_s": round(1e3 / ms, 1), "vcycle_ms": round(ms_cycle, 3),
+                    "stationary_factor": round(rho, 4)}
+        # the same stationary iteration with the single-level smoother
+        for md in ("sync", "async"):
+            mg1 = ab.Multigrid(pat, A, max_levels=1, factor_dtype="f32", build_sweeps=nb,
+                               apply_sweeps_lower=2, apply_sweeps_upper=2, coarse_smooth=1, mode=md)
+            mg1.setup(A)
+            x.zero_()
+            rr = torch.empty_like(b)
+            z = torch.empty_like(b)
+            for _ in range(10):
+                rr.copy_(b)
+                ab.bsr_spmv(pat, A, x, rr, alpha=-1.0, beta=1.0)
+                mg1.apply(rr, z)
+                x.add_(z)
+            rr.copy_(b)
+            ab.bsr_spmv(pat, A, x, rr, alpha=-1.0, beta=1.0)
+            row[f"smoother_only_f32_{md}_2+2_stationary_factor"] = round(
+                (float(torch.linalg.vector_norm(rr)) / float(torch.linalg.vector_norm(b))) ** 0.1, 4)
+        out[name] = row
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = _dist()
@@ -788,6 +887,8 @@ def main():
                     help="only the block vs scalar (Chow-Patel) ILU(0) comparison")
     ap.add_argument("--continuation", action="store_true",
                     help="only the pseudo-time continuation of a steady model problem")
+    ap.add_argument("--multigrid", action="store_true",
+                    help="only block ILU as a multigrid smoother (V-cycle preconditioner)")
     ap.add_argument("--batch-build-sweeps", type=int, default=4)
     ap.add_argument("--batch-apply-sweeps", type=int, default=3)
     args = ap.parse_args()
@@ -811,6 +912,9 @@ def main():
         return 0
     if args.scalar:
         print(json.dumps(run_scalar_vs_block(args)))
+        return 0
+    if args.multigrid:
+        print(json.dumps(run_multigrid(args)))
         return 0
     return run_gpu(args)
 

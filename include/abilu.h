@@ -268,6 +268,99 @@ abilu_status fgmres_solve(abilu_pattern p, const double *A_vals, abilu_factors f
                           fgmres_result *res, abilu_stream stream);
 
 /*
+ * Multigrid with block ILU smoothing.  The paper's closing section names
+ * asynchronous block ILU iterations as fine-grain parallel multigrid smoothers
+ * as future work (with the study of their smoothing property) and fixes no
+ * cycle; this is the library's: a V-cycle on Galerkin coarse operators of an
+ * aggregation hierarchy whose smoother on every level is
+ *   x += M^{-1} (b - A x),  M = L U the block ILU(0) of that level's matrix,
+ * built by the sweeps of abilu_build and applied by those of abilu_apply.
+ *
+ * Hierarchy.  Strength ||A_ij||_F^2 (entries summed in storage order); in
+ * row i, j != i is strong when it is > 0 and >= theta^2 max_{k != i}
+ * ||A_ik||^2.  Pass 1 (cells ascending): an unplaced cell with a strong
+ * coupling and no placed strong neighbour roots an aggregate of itself and
+ * its strong neighbours; pass 2: a leftover cell joins the pass-1 aggregate of
+ * its strongest placed neighbour (lowest column on ties), or stands alone.
+ * Aggregates are numbered in creation order.  Transfer is piecewise constant
+ * (P_{i,agg(i)} = I_4, restriction P^T) and A_c = P^T A P, coarse blocks
+ * summed in ascending fine position.  Coarsening stops at max_levels levels,
+ * at or below min_coarse cells, or when aggregation stops reducing the count.
+ *
+ * Cycle, on level l from x = 0: pre_smooth steps, b_c = P^T (b - A x), the
+ * cycle on level l+1 for x_c, x += P x_c, post_smooth steps; the coarsest level
+ * takes coarse_smooth steps.  Each step applies M^{-1} with apply_sweeps_lower
+ * / apply_sweeps_upper triangular sweeps in `mode`; vectors are FP64, factors
+ * in factor_dtype.
+ */
+#define ABILU_MG_MAX_LEVELS 16
+typedef struct {
+    int32_t max_levels;          /* 1..ABILU_MG_MAX_LEVELS */
+    int32_t min_coarse;          /* stop coarsening at or below this many cells (>= 1) */
+    double theta;                /* strong-coupling threshold, 0 <= theta <= 1 */
+    int32_t factor_dtype;        /* abilu_dtype of every level's factors (block variant) */
+    int32_t build_sweeps;        /* build sweeps per level at set-up */
+    int32_t apply_sweeps_lower;  /* sweeps on L per smoothing step */
+    int32_t apply_sweeps_upper;  /* sweeps on U per smoothing step */
+    int32_t pre_smooth;          /* smoothing steps before the coarse correction */
+    int32_t post_smooth;         /* smoothing steps after it */
+    int32_t coarse_smooth;       /* smoothing steps on the coarsest level */
+    int32_t mode;                /* abilu_mode of the builds and the smoothing sweeps */
+    int32_t init;                /* abilu_init of the builds (warm start keeps each level's factors) */
+} abilu_mg_opts;
+typedef struct abilu_mg_s *abilu_mg;
+
+/* Defaults: 10 levels, min_coarse 512, theta 0.25, FP32 factors, 4 build and
+ * 2+2 apply sweeps, 1 pre-, 1 post- and 2 coarsest-level smoothing steps,
+ * ABILU_SYNC, builds from A. */
+void abilu_mg_default_opts(abilu_mg_opts *opts);
+
+/*
+ * abilu_mg_create: the hierarchy of pattern `p` with values `A_vals` (device,
+ * double[nnzb][4][4]; they set the strengths, and the aggregation stays fixed
+ * for the handle's life): coarse patterns, transfer lists, coarse values,
+ * factor storage and work vectors of every level, owned by the handle.  The
+ * handle keeps `p` (not a copy): destroy the handle first.  Synchronises
+ * `stream`.  ABILU_EINVAL on bad options.
+ * abilu_mg_setup: numeric set-up for new values on the same pattern: the
+ * coarse values, then `build_sweeps` block ILU sweeps on every level (with the
+ * handle's mode and init).  A_vals must stay valid while the handle applies
+ * the cycle.  Asynchronous on `stream`.
+ * abilu_mg_apply: z = one V-cycle applied to r (double[n][4] each, device,
+ * distinct).  Asynchronous on `stream`.
+ * abilu_mg_levels: host int64_t[2 * ABILU_MG_MAX_LEVELS + 1]: out[0] = levels,
+ * out[1 + 2l] = cells and out[2 + 2l] = blocks of level l.
+ * abilu_mg_level_data: copies level l's aggregates (agg int32[n_l], each
+ * cell's aggregate on level l+1; not for the coarsest level), pattern
+ * (rowptr int32[n_l+1], colind int32[nnzb_l]), values (double
+ * [nnzb_l][4][4]) and block ILU factors in FP64, laid out as
+ * abilu_factors_export writes them (X double[nnzb_l][4][4], Dinv
+ * double[n_l][4][4]); device pointers, any may be NULL.  Level 0's pattern
+ * and values are the caller's.  Asynchronous on `stream`.
+ */
+abilu_status abilu_mg_create(abilu_pattern p, const double *A_vals, const abilu_mg_opts *opts,
+                             abilu_stream stream, abilu_mg *out);
+void abilu_mg_destroy(abilu_mg mg);
+abilu_status abilu_mg_setup(abilu_mg mg, const double *A_vals, abilu_stream stream);
+abilu_status abilu_mg_apply(abilu_mg mg, const double *r, double *z, abilu_stream stream);
+abilu_status abilu_mg_levels(abilu_mg mg, int64_t *out);
+abilu_status abilu_mg_level_data(abilu_mg mg, int32_t level, int32_t *agg, int32_t *rowptr,
+                                 int32_t *colind, double *vals, double *X, double *Dinv,
+                                 abilu_stream stream);
+
+/*
+ * FGMRES(m) (as fgmres_solve, Sec. 2 and Sec. 6 setup) right-preconditioned
+ * by one V-cycle per Arnoldi step on the level-0 pattern of `mg`.  opts->build:
+ * abilu_mg_setup(mg, A_vals) inside the solve; otherwise the cycle uses the
+ * values of the last set-up, and A_vals must be those same values.  The
+ * smoother settings come from the handle (opts' sweep counts and mode are not
+ * used).  Synchronises `stream`; statuses as fgmres_solve (singular blocks
+ * counted over all levels).
+ */
+abilu_status fgmres_solve_mg(abilu_mg mg, const double *A_vals, const double *b, double *x,
+                             const fgmres_opts *opts, fgmres_result *res, abilu_stream stream);
+
+/*
  * Batched solves: many independent systems of uneven size (for example one
  * Jacobian per grid block or per request) handled by the same launches.  Each
  * system is the problem above, solved by the same method; the batch runs every

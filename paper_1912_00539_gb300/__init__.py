@@ -3,6 +3,6 @@
 The computation lives in libabilu.so (hand-written sm_103a CUDA behind the C
 ABI of include/abilu.h); ``abilu`` is its thin Python binding.
 """
-from .abilu import (AbiluError, Batch, Factors, Pattern, SolveResult,  # noqa: F401
-                    add_block_diagonal, bsr_spmv, default_opts, fgmres_solve, gather_blocks,
-                    kernel_launches, order, permute_pattern, to_f32, version)
+from .abilu import (AbiluError, Batch, Factors, Multigrid, Pattern, SolveResult,  # noqa: F401
+                    add_block_diagonal, bsr_spmv, default_opts, fgmres_solve, fgmres_solve_mg,
+                    gather_blocks, kernel_launches, order, permute_pattern, to_f32, version)

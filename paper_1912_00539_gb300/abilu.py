@@ -37,7 +37,9 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_batch_destroy", "abilu_batch_counts", "abilu_batch_set_system",
            "abilu_batch_solve", "abilu_batch_get_solution", "abilu_order",
            "abilu_permute_pattern", "abilu_gather_blocks", "abilu_add_block_diagonal",
-           "abilu_to_f32")
+           "abilu_to_f32", "abilu_mg_default_opts", "abilu_mg_create", "abilu_mg_destroy",
+           "abilu_mg_setup", "abilu_mg_apply", "abilu_mg_levels", "abilu_mg_level_data",
+           "fgmres_solve_mg")
 
 
 class FgmresOpts(C.Structure):
@@ -45,6 +47,17 @@ class FgmresOpts(C.Structure):
                 ("build_sweeps", C.c_int32), ("apply_sweeps_lower", C.c_int32),
                 ("apply_sweeps_upper", C.c_int32), ("mode", C.c_int32), ("build", C.c_int32),
                 ("init", C.c_int32), ("reorth", C.c_int32), ("zero_guess", C.c_int32)]
+
+
+class MgOpts(C.Structure):
+    _fields_ = [("max_levels", C.c_int32), ("min_coarse", C.c_int32), ("theta", C.c_double),
+                ("factor_dtype", C.c_int32), ("build_sweeps", C.c_int32),
+                ("apply_sweeps_lower", C.c_int32), ("apply_sweeps_upper", C.c_int32),
+                ("pre_smooth", C.c_int32), ("post_smooth", C.c_int32),
+                ("coarse_smooth", C.c_int32), ("mode", C.c_int32), ("init", C.c_int32)]
+
+
+MG_MAX_LEVELS = 16
 
 
 class FgmresResult(C.Structure):
@@ -92,6 +105,20 @@ _lib.abilu_batch_counts.argtypes = [_vp, C.POINTER(_i64)]
 _lib.abilu_batch_set_system.argtypes = [_vp, _i32, _vp, _vp, _vp]
 _lib.abilu_batch_solve.argtypes = [_vp, C.POINTER(FgmresOpts), C.POINTER(FgmresResult), _vp]
 _lib.abilu_batch_get_solution.argtypes = [_vp, _i32, _vp, _vp]
+_lib.abilu_mg_default_opts.argtypes = [C.POINTER(MgOpts)]
+_lib.abilu_mg_default_opts.restype = None
+_lib.abilu_mg_create.argtypes = [_vp, _vp, C.POINTER(MgOpts), _vp, C.POINTER(_vp)]
+_lib.abilu_mg_destroy.argtypes = [_vp]
+_lib.abilu_mg_destroy.restype = None
+_lib.abilu_mg_setup.argtypes = [_vp, _vp, _vp]
+_lib.abilu_mg_apply.argtypes = [_vp, _vp, _vp, _vp]
+_lib.abilu_mg_levels.argtypes = [_vp, C.POINTER(_i64)]
+_lib.abilu_mg_level_data.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.fgmres_solve_mg.argtypes = [_vp, _vp, _vp, _vp, C.POINTER(FgmresOpts),
+                                 C.POINTER(FgmresResult), _vp]
+for _nm in ("abilu_mg_create", "abilu_mg_setup", "abilu_mg_apply", "abilu_mg_levels",
+            "abilu_mg_level_data", "fgmres_solve_mg"):
+    getattr(_lib, _nm).restype = C.c_int
 for _nm in ("abilu_batch_create", "abilu_batch_counts", "abilu_batch_set_system",
             "abilu_batch_solve", "abilu_batch_get_solution", "abilu_order",
            "abilu_permute_pattern", "abilu_gather_blocks", "abilu_add_block_diagonal",
@@ -420,3 +447,85 @@ class Batch:
         if h:
             _lib.abilu_batch_destroy(h)
             self.handle = None
+
+
+class Multigrid:
+    """V-cycle with block ILU smoothing on an aggregation hierarchy (abilu_mg_*)."""
+
+    def __init__(self, pattern: Pattern, A, max_levels=10, min_coarse=512, theta=0.25,
+                 factor_dtype="f32", build_sweeps=4, apply_sweeps_lower=2, apply_sweeps_upper=2,
+                 pre_smooth=1, post_smooth=1, coarse_smooth=2, mode="sync", init="a",
+                 stream=None):
+        import torch
+        o = MgOpts(int(max_levels), int(min_coarse), float(theta), DTYPES[factor_dtype],
+                   int(build_sweeps), int(apply_sweeps_lower), int(apply_sweeps_upper),
+                   int(pre_smooth), int(post_smooth), int(coarse_smooth), MODES[mode], INITS[init])
+        h = C.c_void_p()
+        _check(_lib.abilu_mg_create(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
+                                    C.byref(o), _stream(stream), C.byref(h)))
+        self.handle = h
+        self.pattern = pattern   # the handle keeps the pattern: keep it alive
+        self.A = A               # the values of the last set-up
+        out = (C.c_int64 * (2 * MG_MAX_LEVELS + 1))()
+        _check(_lib.abilu_mg_levels(h, out))
+        self.nlevels = int(out[0])
+        self.cells = [int(out[1 + 2 * k]) for k in range(self.nlevels)]
+        self.blocks = [int(out[2 + 2 * k]) for k in range(self.nlevels)]
+
+    def setup(self, A, stream=None):
+        import torch
+        _check(_lib.abilu_mg_setup(self.handle, _ptr(A, torch.float64, 16 * self.pattern.nnzb, "A"),
+                                   _stream(stream)))
+        self.A = A
+
+    def apply(self, r, z, stream=None):
+        import torch
+        nv = 4 * self.pattern.n
+        _check(_lib.abilu_mg_apply(self.handle, _ptr(r, torch.float64, nv, "r"),
+                                   _ptr(z, torch.float64, nv, "z"), _stream(stream)))
+
+    def level(self, k, factors=False, stream=None) -> dict:
+        """Level k's aggregates (None on the coarsest), pattern and values, and
+        with factors=True its block ILU factors in FP64 (X in the pattern
+        layout, Dinv) - device tensors."""
+        import torch
+        n, nb = self.cells[k], self.blocks[k]
+        agg = torch.empty(n, dtype=torch.int32, device="cuda") if k < self.nlevels - 1 else None
+        rp = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+        ci = torch.empty(nb, dtype=torch.int32, device="cuda")
+        v = torch.empty((nb, 4, 4), dtype=torch.float64, device="cuda")
+        X = torch.empty((nb, 4, 4), dtype=torch.float64, device="cuda") if factors else None
+        D = torch.empty((n, 4, 4), dtype=torch.float64, device="cuda") if factors else None
+        _check(_lib.abilu_mg_level_data(self.handle, int(k),
+                                        _ptr(agg, torch.int32) if agg is not None else None,
+                                        _ptr(rp, torch.int32), _ptr(ci, torch.int32),
+                                        _ptr(v, torch.float64),
+                                        _ptr(X, torch.float64) if factors else None,
+                                        _ptr(D, torch.float64) if factors else None,
+                                        _stream(stream)))
+        return dict(agg=agg, rowptr=rp, colind=ci, vals=v, X=X, Dinv=D)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.abilu_mg_destroy(h)
+            self.handle = None
+
+
+def fgmres_solve_mg(mg: Multigrid, A, b, x, restart=30, max_iters=2500, rtol=1e-6, build=True,
+                    reorth=False, zero_guess=False, stream=None,
+                    raise_on_noconv=False) -> SolveResult:
+    """FGMRES right-preconditioned by one V-cycle per step (fgmres_solve_mg)."""
+    import torch
+    o = FgmresOpts(int(restart), int(max_iters), float(rtol), 0, 0, 0, 0, int(bool(build)), 0,
+                   int(bool(reorth)), int(bool(zero_guess)))
+    r = FgmresResult()
+    nv = 4 * mg.pattern.n
+    st = _lib.fgmres_solve_mg(mg.handle, _ptr(A, torch.float64, 16 * mg.pattern.nnzb, "A"),
+                              _ptr(b, torch.float64, nv, "b"), _ptr(x, torch.float64, nv, "x"),
+                              C.byref(o), C.byref(r), _stream(stream))
+    _check(st, allow=(OK, WARN_SINGULAR) if raise_on_noconv else (OK, WARN_SINGULAR, ENOCONV))
+    if build:
+        mg.A = A
+    return SolveResult(r.iters, r.restarts, r.rel_resid_est, r.rel_resid_true,
+                       r.singular_blocks, st)

@@ -124,6 +124,17 @@ struct Skip {
     const int *chunk_sys;
     const int *sys_done;
 };
+// A right preconditioner z = M^{-1} v for fgmres_run, applied once per
+// Arnoldi step on the solve's stream; its kernels return at once while
+// skip.flag is set.  v32 (NULL: none) receives an FP32 copy of each
+// normalised v from FGMRES (the input FP32/BF16 factors read).
+struct Precond {
+    abilu_status (*fn)(void *ctx, const double *v, const float *v32, double *z, cudaStream_t st,
+                       Skip skip);
+    void *ctx;
+    float *v32;
+};
+
 __device__ __forceinline__ bool skip_all(const Skip &s) {
     return s.flag && *s.flag;
 }

@@ -388,43 +388,45 @@ size_t host_status_bytes() { return sizeof(HostStatus); }
 int max_restart() { return MAXM; }
 }  // namespace abilu
 
-extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_factors f,
-                                     const double *b, double *x, const fgmres_opts *opts,
-                                     fgmres_result *res, abilu_stream stream) {
-    if (!p || !A || !f || !b || !x || !opts || !res)
-        return fail(ABILU_EINVAL, "fgmres_solve: NULL argument");
-    memset(res, 0, sizeof *res);
-    if (f->p != p) return fail(ABILU_EINVAL, "fgmres_solve: factors belong to another pattern");
+namespace abilu {
+
+// block ILU(0) preconditioner of fgmres_solve
+struct IluPc {
+    abilu_factors f;
+    int nl, nu;
+    abilu_mode mode;
+};
+static abilu_status ilu_pc(void *ctx, const double *v, const float *v32, double *z,
+                           cudaStream_t st, Skip skip) {
+    const IluPc *c = static_cast<const IluPc *>(ctx);
+    return apply_dispatch(c->f, v, v32, z, c->nl, c->nu, c->mode, st, skip);
+}
+
+// FGMRES(m) on pattern P with the preconditioner `pc`; the Krylov basis, the
+// device solve state and the reductions' partials live in `ws` (a factors
+// handle of P).  Singular-block and timeout counters are collected from the
+// handles `cnt[0..ncnt)`.
+abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws, const Precond &pc,
+                        const double *b, double *x, const fgmres_opts *opts, fgmres_result *res,
+                        cudaStream_t st, abilu_factors const *cnt, int ncnt) {
     const int m = opts->restart;
-    if (m < 1 || m > MAXM) return fail(ABILU_EINVAL, "fgmres_solve: restart must be in 1..%d", MAXM);
-    if (opts->max_iters < 0 || !(opts->rtol >= 0.0) || opts->apply_sweeps_lower < 0 ||
-        opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 ||
-        (opts->mode != ABILU_SYNC && opts->mode != ABILU_ASYNC))
-        return fail(ABILU_EINVAL, "fgmres_solve: bad options");
-    cudaStream_t st = S(stream);
-    abilu_status s = ensure_krylov(f, m);
+    abilu_status s = ensure_krylov(ws, m);
     if (s != ABILU_OK) return s;
-    const PatternView &P = p->v;
     const long long nv = (long long)P.n * BS, nv2 = nv / 2;
-    double *V = f->krylov;
+    double *V = ws->krylov;
     double *Z = V + (size_t)(m + 1) * nv;
     double *w = Z + (size_t)m * nv;
-    SolveState *SS = reinterpret_cast<SolveState *>(f->scal);
-    HostStatus *hs = reinterpret_cast<HostStatus *>(f->host_status);
+    SolveState *SS = reinterpret_cast<SolveState *>(ws->scal);
+    HostStatus *hs = reinterpret_cast<HostStatus *>(ws->host_status);
     const int nred = red_ctas();
     const int nres = nred / 4 * 3;   // k_residual: 3 CTAs per SM
-    const abilu_mode mode = (abilu_mode)opts->mode;
     const Skip skip{&SS->done, nullptr, nullptr};
-    float *v32 = reinterpret_cast<float *>(f->r32);  // NULL for FP64 factors
+    float *v32 = pc.v32;
 
-    if (opts->build) {
-        s = build_dispatch(f, A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
-        if (s != ABILU_OK) return s;
-    }
     ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
     if (opts->zero_guess) ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
-    k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 1,
+    k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, ws->partials, 1,
                                                       opts->zero_guess ? 1 : 0);
     k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
     ABILU_LAUNCH_CHECK("fgmres init");
@@ -439,15 +441,14 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     for (bool first = true; first || (!h.converged && h.iters < opts->max_iters); first = false) {
         int j = 0;
         for (; j < m; j++) {
-            s = apply_dispatch(f, V + (size_t)j * nv, v32, Z + (size_t)j * nv, opts->apply_sweeps_lower,
-                               opts->apply_sweeps_upper, mode, st, skip);
+            s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
-            k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, f->partials, 0);
-            k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, f->partials, 0, !opts->reorth);
+            k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, ws->partials, 0);
+            k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, ws->partials, 0, !opts->reorth);
             if (opts->reorth) {
-                k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, f->partials, 1);
-                k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, f->partials, 1, 1);
+                k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, ws->partials, 1);
+                k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, ws->partials, 1, 1);
             }
             k_scale<<<counted(nred), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
             cudaError_t e = cudaGetLastError();
@@ -460,7 +461,7 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
         }
         if (ret != ABILU_OK) break;
         k_xupdate<<<counted(nred), RED_THREADS, 0, st>>>(Z, nv2, x, SS);
-        k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, f->partials, 0, 0);
+        k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, ws->partials, 0, 0);
         k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres restart"); break; }
@@ -478,18 +479,57 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     res->restarts = h.restarts;
     res->rel_resid_est = h.est;
     res->rel_resid_true = h.bnorm > 0.0 ? h.beta / h.bnorm : 0.0;
-    unsigned long long cv[5] = {0, 0, 0, 0, 0};
-    cudaMemcpy(cv, f->ctr, sizeof cv, cudaMemcpyDeviceToHost);
-    const unsigned long long ns = cv[0];
-    res->singular_blocks = (int64_t)ns;
-    if (cv[4] && ret == ABILU_OK) {  // a staged sweep's bounded wait ran out: results invalid
-        cudaMemset(f->ctr + 4, 0, sizeof(unsigned long long));
-        ret = fail(ABILU_ETIMEOUT, "fgmres_solve: %llu pipeline waits timed out", cv[4]);
+    unsigned long long ns = 0, nto = 0;
+    for (int k = 0; k < ncnt; k++) {
+        unsigned long long cv[5] = {0, 0, 0, 0, 0};
+        cudaMemcpy(cv, cnt[k]->ctr, sizeof cv, cudaMemcpyDeviceToHost);
+        ns += cv[0];
+        if (cv[4]) {
+            nto += cv[4];
+            cudaMemset(cnt[k]->ctr + 4, 0, sizeof(unsigned long long));
+        }
     }
+    res->singular_blocks = (int64_t)ns;
+    if (nto && ret == ABILU_OK)  // a staged sweep's bounded wait ran out: results invalid
+        ret = fail(ABILU_ETIMEOUT, "fgmres_solve: %llu pipeline waits timed out", nto);
     if (ret == ABILU_OK) {
         if (!h.converged) ret = fail(ABILU_ENOCONV, "fgmres_solve: %d iterations, relative residual %.3e > rtol %.3e", h.iters, res->rel_resid_true, opts->rtol);
         else if (ns > 0) ret = fail(ABILU_WARN_SINGULAR, "fgmres_solve: %llu singular diagonal blocks replaced", ns);
     }
     res->status = ret;
     return ret;
+}
+
+// options shared by every FGMRES entry point
+abilu_status fgmres_check_opts(const fgmres_opts *opts, const char *who) {
+    if (opts->restart < 1 || opts->restart > MAXM)
+        return fail(ABILU_EINVAL, "%s: restart must be in 1..%d", who, MAXM);
+    if (opts->max_iters < 0 || !(opts->rtol >= 0.0))
+        return fail(ABILU_EINVAL, "%s: bad options", who);
+    return ABILU_OK;
+}
+
+}  // namespace abilu
+
+extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_factors f,
+                                     const double *b, double *x, const fgmres_opts *opts,
+                                     fgmres_result *res, abilu_stream stream) {
+    if (!p || !A || !f || !b || !x || !opts || !res)
+        return fail(ABILU_EINVAL, "fgmres_solve: NULL argument");
+    memset(res, 0, sizeof *res);
+    if (f->p != p) return fail(ABILU_EINVAL, "fgmres_solve: factors belong to another pattern");
+    abilu_status s = fgmres_check_opts(opts, "fgmres_solve");
+    if (s != ABILU_OK) return s;
+    if (opts->apply_sweeps_lower < 0 || opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 ||
+        (opts->mode != ABILU_SYNC && opts->mode != ABILU_ASYNC))
+        return fail(ABILU_EINVAL, "fgmres_solve: bad options");
+    cudaStream_t st = S(stream);
+    const abilu_mode mode = (abilu_mode)opts->mode;
+    if (opts->build) {
+        s = build_dispatch(f, A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
+        if (s != ABILU_OK) return s;
+    }
+    IluPc ctx{f, opts->apply_sweeps_lower, opts->apply_sweeps_upper, mode};
+    const Precond pc{ilu_pc, &ctx, reinterpret_cast<float *>(f->r32)};  // v32: NULL for FP64 factors
+    return fgmres_run(p->v, A, f, pc, b, x, opts, res, st, &f, 1);
 }

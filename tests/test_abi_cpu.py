@@ -57,3 +57,21 @@ def test_argument_errors_before_any_device_work(lib):
     r = lib.FgmresResult()
     o = lib.default_opts()
     assert lib._lib.fgmres_solve(None, None, None, None, None, C.byref(o), C.byref(r), None) == lib.EINVAL
+
+
+def test_multigrid_defaults_and_argument_errors(lib):
+    o = lib.MgOpts()
+    lib._lib.abilu_mg_default_opts(C.byref(o))
+    assert (o.max_levels, o.min_coarse, o.theta) == (10, 512, 0.25)
+    assert (o.factor_dtype, o.build_sweeps, o.apply_sweeps_lower, o.apply_sweeps_upper) == (1, 4, 2, 2)
+    assert (o.pre_smooth, o.post_smooth, o.coarse_smooth, o.mode, o.init) == (1, 1, 2, 0, 0)
+    h = C.c_void_p()
+    assert lib._lib.abilu_mg_create(None, None, C.byref(o), None, C.byref(h)) == lib.EINVAL
+    assert not h.value
+    assert lib._lib.abilu_mg_setup(None, None, None) == lib.EINVAL
+    assert lib._lib.abilu_mg_apply(None, None, None, None) == lib.EINVAL
+    out = (C.c_int64 * 33)()
+    assert lib._lib.abilu_mg_levels(None, out) == lib.EINVAL
+    r = lib.FgmresResult()
+    fo = lib.default_opts()
+    assert lib._lib.fgmres_solve_mg(None, None, None, None, C.byref(fo), C.byref(r), None) == lib.EINVAL
