@@ -311,6 +311,28 @@ def run_profile_solves(args):
     return 0
 
 
+def run_profile_mg(args):
+    """Warm-up plus --profile-mg FGMRES solves preconditioned by the V-cycle
+    (512x512 workload, FP32 factors, synchronous 2+2 smoothing, 6 build sweeps
+    per level): the command the multigrid launch list is taken on."""
+    import torch
+    import paper_1912_00539_gb300 as ab
+    s = _system()
+    pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+    A = torch.from_numpy(s.vals).cuda()
+    b = torch.from_numpy(s.b).cuda()
+    x = torch.zeros_like(b)
+    mg = ab.Multigrid(pat, A, factor_dtype="f32", build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=2,
+                      apply_sweeps_upper=2, mode="sync")
+    for _ in range(args.warmup + args.profile_mg):
+        r = ab.fgmres_solve_mg(mg, A, b, x, restart=RESTART, rtol=RTOL, zero_guess=True,
+                               raise_on_noconv=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"solves": args.warmup + args.profile_mg, "levels": mg.cells,
+                      "iters": r.iters, "rel_resid_true": r.rel_resid_true}))
+    return 0
+
+
 def run_batched(args, nsys=64, steps=3):
     """64 uneven systems (2k-200k cells, aspect 1/8-8, CFL 10-1e4), FP32
     factors, FGMRES(30) to 1e-6: the batch solved in the same launches vs the
@@ -642,35 +664,37 @@ def run_multigrid(args):
         _, ro = oracle.fgmres_mg(lv, s.b, 2, 2, pre=1, post=1, coarse=2, restart=st["restart"],
                                  rtol=st["rtol"], max_iters=300)
         row["oracle_mg_f64_2+2_iters"] = ro.iters
-        for md in ("sync", "async"):
-            for sw in (1, 2):
-                mg = ab.Multigrid(pat, A, factor_dtype="f32", build_sweeps=nb,
-                                  apply_sweeps_lower=sw, apply_sweeps_upper=sw, mode=md)
+        for md, sw, mc in (("sync", 1, 512), ("sync", 2, 512), ("async", 1, 512),
+                           ("async", 2, 512), ("sync", 2, 8192), ("async", 2, 8192),
+                           ("sync", 2, 65536), ("async", 2, 65536)):
+            mg = ab.Multigrid(pat, A, factor_dtype="f32", build_sweeps=nb,
+                              apply_sweeps_lower=sw, apply_sweeps_upper=sw, mode=md,
+                              min_coarse=mc)
 
-                def solve():
-                    x.zero_()
-                    return ab.fgmres_solve_mg(mg, A, b, x, restart=st["restart"], rtol=st["rtol"],
-                                              max_iters=300)
-                r, ms = timed(solve, 5)
-                rr = torch.empty_like(b)
-                z = torch.empty_like(b)
-                _, ms_cycle = timed(lambda: mg.apply(b, z), 20)
-                # V-cycle as a stationary iteration: residual reduction per cycle
+            def solve():
                 x.zero_()
-                bnorm = float(torch.linalg.vector_norm(b))
-                for _ in range(10):
-                    rr.copy_(b)
-                    ab.bsr_spmv(pat, A, x, rr, alpha=-1.0, beta=1.0)
-                    mg.apply(rr, z)
-                    x.add_(z)
+                return ab.fgmres_solve_mg(mg, A, b, x, restart=st["restart"], rtol=st["rtol"],
+                                          max_iters=300)
+            r, ms = timed(solve, 5)
+            rr = torch.empty_like(b)
+            z = torch.empty_like(b)
+            _, ms_cycle = timed(lambda: mg.apply(b, z), 20)
+            # V-cycle as a stationary iteration: residual reduction per cycle
+            x.zero_()
+            bnorm = float(torch.linalg.vector_norm(b))
+            for _ in range(10):
                 rr.copy_(b)
                 ab.bsr_spmv(pat, A, x, rr, alpha=-1.0, beta=1.0)
-                rho = (float(torch.linalg.vector_norm(rr)) / bnorm) ** 0.1
-                row[f"mg_f32_{md}_{sw}+{sw}"] = {
-                    "levels": mg.nlevels, "cells": mg.cells, "iters": r.iters,
-                    "rel_resid_true": _r(r.rel_resid_true), "ms": round(ms, 3),
-                    "solves_per_s": round(1e3 / ms, 1), "vcycle_ms": round(ms_cycle, 3),
-                    "stationary_factor": round(rho, 4)}
+                mg.apply(rr, z)
+                x.add_(z)
+            rr.copy_(b)
+            ab.bsr_spmv(pat, A, x, rr, alpha=-1.0, beta=1.0)
+            rho = (float(torch.linalg.vector_norm(rr)) / bnorm) ** 0.1
+            row[f"mg_f32_{md}_{sw}+{sw}_min{mc}"] = {
+                "levels": mg.nlevels, "cells": mg.cells, "iters": r.iters,
+                "rel_resid_true": _r(r.rel_resid_true), "ms": round(ms, 3),
+                "solves_per_s": round(1e3 / ms, 1), "vcycle_ms": round(ms_cycle, 3),
+                "stationary_factor": round(rho, 4)}
         # the same stationary iteration with the single-level smoother
         for md in ("sync", "async"):
             mg1 = ab.Multigrid(pat, A, max_levels=1, factor_dtype="f32", build_sweeps=nb,
@@ -880,6 +904,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true")
     ap.add_argument("--profile-solves", type=int, default=0)
+    ap.add_argument("--profile-mg", type=int, default=0,
+                    help="warm-up plus this many multigrid-preconditioned solves, for ncu")
     ap.add_argument("--batched", action="store_true", help="only the batched workload")
     ap.add_argument("--serving", action="store_true", help="only the serving workload")
     ap.add_argument("--viscous", action="store_true", help="only the viscous-like workload")
@@ -898,6 +924,8 @@ def main():
         return run_kernels_only(args)
     if args.profile_solves:
         return run_profile_solves(args)
+    if args.profile_mg:
+        return run_profile_mg(args)
     if args.batched:
         print(json.dumps(run_batched(args)))
         return 0

@@ -31,8 +31,9 @@
 //   pre_smooth smoothing steps, b_c = P^T (b - A x), the cycle on level l+1,
 //   x += P x_c, post_smooth steps; the coarsest level takes coarse_smooth
 //   steps.  The first step from x = 0 is x = M^{-1} b (no residual pass).
-//   Kernels: the residual (the SpMV's FMA chain, spmv.cuh), the residual
-//   restricted per aggregate in one pass, the prolongation, x += z.
+//   Kernels: the residual (the SpMV's FMA chain, spmv.cuh; a quad per row,
+//   coalesced), the restriction (a quad per aggregate summing its cells'
+//   residuals in ascending order), the prolongation, x += z.
 #include <string.h>
 
 #include <algorithm>
@@ -74,7 +75,9 @@ k_block_norm2(const double *__restrict__ A, long long nnzb, double *__restrict__
 }
 
 // Ac[c] = sum of A[gidx[t]], t = gptr[c] .. gptr[c+1]-1 (ascending fine
-// positions); a quad per coarse block, thread q sums row q
+// positions); a quad per coarse block, thread q sums row q.  Up to four fine
+// blocks are loaded before they are added (in list order), so the gathers of
+// a coarse block overlap instead of forming a chain.
 __global__ void __launch_bounds__(MG_THREADS)
 k_galerkin(long long nnzb_c, const int *__restrict__ gptr, const int *__restrict__ gidx,
            const double *__restrict__ A, double *__restrict__ Ac) {
@@ -82,11 +85,18 @@ k_galerkin(long long nnzb_c, const int *__restrict__ gptr, const int *__restrict
     const int q = threadIdx.x & 3;
     if (c >= nnzb_c) return;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int t = gptr[c]; t < gptr[c + 1]; t++) {
-        double v[4];
-        ld_row(A + (size_t)gidx[t] * BB + q * BS, v);
+    const int t1 = gptr[c + 1];
+    for (int t = gptr[c]; t < t1; t += 4) {
+        double v[4][4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) s[k] = __dadd_rn(s[k], v[k]);
+        for (int u = 0; u < 4; u++)
+            if (t + u < t1) ld_row(A + (size_t)__ldg(gidx + t + u) * BB + q * BS, v[u]);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (t + u < t1) {
+#pragma unroll
+                for (int k = 0; k < 4; k++) s[k] = __dadd_rn(s[k], v[u][k]);
+            }
     }
     st_row(Ac + (size_t)c * BB + q * BS, s);
 }
@@ -102,22 +112,25 @@ k_mg_residual(PatternView P, const double *__restrict__ A, const double *__restr
     r[o] = b[o] - row_dot_blocks(P, A, x, i, q);
 }
 
-// bc[I] = sum over the cells i of aggregate I, ascending, of (b - A x)_i: the
-// residual and its restriction P^T in one pass (XZERO: x = 0, so b itself)
-template <bool XZERO>
+// Restriction bc = P^T r: bc[I] = sum over the cells i of aggregate I, in
+// ascending order, of r_i.  A quad per aggregate, thread q sums component q;
+// up to four members' entries are loaded before they are added in order.
 __global__ void __launch_bounds__(MG_THREADS)
-k_mg_restrict(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
-              const double *__restrict__ x, const int *__restrict__ mptr,
+k_mg_restrict(const double *__restrict__ r, const int *__restrict__ mptr,
               const int *__restrict__ mem, int nc, double *__restrict__ bc, Skip skip) {
     if (skip_all(skip)) return;
     const int I = blockIdx.x * MG_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (I >= nc) return;
     double s = 0.0;
-    for (int t = mptr[I]; t < mptr[I + 1]; t++) {
-        const int i = mem[t];
-        double ri = b[(size_t)i * BS + q];
-        if constexpr (!XZERO) ri = ri - row_dot_blocks(P, A, x, i, q);
-        s += ri;
+    const int t1 = mptr[I + 1];
+    for (int t = mptr[I]; t < t1; t += 4) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (t + u < t1) v[u] = __ldg(r + (size_t)__ldg(mem + t + u) * BS + q);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (t + u < t1) s += v[u];
     }
     bc[(size_t)I * BS + q] = s;
 }
@@ -361,13 +374,14 @@ static abilu_status vcycle(abilu_mg mg, int l, const double *b, double *x, cudaS
     }
     MgLevel &Cl = mg->L[l + 1];
     if ((s = smooth(mg, l, o.pre_smooth, b, x, &xzero, st, skip)) != ABILU_OK) return s;
-    const int g = grid_of(4LL * Cl.n);
-    if (xzero)
-        k_mg_restrict<true><<<counted(g), MG_THREADS, 0, st>>>(L.p->v, L.A, b, x, L.mptr, L.mem,
-                                                               Cl.n, Cl.b, skip);
-    else
-        k_mg_restrict<false><<<counted(g), MG_THREADS, 0, st>>>(L.p->v, L.A, b, x, L.mptr, L.mem,
-                                                                Cl.n, Cl.b, skip);
+    const double *rf = b;   // the fine residual: b itself while x = 0
+    if (!xzero) {
+        k_mg_residual<<<counted(grid_of(4LL * L.n)), MG_THREADS, 0, st>>>(L.p->v, L.A, b, x, L.r, skip);
+        ABILU_LAUNCH_CHECK("k_mg_residual");
+        rf = L.r;
+    }
+    k_mg_restrict<<<counted(grid_of(4LL * Cl.n)), MG_THREADS, 0, st>>>(rf, L.mptr, L.mem, Cl.n, Cl.b,
+                                                                        skip);
     ABILU_LAUNCH_CHECK("k_mg_restrict");
     if ((s = vcycle(mg, l + 1, Cl.b, Cl.x, st, skip)) != ABILU_OK) return s;
     const long long n4 = 4LL * L.n;
