@@ -101,6 +101,14 @@ def _load():
         lib.orc_fgmres_mg.argtypes = [C.POINTER(_Mg), _PD, _PD, C.c_int, C.c_int, f64,
                                       C.POINTER(_Res), _PD]
         lib.orc_fgmres_mg.restype = C.c_int
+        lib.orc_lu_pattern.argtypes = [i32, _PI, _PI, _PI, _PI]
+        lib.orc_lu_pattern.restype = C.c_long
+        lib.orc_keep_largest.argtypes = [C.c_long, _PD, C.c_long, C.POINTER(C.c_ubyte)]
+        lib.orc_keep_largest.restype = C.c_long
+        lib.orc_fgmres_ilu_pattern.argtypes = [i32, _PI, _PI, _PD, _PI, _PI, _PD, _PD, C.c_int,
+                                               C.c_int, _PD, _PD, C.c_int, C.c_int, f64,
+                                               C.POINTER(_Res), _PD]
+        lib.orc_fgmres_ilu_pattern.restype = C.c_int
         for nm in ("orc_lower_sweep", "orc_upper_sweep", "orc_lower_solve", "orc_upper_solve",
                    "orc_apply", "orc_spmv", "orc_jacobi_norms", "orc_silu_lower_sweep",
                    "orc_silu_upper_sweep", "orc_silu_apply"):
@@ -478,5 +486,112 @@ def fgmres_mg(levels, b, n_lower, n_upper, pre=1, post=1, coarse=2, restart=30,
     hist = np.full(max_iters + 1, np.nan)
     _load().orc_fgmres_mg(C.byref(mg), pb, x.ctypes.data_as(_PD), int(restart), int(max_iters),
                           float(rtol), C.byref(res), hist.ctypes.data_as(_PD))
+    return x, FgmresResult(res.iters, res.restarts, bool(res.converged), res.rel_resid_est,
+                           res.rel_resid_true, hist[: res.iters + 1])
+
+
+# ------------------------------------------------- threshold block ILU (f4)
+# A threshold block ILU by fixed-point sweeps, the extension the paper names
+# last (parallel threshold ILU, ParILUT): the pattern grows by the fill of L U
+# and is cut back to the largest blocks, with one synchronous sweep after each
+# change.  The paper gives no algorithm; this is the library's reading.
+
+def lu_pattern(rowptr, colind):
+    """Block pattern of L U (L unit lower, U upper, both on the given pattern)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    rpo = np.empty(n + 1, np.int32)
+    nnz = _load().orc_lu_pattern(n, prp, pci, rpo.ctypes.data_as(_PI), None)
+    if nnz < 0:
+        raise MemoryError("orc_lu_pattern")
+    cio = np.empty(max(nnz, 1), np.int32)
+    _load().orc_lu_pattern(n, prp, pci, rpo.ctypes.data_as(_PI), cio.ctypes.data_as(_PI))
+    return rpo, np.ascontiguousarray(cio[:nnz])
+
+
+def keep_largest(key, budget):
+    """Mask of the entries above the (budget+1)-th largest key (all if <= budget)."""
+    key, pk = _d(key)
+    keep = np.empty(len(key), np.uint8)
+    _load().orc_keep_largest(len(key), pk, int(budget), keep.ctypes.data_as(C.POINTER(C.c_ubyte)))
+    return keep.astype(bool)
+
+
+def block_norm2(vals):
+    """Squared Frobenius norm of each block, entries summed in storage order."""
+    v = np.asarray(vals, np.float64).reshape(-1, 16)
+    s = np.zeros(len(v))
+    for e in range(16):
+        s = s + v[:, e] * v[:, e]
+    return s
+
+
+def map_blocks(rowptr, colind, vals, rowptr_new, colind_new):
+    """Blocks of `vals` (on rowptr/colind) placed on the new pattern, zero where absent."""
+    n = len(rowptr) - 1
+    key = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr)) * n + colind
+    key_new = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr_new)) * n + colind_new
+    pos = np.searchsorted(key, key_new)
+    pos = np.minimum(pos, max(len(key) - 1, 0))
+    found = (len(key) > 0) & (key[pos] == key_new)
+    out = np.zeros((len(colind_new), 4, 4))
+    out[found] = np.asarray(vals).reshape(-1, 4, 4)[pos[found]]
+    return out
+
+
+def parilut(rowptr, colind, A, fill=2.0, iters=3, sweeps=2):
+    """Threshold block ILU -> (rowptr, colind, X, Dinv) on its final pattern.
+
+    Budgets: floor(fill * blocks) strictly lower and strictly upper blocks, the
+    block counts of A's pattern.  Start: X^0 = A, `sweeps` synchronous sweeps
+    on A's pattern.  Then `iters` times: (1) the pattern becomes that of L U
+    (which contains it), new blocks start at zero, A is taken as zero outside
+    its own pattern, `sweeps` synchronous sweeps; (2) of the strictly lower
+    blocks keep those whose squared norm exceeds the (budget+1)-th largest,
+    likewise upper (diagonal blocks always), `sweeps` synchronous sweeps on the
+    kept pattern."""
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    colind = np.ascontiguousarray(colind, np.int32)
+    A = np.ascontiguousarray(A, np.float64)
+    n = len(rowptr) - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    budget_l = int(np.floor(fill * np.sum(rows > colind)))
+    budget_u = int(np.floor(fill * np.sum(rows < colind)))
+    X, D, _ = bilu_sync(rowptr, colind, A, sweeps)
+    rp, ci = rowptr, colind
+    for _ in range(iters):
+        rp2, ci2 = lu_pattern(rp, ci)
+        X2 = map_blocks(rp, ci, X, rp2, ci2)
+        A2 = map_blocks(rowptr, colind, A, rp2, ci2)
+        for _ in range(sweeps):
+            X2, D, _ = bilu_sync_sweep(rp2, ci2, A2, X2, D)
+        r2 = np.repeat(np.arange(n), np.diff(rp2))
+        key = block_norm2(X2)
+        keep = r2 == ci2
+        low, up = r2 > ci2, r2 < ci2
+        keep[low] = keep_largest(key[low], budget_l)
+        keep[up] = keep_largest(key[up], budget_u)
+        ci = np.ascontiguousarray(ci2[keep])
+        rp = np.concatenate([[0], np.cumsum(np.bincount(r2[keep], minlength=n))]).astype(np.int32)
+        X, As = X2[keep], A2[keep]
+        for _ in range(sweeps):
+            X, D, _ = bilu_sync_sweep(rp, ci, As, X, D)
+    return rp, ci, X, D
+
+
+def fgmres_ilu_pattern(rowptr, colind, A, rowptr_f, colind_f, X, Dinv, b, n_lower, n_upper,
+                       restart=30, max_iters=2500, rtol=1e-6):
+    """FGMRES on A preconditioned by block ILU factors on their own pattern."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    _, keepf, prf, pcf = _pattern(rowptr_f, colind_f)
+    A, pA = _d(A)
+    X, pX = _d(X)
+    Dinv, pD = _d(Dinv)
+    b, pb = _d(b)
+    x = np.zeros((n, 4))
+    res = _Res()
+    hist = np.full(max_iters + 1, np.nan)
+    _load().orc_fgmres_ilu_pattern(n, prp, pci, pA, prf, pcf, pX, pD, int(n_lower), int(n_upper),
+                                   pb, x.ctypes.data_as(_PD), int(restart), int(max_iters),
+                                   float(rtol), C.byref(res), hist.ctypes.data_as(_PD))
     return x, FgmresResult(res.iters, res.restarts, bool(res.converged), res.rel_resid_est,
                            res.rel_resid_true, hist[: res.iters + 1])

@@ -1151,3 +1151,113 @@ int orc_fgmres_mg(const orc_mg *mg, const double *b, double *x, int m, int max_i
     return orc_fgmres_pc(L->n, L->rowptr, L->colind, L->A, mg_pc, (void *)mg, b, x, m, max_iters,
                          rtol, res, hist);
 }
+
+/* --------------------------------------------------- threshold block ILU */
+/*
+ * Building blocks of a threshold block ILU computed by fixed-point sweeps (the
+ * paper's closing section names a parallel threshold ILU, ParILUT, as the
+ * next extension of its sweeps).  The loop itself (oracle/__init__.py,
+ * parilut) alternates: add the fill of L U to the pattern, one synchronous
+ * sweep, keep the largest blocks, one synchronous sweep.
+ */
+
+static int cmp_idx(const void *a, const void *b)
+{
+    idx_t x = *(const idx_t *)a, y = *(const idx_t *)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Block pattern of L U for factors on the pattern (rowptr, colind), L unit
+ * lower (its diagonal blocks are identities) and U upper: row i holds every
+ * column j >= k of row k, for k = i and for every column k < i of row i.
+ * rowptr_out[n+1]; colind_out (NULL: count only) sorted per row.  Returns the
+ * number of blocks (-1: out of memory).
+ */
+long orc_lu_pattern(idx_t n, const idx_t *rowptr, const idx_t *colind, idx_t *rowptr_out,
+                    idx_t *colind_out)
+{
+    idx_t *mark = malloc(sizeof(idx_t) * (size_t)n);
+    idx_t *buf = malloc(sizeof(idx_t) * (size_t)n);
+    if (!mark || !buf) {
+        free(mark); free(buf);
+        return -1;
+    }
+    for (idx_t i = 0; i < n; i++)
+        mark[i] = -1;
+    long nnz = 0;
+    rowptr_out[0] = 0;
+    for (idx_t i = 0; i < n; i++) {
+        idx_t cnt = 0;
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t k = colind[p];
+            if (k > i)
+                break;
+            /* k = i (the unit diagonal of L) or k < i: the upper part of row k */
+            for (long q = rowptr[k]; q < rowptr[k + 1]; q++) {
+                idx_t j = colind[q];
+                if (j < k || mark[j] == i)
+                    continue;
+                mark[j] = i;
+                buf[cnt++] = j;
+            }
+        }
+        qsort(buf, (size_t)cnt, sizeof(idx_t), cmp_idx);
+        if (colind_out)
+            memcpy(colind_out + nnz, buf, sizeof(idx_t) * (size_t)cnt);
+        nnz += cnt;
+        rowptr_out[i + 1] = (idx_t)nnz;
+    }
+    free(mark); free(buf);
+    return nnz;
+}
+
+static int cmp_desc(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x < y) - (x > y);
+}
+
+/*
+ * keep[t] = 1 for the entries whose key exceeds the (budget+1)-th largest key
+ * (every entry when there are at most `budget`): at most `budget` entries,
+ * and of two entries with equal keys both or neither.  Returns the number kept.
+ */
+long orc_keep_largest(long m, const double *key, long budget, unsigned char *keep)
+{
+    if (m <= budget) {
+        memset(keep, 1, (size_t)m);
+        return m;
+    }
+    double *s = malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    if (!s)
+        return -1;
+    memcpy(s, key, sizeof(double) * (size_t)m);
+    qsort(s, (size_t)m, sizeof(double), cmp_desc);
+    const double v = s[budget];
+    long kept = 0;
+    for (long t = 0; t < m; t++) {
+        keep[t] = key[t] > v;
+        kept += keep[t];
+    }
+    free(s);
+    return kept;
+}
+
+/* FGMRES on A (pattern rowptr/colind) preconditioned by block ILU factors on
+ * their own pattern (rowptr_f/colind_f), e.g. the filled pattern of the
+ * threshold ILU */
+int orc_fgmres_ilu_pattern(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+                           const idx_t *rowptr_f, const idx_t *colind_f, const double *X,
+                           const double *Dinv, int n_lower, int n_upper, const double *b,
+                           double *x, int m, int max_iters, double rtol, orc_fgmres_result *res,
+                           double *hist)
+{
+    ilu_pc_ctx c = {n, rowptr_f, colind_f, X, Dinv, n_lower, n_upper, NULL};
+    c.work = calloc((size_t)2 * n * BS, sizeof(double));
+    if (!c.work)
+        return -1;
+    int rc = orc_fgmres_pc(n, rowptr, colind, A, ilu_pc, &c, b, x, m, max_iters, rtol, res, hist);
+    free(c.work);
+    return rc;
+}
