@@ -716,6 +716,78 @@ def run_multigrid(args):
     return out
 
 
+def run_parilut(args):
+    """Threshold block ILU (fill of L U added, largest blocks kept, synchronous
+    sweeps; FP64 factors) against block ILU(0) on the 512x512 and viscous-like
+    grids: set-up time, blocks, FGMRES iterations and solve time with the
+    factors reused (the threshold factorisation is a set-up that several
+    right-hand sides or pseudo-time steps share), with the oracle's counts."""
+    import numpy as np
+    import torch
+    import abilu_inputs as gen
+    import oracle
+    import paper_1912_00539_gb300 as ab
+    out = {}
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch, 2)
+        e0.record()
+        for _ in range(reps):
+            r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / reps
+
+    for name in ("inviscid_512x512", "viscous_1024x256_rcm"):
+        s = gen.workload(name)
+        st = gen.SOLVER_SETTINGS[name]
+        na = st["apply_sweeps"]
+        pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+        A = torch.from_numpy(s.vals).cuda()
+        b = torch.from_numpy(np.ascontiguousarray(s.b)).cuda()
+        x = torch.zeros_like(b)
+        row = {"A_blocks": int(s.nnzb)}
+        for dt in ("f64", "f32"):
+            fac = ab.Factors(pat, dt)
+            fac.build(A, st["build_sweeps"], mode="async")
+
+            def solve0():
+                x.zero_()
+                return ab.fgmres_solve(pat, A, fac, b, x, restart=st["restart"], rtol=st["rtol"],
+                                       apply_sweeps_lower=na, apply_sweeps_upper=na, mode="async",
+                                       build=False, max_iters=300)
+            r, ms = timed(solve0, 5)
+            row[f"ilu0_{dt}_async"] = {"iters": r.iters, "solve_ms": round(ms, 3)}
+        for fill in (1.5, 2.0):
+            t0 = time.perf_counter()
+            fpat, ffac = ab.parilut(pat, A, fill=fill, iters=3, sweeps=2)
+            t_setup = time.perf_counter() - t0
+            _, t_setup2 = timed(lambda: ab.parilut(pat, A, fill=fill, iters=3, sweeps=2), 2)
+            rec = {"blocks": fpat.nnzb, "setup_ms": round(t_setup2, 2),
+                   "first_setup_ms": round(t_setup * 1e3, 1)}
+            for md in ("sync", "async"):
+                def solve():
+                    x.zero_()
+                    return ab.fgmres_solve(pat, A, ffac, b, x, restart=st["restart"],
+                                           rtol=st["rtol"], apply_sweeps_lower=na,
+                                           apply_sweeps_upper=na, mode=md, build=False,
+                                           max_iters=300)
+                r, ms = timed(solve, 5)
+                rec[f"{md}_iters"] = r.iters
+                rec[f"{md}_solve_ms"] = round(ms, 3)
+                rec[f"{md}_rel_resid_true"] = _r(r.rel_resid_true)
+            rp, ci, Xo, Do = oracle.parilut(s.rowptr, s.colind, s.vals, fill=fill, iters=3, sweeps=2)
+            _, ro = oracle.fgmres_ilu_pattern(s.rowptr, s.colind, s.vals, rp, ci, Xo, Do, s.b, na,
+                                              na, restart=st["restart"], max_iters=300)
+            rec["oracle_blocks"] = int(len(ci))
+            rec["oracle_iters"] = ro.iters
+            row[f"threshold_fill{fill}"] = rec
+        out[name] = row
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = _dist()
@@ -915,6 +987,8 @@ def main():
                     help="only the pseudo-time continuation of a steady model problem")
     ap.add_argument("--multigrid", action="store_true",
                     help="only block ILU as a multigrid smoother (V-cycle preconditioner)")
+    ap.add_argument("--parilut", action="store_true",
+                    help="only the threshold block ILU against block ILU(0)")
     ap.add_argument("--batch-build-sweeps", type=int, default=4)
     ap.add_argument("--batch-apply-sweeps", type=int, default=3)
     args = ap.parse_args()
@@ -943,6 +1017,9 @@ def main():
         return 0
     if args.multigrid:
         print(json.dumps(run_multigrid(args)))
+        return 0
+    if args.parilut:
+        print(json.dumps(run_parilut(args)))
         return 0
     return run_gpu(args)
 

@@ -103,6 +103,11 @@ void abilu_pattern_destroy(abilu_pattern p);
  * `out` is host int64_t[7]. */
 abilu_status abilu_pattern_counts(abilu_pattern p, int64_t *out);
 
+/* Copies the pattern's rowptr (int32[n+1]) and colind (int32[nnzb]) into
+ * caller-owned device arrays (either may be NULL).  Asynchronous on `stream`. */
+abilu_status abilu_pattern_arrays(abilu_pattern p, int32_t *rowptr, int32_t *colind,
+                                  abilu_stream stream);
+
 /*
  * Factor storage for one pattern: L (strictly lower blocks), U (strictly upper
  * blocks), inv(U_ii) and U_ii, in `dtype`, plus the work vectors of the
@@ -257,7 +262,8 @@ void fgmres_default_opts(fgmres_opts *opts);
  * Solve A x = b by FGMRES(m) right-preconditioned with block ILU(0) (Sec. 2,
  * Sec. 6 setup): x holds x0 on entry (double[n][4], device) and the solution
  * on return.  `f` is a factors handle of pattern `p` (built inside the solve
- * when opts->build is 1).  Arnoldi, Givens rotations, the SpMV and the true
+ * when opts->build is 1), or, with opts->build = 0, of another pattern with
+ * the same n (the filled pattern of abilu_parilut).  Arnoldi, Givens rotations, the SpMV and the true
  * residual are FP64 whatever the factor dtype.  `res` (host) is filled.
  * Synchronises `stream`.  Returns ABILU_ENOCONV (with res filled) when
  * max_iters is reached above rtol; ABILU_WARN_SINGULAR on a converged solve
@@ -359,6 +365,40 @@ abilu_status abilu_mg_level_data(abilu_mg mg, int32_t level, int32_t *agg, int32
  */
 abilu_status fgmres_solve_mg(abilu_mg mg, const double *A_vals, const double *b, double *x,
                              const fgmres_opts *opts, fgmres_result *res, abilu_stream stream);
+
+/*
+ * Threshold block ILU by fixed-point sweeps.  The paper's closing section
+ * names a parallel threshold ILU (ParILUT) as the next extension of its
+ * sweeps, without an algorithm; this is the library's, in FP64:
+ *   start  X = A on A's pattern, `sweeps` synchronous sweeps of Eq. (bilu);
+ *   `iters` times:
+ *     fill  the pattern becomes that of L U (L unit lower, U upper; it
+ *           contains the current one); new blocks start at zero and A is zero
+ *           outside its own pattern; `sweeps` synchronous sweeps;
+ *     drop  the strictly lower blocks whose squared Frobenius norm exceeds the
+ *           (budget+1)-th largest are kept (all of them if at most budget),
+ *           likewise the strictly upper ones, budgets floor(fill x the counts
+ *           of A's pattern); diagonal blocks always; `sweeps` synchronous
+ *           sweeps on the kept pattern.
+ * abilu_parilut returns a new pattern handle (the final pattern, n cells) and
+ * FP64 factors on it, both owned by the caller (abilu_pattern_destroy,
+ * abilu_factors_destroy): abilu_apply, abilu_factors_export (in the new
+ * pattern's layout) and fgmres_solve (with opts->build = 0) take them.
+ * Synchronises `stream`.  ABILU_EINVAL on bad options or when a row of L U
+ * would exceed 192 blocks.  iters = 0 gives block ILU(0) after `sweeps`
+ * sweeps, on a copy of A's pattern.
+ */
+typedef struct {
+    double fill;        /* budget factor, >= 0 (2.0: twice A's lower / upper blocks) */
+    int32_t iters;      /* fill-and-drop steps, >= 0 */
+    int32_t sweeps;     /* synchronous sweeps after the start and after every change, >= 0 */
+} abilu_parilut_opts;
+
+/* Defaults: fill 2.0, 3 steps, 2 sweeps. */
+void abilu_parilut_default_opts(abilu_parilut_opts *opts);
+abilu_status abilu_parilut(abilu_pattern p, const double *A_vals, const abilu_parilut_opts *opts,
+                           abilu_stream stream, abilu_pattern *pattern_out,
+                           abilu_factors *factors_out);
 
 /*
  * Batched solves: many independent systems of uneven size (for example one

@@ -101,6 +101,8 @@ def _load():
         lib.orc_fgmres_mg.argtypes = [C.POINTER(_Mg), _PD, _PD, C.c_int, C.c_int, f64,
                                       C.POINTER(_Res), _PD]
         lib.orc_fgmres_mg.restype = C.c_int
+        lib.orc_fix_constant_upper.argtypes = [i32, _PI, _PI, _PD, _PD]
+        lib.orc_fix_constant_upper.restype = None
         lib.orc_lu_pattern.argtypes = [i32, _PI, _PI, _PI, _PI]
         lib.orc_lu_pattern.restype = C.c_long
         lib.orc_keep_largest.argtypes = [C.c_long, _PD, C.c_long, C.POINTER(C.c_ubyte)]
@@ -525,6 +527,16 @@ def block_norm2(vals):
     return s
 
 
+def fix_constant_upper(rowptr, colind, A, X):
+    """Copy of X with every strictly upper block that has no product pair set
+    to A's block (its update is constant; a build sets it before sweeping)."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    A, pA = _d(A)
+    X = np.array(X, np.float64)
+    _load().orc_fix_constant_upper(n, prp, pci, pA, X.ctypes.data_as(_PD))
+    return X
+
+
 def map_blocks(rowptr, colind, vals, rowptr_new, colind_new):
     """Blocks of `vals` (on rowptr/colind) placed on the new pattern, zero where absent."""
     n = len(rowptr) - 1
@@ -548,7 +560,8 @@ def parilut(rowptr, colind, A, fill=2.0, iters=3, sweeps=2):
     its own pattern, `sweeps` synchronous sweeps; (2) of the strictly lower
     blocks keep those whose squared norm exceeds the (budget+1)-th largest,
     likewise upper (diagonal blocks always), `sweeps` synchronous sweeps on the
-    kept pattern."""
+    kept pattern.  Before the sweeps on a new pattern, its strictly upper
+    blocks without product pairs take A's value (fix_constant_upper)."""
     rowptr = np.ascontiguousarray(rowptr, np.int32)
     colind = np.ascontiguousarray(colind, np.int32)
     A = np.ascontiguousarray(A, np.float64)
@@ -562,6 +575,7 @@ def parilut(rowptr, colind, A, fill=2.0, iters=3, sweeps=2):
         rp2, ci2 = lu_pattern(rp, ci)
         X2 = map_blocks(rp, ci, X, rp2, ci2)
         A2 = map_blocks(rowptr, colind, A, rp2, ci2)
+        X2 = fix_constant_upper(rp2, ci2, A2, X2)
         for _ in range(sweeps):
             X2, D, _ = bilu_sync_sweep(rp2, ci2, A2, X2, D)
         r2 = np.repeat(np.arange(n), np.diff(rp2))
@@ -573,6 +587,7 @@ def parilut(rowptr, colind, A, fill=2.0, iters=3, sweeps=2):
         ci = np.ascontiguousarray(ci2[keep])
         rp = np.concatenate([[0], np.cumsum(np.bincount(r2[keep], minlength=n))]).astype(np.int32)
         X, As = X2[keep], A2[keep]
+        X = fix_constant_upper(rp, ci, As, X)
         for _ in range(sweeps):
             X, D, _ = bilu_sync_sweep(rp, ci, As, X, D)
     return rp, ci, X, D

@@ -1261,3 +1261,30 @@ int orc_fgmres_ilu_pattern(idx_t n, const idx_t *rowptr, const idx_t *colind, co
     free(c.work);
     return rc;
 }
+
+/*
+ * X[p] = A[p] for every strictly upper block (i,j) of the pattern with no
+ * product pair (no k < i with (i,k) and (k,j) in the pattern): its update is
+ * the constant A_ij, and a build sets such blocks to that value before its
+ * first sweep, whatever the initial guess held (a choice of initial guess).
+ */
+void orc_fix_constant_upper(idx_t n, const idx_t *rowptr, const idx_t *colind, const double *A,
+                            double *X)
+{
+    for (idx_t i = 0; i < n; i++)
+        for (long p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            idx_t j = colind[p];
+            if (j <= i)
+                continue;
+            int has_pair = 0;
+            for (long q = rowptr[i]; q < rowptr[i + 1] && !has_pair; q++) {
+                idx_t k = colind[q];
+                if (k >= i)
+                    break;
+                if (find_block(rowptr, colind, k, j) >= 0)
+                    has_pair = 1;
+            }
+            if (!has_pair)
+                memcpy(X + p * BB, A + p * BB, sizeof(double) * BB);
+        }
+}

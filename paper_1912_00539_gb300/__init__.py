@@ -5,4 +5,5 @@ ABI of include/abilu.h); ``abilu`` is its thin Python binding.
 """
 from .abilu import (AbiluError, Batch, Factors, Multigrid, Pattern, SolveResult,  # noqa: F401
                     add_block_diagonal, bsr_spmv, default_opts, fgmres_solve, fgmres_solve_mg,
-                    gather_blocks, kernel_launches, order, permute_pattern, to_f32, version)
+                    gather_blocks, kernel_launches, order, parilut, permute_pattern, to_f32,
+                    version)

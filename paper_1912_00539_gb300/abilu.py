@@ -39,7 +39,8 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_permute_pattern", "abilu_gather_blocks", "abilu_add_block_diagonal",
            "abilu_to_f32", "abilu_mg_default_opts", "abilu_mg_create", "abilu_mg_destroy",
            "abilu_mg_setup", "abilu_mg_apply", "abilu_mg_levels", "abilu_mg_level_data",
-           "fgmres_solve_mg")
+           "fgmres_solve_mg", "abilu_parilut_default_opts", "abilu_parilut",
+           "abilu_pattern_arrays")
 
 
 class FgmresOpts(C.Structure):
@@ -58,6 +59,10 @@ class MgOpts(C.Structure):
 
 
 MG_MAX_LEVELS = 16
+
+
+class ParilutOpts(C.Structure):
+    _fields_ = [("fill", C.c_double), ("iters", C.c_int32), ("sweeps", C.c_int32)]
 
 
 class FgmresResult(C.Structure):
@@ -116,8 +121,14 @@ _lib.abilu_mg_levels.argtypes = [_vp, C.POINTER(_i64)]
 _lib.abilu_mg_level_data.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.fgmres_solve_mg.argtypes = [_vp, _vp, _vp, _vp, C.POINTER(FgmresOpts),
                                  C.POINTER(FgmresResult), _vp]
+_lib.abilu_pattern_arrays.argtypes = [_vp, _vp, _vp, _vp]
+_lib.abilu_pattern_arrays.restype = C.c_int
+_lib.abilu_parilut_default_opts.argtypes = [C.POINTER(ParilutOpts)]
+_lib.abilu_parilut_default_opts.restype = None
+_lib.abilu_parilut.argtypes = [_vp, _vp, C.POINTER(ParilutOpts), _vp, C.POINTER(_vp),
+                               C.POINTER(_vp)]
 for _nm in ("abilu_mg_create", "abilu_mg_setup", "abilu_mg_apply", "abilu_mg_levels",
-            "abilu_mg_level_data", "fgmres_solve_mg"):
+            "abilu_mg_level_data", "fgmres_solve_mg", "abilu_parilut"):
     getattr(_lib, _nm).restype = C.c_int
 for _nm in ("abilu_batch_create", "abilu_batch_counts", "abilu_batch_set_system",
             "abilu_batch_solve", "abilu_batch_get_solution", "abilu_order",
@@ -186,10 +197,28 @@ class Pattern:
         self.handle = h
         self.n, self.nnzb = n, nnzb
 
+    @classmethod
+    def _wrap(cls, handle):
+        """A Python object owning an existing pattern handle."""
+        self = cls.__new__(cls)
+        self.handle = handle
+        c = self.counts()
+        self.n, self.nnzb = c["n"], c["nnzb"]
+        return self
+
     def counts(self) -> dict:
         out = (C.c_int64 * 7)()
         _check(_lib.abilu_pattern_counts(self.handle, out))
         return dict(zip(("n", "nnzb", "nl", "nu", "npairs", "max_row", "nwork"), list(out)))
+
+    def arrays(self, stream=None):
+        """(rowptr, colind) of the pattern as new int32 CUDA tensors."""
+        import torch
+        rp = torch.empty(self.n + 1, dtype=torch.int32, device="cuda")
+        ci = torch.empty(self.nnzb, dtype=torch.int32, device="cuda")
+        _check(_lib.abilu_pattern_arrays(self.handle, _ptr(rp, torch.int32), _ptr(ci, torch.int32),
+                                         _stream(stream)))
+        return rp, ci
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -529,3 +558,17 @@ def fgmres_solve_mg(mg: Multigrid, A, b, x, restart=30, max_iters=2500, rtol=1e-
         mg.A = A
     return SolveResult(r.iters, r.restarts, r.rel_resid_est, r.rel_resid_true,
                        r.singular_blocks, st)
+
+
+def parilut(pattern: Pattern, A, fill=2.0, iters=3, sweeps=2, stream=None):
+    """Threshold block ILU (abilu_parilut): (Pattern, Factors) of the final
+    pattern, FP64 factors.  Use the factors with fgmres_solve(..., build=False)."""
+    import torch
+    o = ParilutOpts(float(fill), int(iters), int(sweeps))
+    hp, hf = C.c_void_p(), C.c_void_p()
+    _check(_lib.abilu_parilut(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
+                              C.byref(o), _stream(stream), C.byref(hp), C.byref(hf)))
+    pat = Pattern._wrap(hp)
+    fac = Factors.__new__(Factors)
+    fac.handle, fac.pattern, fac.dtype, fac.scalar = hf, pat, "f64", False
+    return pat, fac

@@ -517,7 +517,8 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
     if (!p || !A || !f || !b || !x || !opts || !res)
         return fail(ABILU_EINVAL, "fgmres_solve: NULL argument");
     memset(res, 0, sizeof *res);
-    if (f->p != p) return fail(ABILU_EINVAL, "fgmres_solve: factors belong to another pattern");
+    if (f->p != p && (f->p->v.n != p->v.n || opts->build))
+        return fail(ABILU_EINVAL, "fgmres_solve: factors of another pattern need the same n and opts->build = 0");
     abilu_status s = fgmres_check_opts(opts, "fgmres_solve");
     if (s != ABILU_OK) return s;
     if (opts->apply_sweeps_lower < 0 || opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 ||

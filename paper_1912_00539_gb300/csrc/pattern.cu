@@ -109,9 +109,10 @@ __global__ void k_scan_add(int32_t *out, const long long *tile_off, int n) {
     if (idx < n) out[idx] += (int32_t)tile_off[idx / SCAN_TILE];
 }
 
-// out[0..n] = exclusive scan of in[0..n-1]; scratch >= ceil(n/TILE) long longs
-static abilu_status scan(const int32_t *in, int32_t *out, int n, long long *scratch,
-                         unsigned *err, cudaStream_t st) {
+// out[0..n] = exclusive scan of in[0..n-1]; scratch >= ceil(n/TILE) long longs;
+// a total above 2^31 - 1 sets bit 8 of *err
+abilu_status scan_i32(const int32_t *in, int32_t *out, int n, long long *scratch, unsigned *err,
+                      cudaStream_t st) {
     int ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles < 1) ntiles = 1;
     k_scan_tiles<<<counted(ntiles), SCAN_THREADS, 0, st>>>(in, out, scratch, n);
@@ -355,8 +356,8 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
                     herr[0] & PAT_UNSORTED ? "columns not strictly increasing " : "",
                     herr[0] & PAT_NO_DIAG ? "missing diagonal block" : "");
     }
-    TRY(scan(lcnt, lrow, n, scratch, err, st));
-    TRY(scan(ucnt, urow, n, scratch, err, st));
+    TRY(scan_i32(lcnt, lrow, n, scratch, err, st));
+    TRY(scan_i32(ucnt, urow, n, scratch, err, st));
     int32_t nl_nu[2];
     TRY(cu(cudaMemcpyAsync(&nl_nu[0], lrow + n, 4, cudaMemcpyDeviceToHost, st), "read nl"));
     TRY(cu(cudaMemcpyAsync(&nl_nu[1], urow + n, 4, cudaMemcpyDeviceToHost, st), "read nu"));
@@ -370,7 +371,7 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     k_pat_pairs<false><<<counted(gb), 256, 0, st>>>(n, d_rowptr, d_colind, diagpos, lrow, urow, pair_cnt,
                                            nullptr, nullptr);
     TRY(cu(cudaGetLastError(), "k_pat_pairs count"));
-    TRY(scan(pair_cnt, pair_ptr, nnzb, scratch, err, st));
+    TRY(scan_i32(pair_cnt, pair_ptr, nnzb, scratch, err, st));
     int32_t npairs;
     TRY(cu(cudaMemcpyAsync(&npairs, pair_ptr + nnzb, 4, cudaMemcpyDeviceToHost, st), "read npairs"));
     TRY(cu(cudaMemcpyAsync(herr, err, sizeof herr, cudaMemcpyDeviceToHost, st), "read err"));
@@ -390,7 +391,7 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     k_pat_work<false><<<counted(gb), 256, 0, st>>>(n, d_rowptr, d_colind, diagpos, lrow, urow,
                                                    pair_ptr, wcnt, nullptr, nullptr);
     TRY(cu(cudaGetLastError(), "k_pat_work count"));
-    TRY(scan(wcnt, wptr, n, scratch, err, st));
+    TRY(scan_i32(wcnt, wptr, n, scratch, err, st));
     int32_t nwork;
     TRY(cu(cudaMemcpyAsync(&nwork, wptr + n, 4, cudaMemcpyDeviceToHost, st), "read nwork"));
     TRY(cu(cudaStreamSynchronize(st), "sync"));
@@ -437,6 +438,19 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     p->v.wpos = wpos;
     p->max_row = (int)herr[2];
     *out = p;
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_pattern_arrays(abilu_pattern p, int32_t *rowptr, int32_t *colind,
+                                             abilu_stream stream) {
+    if (!p) return fail(ABILU_EINVAL, "pattern_arrays: NULL pattern");
+    cudaStream_t st = S(stream);
+    if (rowptr)
+        ABILU_CUDA(cudaMemcpyAsync(rowptr, p->v.rowptr, sizeof(int32_t) * ((size_t)p->v.n + 1),
+                                   cudaMemcpyDeviceToDevice, st));
+    if (colind)
+        ABILU_CUDA(cudaMemcpyAsync(colind, p->v.colind, sizeof(int32_t) * (size_t)p->v.nnzb,
+                                   cudaMemcpyDeviceToDevice, st));
     return ABILU_OK;
 }
 

@@ -106,3 +106,22 @@ def test_threshold_ilu_cuts_iterations():
     assert r1.converged and r1.iters < r0.iters
     res = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x)
     assert np.linalg.norm(res) / np.linalg.norm(s.b) <= 1e-6
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_fix_constant_upper(name):
+    """Exactly the strictly upper blocks with no product pair (no k < i with
+    (i,k) and (k,j) in the pattern: the strict-lower by strict-upper boolean
+    product is zero there) take A's value; on the triangle-free grids that is
+    every strictly upper block."""
+    s = SYSTEMS[name]()
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal(s.vals.shape)
+    Y = oracle.fix_constant_upper(s.rowptr, s.colind, s.vals, X)
+    M = _mask(s.rowptr, s.colind).astype(int)
+    has_pair = (np.tril(M, -1) @ np.triu(M, 1)) > 0
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    const = (rows < s.colind) & ~has_pair[rows, s.colind]
+    assert np.array_equal(Y[const], s.vals[const]) and np.array_equal(Y[~const], X[~const])
+    if name != "random_triangles":
+        assert np.array_equal(const, rows < s.colind)
