@@ -842,16 +842,18 @@ def run_gpu(args):
 
     # ---- end to end: A and b from pinned host memory, x back, every step.
     # Double-buffered like a serving loop: the next step's A and b stream in
-    # on a copy stream while the current step solves (every step's inputs and
-    # result still cross the host link inside the timed region).
+    # and the previous step's x streams out on a copy stream while the current
+    # step solves (every step's inputs and result still cross the host link
+    # inside the timed region; the last x is waited for before it closes).
     hA = torch.from_numpy(s.vals).pin_memory()
     hb = torch.from_numpy(s.b).pin_memory()
-    hx = torch.empty_like(hb).pin_memory()
+    hx = [torch.empty_like(hb).pin_memory(), torch.empty_like(hb).pin_memory()]
     dA = [torch.empty_like(A), torch.empty_like(A)]
     db = [torch.empty_like(b), torch.empty_like(b)]
-    dx = torch.empty_like(b)
+    dx = [torch.empty_like(b), torch.empty_like(b)]
     copy_stream = torch.cuda.Stream()
     ready = [torch.cuda.Event(), torch.cuda.Event()]
+    solved = [torch.cuda.Event(), torch.cuda.Event()]
 
     def h2d(k):
         with torch.cuda.stream(copy_stream):
@@ -860,16 +862,22 @@ def run_gpu(args):
             ready[k % 2].record(copy_stream)
 
     def e2e_steps(nsteps):
+        # copy-stream order: h2d(k+1), d2h(k), h2d(k+2), ...: step k+2, which
+        # overwrites dx[k % 2], waits for h2d(k+2) and so for d2h(k)
         h2d(0)
         for k in range(nsteps):
             if k + 1 < nsteps:
                 h2d(k + 1)      # buffer (k+1) % 2 was last read by step k-1, finished
             stream.wait_event(ready[k % 2])
-            ab.fgmres_solve(pat, dA[k % 2], fac, db[k % 2], dx, restart=RESTART, rtol=RTOL,
-                            build_sweeps=BUILD_SWEEPS, apply_sweeps_lower=APPLY_SWEEPS,
-                            apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode,
-                            raise_on_noconv=True, zero_guess=True)
-            hx.copy_(dx, non_blocking=True)
+            ab.fgmres_solve(pat, dA[k % 2], fac, db[k % 2], dx[k % 2], restart=RESTART,
+                            rtol=RTOL, build_sweeps=BUILD_SWEEPS,
+                            apply_sweeps_lower=APPLY_SWEEPS, apply_sweeps_upper=APPLY_SWEEPS,
+                            mode=args.mode, raise_on_noconv=True, zero_guess=True)
+            solved[k % 2].record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(solved[k % 2])
+                hx[k % 2].copy_(dx[k % 2], non_blocking=True)
+        stream.wait_stream(copy_stream)
 
     e2e_steps(2)
     torch.cuda.synchronize()
@@ -882,7 +890,7 @@ def run_gpu(args):
     e2e_ms = max_over_ranks(torch, e0.elapsed_time(e1), dev)
     e2e = {"value": job_rate(args.steps, world, e2e_ms), "unit": "solves/s",
            "h2d_bytes_per_step": hA.numel() * 8 + hb.numel() * 8,
-           "d2h_bytes_per_step": hx.numel() * 8}
+           "d2h_bytes_per_step": hx[0].numel() * 8}
 
     # ---- per-kernel rooflines (the dominant kernel by solve time share)
     fk = ab.Factors(pat, "f32")
