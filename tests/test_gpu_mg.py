@@ -254,3 +254,26 @@ def test_full_size_mg(ab, name):
         _iters_ok(mode, res.iters, ro.iters)
         r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
         assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
+
+
+@pytest.mark.parametrize("case", ["one_block", "block_diagonal"])
+def test_degenerate_systems(ab, case):
+    """One cell: a single level (nothing to coarsen), the cycle is the block
+    ILU smoother.  Block-diagonal A: every cell its own aggregate, so
+    aggregation stops at one level; the cycle's steps are exact (M = A)."""
+    if case == "one_block":
+        s = gen.System("one_block", np.array([0, 1], np.int32), np.array([0], np.int32),
+                       np.array([[[4.0, 1, 0, 0], [1, 5, 1, 0], [0, 1, 6, 1], [0, 0, 1, 7]]]),
+                       np.array([[1.0, 2, 3, 4]]), np.arange(1), 1.0)
+    else:
+        s = gen.random_pattern_system(700, 0, seed=9, structure="diagonal")
+    d = Dev(ab, s)
+    mg = ab.Multigrid(d.pat, d.A, min_coarse=1, factor_dtype="f64", build_sweeps=1,
+                      coarse_smooth=1, mode="sync")
+    assert mg.nlevels == 1
+    x = d.vec()
+    res = ab.fgmres_solve_mg(mg, d.A, d.b, x, rtol=1e-10)
+    assert res.converged and res.iters == 1
+    from oracle import dense
+    xo = np.linalg.solve(dense.to_dense(s.rowptr, s.colind, s.vals), s.b.reshape(-1))
+    assert _rel(x.cpu().numpy().reshape(-1), xo) < 1e-12

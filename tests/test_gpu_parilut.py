@@ -132,3 +132,15 @@ def test_full_size_viscous(ab):
     assert res.converged and abs(res.iters - ro.iters) <= max(1, ro.iters // 10)
     r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
     assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
+
+
+def test_block_diagonal_has_no_fill(ab):
+    """Block-diagonal A: L U has no fill and no off-diagonal block to keep;
+    the pattern stays the diagonal and the factors are the exact inverse."""
+    s = gen.random_pattern_system(300, 0, seed=9, structure="diagonal")
+    d = Dev(ab, s)
+    pat, fac = ab.parilut(d.pat, d.A, fill=2.0, iters=2, sweeps=1)
+    rp, ci = pat.arrays()
+    assert np.array_equal(rp.cpu().numpy(), s.rowptr) and np.array_equal(ci.cpu().numpy(), s.colind)
+    X, D = fac.export()
+    assert _rel(D.cpu().numpy(), np.linalg.inv(s.vals)) < 1e-14
