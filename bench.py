@@ -760,11 +760,12 @@ def run_parilut(args):
                                        build=False, max_iters=300)
             r, ms = timed(solve0, 5)
             row[f"ilu0_{dt}_async"] = {"iters": r.iters, "solve_ms": round(ms, 3)}
-        for fill in (1.5, 2.0):
+        for fill, fdt in ((1.5, "f64"), (2.0, "f64"), (1.5, "f32"), (2.0, "f32")):
             t0 = time.perf_counter()
-            fpat, ffac = ab.parilut(pat, A, fill=fill, iters=3, sweeps=2)
+            fpat, ffac = ab.parilut(pat, A, fill=fill, iters=3, sweeps=2, dtype=fdt)
             t_setup = time.perf_counter() - t0
-            _, t_setup2 = timed(lambda: ab.parilut(pat, A, fill=fill, iters=3, sweeps=2), 2)
+            _, t_setup2 = timed(lambda: ab.parilut(pat, A, fill=fill, iters=3, sweeps=2, dtype=fdt),
+                                2)
             rec = {"blocks": fpat.nnzb, "setup_ms": round(t_setup2, 2),
                    "first_setup_ms": round(t_setup * 1e3, 1)}
             for md in ("sync", "async"):
@@ -778,12 +779,14 @@ def run_parilut(args):
                 rec[f"{md}_iters"] = r.iters
                 rec[f"{md}_solve_ms"] = round(ms, 3)
                 rec[f"{md}_rel_resid_true"] = _r(r.rel_resid_true)
-            rp, ci, Xo, Do = oracle.parilut(s.rowptr, s.colind, s.vals, fill=fill, iters=3, sweeps=2)
-            _, ro = oracle.fgmres_ilu_pattern(s.rowptr, s.colind, s.vals, rp, ci, Xo, Do, s.b, na,
-                                              na, restart=st["restart"], max_iters=300)
-            rec["oracle_blocks"] = int(len(ci))
-            rec["oracle_iters"] = ro.iters
-            row[f"threshold_fill{fill}"] = rec
+            if fdt == "f64":
+                rp, ci, Xo, Do = oracle.parilut(s.rowptr, s.colind, s.vals, fill=fill, iters=3,
+                                                sweeps=2)
+                _, ro = oracle.fgmres_ilu_pattern(s.rowptr, s.colind, s.vals, rp, ci, Xo, Do, s.b,
+                                                  na, na, restart=st["restart"], max_iters=300)
+                rec["oracle_blocks"] = int(len(ci))
+                rec["oracle_iters"] = ro.iters
+            row[f"threshold_fill{fill}_{fdt}"] = rec
         out[name] = row
     return out
 

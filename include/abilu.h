@@ -381,20 +381,24 @@ abilu_status fgmres_solve_mg(abilu_mg mg, const double *A_vals, const double *b,
  *           of A's pattern); diagonal blocks always; `sweeps` synchronous
  *           sweeps on the kept pattern.
  * abilu_parilut returns a new pattern handle (the final pattern, n cells) and
- * FP64 factors on it, both owned by the caller (abilu_pattern_destroy,
+ * factors on it, both owned by the caller (abilu_pattern_destroy,
  * abilu_factors_destroy): abilu_apply, abilu_factors_export (in the new
- * pattern's layout) and fgmres_solve (with opts->build = 0) take them.
+ * pattern's layout) and fgmres_solve (with opts->build = 0) take them.  The
+ * factorisation runs in FP64; the returned factors are stored in
+ * factor_dtype (FP32: rounded, with Dinv U for the upper sweeps, as a build
+ * leaves them).
  * Synchronises `stream`.  ABILU_EINVAL on bad options or when a row of L U
  * would exceed 192 blocks.  iters = 0 gives block ILU(0) after `sweeps`
  * sweeps, on a copy of A's pattern.
  */
 typedef struct {
-    double fill;        /* budget factor, >= 0 (2.0: twice A's lower / upper blocks) */
-    int32_t iters;      /* fill-and-drop steps, >= 0 */
-    int32_t sweeps;     /* synchronous sweeps after the start and after every change, >= 0 */
+    double fill;          /* budget factor, >= 0 (2.0: twice A's lower / upper blocks) */
+    int32_t iters;        /* fill-and-drop steps, >= 0 */
+    int32_t sweeps;       /* synchronous sweeps after the start and after every change, >= 0 */
+    int32_t factor_dtype; /* abilu_dtype of the returned factors */
 } abilu_parilut_opts;
 
-/* Defaults: fill 2.0, 3 steps, 2 sweeps. */
+/* Defaults: fill 2.0, 3 steps, 2 sweeps, FP64 factors. */
 void abilu_parilut_default_opts(abilu_parilut_opts *opts);
 abilu_status abilu_parilut(abilu_pattern p, const double *A_vals, const abilu_parilut_opts *opts,
                            abilu_stream stream, abilu_pattern *pattern_out,

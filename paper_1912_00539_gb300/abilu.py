@@ -62,7 +62,8 @@ MG_MAX_LEVELS = 16
 
 
 class ParilutOpts(C.Structure):
-    _fields_ = [("fill", C.c_double), ("iters", C.c_int32), ("sweeps", C.c_int32)]
+    _fields_ = [("fill", C.c_double), ("iters", C.c_int32), ("sweeps", C.c_int32),
+                ("factor_dtype", C.c_int32)]
 
 
 class FgmresResult(C.Structure):
@@ -560,15 +561,16 @@ def fgmres_solve_mg(mg: Multigrid, A, b, x, restart=30, max_iters=2500, rtol=1e-
                        r.singular_blocks, st)
 
 
-def parilut(pattern: Pattern, A, fill=2.0, iters=3, sweeps=2, stream=None):
+def parilut(pattern: Pattern, A, fill=2.0, iters=3, sweeps=2, dtype="f64", stream=None):
     """Threshold block ILU (abilu_parilut): (Pattern, Factors) of the final
-    pattern, FP64 factors.  Use the factors with fgmres_solve(..., build=False)."""
+    pattern, computed in FP64 and stored in `dtype`.  Use the factors with
+    fgmres_solve(..., build=False)."""
     import torch
-    o = ParilutOpts(float(fill), int(iters), int(sweeps))
+    o = ParilutOpts(float(fill), int(iters), int(sweeps), DTYPES[dtype])
     hp, hf = C.c_void_p(), C.c_void_p()
     _check(_lib.abilu_parilut(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),
                               C.byref(o), _stream(stream), C.byref(hp), C.byref(hf)))
     pat = Pattern._wrap(hp)
     fac = Factors.__new__(Factors)
-    fac.handle, fac.pattern, fac.dtype, fac.scalar = hf, pat, "f64", False
+    fac.handle, fac.pattern, fac.dtype, fac.scalar = hf, pat, dtype, False
     return pat, fac

@@ -737,6 +737,19 @@ abilu_status scalar_build(abilu_factors f, const double *A, int nsweeps, abilu_m
                           abilu_init init, cudaStream_t st);
 abilu_status scalar_export(abilu_factors f, double *X, cudaStream_t st);
 
+// Us = Dinv U for FP32 factors whose L, U and Dinv were written directly
+// (imported factors), as a build forms it at its end
+abilu_status form_scaled_upper(abilu_factors f, cudaStream_t st) {
+    const PatternView &P = f->p->v;
+    if (f->dtype != ABILU_F32 || !f->Us || P.nu == 0) return ABILU_OK;
+    const int cf = f->cur;
+    k_scale_upper<float><<<counted((P.n + BUILD_ROWS - 1) / BUILD_ROWS), BUILD_THREADS, 0, st>>>(
+        P, reinterpret_cast<const float *>(f->U[cf]), reinterpret_cast<const float *>(f->D[cf]),
+        reinterpret_cast<float *>(f->Us));
+    ABILU_LAUNCH_CHECK("k_scale_upper");
+    return ABILU_OK;
+}
+
 abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu_mode mode,
                             abilu_init init, cudaStream_t st) {
     if (f->scalar) return scalar_build(f, A, nsweeps, mode, init, st);

@@ -33,6 +33,7 @@ abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu
 abilu_status export_dispatch(abilu_factors f, double *X, double *Dinv, cudaStream_t st);
 abilu_status scan_i32(const int32_t *in, int32_t *out, int n, long long *scratch, unsigned *err,
                       cudaStream_t st);
+abilu_status form_scaled_upper(abilu_factors f, cudaStream_t st);
 __global__ void k_block_norm2(const double *__restrict__ A, long long nnzb, double *__restrict__ w);
 
 constexpr int PLU_THREADS = 128;
@@ -105,11 +106,12 @@ k_map_blocks(int n, const int32_t *__restrict__ rp_new, const int32_t *__restric
 }
 
 // Factors from X in the pattern layout (L_ij at column < row, U_ij at column
-// > row, U_ii on the diagonal) and Dinv: the compact arrays of iterate `cur`
+// > row, U_ii on the diagonal) and Dinv: the compact arrays of iterate `cur`,
+// rounded to the storage type T
+template <typename T>
 __global__ void __launch_bounds__(PLU_THREADS)
 k_import(PatternView P, const double *__restrict__ X, const double *__restrict__ Dinv,
-         double *__restrict__ L, double *__restrict__ U, double *__restrict__ D,
-         double *__restrict__ Udiag) {
+         T *__restrict__ L, T *__restrict__ U, T *__restrict__ D, T *__restrict__ Udiag) {
     const int i = blockIdx.x * (PLU_THREADS / 4) + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     const int p0 = P.rowptr[i], p1 = P.rowptr[i + 1], dp = P.diagpos[i];
@@ -230,7 +232,7 @@ static abilu_status factors_from(abilu_pattern p, const double *X, const double 
     abilu_status s = abilu_factors_create(p, ABILU_F64, &f);
     if (s != ABILU_OK) return s;
     const int c = f->cur;
-    k_import<<<counted(grid_rows(p->v.n, PLU_THREADS / 4)), PLU_THREADS, 0, st>>>(
+    k_import<double><<<counted(grid_rows(p->v.n, PLU_THREADS / 4)), PLU_THREADS, 0, st>>>(
         p->v, X, Dinv, static_cast<double *>(f->L[c]), static_cast<double *>(f->U[c]),
         static_cast<double *>(f->D[c]), static_cast<double *>(f->Udiag));
     cudaError_t e = cudaGetLastError();
@@ -278,6 +280,33 @@ static abilu_status select_thresholds(int n, const int32_t *rowptr, const int32_
     return ABILU_OK;
 }
 
+// the final FP64 factors stored in `dtype` (FP32: with Dinv U for the upper
+// sweeps): a new handle on the same pattern
+template <typename T>
+static abilu_status store_as(abilu_factors f64, abilu_dtype dtype, double *X, double *D,
+                             cudaStream_t st, abilu_factors *out) {
+    abilu_pattern p = f64->p;
+    abilu_status s = export_dispatch(f64, X, D, st);
+    if (s != ABILU_OK) return s;
+    abilu_factors f = nullptr;
+    if ((s = abilu_factors_create(p, dtype, &f)) != ABILU_OK) return s;
+    const int c = f->cur;
+    k_import<T><<<counted(grid_rows(p->v.n, PLU_THREADS / 4)), PLU_THREADS, 0, st>>>(
+        p->v, X, D, static_cast<T *>(f->L[c]), static_cast<T *>(f->U[c]), static_cast<T *>(f->D[c]),
+        static_cast<T *>(f->Udiag));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        abilu_factors_destroy(f);
+        return cuda_fail(e, "k_import");
+    }
+    if ((s = form_scaled_upper(f, st)) != ABILU_OK) {
+        abilu_factors_destroy(f);
+        return s;
+    }
+    *out = f;
+    return ABILU_OK;
+}
+
 static abilu_status read_total(const int32_t *ptr_n, const unsigned *err, cudaStream_t st,
                                int32_t *total) {
     unsigned e = 0;
@@ -298,6 +327,7 @@ extern "C" void abilu_parilut_default_opts(abilu_parilut_opts *o) {
     o->fill = 2.0;
     o->iters = 3;
     o->sweeps = 2;
+    o->factor_dtype = ABILU_F64;
 }
 
 extern "C" abilu_status abilu_parilut(abilu_pattern pA, const double *A,
@@ -309,7 +339,8 @@ extern "C" abilu_status abilu_parilut(abilu_pattern pA, const double *A,
     *factors_out = nullptr;
     if ((reinterpret_cast<uintptr_t>(A) & 15u) != 0)
         return fail(ABILU_EINVAL, "abilu_parilut: A_vals must be 16-byte aligned");
-    if (!(o->fill >= 0.0 && o->fill <= 1e9) || o->iters < 0 || o->sweeps < 0)
+    if (!(o->fill >= 0.0 && o->fill <= 1e9) || o->iters < 0 || o->sweeps < 0 ||
+        (o->factor_dtype != ABILU_F64 && o->factor_dtype != ABILU_F32 && o->factor_dtype != ABILU_BF16))
         return fail(ABILU_EINVAL, "abilu_parilut: bad options");
     cudaStream_t st = S(stream);
     const PatternView &VA = pA->v;
@@ -341,6 +372,16 @@ extern "C" abilu_status abilu_parilut(abilu_pattern pA, const double *A,
             FactorsGuard fo;
             if ((s = abilu_factors_create(pc.p, ABILU_F64, &fo.f)) != ABILU_OK) return s;
             if ((s = build_dispatch(fo.f, A, o->sweeps, ABILU_SYNC, ABILU_INIT_FROM_A, st)) != ABILU_OK) return s;
+            if (o->factor_dtype != ABILU_F64) {
+                double *Xs = nullptr;
+                if ((s = bufs.get(&Xs, (size_t)VA.nnzb * BB)) != ABILU_OK) return s;
+                FactorsGuard fn;
+                s = o->factor_dtype == ABILU_F32
+                        ? store_as<float>(fo.f, ABILU_F32, Xs, D, st, &fn.f)
+                        : store_as<__nv_bfloat16>(fo.f, ABILU_BF16, Xs, D, st, &fn.f);
+                if (s != ABILU_OK) return s;
+                std::swap(fo.f, fn.f);
+            }
             ABILU_CUDA(cudaStreamSynchronize(st));
             *pattern_out = pc.p;
             *factors_out = fo.f;
@@ -414,6 +455,14 @@ extern "C" abilu_status abilu_parilut(abilu_pattern pA, const double *A,
         FactorsGuard f3;
         if ((s = factors_from(p3.p, X3, D, A3, o->sweeps, st, &f3.f)) != ABILU_OK) return s;
         if (it == o->iters - 1) {
+            if (o->factor_dtype != ABILU_F64) {
+                FactorsGuard fn;
+                s = o->factor_dtype == ABILU_F32
+                        ? store_as<float>(f3.f, ABILU_F32, X3, D, st, &fn.f)
+                        : store_as<__nv_bfloat16>(f3.f, ABILU_BF16, X3, D, st, &fn.f);
+                if (s != ABILU_OK) return s;
+                std::swap(f3.f, fn.f);   // the FP64 factors are released with fn
+            }
             ABILU_CUDA(cudaStreamSynchronize(st));
             *pattern_out = p3.p;
             *factors_out = f3.f;

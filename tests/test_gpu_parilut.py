@@ -144,3 +144,29 @@ def test_block_diagonal_has_no_fill(ab):
     assert np.array_equal(rp.cpu().numpy(), s.rowptr) and np.array_equal(ci.cpu().numpy(), s.colind)
     X, D = fac.export()
     assert _rel(D.cpu().numpy(), np.linalg.inv(s.vals)) < 1e-14
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-6), ("bf16", 8e-3)])
+def test_narrow_storage_of_the_factors(ab, dsys, dtype, tol):
+    """Factors computed in FP64 and stored in FP32 / BF16: the stored values
+    are the oracle's rounded (unit roundoff 6e-8 / 3.9e-3 of the largest
+    entry), and FGMRES with them converges like the FP64 ones (FP32: the
+    oracle's iteration count within 10%, at least 1)."""
+    s = dsys.s
+    pat, fac = ab.parilut(dsys.pat, dsys.A, fill=2.0, iters=3, sweeps=2, dtype=dtype)
+    rp, ci, Xo, Do = oracle.parilut(s.rowptr, s.colind, s.vals, fill=2.0, iters=3, sweeps=2)
+    grp, gci = pat.arrays()
+    assert np.array_equal(grp.cpu().numpy(), rp) and np.array_equal(gci.cpu().numpy(), ci)
+    X, D = fac.export()
+    assert _rel(X.cpu().numpy(), Xo) < tol and _rel(D.cpu().numpy(), Do) < tol
+    x = dsys.vec()
+    res = ab.fgmres_solve(dsys.pat, dsys.A, fac, dsys.b, x, restart=30, rtol=1e-6,
+                          apply_sweeps_lower=3, apply_sweeps_upper=3, mode="sync", build=False,
+                          max_iters=300)
+    _, ro = oracle.fgmres_ilu_pattern(s.rowptr, s.colind, s.vals, rp, ci, Xo, Do, s.b, 3, 3,
+                                      restart=30, max_iters=300)
+    assert res.converged
+    if dtype == "f32":
+        assert abs(res.iters - ro.iters) <= max(1, ro.iters // 10), (res.iters, ro.iters)
+    r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
