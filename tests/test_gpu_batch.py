@@ -149,3 +149,29 @@ def test_graph_and_host_driven_cycles_agree(ab, mode, monkeypatch):
             assert [r.iters for r in rg] == [r.iters for r in rh]
             for a, b in zip(xg, xh):
                 np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.slow
+def test_full_batch_of_64_uneven_systems(ab):
+    """The batched workload at full size: 64 systems of 2k-200k cells
+    (log-uniform, seeded aspect ratios and CFL 10-1e4) in one batch, FP32
+    factors, synchronous 4 build / 3+3 apply sweeps: every system converges to
+    a true FP64 residual <= 1e-6 (the oracle's SpMV) with the FP64 oracle's
+    iteration count for that system within 10% (at least 1)."""
+    import torch
+    systems = gen.batch_systems()
+    assert len(systems) == 64
+    devs = [_dev(s) for s in systems]
+    batch = ab.Batch([(d[0], d[1]) for d in devs], dtype="f32")
+    for k, d in enumerate(devs):
+        batch.set_system(k, d[2], d[3])
+    res = batch.solve(restart=30, rtol=1e-6, build_sweeps=4, apply_sweeps_lower=3,
+                      apply_sweeps_upper=3, mode="sync")
+    for k, (s, d) in enumerate(zip(systems, devs)):
+        x = torch.empty_like(d[3])
+        batch.solution(k, x)
+        r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
+        assert res[k].converged and np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6, k
+        Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 4)
+        _, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, 3, 3, restart=30, rtol=1e-6)
+        assert abs(res[k].iters - ro.iters) <= max(1, ro.iters // 10), (k, res[k].iters, ro.iters)

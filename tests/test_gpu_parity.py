@@ -573,3 +573,53 @@ def test_diagnostics_match_oracle(ab, dsys, dtype, nsweeps):
     assert abs(g["lu_defect_max"] - d_ref) <= 1e-11 * scale
     assert abs(g["jacobi_norm_L"] - ln) <= 1e-12 * max(ln, 1.0)
     assert abs(g["jacobi_norm_U"] - un) <= 1e-10 * max(un, 1.0)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("order", ["rcm", "line"])
+def test_full_size_viscous_parity(ab, order):
+    """The viscous-like 1024x256 workload (CFL 1e4, wall-normal coupling x100)
+    in both orderings at its solver settings (8 build, 6+6 apply sweeps,
+    FGMRES(50)): SpMV and one FP64 synchronous build sweep element by element
+    (each inverse diagonal block to 64 u times its condition number: the two
+    sides invert by different, equally valid methods);
+    FP32-factor solves converge to a true FP64 residual <= 1e-6 with the FP64
+    oracle's iteration count within 10% (synchronous) or at most 10% above it
+    (asynchronous: newer values, the build nearer its fixed point)."""
+    name = f"viscous_1024x256_{order}"
+    s = gen.workload(name)
+    st = gen.SOLVER_SETTINGS[name]
+    d = Dev(ab, s)
+    x = np.random.default_rng(19).standard_normal((s.n, 4))
+    y = d.vec()
+    ab.bsr_spmv(d.pat, d.A, d.vec(x), y)
+    assert _rel(y.cpu().numpy(), oracle.spmv(s.rowptr, s.colind, s.vals, x)) < 1e-14
+    fac = ab.Factors(d.pat, "f64")
+    fac.build(d.A, 1, mode="sync")
+    X, D = fac.export()
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 1)
+    assert _rel(X.cpu().numpy(), Xo) < 1e-12
+    # U_jj here reaches cond 9e6: two exact-arithmetic-equivalent inversions
+    # (the GPU's adjugate, the oracle's Gauss-Jordan) differ by up to cond(U_jj)
+    # units in the last place, so each inverse is held to 64 u cond(U_jj)
+    rows = np.repeat(np.arange(s.n), np.diff(s.rowptr))
+    cond = np.linalg.cond(Xo[rows == s.colind])
+    err = np.abs(D.cpu().numpy() - Do).max(axis=(1, 2)) / np.abs(Do).max(axis=(1, 2))
+    assert np.all(err <= 64 * 2.0 ** -53 * cond), float((err / cond).max())
+    nb, na, m = st["build_sweeps"], st["apply_sweeps"], st["restart"]
+    Xn, Dn, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, nb)
+    _, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xn, Dn, s.b, na, na, restart=m, rtol=1e-6)
+    assert ro.converged
+    for mode in ("sync", "async"):
+        f32 = ab.Factors(d.pat, "f32")
+        xs = d.vec()
+        res = ab.fgmres_solve(d.pat, d.A, f32, d.b, xs, restart=m, rtol=1e-6, build_sweeps=nb,
+                              apply_sweeps_lower=na, apply_sweeps_upper=na, mode=mode)
+        assert res.converged and res.rel_resid_true <= 1e-6
+        tol = max(1, ro.iters // 10)
+        if mode == "sync":
+            assert abs(res.iters - ro.iters) <= tol, (mode, res.iters, ro.iters)
+        else:
+            assert res.iters <= ro.iters + tol, (mode, res.iters, ro.iters)
+        r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, xs.cpu().numpy())
+        assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
