@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(APPLY_THREADS)
 k_async_start(PatternView P, const T *__restrict__ D, const VT *__restrict__ r,
               VT *__restrict__ y, VT *__restrict__ x1, VT *__restrict__ yh, double *__restrict__ z,
               unsigned long long *tickets, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     if (blockIdx.x == 0 && threadIdx.x < 2) tickets[threadIdx.x] = 0ull;
     if (skip_chunk(skip, blockIdx.x)) return;
@@ -275,6 +277,8 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
              const float *__restrict__ rhs, const float *vin, float *v, int nsweeps, int sync_last,
              float *__restrict__ x1, float *__restrict__ yh, double *__restrict__ z,
              unsigned long long *ticket, unsigned long long *err, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     __shared__ __align__(128) PipeStage<T> st[2];
     __shared__ __align__(8) uint64_t full[2], empty[2];
@@ -477,7 +481,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
         VT *x1 = nu >= 2 ? x[0] : nullptr;     // x^1, updated in place by the upper sweeps
         VT *yh = SC && nu >= 2 ? y[1] : nullptr;
         double *z1 = nu == 1 ? z : nullptr;
-        k_async_start<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
+        launch_pdl(k_async_start<T, VT>, grid, APPLY_THREADS, 0, st,
             P, D, rv, y[0], nl == 1 ? x1 : nullptr, nl == 1 ? yh : nullptr, nl == 1 ? z1 : nullptr,
             tk, skip);
         ABILU_LAUNCH_CHECK("k_async_start");
@@ -486,7 +490,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             if constexpr (sizeof(VT) == 4) {  // staged pipeline (FP32/BF16 factors)
                 const int c = staged_ctas<false, false, false, T>();
                 const int g = (int)(c < nchunks ? c : nchunks);
-                k_tri_staged<false, false, false, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+                launch_pdl(k_tri_staged<false, false, false, T>, g, PIPE_THREADS, 0, st,
                     P, L, D, rv, nullptr, y[0], nl - 1, 0, x1, yh, z1, tk, err, skip);
             } else {
                 const int ctas_l = lower_async_ctas<T, VT>();
@@ -500,7 +504,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             if constexpr (sizeof(VT) == 4) {
                 const int c = staged_ctas<true, SC, false, T>();
                 const int g = (int)(c < nchunks ? c : nchunks);
-                k_tri_staged<true, SC, false, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+                launch_pdl(k_tri_staged<true, SC, false, T>, g, PIPE_THREADS, 0, st,
                     P, UU, D, SC ? y[1] : y[0], nullptr, x[0], nu - 1, 0, nullptr, nullptr, z, tk + 1,
                     err, skip);
             } else {
@@ -550,7 +554,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
         if constexpr (sizeof(VT) == 4) {
             const int c = staged_ctas<true, SC, true, T>();
             const int g = c < grid ? c : grid;
-            k_tri_staged<true, SC, true, T><<<counted(g), PIPE_THREADS, 0, st>>>(
+            launch_pdl(k_tri_staged<true, SC, true, T>, g, PIPE_THREADS, 0, st,
                 P, UU, D, yfin, xin, last ? nullptr : x[s & 1], 1, last ? 1 : 0, nullptr, nullptr,
                 last ? z : nullptr, nullptr, f->ctr + 4, skip);
         } else {

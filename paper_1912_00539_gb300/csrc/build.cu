@@ -410,6 +410,8 @@ __global__ void __launch_bounds__(BUILD_THREADS, 5)   // 48 registers: measured 
 k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T *D, T *Udiag,
                      int nsweeps, int max_warps, unsigned long long *nsing,
                      unsigned long long *ticket, unsigned long long *err, int *done) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
     // at most one warp per chunk: more would sweep the same blocks at once
     if (blockIdx.x * (BUILD_THREADS / 32) + (threadIdx.x >> 5) >= max_warps) return;
@@ -505,6 +507,8 @@ __global__ void __launch_bounds__(BUILD_THREADS, sizeof(T) == 8 ? 3 : 4)
 k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__ A32,
                 T *__restrict__ L, T *__restrict__ U, T *__restrict__ Uother, T *__restrict__ D,
                 T *__restrict__ Udiag, int init_from_a, unsigned long long *nsing) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh_u[BuildShared<T>::D];
     __shared__ double sh_d[BuildShared<T>::D];
     __shared__ __align__(16) float sh_q[BuildShared<T>::F];
@@ -559,6 +563,8 @@ k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__
 template <typename T>
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_scale_upper(PatternView P, const T *__restrict__ U, const T *__restrict__ D, T *__restrict__ Us) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * BUILD_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
     float d[4];
@@ -640,10 +646,10 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
         }
         const int c = f->cur;
         if (done)
-            k_build_blocks_async<T, true><<<counted(ctas), BUILD_THREADS, 0, st>>>(
+            launch_pdl(k_build_blocks_async<T, true>, ctas, BUILD_THREADS, 0, st,
                 P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done);
         else
-            k_build_blocks_async<T, false><<<counted(ctas), BUILD_THREADS, 0, st>>>(
+            launch_pdl(k_build_blocks_async<T, false>, ctas, BUILD_THREADS, 0, st,
                 P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done);
         ABILU_LAUNCH_CHECK("k_build_blocks_async");
     }
@@ -699,7 +705,7 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
     constexpr bool narrow = sizeof(T) < 8;
     float *A32 = narrow ? reinterpret_cast<float *>(f->A32) : nullptr;
     const int c = f->cur;
-    k_build_prepare<T><<<counted(grid), BUILD_THREADS, 0, st>>>(
+    launch_pdl(k_build_prepare<T>, grid, BUILD_THREADS, 0, st,
         P, A, A32, L[c], U[c], mode == ABILU_SYNC ? U[1 - c] : nullptr, D[c], Ud,
         init == ABILU_INIT_FROM_A ? 1 : 0, f->ctr);
     ABILU_LAUNCH_CHECK("k_build_prepare");
@@ -710,7 +716,7 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
         }
         const int cf = f->cur;
         if (f->Us && P.nu > 0) {
-            k_scale_upper<T><<<counted(grid), BUILD_THREADS, 0, st>>>(
+            launch_pdl(k_scale_upper<T>, grid, BUILD_THREADS, 0, st,
                 P, reinterpret_cast<const T *>(f->U[cf]), reinterpret_cast<const T *>(f->D[cf]),
                 reinterpret_cast<T *>(f->Us));
             ABILU_LAUNCH_CHECK("k_scale_upper");
@@ -743,7 +749,7 @@ abilu_status form_scaled_upper(abilu_factors f, cudaStream_t st) {
     const PatternView &P = f->p->v;
     if (f->dtype != ABILU_F32 || !f->Us || P.nu == 0) return ABILU_OK;
     const int cf = f->cur;
-    k_scale_upper<float><<<counted((P.n + BUILD_ROWS - 1) / BUILD_ROWS), BUILD_THREADS, 0, st>>>(
+    launch_pdl(k_scale_upper<float>, (P.n + BUILD_ROWS - 1) / BUILD_ROWS, BUILD_THREADS, 0, st,
         P, reinterpret_cast<const float *>(f->U[cf]), reinterpret_cast<const float *>(f->D[cf]),
         reinterpret_cast<float *>(f->Us));
     ABILU_LAUNCH_CHECK("k_scale_upper");

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <utility>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -301,6 +302,33 @@ __device__ __forceinline__ void st_row(__nv_bfloat16 *p, const float v[4]) {
     u.x = *reinterpret_cast<unsigned *>(&a);
     u.y = *reinterpret_cast<unsigned *>(&b);
     *reinterpret_cast<uint2 *>(p) = u;
+}
+
+
+// Programmatic dependent launch.  The kernels of the solve path are launched
+// with programmatic stream serialization: a kernel's CTAs may be scheduled
+// while the previous kernel of the stream drains its last wave, so launch
+// latency and the tail overlap.  Every such kernel calls pdl_wait() before
+// its first global access (griddepcontrol.wait returns once the previous
+// grid has completed and its writes are visible; it is a no-op for a normal
+// launch), then pdl_trigger() to let the next kernel be scheduled in turn.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    note_launch();
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
 // Quad helpers: the 4 threads of an aligned group of 4 lanes cooperate on one

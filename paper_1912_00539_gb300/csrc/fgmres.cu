@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(RED_THREADS, 3)
 k_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
            const double *__restrict__ x, double *__restrict__ r_out, SolveState *S,
            double *partials, int init, int x_is_zero) {
+    pdl_wait();
+    pdl_trigger();
     // a restart after a cycle in which no step ran (the initial guess had
     // already converged) would recompute the same residual: keep the state
     if (!init && S->kdim == 0) return;
@@ -154,6 +156,8 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
 // the right-hand side the next preconditioner application reads
 __global__ void __launch_bounds__(RED_THREADS)
 k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *S) {
+    pdl_wait();
+    pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
     const double s = S->hn_inv;
     const double2 *a = reinterpret_cast<const double2 *>(vin);
@@ -216,6 +220,8 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
 __global__ void __launch_bounds__(RED_THREADS, 4)
 k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
        SolveState *S, double *partials, int pass) {
+    pdl_wait();
+    pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
     __shared__ double sh_w[RED_WARPS * TILE], sh_o[TILE];
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
@@ -246,6 +252,8 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
 __global__ void __launch_bounds__(RED_THREADS)
 k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict__ w,
          SolveState *S, double *partials, int pass, int final_pass) {
+    pdl_wait();
+    pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
     __shared__ double sh_h[MAXM + 1];
     __shared__ double sh_w[RED_WARPS], sh_o[1];
@@ -322,6 +330,8 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
 // y = R^{-1} g (every CTA, redundantly, in shared memory), then x += Z y
 __global__ void __launch_bounds__(RED_THREADS)
 k_xupdate(const double *__restrict__ Z, long long nv2, double *__restrict__ x, SolveState *S) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double y[MAXM];
     const int kd = S->kdim;
     if (kd == 0) return;
@@ -426,9 +436,9 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
     ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
     if (opts->zero_guess) ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
-    k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, ws->partials, 1,
+    launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1,
                                                       opts->zero_guess ? 1 : 0);
-    k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
+    launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS);
     ABILU_LAUNCH_CHECK("fgmres init");
     cudaEvent_t ev[2];
     ABILU_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
@@ -444,13 +454,13 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
-            k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, ws->partials, 0);
-            k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, ws->partials, 0, !opts->reorth);
+            launch_pdl(k_dots, nred, RED_THREADS, 0, st, V, nv2, j + 1, w, SS, ws->partials, 0);
+            launch_pdl(k_update, nred, RED_THREADS, 0, st, V, nv2, j, w, SS, ws->partials, 0, !opts->reorth);
             if (opts->reorth) {
-                k_dots<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j + 1, w, SS, ws->partials, 1);
-                k_update<<<counted(nred), RED_THREADS, 0, st>>>(V, nv2, j, w, SS, ws->partials, 1, 1);
+                launch_pdl(k_dots, nred, RED_THREADS, 0, st, V, nv2, j + 1, w, SS, ws->partials, 1);
+                launch_pdl(k_update, nred, RED_THREADS, 0, st, V, nv2, j, w, SS, ws->partials, 1, 1);
             }
-            k_scale<<<counted(nred), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
+            launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step"); break; }
             cudaEventRecord(ev[j & 1], st);
@@ -460,9 +470,9 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             }
         }
         if (ret != ABILU_OK) break;
-        k_xupdate<<<counted(nred), RED_THREADS, 0, st>>>(Z, nv2, x, SS);
-        k_residual<<<counted(nres), RED_THREADS, 0, st>>>(P, A, b, x, V, SS, ws->partials, 0, 0);
-        k_scale<<<counted(nred), RED_THREADS, 0, st>>>(V, V, v32, nv2, SS);
+        launch_pdl(k_xupdate, nred, RED_THREADS, 0, st, Z, nv2, x, SS);
+        launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 0, 0);
+        launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres restart"); break; }
         e = cudaStreamSynchronize(st);

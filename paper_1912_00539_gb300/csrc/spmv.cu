@@ -28,6 +28,8 @@ template <bool PLAIN>
 __global__ void __launch_bounds__(SPMV_THREADS)
 k_spmv(PatternView P, const double *__restrict__ A, double alpha, const double *__restrict__ x,
        double beta, double *__restrict__ y, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * SPMV_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
@@ -42,9 +44,9 @@ abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, co
     static_assert(SPMV_ROWS == SKIP_CHUNK_ROWS, "one CTA per 64-row chunk");
     const int grid = (P.n + SPMV_ROWS - 1) / SPMV_ROWS;
     if (alpha == 1.0 && beta == 0.0)
-        k_spmv<true><<<counted(grid), SPMV_THREADS, 0, st>>>(P, A, alpha, x, beta, y, skip);
+        launch_pdl(k_spmv<true>, grid, SPMV_THREADS, 0, st, P, A, alpha, x, beta, y, skip);
     else
-        k_spmv<false><<<counted(grid), SPMV_THREADS, 0, st>>>(P, A, alpha, x, beta, y, skip);
+        launch_pdl(k_spmv<false>, grid, SPMV_THREADS, 0, st, P, A, alpha, x, beta, y, skip);
     ABILU_LAUNCH_CHECK("k_spmv");
     return ABILU_OK;
 }
