@@ -91,6 +91,8 @@ __global__ void __launch_bounds__(APPLY_THREADS)
 k_lower_sync(PatternView P, const T *__restrict__ L, const VT *__restrict__ r,
              const VT *__restrict__ yin, VT *__restrict__ yout, const T *__restrict__ D,
              VT *__restrict__ x1, double *__restrict__ z, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
@@ -108,6 +110,8 @@ template <typename T, typename VT>
 __global__ void __launch_bounds__(APPLY_THREADS)
 k_diag_apply(PatternView P, const T *__restrict__ D, const VT *__restrict__ y,
              VT *__restrict__ x1, double *__restrict__ z, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
@@ -123,6 +127,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, sweep_min_ctas<VT>())
 k_upper_sync(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
              const VT *__restrict__ y, const VT *__restrict__ xin, VT *__restrict__ xout,
              double *__restrict__ z, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip) || skip_chunk(skip, blockIdx.x)) return;
     const int i = blockIdx.x * APPLY_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
@@ -152,6 +158,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, sweep_min_ctas<VT>())
 k_lower_async(PatternView P, const T *__restrict__ L, const VT *__restrict__ r, VT *y,
               int nsweeps, const T *__restrict__ D, VT *__restrict__ x1, VT *__restrict__ yh,
               double *__restrict__ z, unsigned long long *ticket, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     __shared__ unsigned long long s_t;
     const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
@@ -213,6 +221,8 @@ __global__ void __launch_bounds__(APPLY_THREADS)
 k_upper_async(PatternView P, const T *__restrict__ U, const T *__restrict__ D,
               const VT *__restrict__ y, VT *x, double *__restrict__ z, int nsweeps,
               unsigned long long *ticket, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     __shared__ unsigned long long s_t;
     const long long nchunks = (P.n + APPLY_ROWS - 1) / APPLY_ROWS;
@@ -495,7 +505,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             } else {
                 const int ctas_l = lower_async_ctas<T, VT>();
                 const int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
-                k_lower_async<T, VT><<<counted(g), APPLY_THREADS, 0, st>>>(P, L, rv, y[0], nl - 1, D,
+                launch_pdl(k_lower_async<T, VT>, g, APPLY_THREADS, 0, st, P, L, rv, y[0], nl - 1, D,
                                                                            x1, yh, z1, tk, skip);
             }
             ABILU_LAUNCH_CHECK("lower async");
@@ -510,7 +520,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             } else {
                 const int ctas_u = upper_async_ctas<T, VT>();
                 const int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
-                k_upper_async<T, VT, SC><<<counted(g), APPLY_THREADS, 0, st>>>(
+                launch_pdl(k_upper_async<T, VT, SC>, g, APPLY_THREADS, 0, st,
                     P, UU, D, SC ? y[1] : y[0], x[0], z, nu - 1, tk + 1, skip);
             }
             ABILU_LAUNCH_CHECK("upper async");
@@ -526,7 +536,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
     const VT *xfirst;   // x^1
     if (nl == 1) {      // no lower sweep runs: x^1 = Dinv r
         VT *x1 = nu >= 2 ? (SC ? y[0] : x[1]) : nullptr;
-        k_diag_apply<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(P, D, rv, x1,
+        launch_pdl(k_diag_apply<T, VT>, grid, APPLY_THREADS, 0, st, P, D, rv, x1,
                                                                      nu == 1 ? z : nullptr, skip);
         ABILU_LAUNCH_CHECK("k_diag_apply");
         yfin = SC ? y[0] : rv;
@@ -539,7 +549,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             VT *yout = y[s & 1];
             if (last) x1 = nu >= 2 ? (SC ? yout : x[1]) : nullptr;
             // (the staged form was measured slower for this sweep: 19.3 vs 17.1 us)
-            k_lower_sync<T, VT><<<counted(grid), APPLY_THREADS, 0, st>>>(
+            launch_pdl(k_lower_sync<T, VT>, grid, APPLY_THREADS, 0, st,
                 P, L, rv, yprev, (last && SC) ? nullptr : yout, D, last ? x1 : nullptr,
                 (last && nu == 1) ? z : nullptr, skip);
             ABILU_LAUNCH_CHECK("lower sync");
@@ -558,7 +568,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
                 P, UU, D, yfin, xin, last ? nullptr : x[s & 1], 1, last ? 1 : 0, nullptr, nullptr,
                 last ? z : nullptr, nullptr, f->ctr + 4, skip);
         } else {
-            k_upper_sync<T, VT, SC><<<counted(grid), APPLY_THREADS, 0, st>>>(
+            launch_pdl(k_upper_sync<T, VT, SC>, grid, APPLY_THREADS, 0, st,
                 P, UU, D, yfin, xin, last ? nullptr : x[s & 1], last ? z : nullptr, skip);
         }
         ABILU_LAUNCH_CHECK("upper sync");

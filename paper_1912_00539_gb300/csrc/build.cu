@@ -382,6 +382,8 @@ k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__res
                     const T *__restrict__ Uin, const T *__restrict__ Din, T *__restrict__ Lout,
                     T *__restrict__ Uout, T *__restrict__ Dout, T *__restrict__ Udiag,
                     unsigned long long *nsing) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
     const int w = blockIdx.x * WORK_PER_CTA + (threadIdx.x >> 2);
     if (w >= P.nwork) return;  // whole quads leave together
@@ -456,6 +458,8 @@ k_build_sync(PatternView P, const AT *__restrict__ A, const T *__restrict__ Lin,
              const T *__restrict__ Uin, const T *__restrict__ Din, T *__restrict__ Lout,
              T *__restrict__ Uout, T *__restrict__ Dout, T *__restrict__ Udiag,
              unsigned long long *nsing) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh_u[BuildShared<T>::D];
     __shared__ double sh_d[BuildShared<T>::D];
     __shared__ __align__(16) float sh_q[BuildShared<T>::F];
@@ -472,6 +476,8 @@ template <typename T, typename AT>
 __global__ void __launch_bounds__(BUILD_THREADS)
 k_build_async(PatternView P, const AT *__restrict__ A, T *L, T *U, T *D, T *Udiag,
               int nsweeps, unsigned long long *nsing, unsigned long long *ticket) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh_u[BuildShared<T>::D];
     __shared__ double sh_d[BuildShared<T>::D];
     __shared__ __align__(16) float sh_q[BuildShared<T>::F];
@@ -617,7 +623,7 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
     if (mode == ABILU_SYNC) {
         for (int s = 0; s < nsweeps; s++) {
             const int c = f->cur, o = 1 - f->cur;
-            k_build_blocks_sync<T><<<counted(grid), BUILD_THREADS, 0, st>>>(
+            launch_pdl(k_build_blocks_sync<T>, grid, BUILD_THREADS, 0, st,
                 P, A32, L[c], U[c], D[c], L[o], U[o], D[o], s == nsweeps - 1 ? Ud : nullptr, f->ctr);
             ABILU_LAUNCH_CHECK("k_build_blocks_sync");
             f->cur = o;
@@ -667,7 +673,7 @@ static abilu_status sweeps_t(abilu_factors f, const AT *Asrc, int nsweeps, abilu
     if (mode == ABILU_SYNC) {
         for (int s = 0; s < nsweeps; s++) {
             const int c = f->cur, o = 1 - f->cur;
-            k_build_sync<T, AT><<<counted(grid), BUILD_THREADS, 0, st>>>(
+            launch_pdl(k_build_sync<T, AT>, grid, BUILD_THREADS, 0, st,
                 P, Asrc, L[c], U[c], D[c], L[o], U[o], D[o], s == nsweeps - 1 ? Ud : nullptr,
                 f->ctr);
             ABILU_LAUNCH_CHECK("k_build_sync");
@@ -687,7 +693,7 @@ static abilu_status sweeps_t(abilu_factors f, const AT *Asrc, int nsweeps, abilu
         if (ctas < 1) ctas = 1;
         ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, sizeof(unsigned long long), st));
         const int c = f->cur;
-        k_build_async<T, AT><<<counted(ctas), BUILD_THREADS, 0, st>>>(P, Asrc, L[c], U[c], D[c], Ud,
+        launch_pdl(k_build_async<T, AT>, ctas, BUILD_THREADS, 0, st, P, Asrc, L[c], U[c], D[c], Ud,
                                                                       nsweeps, f->ctr, f->ctr + 1);
         ABILU_LAUNCH_CHECK("k_build_async");
     }

@@ -81,6 +81,8 @@ k_block_norm2(const double *__restrict__ A, long long nnzb, double *__restrict__
 __global__ void __launch_bounds__(MG_THREADS)
 k_galerkin(long long nnzb_c, const int *__restrict__ gptr, const int *__restrict__ gidx,
            const double *__restrict__ A, double *__restrict__ Ac) {
+    pdl_wait();
+    pdl_trigger();
     const long long c = ((long long)blockIdx.x * MG_THREADS + threadIdx.x) >> 2;
     const int q = threadIdx.x & 3;
     if (c >= nnzb_c) return;
@@ -105,6 +107,8 @@ k_galerkin(long long nnzb_c, const int *__restrict__ gptr, const int *__restrict
 __global__ void __launch_bounds__(MG_THREADS)
 k_mg_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
               const double *__restrict__ x, double *__restrict__ r, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     const int i = blockIdx.x * MG_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (i >= P.n) return;
@@ -118,6 +122,8 @@ k_mg_residual(PatternView P, const double *__restrict__ A, const double *__restr
 __global__ void __launch_bounds__(MG_THREADS)
 k_mg_restrict(const double *__restrict__ r, const int *__restrict__ mptr,
               const int *__restrict__ mem, int nc, double *__restrict__ bc, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     const int I = blockIdx.x * MG_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
     if (I >= nc) return;
@@ -140,6 +146,8 @@ template <bool ASSIGN>
 __global__ void __launch_bounds__(MG_THREADS)
 k_mg_prolong(const int *__restrict__ agg, const double *__restrict__ xc, double *__restrict__ x,
              long long n4, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     for (long long e = (long long)blockIdx.x * MG_THREADS + threadIdx.x; e < n4;
          e += (long long)gridDim.x * MG_THREADS) {
@@ -152,6 +160,8 @@ k_mg_prolong(const int *__restrict__ agg, const double *__restrict__ xc, double 
 // x += z
 __global__ void __launch_bounds__(MG_THREADS)
 k_mg_axpy(double *__restrict__ x, const double *__restrict__ z, long long n2, Skip skip) {
+    pdl_wait();
+    pdl_trigger();
     if (skip_all(skip)) return;
     double2 *x2 = reinterpret_cast<double2 *>(x);
     const double2 *z2 = reinterpret_cast<const double2 *>(z);
@@ -320,7 +330,7 @@ static int grid_of(long long threads) { return (int)((threads + MG_THREADS - 1) 
 static abilu_status galerkin_values(abilu_mg mg, int l, cudaStream_t st) {
     MgLevel &F = mg->L[l], &Cl = mg->L[l + 1];
     if (Cl.nnzb == 0) return ABILU_OK;
-    k_galerkin<<<counted(grid_of(4 * Cl.nnzb)), MG_THREADS, 0, st>>>(Cl.nnzb, F.gptr, F.gidx, F.A, Cl.Ac);
+    launch_pdl(k_galerkin, grid_of(4 * Cl.nnzb), MG_THREADS, 0, st, Cl.nnzb, F.gptr, F.gidx, F.A, Cl.Ac);
     ABILU_LAUNCH_CHECK("k_galerkin");
     return ABILU_OK;
 }
@@ -347,13 +357,13 @@ static abilu_status smooth(abilu_mg mg, int l, int steps, const double *b, doubl
             *xzero = false;
             continue;
         }
-        k_mg_residual<<<counted(grid_of(4LL * L.n)), MG_THREADS, 0, st>>>(L.p->v, L.A, b, x, L.r, skip);
+        launch_pdl(k_mg_residual, grid_of(4LL * L.n), MG_THREADS, 0, st, L.p->v, L.A, b, x, L.r, skip);
         ABILU_LAUNCH_CHECK("k_mg_residual");
         s = apply_dispatch(L.f, L.r, nullptr, L.z, o.apply_sweeps_lower, o.apply_sweeps_upper, mode,
                            st, skip);
         if (s != ABILU_OK) return s;
         const long long n2 = 2LL * L.n;
-        k_mg_axpy<<<counted(grid_of(n2)), MG_THREADS, 0, st>>>(x, L.z, n2, skip);
+        launch_pdl(k_mg_axpy, grid_of(n2), MG_THREADS, 0, st, x, L.z, n2, skip);
         ABILU_LAUNCH_CHECK("k_mg_axpy");
     }
     return ABILU_OK;
@@ -376,19 +386,19 @@ static abilu_status vcycle(abilu_mg mg, int l, const double *b, double *x, cudaS
     if ((s = smooth(mg, l, o.pre_smooth, b, x, &xzero, st, skip)) != ABILU_OK) return s;
     const double *rf = b;   // the fine residual: b itself while x = 0
     if (!xzero) {
-        k_mg_residual<<<counted(grid_of(4LL * L.n)), MG_THREADS, 0, st>>>(L.p->v, L.A, b, x, L.r, skip);
+        launch_pdl(k_mg_residual, grid_of(4LL * L.n), MG_THREADS, 0, st, L.p->v, L.A, b, x, L.r, skip);
         ABILU_LAUNCH_CHECK("k_mg_residual");
         rf = L.r;
     }
-    k_mg_restrict<<<counted(grid_of(4LL * Cl.n)), MG_THREADS, 0, st>>>(rf, L.mptr, L.mem, Cl.n, Cl.b,
+    launch_pdl(k_mg_restrict, grid_of(4LL * Cl.n), MG_THREADS, 0, st, rf, L.mptr, L.mem, Cl.n, Cl.b,
                                                                         skip);
     ABILU_LAUNCH_CHECK("k_mg_restrict");
     if ((s = vcycle(mg, l + 1, Cl.b, Cl.x, st, skip)) != ABILU_OK) return s;
     const long long n4 = 4LL * L.n;
     if (xzero)
-        k_mg_prolong<true><<<counted(grid_of(n4)), MG_THREADS, 0, st>>>(L.agg, Cl.x, x, n4, skip);
+        launch_pdl(k_mg_prolong<true>, grid_of(n4), MG_THREADS, 0, st, L.agg, Cl.x, x, n4, skip);
     else
-        k_mg_prolong<false><<<counted(grid_of(n4)), MG_THREADS, 0, st>>>(L.agg, Cl.x, x, n4, skip);
+        launch_pdl(k_mg_prolong<false>, grid_of(n4), MG_THREADS, 0, st, L.agg, Cl.x, x, n4, skip);
     ABILU_LAUNCH_CHECK("k_mg_prolong");
     xzero = false;
     return smooth(mg, l, o.post_smooth, b, x, &xzero, st, skip);
