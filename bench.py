@@ -48,10 +48,10 @@ def _dist():
 # kernel code; set an entry to None when its kernel changes until it is
 # captured again)
 PROFILED_TRAFFIC = {
-    "spmv_f64": 295.446016e6 + 15.301120e6,          # k_spmv<1>
-    "build_sweeps_f32": 1.352304e9 + 509.246208e6,   # k_build_blocks_async<float, 0>, 6 sweeps
-    "lower_sweeps_f32": 133.483264e6 + 10.764032e6,  # k_tri_staged lower, 3 sweeps
-    "upper_sweeps_f32": 79.600128e6 + 3.838720e6,    # k_tri_staged upper (scaled), 3 sweeps
+    "spmv_f64": 295.448832e6 + 15.170560e6,          # k_spmv<1>
+    "build_sweeps_f32": 1.351867e9 + 509.248256e6,   # k_build_blocks_async<float, 0>, 6 sweeps
+    "lower_sweeps_f32": 133.699072e6 + 10.779392e6,  # k_tri_staged lower, 3 sweeps
+    "upper_sweeps_f32": 79.993856e6 + 4.602112e6,    # k_tri_staged upper (scaled), 3 sweeps
 }
 
 
