@@ -91,6 +91,8 @@ k_b_residual(PatternView P, const double *__restrict__ A, const double *__restri
              const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
              double *partials, BConf cf, int init, int *hs_done, int *hs_fin, int *sys_done,
              int *bflag) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
     const int chunk = blockIdx.x, s = chunk_sys[chunk];
     BState *St = S + s;
@@ -152,6 +154,8 @@ __global__ void k_b_flags_reset(int *bflag) {
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_scale(const double *vin, double *vout, float *v32, const BState *S,
           const int *__restrict__ chunk_sys) {
+    pdl_wait();
+    pdl_trigger();
     const int chunk = blockIdx.x;
     const BState *St = S + chunk_sys[chunk];
     if (St->done) return;
@@ -177,6 +181,8 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_b_dots(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w, BState *S,
          const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0, double *partials,
          int pass) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh_w[RED_WARPS * BTILE], sh_o[BTILE];
     const int chunk = blockIdx.x, s = chunk_sys[chunk];
     BState *St = S + s;
@@ -215,6 +221,8 @@ k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ 
            const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
            double *partials, BConf cf, int pass, int final_pass, int *hs_done, int *sys_done,
            int *bflag) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double sh_h[BMAXM + 1];
     __shared__ double sh_w[RED_WARPS], sh_o[1];
     const int chunk = blockIdx.x, s = chunk_sys[chunk];
@@ -289,6 +297,8 @@ __global__ void k_b_ysolve(BState *S, int nsys) {
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_xupdate(const double *__restrict__ Z, size_t nv, double *__restrict__ x, const BState *S,
             const int *__restrict__ chunk_sys) {
+    pdl_wait();
+    pdl_trigger();
     const int chunk = blockIdx.x;
     const BState *St = S + chunk_sys[chunk];
     const int kd = St->kdim;
@@ -534,19 +544,19 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
                                     (abilu_mode)opts->mode, st, skip);
     if (s != ABILU_OK) return s;
     if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
-    k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
+    launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
                                                    b->partials, 0);
-    k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
+    launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
                                                      b->partials, cf, 0, !opts->reorth, b->hs_done,
                                                      b->sys_done, b->bflag);
     if (opts->reorth) {
-        k_b_dots<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
+        launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
                                                        b->sys_chunk0, b->partials, 1);
-        k_b_update<<<counted(nck), RED_THREADS, 0, st>>>(V, nv, j, w, b->S, b->chunk_sys,
+        launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
                                                          b->sys_chunk0, b->partials, cf, 1, 1,
                                                          b->hs_done, b->sys_done, b->bflag);
     }
-    k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(w, V + (size_t)(j + 1) * nv, v32, b->S,
+    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
                                                     b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch step");
     return ABILU_OK;
@@ -560,12 +570,12 @@ static abilu_status enqueue_restart(abilu_batch b, const BConf &cf, cudaStream_t
     double *V = b->krylov, *Z = V + (size_t)(m + 1) * nv;
     float *v32 = reinterpret_cast<float *>(b->fac->r32);
     k_b_ysolve<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
-    k_b_xupdate<<<counted(nck), RED_THREADS, 0, st>>>(Z, nv, b->x, b->S, b->chunk_sys);
+    launch_pdl(k_b_xupdate, nck, RED_THREADS, 0, st, Z, nv, b->x, b->S, b->chunk_sys);
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
-    k_b_residual<<<counted(nck), RED_THREADS, 0, st>>>(P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
+    launch_pdl(k_b_residual, nck, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
                                                        b->sys_chunk0, b->partials, cf, 0, b->hs_done,
                                                        b->hs_fin, b->sys_done, b->bflag);
-    k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(V, V, v32, b->S, b->chunk_sys);
+    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch restart");
     return ABILU_OK;
 }
@@ -675,10 +685,10 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
     ABILU_CUDA(cudaMemsetAsync(b->S, 0, sizeof(BState) * nsys, st));
     k_b_init<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
-    k_b_residual<<<counted(nck), RED_THREADS, 0, st>>>(P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
+    launch_pdl(k_b_residual, nck, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
                                                        b->sys_chunk0, b->partials, cf, 1, b->hs_done,
                                                        b->hs_fin, b->sys_done, b->bflag);
-    k_b_scale<<<counted(nck), RED_THREADS, 0, st>>>(V, V, v32, b->S, b->chunk_sys);
+    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch init");
     // the cycle graph: captured once per (restart, sweeps, mode, reorth, factor
     // buffer), replayed for every cycle of every later solve
