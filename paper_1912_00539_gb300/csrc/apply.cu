@@ -506,7 +506,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
                 const int ctas_l = lower_async_ctas<T, VT>();
                 const int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
                 launch_pdl(k_lower_async<T, VT>, g, APPLY_THREADS, 0, st, P, L, rv, y[0], nl - 1, D,
-                                                                           x1, yh, z1, tk, skip);
+                    x1, yh, z1, tk, skip);
             }
             ABILU_LAUNCH_CHECK("lower async");
         }
@@ -537,7 +537,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
     if (nl == 1) {      // no lower sweep runs: x^1 = Dinv r
         VT *x1 = nu >= 2 ? (SC ? y[0] : x[1]) : nullptr;
         launch_pdl(k_diag_apply<T, VT>, grid, APPLY_THREADS, 0, st, P, D, rv, x1,
-                                                                     nu == 1 ? z : nullptr, skip);
+            nu == 1 ? z : nullptr, skip);
         ABILU_LAUNCH_CHECK("k_diag_apply");
         yfin = SC ? y[0] : rv;
         xfirst = x1;

@@ -545,19 +545,19 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
     if (s != ABILU_OK) return s;
     if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
     launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
-                                                   b->partials, 0);
+        b->partials, 0);
     launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
-                                                     b->partials, cf, 0, !opts->reorth, b->hs_done,
-                                                     b->sys_done, b->bflag);
+        b->partials, cf, 0, !opts->reorth, b->hs_done,
+        b->sys_done, b->bflag);
     if (opts->reorth) {
         launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-                                                       b->sys_chunk0, b->partials, 1);
+            b->sys_chunk0, b->partials, 1);
         launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-                                                         b->sys_chunk0, b->partials, cf, 1, 1,
-                                                         b->hs_done, b->sys_done, b->bflag);
+            b->sys_chunk0, b->partials, cf, 1, 1,
+            b->hs_done, b->sys_done, b->bflag);
     }
     launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
-                                                    b->chunk_sys);
+        b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch step");
     return ABILU_OK;
 }
@@ -573,8 +573,8 @@ static abilu_status enqueue_restart(abilu_batch b, const BConf &cf, cudaStream_t
     launch_pdl(k_b_xupdate, nck, RED_THREADS, 0, st, Z, nv, b->x, b->S, b->chunk_sys);
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
     launch_pdl(k_b_residual, nck, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
-                                                       b->sys_chunk0, b->partials, cf, 0, b->hs_done,
-                                                       b->hs_fin, b->sys_done, b->bflag);
+        b->sys_chunk0, b->partials, cf, 0, b->hs_done,
+        b->hs_fin, b->sys_done, b->bflag);
     launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch restart");
     return ABILU_OK;
@@ -686,8 +686,8 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
     k_b_init<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
     launch_pdl(k_b_residual, nck, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
-                                                       b->sys_chunk0, b->partials, cf, 1, b->hs_done,
-                                                       b->hs_fin, b->sys_done, b->bflag);
+        b->sys_chunk0, b->partials, cf, 1, b->hs_done,
+        b->hs_fin, b->sys_done, b->bflag);
     launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch init");
     // the cycle graph: captured once per (restart, sweeps, mode, reorth, factor

@@ -694,7 +694,7 @@ static abilu_status sweeps_t(abilu_factors f, const AT *Asrc, int nsweeps, abilu
         ABILU_CUDA(cudaMemsetAsync(f->ctr + 1, 0, sizeof(unsigned long long), st));
         const int c = f->cur;
         launch_pdl(k_build_async<T, AT>, ctas, BUILD_THREADS, 0, st, P, Asrc, L[c], U[c], D[c], Ud,
-                   nsweeps, f->ctr, f->ctr + 1);
+            nsweeps, f->ctr, f->ctr + 1);
         ABILU_LAUNCH_CHECK("k_build_async");
     }
     return ABILU_OK;

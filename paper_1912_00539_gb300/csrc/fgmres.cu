@@ -437,7 +437,7 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
     if (opts->zero_guess) ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
     launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1,
-                                                      opts->zero_guess ? 1 : 0);
+        opts->zero_guess ? 1 : 0);
     launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS);
     ABILU_LAUNCH_CHECK("fgmres init");
     cudaEvent_t ev[2];

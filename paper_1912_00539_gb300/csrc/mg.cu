@@ -391,7 +391,7 @@ static abilu_status vcycle(abilu_mg mg, int l, const double *b, double *x, cudaS
         rf = L.r;
     }
     launch_pdl(k_mg_restrict, grid_of(4LL * Cl.n), MG_THREADS, 0, st, rf, L.mptr, L.mem, Cl.n, Cl.b,
-                                                                        skip);
+        skip);
     ABILU_LAUNCH_CHECK("k_mg_restrict");
     if ((s = vcycle(mg, l + 1, Cl.b, Cl.x, st, skip)) != ABILU_OK) return s;
     const long long n4 = 4LL * L.n;
