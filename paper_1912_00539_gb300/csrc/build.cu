@@ -88,9 +88,12 @@ __device__ __forceinline__ bool inv4_adj(const double *a, double *r) {
 // (det == 0 or non-finite: replaced by the identity, modified iteration,
 // Sec. 4.2).  `sh` is this quad's scratch of QUAD_SCRATCH floats (U, X0, R);
 // the stride of 52 floats puts the 8 quads of a warp on distinct banks.
+// refine = false returns X0 (the intermediate sweeps of a synchronous build:
+// their inverses only feed the next sweep; its last sweep refines the Dinv
+// that the application uses).
 constexpr int QUAD_SCRATCH = 52;
 __device__ __forceinline__ bool quad_inv4_refined(const float u_row[4], float x_row[4],
-                                                  float *sh) {
+                                                  float *sh, bool refine = true) {
     const int q = threadIdx.x & 3;
     const unsigned m = quad_mask();
     float *shU = sh, *shX = sh + 16, *shR = sh + 32;
@@ -127,6 +130,11 @@ __device__ __forceinline__ bool quad_inv4_refined(const float u_row[4], float x_
     const float id = 1.0f / det;
 #pragma unroll
     for (int c = 0; c < 4; c++) x0[c] *= id;
+    if (!refine) {   // the FP32 adjugate alone (relative error about cond(U) u)
+#pragma unroll
+        for (int c = 0; c < 4; c++) x_row[c] = x0[c];
+        return false;
+    }
     reinterpret_cast<float4 *>(shX)[q] = make_float4(x0[0], x0[1], x0[2], x0[3]);
     __syncwarp(m);
     float X[16];
@@ -368,9 +376,10 @@ __device__ __forceinline__ void build_block(const PatternView &P, int w,
         st_row_sel<VOL>(Lout + (size_t)dst * BB + q * BS, o);
     } else if (kind == WORK_U) {
         st_row_sel<VOL>(Uout + (size_t)dst * BB + q * BS, s);
-    } else {  // U_ii = S, Dinv_i = inv(U_ii)
+    } else {  // U_ii = S, Dinv_i = inv(U_ii), refined in the last sweep of a synchronous
+              // build (Udiag passed) and in every asynchronous update
         float x[4];
-        if (quad_inv4_refined(s, x, sh_q) && q == 0) atomicAdd(nsing, 1ull);
+        if (quad_inv4_refined(s, x, sh_q, VOL || Udiag != nullptr) && q == 0) atomicAdd(nsing, 1ull);
         st_row_sel<VOL>(Dout + (size_t)dst * BB + q * BS, x);
         if (Udiag) st_row_sel<false>(Udiag + (size_t)dst * BB + q * BS, s);
     }
