@@ -50,6 +50,8 @@ using namespace abilu;
 
 static void factors_free(abilu_factors f) {
     if (!f) return;
+    for (void *e : f->ev)
+        if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
     if (f->krylov) cudaFree(f->krylov);
     if (f->mem) cudaFree(f->mem);
     if (f->host_status) cudaFreeHost(f->host_status);

@@ -106,6 +106,7 @@ struct abilu_factors_s {
     double *scal;              // small device scalars (Hessenberg, Givens, ...)
     double *partials;          // per-CTA reduction partials
     void *host_status;         // pinned host mirror of the solve status
+    void *ev[2];               // FGMRES look-ahead events (cudaEvent_t), made on first use
     void *mem;
 };
 

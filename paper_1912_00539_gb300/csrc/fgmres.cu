@@ -41,6 +41,7 @@ constexpr int TILE = 6;   // Krylov vectors per pass of the dot kernel (64 regis
 struct HostStatus {       // pinned, host-mapped mirror
     int done, iters, converged, kdim, restarts, breakdown;
     double est, beta, bnorm;
+    unsigned long long nsing, ntimeout;   // factor handles' counters at the end of a solve
 };
 
 struct SolveState {       // device
@@ -357,6 +358,17 @@ k_xupdate(const double *__restrict__ Z, long long nv2, double *__restrict__ x, S
     }
 }
 
+// the singular-block and timed-out-wait counters of one factors handle into
+// the host-mapped status (first: assign, else add), so the host reads them
+// with the status after its final stream synchronisation
+__global__ void k_counters(const unsigned long long *ctr, HostStatus *hs, int first) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    volatile HostStatus *vh = hs;
+    vh->nsing = (first ? 0ull : vh->nsing) + ctr[0];
+    vh->ntimeout = (first ? 0ull : vh->ntimeout) + ctr[4];
+    __threadfence_system();
+}
+
 __global__ void k_solve_init(SolveState *S, HostStatus *hs, double rtol, int max_iters, int m) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     S->rtol = rtol;
@@ -391,6 +403,7 @@ static HostStatus read_status(const HostStatus *p) {
     h.done = v->done; h.iters = v->iters; h.converged = v->converged; h.kdim = v->kdim;
     h.restarts = v->restarts; h.breakdown = v->breakdown;
     h.est = v->est; h.beta = v->beta; h.bnorm = v->bnorm;
+    h.nsing = v->nsing; h.ntimeout = v->ntimeout;
     return h;
 }
 size_t solve_state_bytes() { return sizeof(SolveState); }
@@ -440,9 +453,11 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
         opts->zero_guess ? 1 : 0);
     launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS);
     ABILU_LAUNCH_CHECK("fgmres init");
-    cudaEvent_t ev[2];
-    ABILU_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    ABILU_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    // the look-ahead events live in the workspace handle (made on first use)
+    for (int k = 0; k < 2; k++)
+        if (!ws->ev[k]) ABILU_CUDA(cudaEventCreateWithFlags(reinterpret_cast<cudaEvent_t *>(&ws->ev[k]),
+                                                            cudaEventDisableTiming));
+    cudaEvent_t ev[2] = {static_cast<cudaEvent_t>(ws->ev[0]), static_cast<cudaEvent_t>(ws->ev[1])};
     // No wait for the initial residual: the first cycle is enqueued at once,
     // and its kernels return at once if the initial guess already converged
     // (the device flag is set).  The host reads the status one step behind.
@@ -481,24 +496,17 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
     }
     if (ret == ABILU_OK && h.bnorm == 0.0)  // b = 0: the solution is x = 0
         ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
+    for (int k = 0; k < ncnt; k++)
+        k_counters<<<counted(1), 32, 0, st>>>(cnt[k]->ctr, hs, k == 0);
     cudaStreamSynchronize(st);
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
     h = read_status(hs);
     res->iters = h.iters;
     res->restarts = h.restarts;
     res->rel_resid_est = h.est;
     res->rel_resid_true = h.bnorm > 0.0 ? h.beta / h.bnorm : 0.0;
-    unsigned long long ns = 0, nto = 0;
-    for (int k = 0; k < ncnt; k++) {
-        unsigned long long cv[5] = {0, 0, 0, 0, 0};
-        cudaMemcpy(cv, cnt[k]->ctr, sizeof cv, cudaMemcpyDeviceToHost);
-        ns += cv[0];
-        if (cv[4]) {
-            nto += cv[4];
-            cudaMemset(cnt[k]->ctr + 4, 0, sizeof(unsigned long long));
-        }
-    }
+    const unsigned long long ns = h.nsing, nto = h.ntimeout;
+    if (nto)   // reset the timed-out-wait words (never expected)
+        for (int k = 0; k < ncnt; k++) cudaMemset(cnt[k]->ctr + 4, 0, sizeof(unsigned long long));
     res->singular_blocks = (int64_t)ns;
     if (nto && ret == ABILU_OK)  // a staged sweep's bounded wait ran out: results invalid
         ret = fail(ABILU_ETIMEOUT, "fgmres_solve: %llu pipeline waits timed out", nto);
