@@ -21,6 +21,7 @@ value = solves of all ranks / max wall time over ranks.  Other workloads:
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -80,19 +81,26 @@ def _peaks():
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
-    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    Q = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
+        self.t0 = self.t1 = None
+
+    def begin(self):
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        self.t1 = datetime.datetime.now()
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -107,24 +115,33 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 7:
+            if len(f) < 8:
                 continue
             try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(f[1]), float(f[2]),
+                             {nm for nm, v in zip(names, f[4:8]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[3:7]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        # the samples taken inside [begin, end]; a region shorter than the
+        # sampling interval keeps the sample nearest to its middle
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 <= r[0] <= self.t1]
+        if not inside:
+            mid = self.t0 + (self.t1 - self.t0) / 2 if self.t0 and self.t1 else rows[0][0]
+            inside = [min(rows, key=lambda r: abs((r[0] - mid).total_seconds()))]
+        reasons = set().union(*(r[3] for r in inside))
+        out = {"sm_mhz": statistics.median(r[1] for r in inside),
+               "sm_max_mhz": max(r[2] for r in inside), "reasons": sorted(reasons),
+               "samples": len(inside), "samples_total": len(rows)}
+        if self.t0 and self.t1:
+            out["region_s"] = round((self.t1 - self.t0).total_seconds(), 3)
+        return out
 
 
 def _system():
@@ -817,6 +834,10 @@ def run_gpu(args):
                                apply_sweeps_upper=APPLY_SWEEPS, mode=args.mode,
                                raise_on_noconv=True, zero_guess=True)
 
+    # the build inside each timed solve records CUDA events around its sweep
+    # kernels on the solve's stream: the dominant kernel's duration is read
+    # from the timed region itself
+    fac.timing(True)
     for _ in range(args.warmup):
         res = solve()
 
@@ -829,16 +850,20 @@ def run_gpu(args):
     evs = _events(torch, args.steps + 1)
     barrier()
     clocks.start()
+    clocks.begin()
     l0 = ab.kernel_launches()
     evs[0].record(stream)
-    iters = []
+    iters, sweep_ms = [], []
     for k in range(args.steps):
         res = solve()
+        sweep_ms.append(fac.sweep_ms())
         iters.append(res.iters)
         evs[k + 1].record(stream)
     barrier()
+    clocks.end()
     launches = ab.kernel_launches() - l0
     clk = clocks.stop()
+    fac.timing(False)
     step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = max_over_ranks(torch, evs[0].elapsed_time(evs[-1]), dev)
     value = job_rate(args.steps, world, total_ms)
@@ -911,10 +936,21 @@ def run_gpu(args):
     share = {k: kern[k]["us"] * per_solve[k] for k in kern}
     dom = max(share, key=share.get)
     dk = kern[dom]
-    roof = {"bound": "hbm", "kernel": dom, "achieved": round(dk["GBs"], 1), "peak": peak,
-            "unit": "GB/s", "frac": round(dk["frac"], 4),
+    # the build sweeps' duration from the timed solves themselves (events
+    # around the sweep kernels of each solve's build); other kernels: isolated
+    timing = "isolated"
+    dom_us = dk["us"]
+    if dom.startswith("build_sweep"):
+        per_build = 1 if args.mode == "async" else BUILD_SWEEPS   # launches per build
+        dom_us = statistics.mean(sweep_ms) * 1e3 / per_build
+        timing = "timed region"
+    dom_gbs = dk["bytes"] / (dom_us * 1e-6) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(dom_gbs, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(dom_gbs / peak, 4),
             "traffic": PROFILED_TRAFFIC.get(dom), "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": dk["bytes"], "sweeps_per_launch": dk["sweeps"]}
+            "algorithmic_bytes_per_launch": dk["bytes"], "sweeps_per_launch": dk["sweeps"],
+            "us_per_launch": round(dom_us, 2), "timing": timing,
+            "us_per_launch_isolated": round(dk["us"], 2)}
     kernels = {k: {"us_per_call": round(v["us"], 2), "GBs": round(v["GBs"], 1),
                    "frac_of_measured_peak": round(v["frac"], 4),
                    "us_per_solve": round(share[k], 1)} for k, v in kern.items()}
@@ -978,7 +1014,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f64"])

@@ -230,6 +230,20 @@ abilu_status abilu_factors_diagnostics(abilu_factors f, const double *A_vals, do
  * (the results of that application are then invalid; never expected). */
 abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_blocks, abilu_stream stream);
 
+/* Instrumentation of the build sweeps (Eq. bilu; the paper times its sweeps
+ * the same way, Sec. 6).  With `enable` nonzero, every later build of block
+ * factors on this handle (abilu_build, or the build inside fgmres_solve)
+ * records two CUDA events on its stream, right before its first and right
+ * after its last sweep kernel (the preparation pass over A and the scaled
+ * upper blocks are outside them); `enable` 0 stops it.  The events are the
+ * handle's, created by the first enabling call (ABILU_ECUDA if that fails).
+ * abilu_factors_sweep_time waits for the second event of the last timed build
+ * and returns the device time between the two in *ms (host, milliseconds);
+ * ABILU_EINVAL if no build was timed since timing was enabled (scalar factors
+ * are never timed). */
+abilu_status abilu_factors_timing(abilu_factors f, int enable);
+abilu_status abilu_factors_sweep_time(abilu_factors f, float *ms);
+
 typedef struct {
     int32_t restart;            /* m of FGMRES(m); 1..64 */
     int32_t max_iters;          /* total Arnoldi steps over all restarts */

@@ -32,7 +32,7 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_pattern_counts", "abilu_factors_create", "abilu_factors_destroy",
            "abilu_factors_create_scalar", "abilu_build",
            "abilu_apply", "bsr_spmv", "abilu_factors_export", "abilu_factors_status",
-           "abilu_factors_diagnostics",
+           "abilu_factors_timing", "abilu_factors_sweep_time", "abilu_factors_diagnostics",
            "fgmres_default_opts", "fgmres_solve", "abilu_apply_noalloc", "abilu_batch_create",
            "abilu_batch_destroy", "abilu_batch_counts", "abilu_batch_set_system",
            "abilu_batch_solve", "abilu_batch_get_solution", "abilu_order",
@@ -97,6 +97,10 @@ _lib.abilu_gather_blocks.argtypes = [_i64, _vp, _vp, _vp, _vp]
 _lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
+_lib.abilu_factors_timing.argtypes = [_vp, C.c_int]
+_lib.abilu_factors_timing.restype = C.c_int
+_lib.abilu_factors_sweep_time.argtypes = [_vp, C.POINTER(C.c_float)]
+_lib.abilu_factors_sweep_time.restype = C.c_int
 _lib.abilu_factors_diagnostics.argtypes = [_vp, _vp, C.POINTER(_f64), _vp]
 _lib.abilu_factors_diagnostics.restype = C.c_int
 _lib.fgmres_default_opts.argtypes = [C.POINTER(FgmresOpts)]
@@ -270,6 +274,17 @@ class Factors:
                                               out, _stream(stream)))
         return dict(zip(("ilu_residual_l1", "lu_defect_max", "jacobi_norm_L", "jacobi_norm_U"),
                         list(out)))
+
+    def timing(self, enable: bool = True):
+        """Record CUDA events around the sweep kernels of every later build
+        (abilu_factors_timing); sweep_ms() reads the last one."""
+        _check(_lib.abilu_factors_timing(self.handle, int(bool(enable))))
+
+    def sweep_ms(self) -> float:
+        """Device time of the last timed build's sweep kernels, in ms."""
+        v = C.c_float()
+        _check(_lib.abilu_factors_sweep_time(self.handle, C.byref(v)))
+        return v.value
 
     def singular_blocks(self, stream=None) -> int:
         v = C.c_int64()

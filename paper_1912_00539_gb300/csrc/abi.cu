@@ -52,6 +52,8 @@ static void factors_free(abilu_factors f) {
     if (!f) return;
     for (void *e : f->ev)
         if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
+    for (void *e : f->tev)
+        if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
     if (f->krylov) cudaFree(f->krylov);
     if (f->mem) cudaFree(f->mem);
     if (f->host_status) cudaFreeHost(f->host_status);
@@ -140,6 +142,26 @@ extern "C" abilu_status abilu_build(abilu_factors f, const double *A, int nsweep
     if (init != ABILU_INIT_FROM_A && init != ABILU_INIT_FROM_PREVIOUS)
         return fail(ABILU_EINVAL, "build: bad init");
     return build_dispatch(f, A, nsweeps, mode, init, S(stream));
+}
+
+extern "C" abilu_status abilu_factors_timing(abilu_factors f, int enable) {
+    if (!f) return fail(ABILU_EINVAL, "factors_timing: NULL factors");
+    if (enable) {
+        for (int k = 0; k < 2; k++)
+            if (!f->tev[k]) ABILU_CUDA(cudaEventCreate(reinterpret_cast<cudaEvent_t *>(&f->tev[k])));
+    }
+    f->timing = enable != 0;
+    f->timed = 0;
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_factors_sweep_time(abilu_factors f, float *ms) {
+    if (!f || !ms) return fail(ABILU_EINVAL, "factors_sweep_time: NULL argument");
+    if (!f->timed) return fail(ABILU_EINVAL, "factors_sweep_time: no timed build since timing was enabled");
+    cudaEvent_t e0 = static_cast<cudaEvent_t>(f->tev[0]), e1 = static_cast<cudaEvent_t>(f->tev[1]);
+    ABILU_CUDA(cudaEventSynchronize(e1));
+    ABILU_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return ABILU_OK;
 }
 
 extern "C" abilu_status abilu_apply(abilu_factors f, const double *r, double *z, int nl, int nu,

@@ -107,6 +107,9 @@ struct abilu_factors_s {
     double *partials;          // per-CTA reduction partials
     void *host_status;         // pinned host mirror of the solve status
     void *ev[2];               // FGMRES look-ahead events (cudaEvent_t), made on first use
+    void *tev[2];              // build timing events (cudaEvent_t), made by abilu_factors_timing
+    int timing;                // nonzero: builds record tev[0], tev[1] around their sweep kernels
+    int timed;                 // a build recorded tev since timing was enabled
     void *mem;
 };
 

@@ -555,6 +555,38 @@ def test_zero_guess_equals_explicit_zero_start(ab):
     assert torch.equal(x0, x1)
 
 
+@pytest.mark.parametrize("dtype,mode", [("f64", "sync"), ("f64", "async"), ("f32", "sync"),
+                                        ("f32", "async"), ("bf16", "sync")])
+def test_build_timing_events(ab, dtype, mode):
+    """Build timing (abilu_factors_timing / abilu_factors_sweep_time): no time
+    before a timed build or after timing is switched off; a timed build, alone
+    or inside fgmres_solve, gives a positive device time; a synchronous build
+    with timing on gives bit for bit the factors of one without."""
+    import torch
+    d = Dev(ab, gen.small_system(37, 11, seed=2))
+    f1, f2 = ab.Factors(d.pat, dtype), ab.Factors(d.pat, dtype)
+    with pytest.raises(ab.AbiluError):
+        f1.sweep_ms()
+    f1.timing(True)
+    with pytest.raises(ab.AbiluError):
+        f1.sweep_ms()
+    f1.build(d.A, 3, mode)
+    f2.build(d.A, 3, mode)
+    assert f1.sweep_ms() > 0.0
+    if mode == "sync":
+        X1, D1 = f1.export()
+        X2, D2 = f2.export()
+        assert torch.equal(X1, X2) and torch.equal(D1, D2)
+    f1.timing(True)   # re-enabling forgets the last time
+    with pytest.raises(ab.AbiluError):
+        f1.sweep_ms()
+    res = ab.fgmres_solve(d.pat, d.A, f1, d.b, d.vec(), build_sweeps=2, mode=mode)
+    assert res.converged and f1.sweep_ms() > 0.0
+    f1.timing(False)
+    with pytest.raises(ab.AbiluError):
+        f1.sweep_ms()
+
+
 @pytest.mark.parametrize("dtype,nsweeps", [("f64", 0), ("f64", 3), ("f32", 3)])
 def test_diagnostics_match_oracle(ab, dsys, dtype, nsweeps):
     """GPU diagnostics (Sec. 6.2 quantities) equal the oracle's evaluated on the
