@@ -50,7 +50,7 @@ def _dist():
 # captured again)
 PROFILED_TRAFFIC = {
     "spmv_f64": 295.448832e6 + 15.170560e6,          # k_spmv<1>
-    "build_sweeps_f32": 1.351867e9 + 509.248256e6,   # k_build_blocks_async<float, 0>, 6 sweeps
+    "build_sweeps_f32": 1.351872e9 + 509.619456e6,   # k_build_blocks_async<float, 0>, 6 sweeps
     "lower_sweeps_f32": 133.699072e6 + 10.779392e6,  # k_tri_staged lower, 3 sweeps
     "upper_sweeps_f32": 79.993856e6 + 4.602112e6,    # k_tri_staged upper (scaled), 3 sweeps
 }
