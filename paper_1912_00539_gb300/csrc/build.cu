@@ -711,10 +711,12 @@ static abilu_status sweeps_t(abilu_factors f, const AT *Asrc, int nsweeps, abilu
 
 // With timing enabled on the handle, a build records tev[0] before its sweep
 // kernels and tev[1] after them on its stream (abilu_factors_sweep_time).
-static void timing_mark(abilu_factors f, int k, cudaStream_t st) {
-    if (!f->timing) return;
-    cudaEventRecord(static_cast<cudaEvent_t>(f->tev[k]), st);
+static abilu_status timing_mark(abilu_factors f, int k, cudaStream_t st) {
+    if (!f->timing) return ABILU_OK;
+    if (k == 0) f->timed = 0;   // a build that fails between the marks leaves no time
+    ABILU_CUDA(cudaEventRecord(static_cast<cudaEvent_t>(f->tev[k]), st));
     if (k == 1) f->timed = 1;
+    return ABILU_OK;
 }
 
 template <typename T>
@@ -734,10 +736,10 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
     ABILU_LAUNCH_CHECK("k_build_prepare");
     if constexpr (narrow) {
         if (nsweeps > 0) {
-            timing_mark(f, 0, st);
-            abilu_status s = block_sweeps_t<T>(f, A32, nsweeps, mode, st);
+            abilu_status s = timing_mark(f, 0, st);
+            if (s == ABILU_OK) s = block_sweeps_t<T>(f, A32, nsweeps, mode, st);
+            if (s == ABILU_OK) s = timing_mark(f, 1, st);
             if (s != ABILU_OK) return s;
-            timing_mark(f, 1, st);
         }
         const int cf = f->cur;
         if (f->Us && P.nu > 0) {
@@ -749,9 +751,9 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
         return ABILU_OK;
     } else {
         if (nsweeps == 0) return ABILU_OK;
-        timing_mark(f, 0, st);
-        abilu_status s = sweeps_t<T, double>(f, A, nsweeps, mode, st);
-        if (s == ABILU_OK) timing_mark(f, 1, st);
+        abilu_status s = timing_mark(f, 0, st);
+        if (s == ABILU_OK) s = sweeps_t<T, double>(f, A, nsweeps, mode, st);
+        if (s == ABILU_OK) s = timing_mark(f, 1, st);
         return s;
     }
 }
