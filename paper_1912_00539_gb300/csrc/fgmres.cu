@@ -488,18 +488,25 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
         launch_pdl(k_xupdate, nred, RED_THREADS, 0, st, Z, nv2, x, SS);
         launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 0, 0);
         launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS);
+        // the handles' counters into the status with every cycle's result, so
+        // the synchronisation that ends the last cycle also ends the solve
+        for (int k = 0; k < ncnt; k++)
+            k_counters<<<counted(1), 32, 0, st>>>(cnt[k]->ctr, hs, k == 0);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres restart"); break; }
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres sync"); break; }
         h = read_status(hs);
     }
-    if (ret == ABILU_OK && h.bnorm == 0.0)  // b = 0: the solution is x = 0
+    const bool zero_b = ret == ABILU_OK && h.bnorm == 0.0;
+    if (zero_b)  // b = 0: the solution is x = 0
         ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
-    for (int k = 0; k < ncnt; k++)
-        k_counters<<<counted(1), 32, 0, st>>>(cnt[k]->ctr, hs, k == 0);
-    cudaStreamSynchronize(st);
-    h = read_status(hs);
+    if (ret != ABILU_OK || zero_b) {   // a cycle that did not finish, or the memset
+        for (int k = 0; k < ncnt; k++)
+            k_counters<<<counted(1), 32, 0, st>>>(cnt[k]->ctr, hs, k == 0);
+        cudaStreamSynchronize(st);
+        h = read_status(hs);
+    }
     res->iters = h.iters;
     res->restarts = h.restarts;
     res->rel_resid_est = h.est;
