@@ -245,22 +245,23 @@ k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ 
     reduce_sys<1, PSTRIDE>(partials, c0, c1, BMAXM + 1, 1, sh_w, sh_o);
     if (threadIdx.x != 0) return;
     const double hn = sqrt(sh_o[0]);
-    double col[BMAXM + 1];
-    for (int i = 0; i <= j; i++) col[i] = St->h[i] + (pass == 1 ? St->h2[i] : 0.0);
-    col[j + 1] = hn;
+    // the previous rotations, i = 0 .. j-1, each mixing entries i and i+1 of
+    // the new column: entry i+1 is still the Gram-Schmidt coefficient when
+    // rotation i reaches it, so one carried value replaces a column array
+    // (which lived in local memory)
+    double a = St->h[0] + (pass == 1 ? St->h2[0] : 0.0);
     for (int i = 0; i < j; i++) {
-        const double a = col[i], c = col[i + 1];
-        col[i] = St->cs[i] * a + St->sn[i] * c;
-        col[i + 1] = -St->sn[i] * a + St->cs[i] * c;
+        const double c = St->h[i + 1] + (pass == 1 ? St->h2[i + 1] : 0.0);
+        St->H[i * BMAXM + j] = St->cs[i] * a + St->sn[i] * c;
+        a = -St->sn[i] * a + St->cs[i] * c;
     }
-    const double a = col[j], c = col[j + 1];
+    const double c = hn;
     const double d = sqrt(a * a + c * c);
     double cs = 1.0, sn = 0.0;
     if (d != 0.0) { cs = a / d; sn = c / d; }
     St->cs[j] = cs;
     St->sn[j] = sn;
-    col[j] = cs * a + sn * c;
-    for (int i = 0; i <= j; i++) St->H[i * BMAXM + j] = col[i];
+    St->H[j * BMAXM + j] = cs * a + sn * c;
     const double gj = St->g[j];
     St->g[j + 1] = -sn * gj;
     St->g[j] = cs * gj;

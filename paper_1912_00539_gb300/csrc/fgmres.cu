@@ -83,19 +83,29 @@ __device__ __forceinline__ bool last_cta(SolveState *S) {
 
 // In the last CTA: out[k] = sum over CTAs c of partials[c*stride + k0 + k],
 // k < kn <= TILE.  Thread t adds the partials of CTAs t, t+256, ... in that
-// order (independent loads, one latency round), then a fixed-order block
-// reduction: deterministic for a fixed grid.  Every thread of the CTA calls it.
+// order (the loads of R of them issued before their adds), then a fixed-order
+// block reduction: deterministic for a fixed grid.  Every thread of the CTA
+// calls it.
 template <int K>
 __device__ __forceinline__ void reduce_partials(const double *partials, int stride, int k0,
                                                 int kn, double *sh_w, double *out) {
+    constexpr int R = K <= 2 ? 4 : 1;   // CTAs whose partials are loaded before any add
     double v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = 0.0;
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x) {
-        const double *p = partials + (size_t)c * stride + k0;
+    for (int c0 = threadIdx.x; c0 < (int)gridDim.x; c0 += R * blockDim.x) {
+        double t[R][K];
 #pragma unroll
-        for (int k = 0; k < K; k++)
-            if (k < kn) v[k] += __ldcg(p + k);
+        for (int r = 0; r < R; r++) {
+            const int c = c0 + r * blockDim.x;
+            const double *p = partials + (size_t)c * stride + k0;
+#pragma unroll
+            for (int k = 0; k < K; k++) t[r][k] = (c < (int)gridDim.x && k < kn) ? __ldcg(p + k) : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int k = 0; k < K; k++) v[k] += t[r][k];
     }
     block_sum<K>(v, sh_w, out, kn);
 }
@@ -211,7 +221,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
             acc[k] = fma(v.y, wv.y, fma(v.x, wv.x, acc[k]));
         }
     }
-    block_sum<K>(acc, sh_w, sh_o, K);
+    block_sum<K, false>(acc, sh_w, sh_o, K);   // k_dots is held to 64 registers
     if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
 }
 
@@ -298,22 +308,23 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
     reduce_partials<1>(partials, MAXM + 2, MAXM + 1, 1, sh_w, sh_o);
     if (threadIdx.x != 0) return;
     const double hn = sqrt(sh_o[0]);
-    double col[MAXM + 1];
-    for (int i = 0; i <= j; i++) col[i] = S->h[i] + (pass == 1 ? S->h2[i] : 0.0);
-    col[j + 1] = hn;
-    for (int i = 0; i < j; i++) {  // previous rotations
-        const double a = col[i], c = col[i + 1];
-        col[i] = S->cs[i] * a + S->sn[i] * c;
-        col[i + 1] = -S->sn[i] * a + S->cs[i] * c;
+    // the previous rotations, i = 0 .. j-1, each mixing entries i and i+1 of
+    // the new column: entry i+1 is still the Gram-Schmidt coefficient when
+    // rotation i reaches it, so one carried value replaces a column array
+    // (which lived in local memory)
+    double a = S->h[0] + (pass == 1 ? S->h2[0] : 0.0);
+    for (int i = 0; i < j; i++) {
+        const double c = S->h[i + 1] + (pass == 1 ? S->h2[i + 1] : 0.0);
+        S->H[i * MAXM + j] = S->cs[i] * a + S->sn[i] * c;
+        a = -S->sn[i] * a + S->cs[i] * c;
     }
-    const double a = col[j], c = col[j + 1];
+    const double c = hn;
     const double d = sqrt(a * a + c * c);
     double cs = 1.0, sn = 0.0;
     if (d != 0.0) { cs = a / d; sn = c / d; }
     S->cs[j] = cs;
     S->sn[j] = sn;
-    col[j] = cs * a + sn * c;
-    for (int i = 0; i <= j; i++) S->H[i * MAXM + j] = col[i];
+    S->H[j * MAXM + j] = cs * a + sn * c;
     const double gj = S->g[j];
     S->g[j + 1] = -sn * gj;
     S->g[j] = cs * gj;
