@@ -174,12 +174,23 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
     const double2 *a = reinterpret_cast<const double2 *>(vin);
     double2 *o = reinterpret_cast<double2 *>(vout);
     float2 *o32 = reinterpret_cast<float2 *>(v32);
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2;
-         e += (long long)gridDim.x * blockDim.x) {
-        double2 t = a[e];
-        t = make_double2(t.x * s, t.y * s);
-        o[e] = t;
-        if (v32) o32[e] = make_float2(to_f32_int(t.x), to_f32_int(t.y));
+    // four grid strides per iteration: four loads in flight per thread before
+    // any store (a streaming kernel with a few elements per thread is bound by
+    // the loads it keeps in flight)
+    constexpr int U = 4;
+    const long long st = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nv2; e += U * st) {
+        double2 t[U];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (e + u * st < nv2) t[u] = a[e + u * st];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (e + u * st >= nv2) break;
+            const double2 r = make_double2(t[u].x * s, t[u].y * s);
+            o[e + u * st] = r;
+            if (v32) o32[e + u * st] = make_float2(to_f32_int(r.x), to_f32_int(r.y));
+        }
     }
 }
 
