@@ -196,7 +196,7 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
 
 // Partial dot products of K consecutive basis vectors with w for this CTA.
 // K is a compile-time width so no predicated-off FP64 FMA is issued.
-template <int K>
+template <int K, bool PIPE>
 __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long long nv2,
                                           int k0, const double2 *__restrict__ w2,
                                           double *sh_w, double *sh_o, double *partials) {
@@ -205,10 +205,37 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
     for (int k = 0; k < K; k++) acc[k] = 0.0;
     const long long st = (long long)gridDim.x * blockDim.x;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    // narrow tiles: two grid strides per iteration, twice the loads in flight
-    // with the same accumulation order (e, e + st, e + 2 st, ...); wide tiles
-    // already have K + 1 loads in flight (and the registers to match)
-    if constexpr (K <= 4) {
+    // PIPE (the kernels of one or two basis vectors): software-pipelined, the
+    // next element's loads issued before this element's FMAs, so the FP64 work
+    // overlaps the memory latency instead of following it (both take
+    // microseconds here); the accumulation order (e, e + st, e + 2 st, ...) is
+    // the plain loop's, so the result is the same bit for bit
+    if constexpr (PIPE) {
+        if (e < nv2) {
+            double2 wn = w2[e], vn[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) vn[k] = V2[(size_t)(k0 + k) * nv2 + e];
+            for (;;) {
+                const double2 wc = wn;
+                double2 vc[K];
+#pragma unroll
+                for (int k = 0; k < K; k++) vc[k] = vn[k];
+                const long long en = e + st;
+                if (en < nv2) {
+                    wn = w2[en];
+#pragma unroll
+                    for (int k = 0; k < K; k++) vn[k] = V2[(size_t)(k0 + k) * nv2 + en];
+                }
+#pragma unroll
+                for (int k = 0; k < K; k++) acc[k] = fma(vc[k].y, wc.y, fma(vc[k].x, wc.x, acc[k]));
+                e = en;
+                if (e >= nv2) break;
+            }
+        }
+    } else if constexpr (K <= 4) {
+        // two grid strides per iteration, twice the loads in flight, same
+        // accumulation order (the general kernel has no registers left to
+        // pipeline)
         for (; e + st < nv2; e += 2 * st) {
             const double2 wa = w2[e], wb = w2[e + st];
             double2 va[K], vb[K];
@@ -224,7 +251,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
             }
         }
     }
-    for (; e < nv2; e += st) {
+    for (; e < nv2; e += st) {   // wide tiles (K + 1 loads in flight already) and tails
         const double2 wv = w2[e];
 #pragma unroll
         for (int k = 0; k < K; k++) {
@@ -238,35 +265,54 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
 
 // h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2).  The grid is
 // 4 CTAs per SM and all of them must be resident at once (one wave), so the
-// kernel is held to 64 registers.
+// kernel is held to 64 registers.  NW = 0: any jp1, in tiles of up to TILE
+// vectors; NW = 1 or 2: jp1 == NW, one software-pipelined tile (its own
+// kernel, so the general one keeps its register allocation).
+template <int NW>
 __global__ void __launch_bounds__(RED_THREADS, 4)
 k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
        SolveState *S, double *partials, int pass) {
     pdl_wait();
     pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
-    __shared__ double sh_w[RED_WARPS * TILE], sh_o[TILE];
+    constexpr int T = NW > 0 ? NW : TILE;
+    __shared__ double sh_w[RED_WARPS * T], sh_o[T];
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const double2 *V2 = reinterpret_cast<const double2 *>(V);
-    for (int k0 = 0; k0 < jp1; k0 += TILE) {
-        switch (jp1 - k0 < TILE ? jp1 - k0 : TILE) {
-        case 1: dots_tile<1>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        case 2: dots_tile<2>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        case 3: dots_tile<3>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        case 4: dots_tile<4>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        case 5: dots_tile<5>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-        default: dots_tile<6>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+    if constexpr (NW > 0) {
+        dots_tile<NW, true>(V2, nv2, 0, w2, sh_w, sh_o, partials);
+    } else {
+        for (int k0 = 0; k0 < jp1; k0 += TILE) {
+            switch (jp1 - k0 < TILE ? jp1 - k0 : TILE) {
+            case 1: dots_tile<1, false>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 2: dots_tile<2, false>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 3: dots_tile<3, false>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 4: dots_tile<4, false>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 5: dots_tile<5, false>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            default: dots_tile<6, false>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            }
         }
     }
     if (!last_cta(S)) return;
     double *h = pass == 0 ? S->h : S->h2;
-    for (int k0 = 0; k0 < jp1; k0 += TILE) {
-        const int kn = jp1 - k0 < TILE ? jp1 - k0 : TILE;
-        reduce_partials<TILE>(partials, MAXM + 2, k0, kn, sh_w, sh_o);
+    for (int k0 = 0; k0 < jp1; k0 += T) {
+        const int kn = jp1 - k0 < T ? jp1 - k0 : T;
+        reduce_partials<T>(partials, MAXM + 2, k0, kn, sh_w, sh_o);
         if (threadIdx.x < kn) h[k0 + threadIdx.x] = sh_o[threadIdx.x];
         __syncthreads();
     }
     if (threadIdx.x == 0) S->counter = 0;
+}
+
+// k_dots for jp1 basis vectors (the pipelined kernels for one or two)
+static void launch_dots(int nred, cudaStream_t st, const double *V, long long nv2, int jp1,
+                        const double *w, SolveState *S, double *partials, int pass) {
+    if (jp1 == 1)
+        launch_pdl(k_dots<1>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
+    else if (jp1 == 2)
+        launch_pdl(k_dots<2>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
+    else
+        launch_pdl(k_dots<0>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
 }
 
 // w -= sum_k h[k] V_k; on the final pass also ||w||^2, and the last CTA
@@ -491,10 +537,10 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
-            launch_pdl(k_dots, nred, RED_THREADS, 0, st, V, nv2, j + 1, w, SS, ws->partials, 0);
+            launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
             launch_pdl(k_update, nred, RED_THREADS, 0, st, V, nv2, j, w, SS, ws->partials, 0, !opts->reorth);
             if (opts->reorth) {
-                launch_pdl(k_dots, nred, RED_THREADS, 0, st, V, nv2, j + 1, w, SS, ws->partials, 1);
+                launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 1);
                 launch_pdl(k_update, nred, RED_THREADS, 0, st, V, nv2, j, w, SS, ws->partials, 1, 1);
             }
             launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
