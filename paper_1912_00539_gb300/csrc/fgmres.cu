@@ -205,7 +205,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
     for (int k = 0; k < K; k++) acc[k] = 0.0;
     const long long st = (long long)gridDim.x * blockDim.x;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    // PIPE (the kernels of one or two basis vectors): software-pipelined, the
+    // PIPE (the kernels of one to four basis vectors): software-pipelined, the
     // next element's loads issued before this element's FMAs, so the FP64 work
     // overlaps the memory latency instead of following it (both take
     // microseconds here); the accumulation order (e, e + st, e + 2 st, ...) is
@@ -266,8 +266,9 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
 // h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2).  The grid is
 // 4 CTAs per SM and all of them must be resident at once (one wave), so the
 // kernel is held to 64 registers.  NW = 0: any jp1, in tiles of up to TILE
-// vectors; NW = 1 or 2: jp1 == NW, one software-pipelined tile (its own
-// kernel, so the general one keeps its register allocation).
+// vectors; NW = 1 .. 4: jp1 == NW, one software-pipelined tile (its own
+// kernel, so the general one keeps its register allocation; five vectors
+// would spill).
 template <int NW>
 __global__ void __launch_bounds__(RED_THREADS, 4)
 k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
@@ -304,20 +305,67 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
     if (threadIdx.x == 0) S->counter = 0;
 }
 
-// k_dots for jp1 basis vectors (the pipelined kernels for one or two)
+// k_dots for jp1 basis vectors (the pipelined kernels for one to four)
 static void launch_dots(int nred, cudaStream_t st, const double *V, long long nv2, int jp1,
                         const double *w, SolveState *S, double *partials, int pass) {
     if (jp1 == 1)
         launch_pdl(k_dots<1>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
     else if (jp1 == 2)
         launch_pdl(k_dots<2>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
+    else if (jp1 == 3)
+        launch_pdl(k_dots<3>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
+    else if (jp1 == 4)
+        launch_pdl(k_dots<4>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
     else
         launch_pdl(k_dots<0>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
 }
 
+// w_e -= sum_k h[k] V_k,e for this thread's elements e (grid stride), J = j + 1
+// basis vectors, software-pipelined: the next element's loads are issued
+// before this element's FMAs, so the FP64 work overlaps the memory latency.
+// Same operations in the same order as the plain loop (bit for bit).
+template <int J>
+__device__ __forceinline__ void update_pipelined(const double2 *__restrict__ V2, long long nv2,
+                                                 double2 *__restrict__ w2, const double *sh_h,
+                                                 double &nrm) {
+    const long long st = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nv2) return;
+    double h[J];
+#pragma unroll
+    for (int k = 0; k < J; k++) h[k] = sh_h[k];
+    double2 wn = w2[e], vn[J];
+#pragma unroll
+    for (int k = 0; k < J; k++) vn[k] = V2[(size_t)k * nv2 + e];
+    for (;;) {
+        double2 t = wn, vc[J];
+#pragma unroll
+        for (int k = 0; k < J; k++) vc[k] = vn[k];
+        const long long en = e + st;
+        if (en < nv2) {
+            wn = w2[en];
+#pragma unroll
+            for (int k = 0; k < J; k++) vn[k] = V2[(size_t)k * nv2 + en];
+        }
+#pragma unroll
+        for (int k = 0; k < J; k++) {
+            t.x -= h[k] * vc[k].x;
+            t.y -= h[k] * vc[k].y;
+        }
+        w2[e] = t;
+        nrm = fma(t.y, t.y, fma(t.x, t.x, nrm));
+        e = en;
+        if (e >= nv2) break;
+    }
+}
+
 // w -= sum_k h[k] V_k; on the final pass also ||w||^2, and the last CTA
-// performs the Givens update of column j and the convergence test.
-__global__ void __launch_bounds__(RED_THREADS)
+// performs the Givens update of column j and the convergence test.  J = 0:
+// any j; J = 1 .. 3: j + 1 == J, the pipelined loop (its own kernel; four
+// vectors would spill).  Held to 64 registers so that all 4 CTAs per SM
+// stay resident.
+template <int J>
+__global__ void __launch_bounds__(RED_THREADS, 4)
 k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict__ w,
          SolveState *S, double *partials, int pass, int final_pass) {
     pdl_wait();
@@ -334,6 +382,10 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
     double nrm[1] = {0.0};
     const long long st = (long long)gridDim.x * blockDim.x;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (J > 0) {
+        update_pipelined<J>(V2, nv2, w2, sh_h, nrm[0]);
+        e = nv2;   // every element done
+    }
     for (; e + st < nv2; e += 2 * st) {  // two grid strides per iteration
         double2 ta = w2[e], tb = w2[e + st];
         for (int k = 0; k < jp1; k++) {
@@ -394,6 +446,22 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
     S->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
     S->counter = 0;
     publish(S);
+}
+
+// k_update for step j (the pipelined kernels for one to three basis vectors)
+template <int J>
+static void launch_update_j(int nred, cudaStream_t st, const double *V, long long nv2, int j,
+                            double *w, SolveState *S, double *partials, int pass, int fin) {
+    launch_pdl(k_update<J>, nred, RED_THREADS, 0, st, V, nv2, j, w, S, partials, pass, fin);
+}
+static void launch_update(int nred, cudaStream_t st, const double *V, long long nv2, int j,
+                          double *w, SolveState *S, double *partials, int pass, int fin) {
+    switch (j + 1) {
+    case 1: launch_update_j<1>(nred, st, V, nv2, j, w, S, partials, pass, fin); break;
+    case 2: launch_update_j<2>(nred, st, V, nv2, j, w, S, partials, pass, fin); break;
+    case 3: launch_update_j<3>(nred, st, V, nv2, j, w, S, partials, pass, fin); break;
+    default: launch_update_j<0>(nred, st, V, nv2, j, w, S, partials, pass, fin); break;
+    }
 }
 
 // y = R^{-1} g (every CTA, redundantly, in shared memory), then x += Z y
@@ -538,10 +606,10 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             if (s != ABILU_OK) { ret = s; break; }
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
             launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
-            launch_pdl(k_update, nred, RED_THREADS, 0, st, V, nv2, j, w, SS, ws->partials, 0, !opts->reorth);
+            launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, !opts->reorth);
             if (opts->reorth) {
                 launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 1);
-                launch_pdl(k_update, nred, RED_THREADS, 0, st, V, nv2, j, w, SS, ws->partials, 1, 1);
+                launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 1, 1);
             }
             launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
             cudaError_t e = cudaGetLastError();
