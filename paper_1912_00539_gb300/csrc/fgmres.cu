@@ -209,7 +209,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
     // next element's loads issued before this element's FMAs, so the FP64 work
     // overlaps the memory latency instead of following it (both take
     // microseconds here); the accumulation order (e, e + st, e + 2 st, ...) is
-    // the plain loop's, so the result is the same bit for bit
+    // the plain loop's, so each thread's sums are the same bit for bit
     if constexpr (PIPE) {
         if (e < nv2) {
             double2 wn = w2[e], vn[K];
