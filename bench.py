@@ -216,7 +216,8 @@ def kernel_rooflines(torch, ab, pat, A, fac, s, peak, mode="async"):
     """Average duration of the hot kernels, each isolated as the difference of
     two public calls timed with CUDA events on the launching stream
     (back-to-back calls after warm-up), and achieved GB/s from the algorithmic
-    bytes of one launch (formulas in the design doc).  FP32 factors."""
+    bytes of one launch (the per-kernel formulas are written out below).  FP32
+    factors."""
     N, nnzb = s.n, s.nnzb
     E = (nnzb - N) // 2
     f, v = 4, 4   # FP32 factors, FP32 apply vectors

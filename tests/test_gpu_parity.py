@@ -7,7 +7,7 @@ Tolerances (max-norm error relative to the max-norm of the oracle's result):
 * SpMV: 1e-14 (16 products per block row entry, FMA rounding only).
 * FP32 arithmetic on factors that the test exports from the GPU: 2e-6
   (unit roundoff 6e-8 times the ~10-term sums and 4x4 products of a sweep
-  chain; see DESIGN.md).
+  chain).
 * FP32 / BF16 factor storage against the FP64 oracle build: 1e-4 / 4e-2
   (storage unit roundoff 6e-8 / 3.9e-3 amplified by the sweeps).
 Integer results (pattern counts, pair lists) are exact.
