@@ -612,6 +612,7 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
     abilu_status ret = ABILU_OK;
     for (bool first = true; first || (!h.converged && h.iters < opts->max_iters); first = false) {
         int j = 0;
+        double e_prev = -1.0;   // the estimate after step j-2, as the host last read it
         for (; j < m; j++) {
             s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
@@ -628,7 +629,18 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             cudaEventRecord(ev[j & 1], st);
             if (j >= 1) {  // look at step j-1 while step j runs
                 cudaEventSynchronize(ev[(j - 1) & 1]);
-                if (reinterpret_cast<volatile HostStatus *>(hs)->done) { j++; break; }
+                const volatile HostStatus *vh = reinterpret_cast<volatile HostStatus *>(hs);
+                if (vh->done) { j++; break; }
+                // when the estimates after steps j-2 and j-1, extrapolated
+                // geometrically, put step j at the tolerance, wait for step j
+                // before enqueuing step j+1: a step past the end of the cycle
+                // would be launched only to return at once
+                const double e1 = vh->est;
+                if (e_prev > 0.0 && e1 < e_prev && e1 * (e1 / e_prev) <= opts->rtol) {
+                    cudaEventSynchronize(ev[j & 1]);
+                    if (vh->done) { j++; break; }
+                }
+                e_prev = e1;
             }
         }
         if (ret != ABILU_OK) break;
