@@ -16,6 +16,10 @@
 // overlaps on the GPU (different streams, or different host threads) race on
 // it and produce wrong results; serialise them on one stream.  Nothing in the
 // array has to start at zero: each call writes every scratch entry it reads.
+//
+// The pattern is trusted as far as abilu_pattern_create would accept it; the
+// sweep only skips a column outside [0, n), so a malformed column index reads
+// nothing out of bounds (the result of such a row is then meaningless).
 #include <mutex>
 
 #include "common.cuh"
@@ -46,7 +50,7 @@ k_noalloc_sweep(int n, const int32_t *__restrict__ rowptr, const int32_t *__rest
         const int p1 = rowptr[i + 1];
         for (int p = rowptr[i]; p < p1; p++) {
             const int j = colind[p];
-            if (upper ? j <= i : j >= i) continue;
+            if (j < 0 || j >= n || (upper ? j <= i : j >= i)) continue;
             double a[4], v[4];
             ld_row(X + (size_t)p * BB + q * BS, a);
             ld_row(in + (size_t)j * BS, v);
@@ -63,7 +67,10 @@ k_noalloc_sweep(int n, const int32_t *__restrict__ rowptr, const int32_t *__rest
 }
 
 // Device address of the scratch array, looked up once per device with that
-// device current (the array's host-side name is only a stand-in).
+// device current (the array's host-side name is only a stand-in).  The cache
+// is never invalidated: after cudaDeviceReset the device's context, and with
+// it this address, is gone, so the entry point must not be used on that
+// device again in this process.
 static double *scratch_for_current_device(abilu_status *st) {
     static std::mutex mu;
     static double *addr[128] = {nullptr};
@@ -104,6 +111,13 @@ extern "C" abilu_status abilu_apply_noalloc(int32_t n, const int32_t *rowptr,
     if (!rowptr || !colind || !X || !Dinv || !r || !z)
         return fail(ABILU_EINVAL, "apply_noalloc: NULL argument");
     if (r == z) return fail(ABILU_EINVAL, "apply_noalloc: r and z must be distinct");
+    // the sweeps read X, Dinv and r with 16-byte vector loads: reject a view
+    // that starts off that boundary here, on the host, before any launch
+    auto al16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    if (!al16(X) || !al16(Dinv) || !al16(r) || !al16(z))
+        return fail(ABILU_EINVAL, "apply_noalloc: X, Dinv, r and z must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(rowptr) & 3u) || (reinterpret_cast<uintptr_t>(colind) & 3u))
+        return fail(ABILU_EINVAL, "apply_noalloc: rowptr and colind must be 4-byte aligned");
     if (nsweeps_lower < 0 || nsweeps_upper < 0)
         return fail(ABILU_EINVAL, "apply_noalloc: negative sweep count");
     abilu_status st;

@@ -45,6 +45,50 @@ def test_noalloc_apply_matches_apply(which):
             assert _rel(z.cpu().numpy(), z_ref.cpu().numpy()) < 1e-12, (nl, nu, call)
 
 
+def test_noalloc_matches_oracle():
+    """The same application as the oracle's synchronous FP64 apply on the same
+    exported factors (1e-12, the FP64 apply tolerance of the parity tests)."""
+    import torch
+    import oracle
+    import paper_1912_00539_gb300.abilu as ab
+    s = gen.random_pattern_system(150, 400, seed=4)
+    rowptr = torch.from_numpy(s.rowptr).cuda()
+    colind = torch.from_numpy(s.colind).cuda()
+    pat = ab.Pattern(rowptr, colind)
+    fac = ab.Factors(pat, "f64")
+    fac.build(torch.from_numpy(s.vals).cuda(), 2, mode="sync")
+    X, D = fac.export()
+    Xh, Dh = X.cpu().numpy(), D.cpu().numpy()
+    r = np.random.default_rng(9).standard_normal((s.n, 4))
+    for nl, nu in ((3, 3), (2, 5)):
+        z = torch.empty((s.n, 4), dtype=torch.float64, device="cuda")
+        ab.apply_noalloc(rowptr, colind, X, D, torch.from_numpy(r).cuda(), z, nl, nu)
+        z_or = oracle.apply(s.rowptr, s.colind, Xh, Dh, r, nl, nu)
+        assert _rel(z.cpu().numpy(), z_or) < 1e-12, (nl, nu)
+
+
+def test_noalloc_rejects_unaligned_views():
+    """A view 8 bytes off a 16-byte boundary is refused on the host with
+    ABILU_EINVAL (nothing is launched)."""
+    import torch
+    import paper_1912_00539_gb300.abilu as ab
+    s = gen.small_system(4, 3, seed=1)
+    n = s.n
+    rowptr = torch.from_numpy(s.rowptr).cuda()
+    colind = torch.from_numpy(s.colind).cuda()
+    X = torch.zeros((s.nnzb, 4, 4), dtype=torch.float64, device="cuda")
+    D = torch.zeros((n, 4, 4), dtype=torch.float64, device="cuda")
+    buf = torch.zeros(4 * n + 2, dtype=torch.float64, device="cuda")
+    r_off = buf[1:1 + 4 * n]          # 8-byte offset, contiguous
+    r = torch.zeros(4 * n, dtype=torch.float64, device="cuda")
+    z = torch.zeros(4 * n, dtype=torch.float64, device="cuda")
+    Xbuf = torch.zeros(16 * s.nnzb + 2, dtype=torch.float64, device="cuda")
+    for args in ((X, D, r_off, z), (X, D, r, buf[1:1 + 4 * n]), (Xbuf[1:1 + 16 * s.nnzb], D, r, z)):
+        with pytest.raises(ab.AbiluError) as e:
+            ab.apply_noalloc(rowptr, colind, *args, 2, 2)
+        assert e.value.status == ab.EINVAL and "aligned" in str(e.value)
+
+
 def test_noalloc_rejects_sizes_beyond_the_limit():
     import torch
     import paper_1912_00539_gb300.abilu as ab
