@@ -172,17 +172,26 @@ abilu_status abilu_apply(abilu_factors f, const double *r, double *z, int nsweep
  *
  * Computes the same z as abilu_apply(..., ABILU_SYNC) on FP64 factors:
  * nsweeps_lower Jacobi sweeps on L y = r from y = 0, then nsweeps_upper on
- * U z = y from z = 0.  rowptr/colind: the pattern (device, as for
- * abilu_pattern_create); X: double[nnzb][4][4] factors in A's pattern layout
- * (L_ij at column < row, U_ij at column > row, the diagonal entry ignored), as
- * abilu_factors_export writes them; Dinv: double[n][4][4] = inv(U_ii); r, z:
- * double[n][4], distinct.  All device pointers, 16-byte aligned, caller-owned.
+ * U z = y from z = 0.  rowptr/colind: the pattern (device int32[n+1],
+ * int32[nnzb], 4-byte aligned), which must be one that abilu_pattern_create
+ * accepts: nothing here validates it (a column outside [0, n) is skipped, so
+ * it reads nothing out of bounds, but the result is then meaningless);
+ * X: double[nnzb][4][4] factors in A's pattern layout (L_ij at column < row,
+ * U_ij at column > row, the diagonal entry ignored), as abilu_factors_export
+ * writes them; Dinv: double[n][4][4] = inv(U_ii); r, z: double[n][4],
+ * distinct.  All device pointers, caller-owned; X, Dinv, r and z must be
+ * 16-byte aligned (ABILU_EINVAL otherwise, checked before any device work).
  *
  * Limit: n <= 65,536 cells (the fixed scratch is 3 vectors of that size,
  * 6 MiB, held by every GPU that loads the library until the process exits);
  * larger n returns ABILU_EINVAL without touching the device.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
+ * with that device current).  With lazy module loading that first call is
+ * also where the library's module is loaded on the device and the 6 MiB array
+ * is reserved, so a caller that may not allocate at all should make one call
+ * during its set-up (any small valid call), and before any stream capture.
+ * The looked-up address is kept for the life of the process: after
+ * cudaDeviceReset on a device this entry point must not be used there again.
  * All calls share the one array: calls whose work overlaps on the GPU
  * (different streams or host threads) race on it; serialise them.  Asynchronous
  * on `stream`; returns ABILU_EINVAL for bad arguments.
@@ -230,6 +239,25 @@ abilu_status abilu_factors_diagnostics(abilu_factors f, const double *A_vals, do
  * (the results of that application are then invalid; never expected). */
 abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_blocks, abilu_stream stream);
 
+/* Spin limit of the bounded device-side waits of this handle's builds and
+ * applications called directly (abilu_build, abilu_apply): polls before a wait
+ * gives up and counts a timeout (read with abilu_factors_status).  0 restores
+ * the library default, 2^24.  fgmres_solve uses its options' spin_limit for
+ * its own duration and leaves the handle's value as it was.  limit >= 0. */
+abilu_status abilu_factors_set_spin_limit(abilu_factors f, int64_t limit);
+
+/* Failure injection for tests of the bounded waits (no counterpart in the
+ * paper).  With `enable` nonzero, the next asynchronous build of block factors
+ * on `f` that uses the ordered variant (the work list has fewer than four
+ * 32-block chunks per resident warp, i.e. every small system) starts its
+ * per-chunk sweep flags one sweep behind, a value no warp ever publishes: the
+ * first wait of every chunk polls `spin_limit` times, gives up, counts a
+ * timeout and the warp stops.  That build leaves the factors partly swept,
+ * and the call that reports its status (fgmres_solve, abilu_factors_status)
+ * returns ABILU_ETIMEOUT.  The flag is cleared by that build; no GPU fault,
+ * trap or hang is involved. */
+abilu_status abilu_factors_inject_stall(abilu_factors f, int enable);
+
 /* Instrumentation of the build sweeps (Eq. bilu; the paper times its sweeps
  * the same way, Sec. 6).  With `enable` nonzero, every later build of block
  * factors on this handle (abilu_build, or the build inside fgmres_solve)
@@ -256,6 +284,10 @@ typedef struct {
     int32_t init;               /* abilu_init for that build */
     int32_t reorth;             /* 0: one classical Gram-Schmidt pass; 1: two passes (CGS2) */
     int32_t zero_guess;         /* 1: start from x0 = 0 (x is overwritten; r0 = b, no SpMV) */
+    int64_t spin_limit;         /* polls of a bounded device-side wait before it gives up and
+                                   the solve returns ABILU_ETIMEOUT (the ordered asynchronous
+                                   build's per-chunk wait, the staged sweeps' barrier waits);
+                                   0: the library default, 2^24; >= 0 */
 } fgmres_opts;
 
 typedef struct {
@@ -269,7 +301,7 @@ typedef struct {
 
 /* Defaults: restart 30, max_iters 2500, rtol 1e-6, 1 build / 3+3 apply sweeps
  * (the paper's choice, Sec. 6.1), ABILU_ASYNC, build from A, reorth 0,
- * zero_guess 0 (x holds x0). */
+ * zero_guess 0 (x holds x0), spin_limit 0 (the library default). */
 void fgmres_default_opts(fgmres_opts *opts);
 
 /*

@@ -40,14 +40,15 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_to_f32", "abilu_mg_default_opts", "abilu_mg_create", "abilu_mg_destroy",
            "abilu_mg_setup", "abilu_mg_apply", "abilu_mg_levels", "abilu_mg_level_data",
            "fgmres_solve_mg", "abilu_parilut_default_opts", "abilu_parilut",
-           "abilu_pattern_arrays")
+           "abilu_pattern_arrays", "abilu_factors_inject_stall", "abilu_factors_set_spin_limit")
 
 
 class FgmresOpts(C.Structure):
     _fields_ = [("restart", C.c_int32), ("max_iters", C.c_int32), ("rtol", C.c_double),
                 ("build_sweeps", C.c_int32), ("apply_sweeps_lower", C.c_int32),
                 ("apply_sweeps_upper", C.c_int32), ("mode", C.c_int32), ("build", C.c_int32),
-                ("init", C.c_int32), ("reorth", C.c_int32), ("zero_guess", C.c_int32)]
+                ("init", C.c_int32), ("reorth", C.c_int32), ("zero_guess", C.c_int32),
+                ("spin_limit", C.c_int64)]
 
 
 class MgOpts(C.Structure):
@@ -97,6 +98,10 @@ _lib.abilu_gather_blocks.argtypes = [_i64, _vp, _vp, _vp, _vp]
 _lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
+_lib.abilu_factors_set_spin_limit.argtypes = [_vp, _i64]
+_lib.abilu_factors_set_spin_limit.restype = C.c_int
+_lib.abilu_factors_inject_stall.argtypes = [_vp, C.c_int]
+_lib.abilu_factors_inject_stall.restype = C.c_int
 _lib.abilu_factors_timing.argtypes = [_vp, C.c_int]
 _lib.abilu_factors_timing.restype = C.c_int
 _lib.abilu_factors_sweep_time.argtypes = [_vp, C.POINTER(C.c_float)]
@@ -286,6 +291,17 @@ class Factors:
         _check(_lib.abilu_factors_sweep_time(self.handle, C.byref(v)))
         return v.value
 
+    def set_spin_limit(self, limit: int = 0):
+        """Polls before a bounded device wait of this handle's direct builds
+        and applications gives up (0: the library default)."""
+        _check(_lib.abilu_factors_set_spin_limit(self.handle, int(limit)))
+
+    def inject_stall(self, enable: bool = True):
+        """Failure injection for tests of the bounded waits
+        (abilu_factors_inject_stall): the next ordered asynchronous build's
+        waits run out after the spin limit and report ABILU_ETIMEOUT."""
+        _check(_lib.abilu_factors_inject_stall(self.handle, int(bool(enable))))
+
     def singular_blocks(self, stream=None) -> int:
         v = C.c_int64()
         _check(_lib.abilu_factors_status(self.handle, C.byref(v), _stream(stream)))
@@ -416,11 +432,11 @@ def default_opts() -> FgmresOpts:
 def fgmres_solve(pattern: Pattern, A, factors: Factors, b, x, restart=30, max_iters=2500,
                  rtol=1e-6, build_sweeps=1, apply_sweeps_lower=3, apply_sweeps_upper=3,
                  mode="async", build=True, init="a", reorth=False, stream=None,
-                 raise_on_noconv=False, zero_guess=False) -> SolveResult:
+                 raise_on_noconv=False, zero_guess=False, spin_limit=0) -> SolveResult:
     import torch
     o = FgmresOpts(int(restart), int(max_iters), float(rtol), int(build_sweeps),
                    int(apply_sweeps_lower), int(apply_sweeps_upper), MODES[mode], int(bool(build)),
-                   INITS[init], int(bool(reorth)), int(bool(zero_guess)))
+                   INITS[init], int(bool(reorth)), int(bool(zero_guess)), int(spin_limit))
     r = FgmresResult()
     nv = 4 * pattern.n
     st = _lib.fgmres_solve(pattern.handle, _ptr(A, torch.float64, 16 * pattern.nnzb, "A"),

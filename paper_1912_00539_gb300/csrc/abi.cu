@@ -207,6 +207,19 @@ extern "C" abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_
     return ABILU_OK;
 }
 
+extern "C" abilu_status abilu_factors_set_spin_limit(abilu_factors f, int64_t limit) {
+    if (!f) return fail(ABILU_EINVAL, "factors_set_spin_limit: NULL handle");
+    if (limit < 0) return fail(ABILU_EINVAL, "factors_set_spin_limit: limit must be >= 0");
+    f->spin_limit = (unsigned long long)limit;
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_factors_inject_stall(abilu_factors f, int enable) {
+    if (!f) return fail(ABILU_EINVAL, "factors_inject_stall: NULL handle");
+    f->stall_flags = enable ? 1 : 0;
+    return ABILU_OK;
+}
+
 namespace abilu {
 __global__ void k_to_f32_int(const double *__restrict__ in, float *__restrict__ out, long long n) {
     const long long st = (long long)gridDim.x * blockDim.x;

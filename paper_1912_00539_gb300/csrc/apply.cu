@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 7)   // 7 x 288 threads per SM: 
 k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
              const float *__restrict__ rhs, const float *vin, float *v, int nsweeps, int sync_last,
              float *__restrict__ x1, float *__restrict__ yh, double *__restrict__ z,
-             unsigned long long *ticket, unsigned long long *err, Skip skip) {
+             unsigned long long *ticket, unsigned long long *err, Skip skip,
+             unsigned long long limit) {
     pdl_wait();
     pdl_trigger();
     if (skip_all(skip)) return;
@@ -308,16 +309,21 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
 
     if (warp == PIPE_CONSUMERS) {  // ---- producer (one lane)
         if (lane != 0) return;
+        // phases armed per stage; before this lane retires (normally or after
+        // a timed-out wait) it waits for the copies of the last ones, so the
+        // CTA keeps its shared memory until every copy it issued has landed
+        int armed[2] = {0, 0};
         for (int k = 0;; k++) {
             const int s = k & 1, u = k >> 1;
-            if (u >= 1 && !mbar_wait(&empty[s], (u - 1) & 1, err)) return;
+            if (u >= 1 && !mbar_wait(&empty[s], (u - 1) & 1, err, limit)) break;
             PipeStage<T> &S = st[s];
             const long long t = SYNC ? (long long)blockIdx.x + (long long)k * gridDim.x
                                      : (long long)atomicAdd(ticket, 1ull);
             if (t >= total) {
                 S.ticket = -1;
                 mbar_arrive(&full[s]);
-                return;
+                armed[s]++;
+                break;
             }
             const int c = (int)(t % nchunks);
             const int chunk = (UPPER && !SYNC) ? (int)(nchunks - 1 - c) : c;
@@ -336,6 +342,7 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
                 if (staged) bytes += (unsigned)(fe - fb) * BB * sizeof(T) + (unsigned)(ce - cb) * 4;
             }
             mbar_arrive_tx(&full[s], bytes);
+            armed[s]++;
             if (run) {
                 bulk_g2s(S.rowp, rowp + i0, PIPE_ROWP * 4, &full[s]);
                 bulk_g2s(S.rhs, rhs + (size_t)i0 * BS, (unsigned)(i1 - i0) * 16, &full[s]);
@@ -345,13 +352,15 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
                 }
             }
         }
+        mbar_drain(full, armed, 2, err, limit);
+        return;
     }
 
     // ---- consumers: a quad per row of the staged chunk
     const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
     for (int k = 0;; k++) {
         const int s = k & 1, u = k >> 1;
-        if (!mbar_wait(&full[s], u & 1, err)) return;
+        if (!mbar_wait(&full[s], u & 1, err, limit)) return;
         const PipeStage<T> &S = st[s];
         const long long t = S.ticket;
         if (t < 0) return;
@@ -496,12 +505,13 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             tk, skip);
         ABILU_LAUNCH_CHECK("k_async_start");
         unsigned long long *err = f->ctr + 4;
+        const unsigned long long lim = spin_limit_or_default(f->spin_limit);
         if (nl >= 2) {
             if constexpr (sizeof(VT) == 4) {  // staged pipeline (FP32/BF16 factors)
                 const int c = staged_ctas<false, false, false, T>();
                 const int g = (int)(c < nchunks ? c : nchunks);
                 launch_pdl(k_tri_staged<false, false, false, T>, g, PIPE_THREADS, 0, st,
-                    P, L, D, rv, nullptr, y[0], nl - 1, 0, x1, yh, z1, tk, err, skip);
+                    P, L, D, rv, nullptr, y[0], nl - 1, 0, x1, yh, z1, tk, err, skip, lim);
             } else {
                 const int ctas_l = lower_async_ctas<T, VT>();
                 const int g = (int)(ctas_l < nchunks ? ctas_l : nchunks);
@@ -516,7 +526,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
                 const int g = (int)(c < nchunks ? c : nchunks);
                 launch_pdl(k_tri_staged<true, SC, false, T>, g, PIPE_THREADS, 0, st,
                     P, UU, D, SC ? y[1] : y[0], nullptr, x[0], nu - 1, 0, nullptr, nullptr, z, tk + 1,
-                    err, skip);
+                    err, skip, lim);
             } else {
                 const int ctas_u = upper_async_ctas<T, VT>();
                 const int g = (int)(ctas_u < nchunks ? ctas_u : nchunks);
@@ -566,7 +576,7 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
             const int g = c < grid ? c : grid;
             launch_pdl(k_tri_staged<true, SC, true, T>, g, PIPE_THREADS, 0, st,
                 P, UU, D, yfin, xin, last ? nullptr : x[s & 1], 1, last ? 1 : 0, nullptr, nullptr,
-                last ? z : nullptr, nullptr, f->ctr + 4, skip);
+                last ? z : nullptr, nullptr, f->ctr + 4, skip, spin_limit_or_default(f->spin_limit));
         } else {
             launch_pdl(k_upper_sync<T, VT, SC>, grid, APPLY_THREADS, 0, st,
                 P, UU, D, yfin, xin, last ? nullptr : x[s & 1], last ? z : nullptr, skip);

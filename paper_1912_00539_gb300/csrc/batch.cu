@@ -368,7 +368,7 @@ struct abilu_batch_s {
     int *hs_done, *hs_fin;      // pinned, host-mapped
     int *sys_done, *bflag;      // device: per-system cycle exit; {all done, active count}
     cudaGraphExec_t graph;      // one restart cycle, captured on first use
-    int gkey[6];
+    int gkey[8];
     long long g_fixed, g_step;  // kernels per replay outside the steps; per step run
     cudaStream_t cap_stream;    // capture happens here: the caller's stream may be the
                                 // legacy default stream, which cannot be captured
@@ -658,10 +658,13 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
     const int m = opts->restart;
     if (m < 1 || m > BMAXM) return fail(ABILU_EINVAL, "batch_solve: restart must be in 1..%d", BMAXM);
     if (opts->max_iters < 0 || !(opts->rtol >= 0.0) || opts->apply_sweeps_lower < 0 ||
-        opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 ||
+        opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 || opts->spin_limit < 0 ||
         (opts->mode != ABILU_SYNC && opts->mode != ABILU_ASYNC))
         return fail(ABILU_EINVAL, "batch_solve: bad options");
     cudaStream_t st = S(stream);
+    // the solve's spin limit for its build and its sweeps (captured graphs
+    // keep it: it is part of the graph key)
+    b->fac->spin_limit = (unsigned long long)opts->spin_limit;
     const PatternView &P = b->pat->v;
     const size_t nv = (size_t)b->rows * BS;
     if (!b->krylov || b->krylov_m < m) {
@@ -693,8 +696,9 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
     ABILU_LAUNCH_CHECK("batch init");
     // the cycle graph: captured once per (restart, sweeps, mode, reorth, factor
     // buffer), replayed for every cycle of every later solve
-    const int key[6] = {m, opts->apply_sweeps_lower, opts->apply_sweeps_upper, opts->mode,
-                        opts->reorth, (int)b->fac->cur};
+    const int key[8] = {m, opts->apply_sweeps_lower, opts->apply_sweeps_upper, opts->mode,
+                        opts->reorth, (int)b->fac->cur, (int)(opts->spin_limit >> 32),
+                        (int)(opts->spin_limit & 0xffffffff)};
     if (b->graph && memcmp(key, b->gkey, sizeof key) != 0) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -728,15 +732,16 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
             cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
             for (int j = 0; j < m; j++) {
                 if ((ret = enqueue_step(b, opts, cf, j, st)) != ABILU_OK) break;
-                cudaEventRecord(ev[j & 1], st);
+                if ((e = cudaEventRecord(ev[j & 1], st)) != cudaSuccess) break;
                 if (j >= 1) {
-                    cudaEventSynchronize(ev[(j - 1) & 1]);
+                    if ((e = cudaEventSynchronize(ev[(j - 1) & 1])) != cudaSuccess) break;
                     if (all_set(b->hs_done, nsys)) break;
                 }
             }
             cudaEventDestroy(ev[0]);
             cudaEventDestroy(ev[1]);
             if (ret != ABILU_OK) break;
+            if (e != cudaSuccess) { ret = cuda_fail(e, "batch step wait"); break; }
             if ((ret = enqueue_restart(b, cf, st)) != ABILU_OK) break;
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -410,17 +410,19 @@ k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__res
 // the same chunk in consecutive sweeps are nchunks apart, so when chunks are
 // few against warps one warp could still be updating chunk c in sweep s while
 // another takes it in sweep s + 1, and the older update's Dinv could land
-// after the newer U_ii.  Then a warp first waits (bounded; a timeout is
-// counted in *err and the warp stops) until done[c] records s completed
-// sweeps, and publishes s + 1 after its writes.  A wait points only to a
-// smaller ticket, held by a resident warp, so every wait ends.
+// after the newer U_ii.  Then a warp first waits (at most `limit` polls; a
+// timeout is counted in *err and the warp stops) until done[c] records s
+// completed sweeps, and publishes s + 1 after its writes.  A wait points only
+// to a smaller ticket, held by a resident warp, so every wait ends.  No bulk
+// copy is in flight in this kernel, so a warp that gives up can simply return.
 constexpr int WARP_CHUNK = 32;
 
 template <typename T, bool ORDERED>
 __global__ void __launch_bounds__(BUILD_THREADS, 5)   // 48 registers: measured fastest (4, 6 slower)
 k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T *D, T *Udiag,
                      int nsweeps, int max_warps, unsigned long long *nsing,
-                     unsigned long long *ticket, unsigned long long *err, int *done) {
+                     unsigned long long *ticket, unsigned long long *err, int *done,
+                     unsigned long long limit) {
     pdl_wait();
     pdl_trigger();
     __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
@@ -441,9 +443,10 @@ k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T
         if constexpr (ORDERED) {  // wait for this chunk's previous sweep
             int ok = 1;
             if (lane == 0) {
-                unsigned it = 0;
-                while (*reinterpret_cast<volatile int *>(done + chunk) < sweep && ++it < PIPE_WAIT_LIMIT) {}
-                ok = it < PIPE_WAIT_LIMIT;
+                unsigned long long it = 0;
+                bool ready;
+                while (!(ready = *reinterpret_cast<volatile int *>(done + chunk) >= sweep) && ++it < limit) {}
+                ok = ready;
                 if (!ok) atomicAdd(err, 1ull);
                 __threadfence();
             }
@@ -657,15 +660,23 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
         int *done = nullptr;
         if ((long long)wchunks < 4LL * warps) {
             done = f->chunk_done;
-            ABILU_CUDA(cudaMemsetAsync(done, 0, sizeof(int) * (size_t)wchunks, st));
+            // failure injection (tests of the bounded wait): every flag at -1,
+            // one sweep behind, which no warp ever publishes, so the first
+            // wait of every chunk runs out after the spin limit
+            const int fill = f->stall_flags ? 0xff : 0;
+            f->stall_flags = 0;
+            ABILU_CUDA(cudaMemsetAsync(done, fill, sizeof(int) * (size_t)wchunks, st));
         }
         const int c = f->cur;
+        const unsigned long long lim = spin_limit_or_default(f->spin_limit);
         if (done)
             launch_pdl(k_build_blocks_async<T, true>, ctas, BUILD_THREADS, 0, st,
-                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done);
+                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done,
+                lim);
         else
             launch_pdl(k_build_blocks_async<T, false>, ctas, BUILD_THREADS, 0, st,
-                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done);
+                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done,
+                lim);
         ABILU_LAUNCH_CHECK("k_build_blocks_async");
     }
     return ABILU_OK;

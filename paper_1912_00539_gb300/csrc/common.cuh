@@ -110,6 +110,11 @@ struct abilu_factors_s {
     void *tev[2];              // build timing events (cudaEvent_t), made by abilu_factors_timing
     int timing;                // nonzero: builds record tev[0], tev[1] around their sweep kernels
     int timed;                 // a build recorded tev since timing was enabled
+    // polls of a bounded device-side wait before it gives up (0: the default,
+    // PIPE_WAIT_LIMIT); set for the duration of an FGMRES solve from its options
+    unsigned long long spin_limit;
+    int stall_flags;           // failure injection: the next ordered async build's chunk
+                               // flags start one sweep behind (abilu_factors_inject_stall)
     void *mem;
 };
 

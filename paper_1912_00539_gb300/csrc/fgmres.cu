@@ -541,6 +541,7 @@ extern "C" void fgmres_default_opts(fgmres_opts *o) {
     o->init = ABILU_INIT_FROM_A;
     o->reorth = 0;
     o->zero_guess = 0;
+    o->spin_limit = 0;
 }
 
 namespace abilu {
@@ -626,9 +627,13 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step"); break; }
-            cudaEventRecord(ev[j & 1], st);
+            e = cudaEventRecord(ev[j & 1], st);
+            if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres event record"); break; }
             if (j >= 1) {  // look at step j-1 while step j runs
-                cudaEventSynchronize(ev[(j - 1) & 1]);
+                // an asynchronous error shows here: stop enqueuing (the mapped
+                // status would be stale)
+                e = cudaEventSynchronize(ev[(j - 1) & 1]);
+                if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step wait"); break; }
                 const volatile HostStatus *vh = reinterpret_cast<volatile HostStatus *>(hs);
                 if (vh->done) { j++; break; }
                 // when the estimates after steps j-2 and j-1, extrapolated
@@ -637,7 +642,8 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
                 // would be launched only to return at once
                 const double e1 = vh->est;
                 if (e_prev > 0.0 && e1 < e_prev && e1 * (e1 / e_prev) <= opts->rtol) {
-                    cudaEventSynchronize(ev[j & 1]);
+                    e = cudaEventSynchronize(ev[j & 1]);
+                    if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step wait"); break; }
                     if (vh->done) { j++; break; }
                 }
                 e_prev = e1;
@@ -690,6 +696,7 @@ abilu_status fgmres_check_opts(const fgmres_opts *opts, const char *who) {
         return fail(ABILU_EINVAL, "%s: restart must be in 1..%d", who, MAXM);
     if (opts->max_iters < 0 || !(opts->rtol >= 0.0))
         return fail(ABILU_EINVAL, "%s: bad options", who);
+    if (opts->spin_limit < 0) return fail(ABILU_EINVAL, "%s: spin_limit must be >= 0", who);
     return ABILU_OK;
 }
 
@@ -710,11 +717,17 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
         return fail(ABILU_EINVAL, "fgmres_solve: bad options");
     cudaStream_t st = S(stream);
     const abilu_mode mode = (abilu_mode)opts->mode;
+    // the solve's spin limit on the handle for the solve's build and
+    // applications, the handle's own afterwards
+    const unsigned long long keep_limit = f->spin_limit;
+    f->spin_limit = (unsigned long long)opts->spin_limit;
     if (opts->build) {
         s = build_dispatch(f, A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
-        if (s != ABILU_OK) return s;
+        if (s != ABILU_OK) { f->spin_limit = keep_limit; return s; }
     }
     IluPc ctx{f, opts->apply_sweeps_lower, opts->apply_sweeps_upper, mode};
     const Precond pc{ilu_pc, &ctx, reinterpret_cast<float *>(f->r32)};  // v32: NULL for FP64 factors
-    return fgmres_run(p->v, A, f, pc, b, x, opts, res, st, &f, 1);
+    s = fgmres_run(p->v, A, f, pc, b, x, opts, res, st, &f, 1);
+    f->spin_limit = keep_limit;
+    return s;
 }

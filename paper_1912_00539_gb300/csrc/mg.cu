@@ -594,9 +594,17 @@ extern "C" abilu_status fgmres_solve_mg(abilu_mg mg, const double *A, const doub
     abilu_status s = fgmres_check_opts(opts, "fgmres_solve_mg");
     if (s != ABILU_OK) return s;
     cudaStream_t st = S(stream);
-    if (opts->build && (s = mg_setup(mg, A, st)) != ABILU_OK) return s;
     abilu_factors cnt[ABILU_MG_MAX_LEVELS];
-    for (int l = 0; l < mg->nlevels; l++) cnt[l] = mg->L[l].f;
-    const Precond pc{mg_pc, mg, nullptr};
-    return fgmres_run(mg->L[0].p->v, A, mg->L[0].f, pc, b, x, opts, res, st, cnt, mg->nlevels);
+    unsigned long long keep[ABILU_MG_MAX_LEVELS];
+    for (int l = 0; l < mg->nlevels; l++) {   // the solve's spin limit on every level
+        cnt[l] = mg->L[l].f;
+        keep[l] = cnt[l]->spin_limit;
+        cnt[l]->spin_limit = (unsigned long long)opts->spin_limit;
+    }
+    if (!opts->build || (s = mg_setup(mg, A, st)) == ABILU_OK) {
+        const Precond pc{mg_pc, mg, nullptr};
+        s = fgmres_run(mg->L[0].p->v, A, mg->L[0].f, pc, b, x, opts, res, st, cnt, mg->nlevels);
+    }
+    for (int l = 0; l < mg->nlevels; l++) cnt[l]->spin_limit = keep[l];
+    return s;
 }

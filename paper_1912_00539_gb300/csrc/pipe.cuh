@@ -4,15 +4,23 @@
 //
 // Rules kept by every caller: global source and shared destination 16-byte
 // aligned, sizes multiples of 16 bytes, at most 2^20 - 1 bytes per barrier
-// phase.  Every wait is bounded: after PIPE_WAIT_LIMIT polls it counts a
-// timeout in a device error word and returns false, and the caller leaves
-// its loop, so no kernel can hang on a barrier.
+// phase.  Every wait is bounded: after `limit` polls (the caller's spin
+// limit, PIPE_WAIT_LIMIT by default) it counts a timeout in a device error
+// word and returns false, and the caller leaves its loop, so no kernel can
+// hang on a barrier.  A CTA that gives up still waits, again bounded, for the
+// bulk copies it has issued before it retires (see mbar_drain), so no copy
+// lands in shared memory that the CTA no longer owns.
 #pragma once
 #include <stdint.h>
 
 namespace abilu {
 
-constexpr unsigned PIPE_WAIT_LIMIT = 1u << 24;
+constexpr unsigned long long PIPE_WAIT_LIMIT = 1ull << 24;
+
+// the spin limit a kernel uses: the caller's, or the default when 0
+__host__ __device__ __forceinline__ unsigned long long spin_limit_or_default(unsigned long long l) {
+    return l ? l : PIPE_WAIT_LIMIT;
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -55,13 +63,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
 }
 
 // wait for the phase with the given parity to complete; false = timed out
-// (counted in *err)
+// after `limit` polls (counted in *err)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
-                                          unsigned long long *err) {
-    for (unsigned it = 0; it < PIPE_WAIT_LIMIT; it++)
+                                          unsigned long long *err, unsigned long long limit) {
+    for (unsigned long long it = 0; it < limit; it++)
         if (mbar_try_wait(bar, parity)) return true;
     atomicAdd(err, 1ull);
     return false;
+}
+
+// Before a producer retires: wait for the last phase it armed on each of its
+// `nstages` full barriers (armed[s] = phases armed on stage s so far), i.e.
+// for every bulk copy it issued, since the phase before the last one was
+// already consumed when the last one was armed.  Bounded like mbar_wait.
+__device__ __forceinline__ void mbar_drain(uint64_t *full, const int *armed, int nstages,
+                                           unsigned long long *err, unsigned long long limit) {
+    for (int s = 0; s < nstages; s++)
+        if (armed[s] > 0) mbar_wait(&full[s], (unsigned)(armed[s] - 1) & 1u, err, limit);
 }
 
 // bulk copy of `bytes` from global memory into shared memory; completion is
