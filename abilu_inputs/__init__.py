@@ -146,8 +146,9 @@ def rcm_order(ptr, idx) -> np.ndarray:
 
     Start node: George-Liu pseudo-peripheral node found from the lowest unvisited
     cell of each connected component.  Cuthill-McKee visits the unvisited
-    neighbours of each node in queue order sorted by (degree, index); the result
-    is reversed.  Returns ``perm`` with perm[new] = old.
+    neighbours of each node in queue order sorted by (degree, index); each
+    component's order is reversed on its own, components in order of their
+    lowest cell.  Returns ``perm`` with perm[new] = old.
     """
     n = len(ptr) - 1
     deg = np.diff(ptr)
@@ -173,10 +174,9 @@ def rcm_order(ptr, idx) -> np.ndarray:
             visited[nxt] = True
             comp.append(nxt)
             frontier = nxt
-        out.append(np.concatenate(comp))
+        out.append(np.concatenate(comp)[::-1])
         done += len(out[-1])
-    cm = np.concatenate(out)
-    return cm[::-1].copy()
+    return np.ascontiguousarray(np.concatenate(out))
 
 
 def line_order(nx: int, ny: int) -> np.ndarray:

@@ -489,25 +489,38 @@ abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x, abilu
 
 /*
  * Orderings of the cell graph (Sec. 5), host code on host arrays.  `kind`:
- *   ABILU_ORDER_RCM       reverse Cuthill-McKee (pseudo-peripheral start,
- *                         neighbours by increasing degree), per component;
+ *   ABILU_ORDER_RCM       reverse Cuthill-McKee, per component (in order of
+ *                         the component's lowest cell, each reversed on its
+ *                         own): breadth-first from a pseudo-peripheral cell
+ *                         (from the lowest cell, the last level's cell of
+ *                         least degree, ties to the lowest index, while its
+ *                         level structure is deeper), each cell's new
+ *                         neighbours by increasing (degree, index); degrees
+ *                         are those of the whole graph;
  *   ABILU_ORDER_1WD       one-way dissection: level sets of a rooted level
- *                         structure every delta = sqrt((3 w + 13) / 2) levels
- *                         (w = mean level width) are separators, the blocks
- *                         between them are numbered first (each by RCM), the
- *                         separators last;
+ *                         structure every delta = max(2, round(sqrt((3 w +
+ *                         13) / 2))) levels (w = mean level width, levels
+ *                         below the last) are separators; the blocks between
+ *                         them, in the order of their first cell in
+ *                         breadth-first order, are numbered first (each by
+ *                         RCM from that cell), the separators of all
+ *                         components last; a component with fewer than
+ *                         2 delta + 1 levels is numbered by RCM;
  *   ABILU_ORDER_LINE      lines of strongly coupled cells (Sec. 5.1) made
  *                         contiguous, each at the position of its first cell;
  *   ABILU_ORDER_LINE_RCM, ABILU_ORDER_LINE_1WD  the graph of lines and
  *                         single cells (Sec. 5.2) ordered by RCM / 1WD, every
  *                         line expanded in place.
- * Lines: a cell is anisotropic when its strongest coupling exceeds its
- * weakest by more than `line_threshold` (> 1); from the most anisotropic free
- * cell a line grows at both ends to the strongest-coupled free neighbour while
- * that coupling exceeds `line_threshold` times the end cell's weakest coupling
- * and is at least the neighbour's strongest coupling / `line_threshold`; a
- * cell with no weak coupling (a side boundary) is measured against the line's
- * last anisotropic cell, at most two such cells in a row.
+ * Lines: a cell is anisotropic when its strongest coupling is at least
+ * `line_threshold` (> 1) times its weakest; from the most anisotropic free
+ * cell (ties: lowest index) a line grows forward, then backward, to the
+ * strongest-coupled free neighbour (ties: lowest index) while that coupling
+ * is at least `line_threshold` times the end cell's weakest coupling and at
+ * least the neighbour's strongest coupling / `line_threshold`; a cell with
+ * no weak coupling (a side boundary) is measured against the line's last
+ * anisotropic cell, at most two such cells in a row (a third ends the line);
+ * a one-cell line is dropped; lines are numbered by their lowest cell.
+ * The coupling of an edge is the larger weight of its two blocks.
  * Couplings: `weights` double[nnzb] per block (e.g. geometric), else the
  * Frobenius norms of `vals` double[nnzb][4][4]; one of them is required for
  * the line kinds, both may be NULL otherwise.  rowptr int32[n+1], colind

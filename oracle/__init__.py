@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "abilu_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "orderings.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -32,10 +33,11 @@ _PD = C.POINTER(C.c_double)
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/liboracle.so (gcc, -O2, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f)
+                                                for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -111,6 +113,8 @@ def _load():
                                                C.c_int, _PD, _PD, C.c_int, C.c_int, f64,
                                                C.POINTER(_Res), _PD]
         lib.orc_fgmres_ilu_pattern.restype = C.c_int
+        lib.orc_order.argtypes = [i32, _PI, _PI, _PD, _PD, C.c_int, f64, _PI, _PI]
+        lib.orc_order.restype = C.c_int
         for nm in ("orc_lower_sweep", "orc_upper_sweep", "orc_lower_solve", "orc_upper_solve",
                    "orc_apply", "orc_spmv", "orc_jacobi_norms", "orc_silu_lower_sweep",
                    "orc_silu_upper_sweep", "orc_silu_apply"):
@@ -610,3 +614,25 @@ def fgmres_ilu_pattern(rowptr, colind, A, rowptr_f, colind_f, X, Dinv, b, n_lowe
                                    float(rtol), C.byref(res), hist.ctypes.data_as(_PD))
     return x, FgmresResult(res.iters, res.restarts, bool(res.converged), res.rel_resid_est,
                            res.rel_resid_true, hist[: res.iters + 1])
+
+
+ORDERINGS = {"rcm": 0, "1wd": 1, "line": 2, "line-rcm": 3, "line-1wd": 4}
+
+
+def order(rowptr, colind, kind="rcm", weights=None, vals=None, threshold=10.0):
+    """Orderings of the cell graph (orderings.c; Sec. 5, 5.1, 5.2):
+    (perm, line_of), perm[k] = the old index of the cell numbered k, line_of[c]
+    = the line of cell c or -1."""
+    n, keep, prp, pci = _pattern(rowptr, colind)
+    pw = pv = None
+    if weights is not None:
+        w, pw = _d(weights)
+    if vals is not None:
+        v, pv = _d(vals)
+    perm = np.empty(n, np.int32)
+    line_of = np.empty(n, np.int32)
+    rc = _load().orc_order(n, prp, pci, pw, pv, ORDERINGS[kind], float(threshold),
+                           perm.ctypes.data_as(_PI), line_of.ctypes.data_as(_PI))
+    if rc != 0:
+        raise ValueError("orc_order: bad input")
+    return perm, line_of

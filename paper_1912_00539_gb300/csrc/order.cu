@@ -4,8 +4,10 @@
 // the matrix is known to the solver, on the pattern in host memory.
 //
 //  * RCM: breadth-first search from a pseudo-peripheral cell (the last level's
-//    lowest-degree cell, repeated while the eccentricity grows), neighbours in
-//    increasing degree, the whole order reversed; one component after another.
+//    lowest-degree cell, ties to the lowest index, repeated while the number
+//    of levels grows), neighbours in increasing (degree, index), the order
+//    reversed; one component after another (in order of their lowest cell),
+//    each reversed on its own.  Degrees are those of the whole graph.
 //  * 1WD (one-way dissection): a rooted level structure from a
 //    pseudo-peripheral cell; level sets at regular intervals delta are taken as
 //    separators (delta = sqrt((3 w + 13) / 2), w the mean level width, the
@@ -20,8 +22,8 @@
 //    weakest coupling and is within `threshold` of the neighbour's strongest.
 //    A cell with no weak coupling (e.g. on a side boundary, where the weak
 //    direction has no neighbour) is measured against the weakest coupling of
-//    the line's last anisotropic cell, at most two such cells in a row;
-//    lines of one cell are not lines.  Couplings are per-block weights: the caller's
+//    the line's last anisotropic cell, at most two such cells in a row (a
+//    third one in a row ends the line); lines of one cell are not lines.  Couplings are per-block weights: the caller's
 //    (geometric) weights, or the Frobenius norms of the blocks.
 //  * LINE: every line's cells made contiguous, in line order, at the position
 //    of the line's first cell in the input order.  LINE_RCM / LINE_1WD: the
@@ -93,15 +95,22 @@ static std::vector<int> bfs(const Graph &g, int root, const std::vector<int> &ma
     return out;
 }
 
-// pseudo-peripheral cell of the component of `start` (cells with mask == tag)
+// pseudo-peripheral cell of the component of `start` (cells with mask == tag):
+// from the root's level structure, the last level's cell of least degree (ties:
+// lowest index) becomes the root while its level structure is deeper (the
+// number of levels grows strictly and is at most the component's size, so
+// the loop ends)
 static int pseudo_peripheral(const Graph &g, int start, const std::vector<int> &mask, int tag,
                              std::vector<int> &level) {
     int root = start, nlev = 0;
-    for (int it = 0; it < 64; it++) {
+    for (;;) {
         std::vector<int> comp = bfs(g, root, mask, tag, level, &nlev);
         int best = -1;
         for (int v : comp)
-            if (level[v] == nlev - 1 && (best < 0 || degree(g, v) < degree(g, best))) best = v;
+            if (level[v] == nlev - 1 &&
+                (best < 0 || degree(g, v) < degree(g, best) ||
+                 (degree(g, v) == degree(g, best) && v < best)))
+                best = v;
         int nlev2 = 0;
         for (int v : comp) level[v] = -1;
         std::vector<int> comp2 = bfs(g, best, mask, tag, level, &nlev2);
@@ -109,7 +118,6 @@ static int pseudo_peripheral(const Graph &g, int start, const std::vector<int> &
         if (nlev2 <= nlev) return root;
         root = best;
     }
-    return root;
 }
 
 // Cuthill-McKee order of the component of `start` (mask == tag), appended to out
@@ -255,9 +263,9 @@ static int find_lines(const Graph &g, const int32_t *rowptr, const int32_t *coli
         int run = 0;
         for (int c = s;;) {
             const bool an = aniso[c] >= threshold;
-            if (!an && run > MAX_PLAIN_RUN) break;
             const int u = next(c, an ? wmin[c] : ref);
             if (u < 0) break;
+            if (aniso[u] < threshold && run >= MAX_PLAIN_RUN) break;   // a third in a row
             line_of[u] = id;
             cells.push_back(u);
             if (aniso[u] >= threshold) {

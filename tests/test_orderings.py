@@ -183,3 +183,70 @@ def test_line_orderings_help_the_viscous_grid(ab):
     assert iters["line"] <= iters["rcm"], iters
     assert iters["line-rcm"] <= iters["rcm"], iters
     assert iters["line-1wd"] <= iters["rcm"], iters
+
+
+# ------------------------------------------------- bit-exact against the oracle
+# abilu_order is integer work (with comparisons of FP64 coupling weights), so
+# it must equal the oracle's orderings (oracle/orderings.c, written from the
+# same stated rules) exactly: every permutation entry and every line index.
+
+def _components_system():
+    """Several components, isolated cells, and couplings scaled x100 on a
+    random subset of edges (lines appear)."""
+    rng = np.random.default_rng(21)
+    n = 400
+    e = rng.integers(0, n, size=(420, 2))
+    e = np.unique(np.sort(e[e[:, 0] != e[:, 1]], axis=1), axis=0)
+    off = rng.standard_normal((len(e), 2, 4, 4)) * 0.5
+    off[rng.random(len(e)) < 0.3] *= 100.0
+    rowptr, colind, vals = gen.assemble(n, e, off, 10.0, np.arange(n))
+    return gen.System("components", rowptr, colind, vals, np.zeros((n, 4)), np.arange(n), 10.0)
+
+
+PARITY_GRAPHS = {
+    "viscous_1024x256": lambda: gen.make_system(1024, 256, 301, 302, 303, 1e4, order="natural",
+                                                wall_normal_scale=100.0),
+    "viscous_128x32": lambda: _viscous(128, 32),
+    "isotropic_64x64": lambda: gen.make_system(64, 64, 101, 102, 103, 100.0, order="natural"),
+    "random_triangles": lambda: gen.random_pattern_system(300, 200, seed=9),
+    "components": _components_system,
+}
+KINDS = ["rcm", "1wd", "line", "line-rcm", "line-1wd"]
+
+
+@pytest.fixture(scope="module", params=list(PARITY_GRAPHS))
+def parity_graph(request):
+    return PARITY_GRAPHS[request.param]()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_order_equals_oracle(ab, parity_graph, kind):
+    import oracle
+    s = parity_graph
+    p, l = ab.order(s.rowptr, s.colind, kind, vals=s.vals, line_threshold=10.0)
+    po, lo = oracle.order(s.rowptr, s.colind, kind, vals=s.vals, threshold=10.0)
+    assert np.array_equal(p, po) and np.array_equal(l, lo)
+
+
+@pytest.mark.parametrize("kind", ["line", "line-rcm", "line-1wd"])
+def test_order_with_caller_weights_equals_oracle(ab, kind):
+    """Caller-given (geometric-like) weights: heavy-tailed random per block."""
+    import oracle
+    s = _components_system()
+    w = np.exp(np.random.default_rng(5).normal(0.0, 2.0, len(s.colind)))
+    p, l = ab.order(s.rowptr, s.colind, kind, weights=w, line_threshold=6.0)
+    po, lo = oracle.order(s.rowptr, s.colind, kind, weights=w, threshold=6.0)
+    assert np.array_equal(p, po) and np.array_equal(l, lo)
+    assert (l >= 0).sum() > 20
+
+
+def test_order_matches_hand_worked_cases(ab):
+    import test_oracle_orderings as g
+    for case in g.golden_cases():
+        rp, ci, w = g.golden_pattern(case)
+        for kind, perm in g.golden_expectations(case):
+            p, line_of = ab.order(rp, ci, kind, weights=w,
+                                  line_threshold=case.get("threshold", 10.0))
+            assert p.tolist() == perm, (case["name"], kind)
+            if "line_of" in case:
+                assert line_of.tolist() == case["line_of"], case["name"]
