@@ -232,31 +232,55 @@ def offdiag_blocks(grid: Grid, value_seed: int, wall_normal_scale: float = 1.0) 
     return off
 
 
-def assemble(n: int, edges: np.ndarray, off: np.ndarray, cfl: float, perm: np.ndarray):
-    """BSR arrays in the ordering ``perm`` (perm[new] = old).
+@dataclass
+class AssemblyPlan:
+    """The fixed part of assembling a pattern: the renumbered edge ends and
+    the order that sorts the blocks into BSR (rows, then columns)."""
+    n: int
+    u: np.ndarray
+    v: np.ndarray
+    order: np.ndarray
+    rowptr: np.ndarray
+    colind: np.ndarray
 
-    Diagonal block of row i: diag(1/CFL + sum over off-diagonal blocks of row i
-    of the absolute values in each scalar row).
-    """
+
+def assembly_plan(n: int, edges: np.ndarray, perm: np.ndarray) -> AssemblyPlan:
     inv = np.empty(n, np.int64)
     inv[perm] = np.arange(n)
     u = inv[edges[:, 0]]
     v = inv[edges[:, 1]]
     rows = np.concatenate([u, v, np.arange(n)])
     cols = np.concatenate([v, u, np.arange(n)])
-    absrow = np.zeros((n, BS))
-    np.add.at(absrow, u, np.abs(off[:, 0]).sum(axis=2))
-    np.add.at(absrow, v, np.abs(off[:, 1]).sum(axis=2))
-    diag = np.zeros((n, BS, BS))
-    diag[:, np.arange(BS), np.arange(BS)] = 1.0 / cfl + absrow
-    blocks = np.concatenate([off[:, 0], off[:, 1], diag], axis=0)
     o = np.lexsort((cols, rows))
-    rows, cols, blocks = rows[o], cols[o], blocks[o]
+    rows, cols = rows[o], cols[o]
     rowptr = np.zeros(n + 1, np.int64)
     np.add.at(rowptr, rows + 1, 1)
     rowptr = np.cumsum(rowptr)
-    return (rowptr.astype(np.int32), cols.astype(np.int32),
-            np.ascontiguousarray(blocks, dtype=np.float64))
+    return AssemblyPlan(n, u, v, o, rowptr.astype(np.int32), cols.astype(np.int32))
+
+
+def assemble_values(plan: AssemblyPlan, off: np.ndarray, cfl: float) -> np.ndarray:
+    """Block values of the plan's pattern: the off-diagonal blocks ``off`` and
+    diagonal blocks diag(1/CFL + sum over the row's off-diagonal blocks of the
+    absolute values in each scalar row)."""
+    n = plan.n
+    absrow = np.zeros((n, BS))
+    np.add.at(absrow, plan.u, np.abs(off[:, 0]).sum(axis=2))
+    np.add.at(absrow, plan.v, np.abs(off[:, 1]).sum(axis=2))
+    diag = np.zeros((n, BS, BS))
+    diag[:, np.arange(BS), np.arange(BS)] = 1.0 / cfl + absrow
+    blocks = np.concatenate([off[:, 0], off[:, 1], diag], axis=0)
+    return np.ascontiguousarray(blocks[plan.order], dtype=np.float64)
+
+
+def assemble(n: int, edges: np.ndarray, off: np.ndarray, cfl: float, perm: np.ndarray):
+    """BSR arrays in the ordering ``perm`` (perm[new] = old).
+
+    Diagonal block of row i: diag(1/CFL + sum over off-diagonal blocks of row i
+    of the absolute values in each scalar row).
+    """
+    plan = assembly_plan(n, edges, perm)
+    return plan.rowptr, plan.colind, assemble_values(plan, off, cfl)
 
 
 def make_system(nx, ny, grid_seed, value_seed, rhs_seed, cfl, order="rcm",
@@ -357,13 +381,15 @@ class Request:
 
 
 def value_update(system: System, grid: Grid, base_off: np.ndarray, k: int, cfl0: float,
-                 seed: int):
+                 seed: int, plan: AssemblyPlan = None):
     """Values of update k on a fixed pattern: off-diagonal blocks
     base * (1 + 0.1 N(0,1)), CFL_k = CFL_0 * 4^k, diagonal rebuilt."""
     rng = np.random.default_rng(seed)
     off = base_off * (1.0 + 0.1 * rng.standard_normal(base_off.shape))
     cfl = cfl0 * 4.0 ** k
-    _, _, vals = assemble(system.n, grid.edges, off, cfl, system.perm)
+    if plan is None:
+        plan = assembly_plan(system.n, grid.edges, system.perm)
+    vals = assemble_values(plan, off, cfl)
     b = rng.standard_normal((system.n, BS))[system.perm]
     return vals, np.ascontiguousarray(b), cfl
 
@@ -389,13 +415,14 @@ def serving_stream(rate_hz: float, n_requests: int, seed=5, cells_lo=4000,
         ptr, idx = adjacency(grid.ncells, grid.edges)
         perm = rcm_order(ptr, idx)
         base = offdiag_blocks(grid, int(seeds[1]))
-        rowptr, colind, vals = assemble(grid.ncells, grid.edges, base, cfl0, perm)
+        plan = assembly_plan(grid.ncells, grid.edges, perm)
+        rowptr, colind, vals = plan.rowptr, plan.colind, assemble_values(plan, base, cfl0)
         b = np.random.default_rng(int(seeds[2])).standard_normal((grid.ncells, BS))[perm]
         sysm = System(f"req{rid}_{nx}x{ny}", rowptr, colind, vals, np.ascontiguousarray(b),
                       perm, cfl0, dict(nx=nx, ny=ny))
         ups = [(vals, sysm.b, cfl0)]
         for k in range(1, n_updates):
-            ups.append(value_update(sysm, grid, base, k, cfl0, int(seeds[2 + k])))
+            ups.append(value_update(sysm, grid, base, k, cfl0, int(seeds[2 + k]), plan))
         out.append(Request(rid, float(arrivals[rid]), sysm, ups))
     return out
 

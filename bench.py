@@ -159,21 +159,78 @@ def oracle_solve(s, max_iters=2500):
     return r
 
 
-def cpu_baseline(s, budget_s=12.0):
-    """Full oracle solves (FP64, one host thread) until ~budget_s of CPU time."""
+def oracle_solution(s, max_iters=2500):
+    """The FP64 oracle's solution x and result of the workload's solve."""
+    import oracle
+    X, D, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, BUILD_SWEEPS)
+    return oracle.fgmres(s.rowptr, s.colind, s.vals, X, D, s.b, APPLY_SWEEPS, APPLY_SWEEPS,
+                         restart=RESTART, max_iters=max_iters, rtol=RTOL)
+
+
+def host_cpu():
+    """nproc and the CPU model of this host (lscpu's model name, else
+    /proc/cpuinfo's)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                model = line.split(":", 1)[1].strip()
+                break
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown",
+            "machine": os.uname().machine}
+
+
+def oracle_kernel_ms(s, reps=2):
+    """The oracle's time (one host core, FP64) for one synchronous build sweep,
+    one lower sweep, one upper sweep and one SpMV of workload s, best of reps."""
+    import numpy as np
+    import oracle
+    X, D, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 1)
+    r = np.random.default_rng(1).standard_normal((s.n, 4))
+    y0 = np.zeros_like(r)
+
+    def best(fn):
+        t = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            t.append(time.perf_counter() - t0)
+        return round(1e3 * min(t), 2)
+    return {"build_sweep": best(lambda: oracle.bilu_sync_sweep(s.rowptr, s.colind, s.vals, X, D)),
+            "lower_sweep": best(lambda: oracle.lower_sweep(s.rowptr, s.colind, X, r, y0)),
+            "upper_sweep": best(lambda: oracle.upper_sweep(s.rowptr, s.colind, X, D, r, y0)),
+            "spmv": best(lambda: oracle.spmv(s.rowptr, s.colind, s.vals, r))}
+
+
+def cpu_baseline(s, budget_s=12.0, viscous=None):
+    """Full oracle solves (FP64, one host thread) until ~budget_s of CPU time;
+    the oracle's per-kernel times on this workload (and on `viscous`)."""
     t0 = time.perf_counter()
     n = 0
     while True:
-        r = oracle_solve(s)
+        x_or, r = oracle_solution(s)
         n += 1
         el = time.perf_counter() - t0
         if el >= budget_s or n >= 5:
             break
-    return {"value": n / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} full FP64 oracle solves of the 512x512 workload (sync build "
-                      f"{BUILD_SWEEPS} sweeps, {APPLY_SWEEPS}+{APPLY_SWEEPS} apply sweeps, "
-                      f"FGMRES({RESTART}) to {RTOL:g}, {r.iters} iterations each) in {el:.1f} s "
-                      f"on one host core"}
+    out = {"value": n / el, "unit": "solves/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n} full FP64 oracle solves of the 512x512 workload (sync build "
+                     f"{BUILD_SWEEPS} sweeps, {APPLY_SWEEPS}+{APPLY_SWEEPS} apply sweeps, "
+                     f"FGMRES({RESTART}) to {RTOL:g}, {r.iters} iterations each) in {el:.1f} s "
+                     f"on one host core",
+           **host_cpu(),
+           "oracle_kernel_ms": {WORKLOAD: oracle_kernel_ms(s)}}
+    if viscous is not None:
+        out["oracle_kernel_ms"][viscous.name] = oracle_kernel_ms(viscous)
+    return out, x_or, r
 
 
 def run_reference(args):
@@ -417,44 +474,108 @@ def _r(v):
     return float(f"{v:.4g}") if isinstance(v, float) else v
 
 
-def run_serving(args, n_requests=48):
-    """Poisson stream of requests (4k-1M cells, 5 value updates each, CFL x4 per
-    update), FP32 factors, served with concurrent slots; against plain FP64
-    ABILU served one request at a time on the same GPU."""
-    import torch  # noqa: F401
+def _rd(d):
+    return {k: ({kk: _r(vv) for kk, vv in v.items()} if isinstance(v, dict) else _r(v))
+            for k, v in d.items()}
+
+
+def run_serving(args, n_requests=48, rates=(0.25, 0.5, 1.0, 1.5)):
+    """Poisson stream of requests (4k-1M cells log-uniform, 5 value updates
+    each, CFL x4 per update), FP32 factors, served by continuous batching (every
+    step one update of every admitted request in shared launches, warm-started
+    factors, admission by room in an arena sized to the HBM budget); against
+    plain FP64 ABILU (synchronous sweeps) solving the requests one at a time on
+    the same GPU.  Capacity = solves/s with every request queued at t = 0; the
+    arrival rates are fractions of it."""
+    import torch
     import abilu_inputs as gen
     from paper_1912_00539_gb300 import serving
     t0 = time.perf_counter()
     stream = gen.serving_stream(rate_hz=1.0, n_requests=n_requests, seed=5)
     tgen = time.perf_counter() - t0
+    # every update's values and right-hand side in pinned host memory, once
     unit = [serving.Request(r.rid, r.arrival, r.system.rowptr, r.system.colind,
-                            [(v, b) for v, b, _ in r.updates]) for r in stream]
+                            [(torch.from_numpy(v).pin_memory(), torch.from_numpy(b).pin_memory())
+                             for v, b, _ in r.updates]) for r in stream]
+    del stream
+    n_upd = sum(len(r.updates) for r in unit)
 
     def at_rate(rate):
         return [serving.Request(r.rid, r.arrival / rate, r.rowptr, r.colind, r.updates)
                 for r in unit]
 
-    budget = 0.5 * torch.cuda.get_device_properties(0).total_memory
+    budget = 0.25 * torch.cuda.get_device_properties(0).total_memory
     cfg = dict(build_sweeps=args.batch_build_sweeps, apply_sweeps=args.batch_apply_sweeps)
-    # warm-up (library kernels, allocator)
-    serving.Server(budget, slots=2, dtype="f32", mode=args.mode, **cfg).run(at_rate(1e6)[:2])
-    # capacity: everything queued at t=0, one slot
-    res, wall = serving.Server(budget, slots=1, dtype="f32", mode=args.mode, **cfg).run(at_rate(1e6))
+    srv = serving.Server(budget, dtype="f32", mode=args.mode, **cfg)
+    srv.run(at_rate(1e9)[:3])                       # warm-up (kernels, host paths)
+    res, wall = srv.run(at_rate(1e9))               # capacity: all queued at t = 0
     cap = serving.summarize(res, wall)
-    cap_req_rate = cap["requests"] / cap["wall_s"]
-    out = {"workload": f"{n_requests} requests, 4k-1M cells, 5 updates each",
-           "cells": int(sum(r.n for r in unit)), "generation_s": round(tgen, 1),
-           "single_slot_capacity_solves_per_s": round(cap["solves_per_s"], 1)}
-    for frac in (0.25, 0.5, 1.0, 1.5):
-        res, wall = serving.Server(budget, slots=8, dtype="f32", mode=args.mode,
-                                   **cfg).run(at_rate(frac * cap_req_rate))
-        out[f"f32_rate_{frac}x"] = {k: ({kk: _r(vv) for kk, vv in v.items()} if isinstance(v, dict)
-                                        else _r(v)) for k, v in serving.summarize(res, wall).items()}
-    res, wall = serving.Server(budget, slots=1, dtype="f64", mode="sync",
-                               **cfg).run(at_rate(1.0 * cap_req_rate))
-    out["f64_one_at_a_time_rate_1.0x"] = {k: ({kk: _r(vv) for kk, vv in v.items()}
-                                               if isinstance(v, dict) else _r(v))
-                                           for k, v in serving.summarize(res, wall).items()}
+    req_rate = cap["requests"] / cap["wall_s"]
+    out = {"workload": f"{n_requests} requests, 4k-1M cells (log-uniform), 5 updates each",
+           "cells": int(sum(r.n for r in unit)), "updates": n_upd, "generation_s": round(tgen, 1),
+           "arena": {"cells": srv.cells, "blocks": srv.blocks, "bytes": srv.arena_bytes,
+                     "budget_bytes": budget},
+           "f32_capacity": _rd(cap)}
+    for frac in rates:
+        res, wall = srv.run(at_rate(frac * req_rate))
+        out[f"f32_rate_{frac}x"] = _rd(serving.summarize(res, wall))
+    srv.close()
+    # the baseline: plain FP64 ABILU, one request at a time (all queued at t = 0
+    # for its capacity, and at the 1.0x arrival rate)
+    serving.serve_one_at_a_time(at_rate(1e9)[:2], dtype="f64", mode="sync", **cfg)
+    res, wall = serving.serve_one_at_a_time(at_rate(1e9), dtype="f64", mode="sync", **cfg)
+    out["f64_one_at_a_time_capacity"] = _rd(serving.summarize(res, wall))
+    res, wall = serving.serve_one_at_a_time(at_rate(1.0 * req_rate), dtype="f64", mode="sync",
+                                            **cfg)
+    out["f64_one_at_a_time_rate_1.0x"] = _rd(serving.summarize(res, wall))
+    out["f32_serving_over_f64_one_at_a_time"] = round(
+        cap["solves_per_s"] / out["f64_one_at_a_time_capacity"]["solves_per_s"], 3)
+    return out
+
+
+def viscous_rcm_vs_line(steps=5):
+    """The viscous-like 1024x256 workload in its two orderings (RCM, whole
+    wall-normal lines): FP32 factors, asynchronous, 8 build and 6+6 apply
+    sweeps, FGMRES(50) to 1e-6, against the FP64 oracle's iterations and
+    solution."""
+    import numpy as np
+    import torch
+    import abilu_inputs as gen
+    import oracle
+    import paper_1912_00539_gb300 as ab
+    out = {}
+    for order in ("rcm", "line"):
+        name = f"viscous_1024x256_{order}"
+        s = gen.workload(name)
+        st = gen.SOLVER_SETTINGS[name]
+        pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+        A = torch.from_numpy(s.vals).cuda()
+        b = torch.from_numpy(s.b).cuda()
+        fac = ab.Factors(pat, "f32")
+        x = torch.zeros_like(b)
+
+        def solve():
+            return ab.fgmres_solve(pat, A, fac, b, x, restart=st["restart"], rtol=st["rtol"],
+                                   build_sweeps=st["build_sweeps"],
+                                   apply_sweeps_lower=st["apply_sweeps"],
+                                   apply_sweeps_upper=st["apply_sweeps"], mode="async",
+                                   zero_guess=True)
+        r = solve()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch, 2)
+        e0.record()
+        for _ in range(steps):
+            r = solve()
+        e1.record()
+        torch.cuda.synchronize()
+        Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, st["build_sweeps"])
+        xo, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, st["apply_sweeps"],
+                               st["apply_sweeps"], restart=st["restart"], rtol=st["rtol"])
+        xn = x.cpu().numpy()
+        out[order] = {"solves_per_s": round(steps / (e0.elapsed_time(e1) * 1e-3), 1),
+                      "iters": r.iters, "oracle_f64_iters": ro.iters,
+                      "rel_resid_true": _r(r.rel_resid_true),
+                      "err_vs_oracle": _r(float(np.linalg.norm(xn - xo) / np.linalg.norm(xo)))}
     return out
 
 
@@ -979,16 +1100,50 @@ def run_gpu(args):
             a1.record(stream)
             torch.cuda.synchronize()
             variants[f"{dt}_{md}"] = {"solves_per_s": round(5 / (a0.elapsed_time(a1) * 1e-3), 1),
-                                      "iters": r.iters, "rel_resid_true": r.rel_resid_true}
+                                      "iters": r.iters, "rel_resid_true": r.rel_resid_true,
+                                      "x": xv.cpu().numpy()}
+
+    # ---- latency: >= 200 solves, each between its own events (outside the
+    # timed region, so that p99 is a percentile and not the maximum)
+    nlat = max(200, args.steps)
+    lev = _events(torch, nlat + 1)
+    torch.cuda.synchronize()
+    lev[0].record(stream)
+    for k in range(nlat):
+        solve()
+        lev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    lat_ms = sorted(lev[k].elapsed_time(lev[k + 1]) for k in range(nlat))
+
+    # ---- the other workloads of the benchmark: viscous-like grid in both
+    # orderings, the uneven batch, the serving stream
+    extras = {}
+    if rank == 0 and world == 1 and args.extras:
+        extras["viscous"] = viscous_rcm_vs_line()
+        extras["batched"] = run_batched(args)
+        extras["serving"] = run_serving(args, n_requests=20, rates=(0.5, 1.0))
 
     cpu = None
+    x_gpu = x.cpu().numpy()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(s)
+        import numpy as np
+        vis = None
+        if args.extras:
+            import abilu_inputs as gen
+            vis = gen.workload("viscous_1024x256_rcm")
+        cpu, x_or, r_or = cpu_baseline(s, viscous=vis)
+        nrm = float(np.linalg.norm(x_or))
+        err = {"rel_l2": float(np.linalg.norm(x_gpu - x_or)) / nrm,
+               "rel_max": float(np.abs(x_gpu - x_or).max() / np.abs(x_or).max()),
+               "oracle_iters": r_or.iters, "oracle_rel_resid_true": r_or.rel_resid_true}
+        for name, v in variants.items():
+            v["err_vs_oracle"] = _r(float(np.linalg.norm(v.pop("x") - x_or)) / nrm)
+    for v in variants.values():
+        v.pop("x", None)
 
     if rank == 0:
-        sorted_ms = sorted(step_ms)
-        p50 = statistics.median(sorted_ms)
-        p99 = sorted_ms[min(len(sorted_ms) - 1, int(round(0.99 * (len(sorted_ms) - 1))))]
+        p50 = statistics.median(lat_ms)
+        p99 = lat_ms[min(len(lat_ms) - 1, int(round(0.99 * (len(lat_ms) - 1))))]
         line = {"metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -1001,11 +1156,12 @@ def run_gpu(args):
                            "rel_resid_true": res.rel_resid_true,
                            "parallelism": f"replicas{world}",
                            "l2": "inputs larger than L2 (A = %.0f MB)" % (s.nnzb * 128 / 1e6)},
-                "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4)},
+                "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "samples": nlat},
+                "err_vs_oracle": ({k: _r(v) for k, v in err.items()} if cpu else None),
                 "gpu_launches": int(launches),
                 "e2e": {k: (round(v, 2) if isinstance(v, float) else v) for k, v in e2e.items()},
                 "roofline": roof, "kernels": kernels, "variants": variants,
-                "clocks": clk, "cpu_baseline": cpu}
+                "clocks": clk, "cpu_baseline": cpu, **extras}
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -1022,6 +1178,8 @@ def main():
     ap.add_argument("--mode", default="async", choices=["sync", "async"])
     ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the viscous, batched and serving sections of the default line")
     ap.add_argument("--kernels-only", action="store_true")
     ap.add_argument("--profile-solves", type=int, default=0)
     ap.add_argument("--profile-mg", type=int, default=0,

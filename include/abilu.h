@@ -488,6 +488,68 @@ abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts, fgmres_re
 abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x, abilu_stream stream);
 
 /*
+ * Continuous batching: a server whose every step solves one value update of
+ * each admitted system in shared launches (the batched solve above), while
+ * systems join and leave between steps.  The use it serves is the paper's:
+ * each system is the Jacobian of one flow computation, its values change every
+ * pseudo-time step on a fixed pattern (Sec. 2), and its factors are
+ * warm-started from the previous step's (Sec. 6 setup).
+ *
+ * The server allocates one arena at creation, sized by abilu_server_opts (rows
+ * and blocks of all admitted systems, each padded to a multiple of 64 rows with
+ * identity rows; their strictly lower / upper blocks, product pairs and build
+ * work items, whose defaults suit symmetric patterns; systems; the FGMRES
+ * restart the Krylov workspace is sized for).  Admission and departure
+ * allocate nothing in it:
+ *   abilu_server_add analyses the system's pattern (rowptr/colind: device, as
+ *     for abilu_pattern_create) once, into its own pattern handle, and admits
+ *     it; ABILU_ENOMEM (nothing changed) when the admitted systems would no
+ *     longer fit the arena.  *id (host) names the system.  Synchronises stream.
+ *   abilu_server_remove releases the system's pattern handle at once; its
+ *     share of the arena is free from the next step on.
+ *   abilu_server_step solves, in one batched solve, one update of every
+ *     admitted system: ids[k] lists each admitted system exactly once; A[q]
+ *     (double[nnzb][4][4]), rhs[q] (double[n][4]) and x[q] (output, double
+ *     [n][4]) are HOST arrays of pointers to device or pinned host memory.
+ *     When the list differs from the previous step's, the systems are laid
+ *     out again in the listed order (each analysis relocated into the arena,
+ *     the factors of continuing systems moved with them).  Every step builds
+ *     (opts->build must be 1) with opts' sweeps and mode: a system's first
+ *     step from A, later steps from its previous factors (opts->init is not
+ *     used); FGMRES from x0 = 0 per system; res[q] (host) per listed system.
+ *     Synchronises stream.  Statuses as abilu_batch_solve.
+ *   abilu_server_usage: host int64_t[14]: capacities (rows, blocks, L blocks,
+ *     U blocks, product pairs, work items, systems), then the same quantities
+ *     of the admitted systems.
+ *   abilu_server_arena_bytes: the device bytes of an arena with these options
+ *     (to size one to an HBM budget); no device work.
+ */
+typedef struct {
+    int64_t max_cells;     /* rows of all admitted systems, padding included (>= 64) */
+    int64_t max_blocks;    /* blocks of all admitted systems, padding included (>= 64) */
+    int32_t max_systems;   /* >= 1 */
+    int32_t factor_dtype;  /* abilu_dtype of the factors */
+    int32_t restart;       /* the largest FGMRES(m) of the steps, 1..64 */
+    int64_t max_lower;     /* strictly lower blocks; 0: max_blocks / 2 */
+    int64_t max_upper;     /* strictly upper blocks; 0: max_blocks / 2 */
+    int64_t max_pairs;     /* product pairs of the build; 0: max_blocks */
+    int64_t max_work;      /* build work items; 0: max_blocks */
+} abilu_server_opts;
+typedef struct abilu_server_s *abilu_server;
+abilu_status abilu_server_arena_bytes(const abilu_server_opts *opts, int64_t *bytes);
+abilu_status abilu_server_create(const abilu_server_opts *opts, abilu_stream stream,
+                                 abilu_server *out);
+void abilu_server_destroy(abilu_server s);
+abilu_status abilu_server_add(abilu_server s, int32_t n, int32_t nnzb, const int32_t *rowptr,
+                              const int32_t *colind, abilu_stream stream, int32_t *id);
+abilu_status abilu_server_remove(abilu_server s, int32_t id);
+abilu_status abilu_server_step(abilu_server s, int32_t k, const int32_t *ids,
+                               const double *const *A, const double *const *rhs,
+                               double *const *x, const fgmres_opts *opts, fgmres_result *res,
+                               abilu_stream stream);
+abilu_status abilu_server_usage(abilu_server s, int64_t *out);
+
+/*
  * Orderings of the cell graph (Sec. 5), host code on host arrays.  `kind`:
  *   ABILU_ORDER_RCM       reverse Cuthill-McKee, per component (in order of
  *                         the component's lowest cell, each reversed on its

@@ -40,7 +40,9 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_to_f32", "abilu_mg_default_opts", "abilu_mg_create", "abilu_mg_destroy",
            "abilu_mg_setup", "abilu_mg_apply", "abilu_mg_levels", "abilu_mg_level_data",
            "fgmres_solve_mg", "abilu_parilut_default_opts", "abilu_parilut",
-           "abilu_pattern_arrays", "abilu_factors_inject_stall", "abilu_factors_set_spin_limit")
+           "abilu_pattern_arrays", "abilu_factors_inject_stall", "abilu_factors_set_spin_limit",
+           "abilu_server_arena_bytes", "abilu_server_create", "abilu_server_destroy",
+           "abilu_server_add", "abilu_server_remove", "abilu_server_step", "abilu_server_usage")
 
 
 class FgmresOpts(C.Structure):
@@ -65,6 +67,12 @@ MG_MAX_LEVELS = 16
 class ParilutOpts(C.Structure):
     _fields_ = [("fill", C.c_double), ("iters", C.c_int32), ("sweeps", C.c_int32),
                 ("factor_dtype", C.c_int32)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("max_cells", C.c_int64), ("max_blocks", C.c_int64), ("max_systems", C.c_int32),
+                ("factor_dtype", C.c_int32), ("restart", C.c_int32), ("max_lower", C.c_int64),
+                ("max_upper", C.c_int64), ("max_pairs", C.c_int64), ("max_work", C.c_int64)]
 
 
 class FgmresResult(C.Structure):
@@ -98,6 +106,19 @@ _lib.abilu_gather_blocks.argtypes = [_i64, _vp, _vp, _vp, _vp]
 _lib.abilu_apply_noalloc.restype = C.c_int
 _lib.abilu_factors_export.argtypes = [_vp, _vp, _vp, _vp]
 _lib.abilu_factors_status.argtypes = [_vp, C.POINTER(_i64), _vp]
+_lib.abilu_server_arena_bytes.argtypes = [C.POINTER(ServerOpts), C.POINTER(_i64)]
+_lib.abilu_server_create.argtypes = [C.POINTER(ServerOpts), _vp, C.POINTER(_vp)]
+_lib.abilu_server_destroy.argtypes = [_vp]
+_lib.abilu_server_destroy.restype = None
+_lib.abilu_server_add.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, C.POINTER(_i32)]
+_lib.abilu_server_remove.argtypes = [_vp, _i32]
+_lib.abilu_server_step.argtypes = [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp),
+                                   C.POINTER(_vp), C.POINTER(FgmresOpts), C.POINTER(FgmresResult),
+                                   _vp]
+_lib.abilu_server_usage.argtypes = [_vp, C.POINTER(_i64)]
+for _nm in ("abilu_server_arena_bytes", "abilu_server_create", "abilu_server_add",
+            "abilu_server_remove", "abilu_server_step", "abilu_server_usage"):
+    getattr(_lib, _nm).restype = C.c_int
 _lib.abilu_factors_set_spin_limit.argtypes = [_vp, _i64]
 _lib.abilu_factors_set_spin_limit.restype = C.c_int
 _lib.abilu_factors_inject_stall.argtypes = [_vp, C.c_int]
@@ -507,6 +528,89 @@ class Batch:
         h = getattr(self, "handle", None)
         if h:
             _lib.abilu_batch_destroy(h)
+            self.handle = None
+
+
+def _server_opts(max_cells, max_blocks, max_systems, dtype, restart, max_lower=0, max_upper=0,
+                 max_pairs=0, max_work=0):
+    return ServerOpts(int(max_cells), int(max_blocks), int(max_systems), DTYPES[dtype],
+                      int(restart), int(max_lower), int(max_upper), int(max_pairs), int(max_work))
+
+
+def server_arena_bytes(max_cells, max_blocks, max_systems=64, dtype="f32", restart=30, **caps):
+    """Device bytes of a server arena with these capacities (no device work)."""
+    v = C.c_int64()
+    o = _server_opts(max_cells, max_blocks, max_systems, dtype, restart, **caps)
+    _check(_lib.abilu_server_arena_bytes(C.byref(o), C.byref(v)))
+    return v.value
+
+
+class NativeServer:
+    """Continuous batching (abilu_server_*): every step solves one value update
+    of each admitted system in shared launches; systems join and leave between
+    steps inside one preallocated arena."""
+
+    def __init__(self, max_cells, max_blocks, max_systems=64, dtype="f32", restart=30,
+                 stream=None, **caps):
+        o = _server_opts(max_cells, max_blocks, max_systems, dtype, restart, **caps)
+        h = C.c_void_p()
+        _check(_lib.abilu_server_create(C.byref(o), _stream(stream), C.byref(h)))
+        self.handle = h
+        self.dtype = dtype
+        self.restart = int(restart)
+
+    def add(self, rowptr, colind, stream=None):
+        """Admit a system (device int32 rowptr/colind); returns its id, or None
+        when the arena has no room for it now."""
+        import torch
+        n = rowptr.numel() - 1
+        v = C.c_int32()
+        st = _lib.abilu_server_add(self.handle, n, colind.numel(),
+                                   _ptr(rowptr, torch.int32, what="rowptr"),
+                                   _ptr(colind, torch.int32, what="colind"), _stream(stream),
+                                   C.byref(v))
+        if st == ENOMEM:
+            return None
+        _check(st)
+        return v.value
+
+    def remove(self, sid):
+        _check(_lib.abilu_server_remove(self.handle, int(sid)))
+
+    def usage(self) -> dict:
+        out = (C.c_int64 * 14)()
+        _check(_lib.abilu_server_usage(self.handle, out))
+        names = ("rows", "blocks", "lower", "upper", "pairs", "work", "systems")
+        return {"capacity": dict(zip(names, list(out)[:7])), "used": dict(zip(names, list(out)[7:]))}
+
+    def step(self, ids, A, b, x, restart=30, max_iters=2500, rtol=1e-6, build_sweeps=1,
+             apply_sweeps_lower=3, apply_sweeps_upper=3, mode="async", reorth=False, stream=None,
+             spin_limit=0):
+        """One batched solve of one update of every admitted system: ids, and
+        per system A (nnzb,4,4), b and x (n,4) float64 tensors on the device or
+        in pinned host memory."""
+        k = len(ids)
+        o = FgmresOpts(int(restart), int(max_iters), float(rtol), int(build_sweeps),
+                       int(apply_sweeps_lower), int(apply_sweeps_upper), MODES[mode], 1, 0,
+                       int(bool(reorth)), 1, int(spin_limit))
+        for t in list(A) + list(b) + list(x):
+            if not t.is_contiguous() or t.dtype.itemsize != 8:
+                raise TypeError("server step arrays must be contiguous float64")
+        idv = (C.c_int32 * k)(*[int(i) for i in ids])
+        pa = (C.c_void_p * k)(*[t.data_ptr() for t in A])
+        pb = (C.c_void_p * k)(*[t.data_ptr() for t in b])
+        px = (C.c_void_p * k)(*[t.data_ptr() for t in x])
+        res = (FgmresResult * k)()
+        st = _lib.abilu_server_step(self.handle, k, idv, pa, pb, px, C.byref(o), res,
+                                    _stream(stream))
+        _check(st, allow=(OK, WARN_SINGULAR, ENOCONV))
+        return [SolveResult(r.iters, r.restarts, r.rel_resid_est, r.rel_resid_true,
+                            r.singular_blocks, r.status) for r in res]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.abilu_server_destroy(h)
             self.handle = None
 
 

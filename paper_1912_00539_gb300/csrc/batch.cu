@@ -34,6 +34,8 @@ abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, 
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
                          double beta, double *y, cudaStream_t st, Skip skip);
 void apply_warm(abilu_dtype dt);
+size_t solve_state_bytes();
+int red_ctas();
 
 constexpr int BMAXM = 64;
 constexpr int CHUNK_ROWS = 64;           // rows per CTA = padding unit
@@ -377,6 +379,7 @@ struct abilu_batch_s {
     abilu_pattern pat;
     abilu_factors fac;
     std::vector<void *> allocs;
+    int arena;                  // 1: a server's arena (capacity allocation, re-laid out)
 };
 
 static void batch_free(abilu_batch b) {
@@ -652,22 +655,32 @@ static abilu_status capture_cycle(abilu_batch b, const fgmres_opts *opts, const 
     return ABILU_OK;
 }
 
+static abilu_status batch_solve_core(abilu_batch b, const fgmres_opts *opts, fgmres_result *res,
+                                     cudaStream_t st);
+
 extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts,
                                           fgmres_result *res, abilu_stream stream) {
     if (!b || !opts || !res) return fail(ABILU_EINVAL, "batch_solve: NULL argument");
+    if (b->arena) return fail(ABILU_EINVAL, "batch_solve: a server's arena is solved by abilu_server_step");
+    return batch_solve_core(b, opts, res, S(stream));
+}
+
+static abilu_status batch_solve_core(abilu_batch b, const fgmres_opts *opts, fgmres_result *res,
+                                     cudaStream_t st) {
     const int m = opts->restart;
     if (m < 1 || m > BMAXM) return fail(ABILU_EINVAL, "batch_solve: restart must be in 1..%d", BMAXM);
     if (opts->max_iters < 0 || !(opts->rtol >= 0.0) || opts->apply_sweeps_lower < 0 ||
         opts->apply_sweeps_upper < 0 || opts->build_sweeps < 0 || opts->spin_limit < 0 ||
         (opts->mode != ABILU_SYNC && opts->mode != ABILU_ASYNC))
         return fail(ABILU_EINVAL, "batch_solve: bad options");
-    cudaStream_t st = S(stream);
     // the solve's spin limit for its build and its sweeps (captured graphs
     // keep it: it is part of the graph key)
     b->fac->spin_limit = (unsigned long long)opts->spin_limit;
     const PatternView &P = b->pat->v;
     const size_t nv = (size_t)b->rows * BS;
     if (!b->krylov || b->krylov_m < m) {
+        if (b->arena)   // the arena's Krylov workspace is sized once, at creation
+            return fail(ABILU_EINVAL, "server step: restart %d exceeds the server's %d", m, b->krylov_m);
         if (b->krylov) cudaFree(b->krylov);
         b->krylov = nullptr;
         if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
@@ -776,4 +789,553 @@ extern "C" abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts
     else if (ret == ABILU_OK && ns)
         ret = fail(ABILU_WARN_SINGULAR, "batch_solve: %llu singular diagonal blocks replaced", ns);
     return ret;
+}
+
+// ===================================================================== server
+// Continuous batching (abilu_server_*): the systems of many requests share
+// every launch of a step -- one batched solve of one value update of every
+// admitted system -- and systems join and leave between steps.
+//
+// The server owns an arena: a batch allocated once for capacities (rows,
+// blocks, L and U blocks, product pairs, work items, systems), so admission
+// and departure allocate and free nothing in it.  Each admitted system's
+// pattern is analysed once, at admission, into its own pattern handle (local
+// indices).  Whenever the set of systems in a step differs from the arena's
+// current layout, the systems are laid out packed, in the step's order: each
+// local analysis is copied into the arena with its row, block, L, U, pair and
+// work offsets added (k_relocate; plus the padding rows to a multiple of 64:
+// identity diagonal blocks, b = 0, one diagonal work item each), and the
+// factors of the systems that continue are moved from their old place in the
+// current factor buffer to their new place in the other one (the warm start
+// of Sec. 6 setup survives the move).  A departed system's share of the arena
+// is free from the next layout on; its pattern handle is released at once.
+namespace abilu {
+
+struct Reloc {
+    int R, n, np;          // row base, rows, padded rows
+    int B, nnzb;           // block base, blocks (padding blocks follow)
+    int Lb, nl, Ub, nu;    // bases and counts in the compact L and U arrays
+    int Pb, npairs;        // product pairs
+    int Wb, nwork;         // work items (padding diagonal items follow)
+};
+
+__global__ void k_relocate(PatternView s, Reloc o, int32_t *__restrict__ rowptr,
+                           int32_t *__restrict__ colind, int32_t *__restrict__ diagpos,
+                           int32_t *__restrict__ lrow, int32_t *__restrict__ urow,
+                           int32_t *__restrict__ lcol, int32_t *__restrict__ ucol,
+                           int32_t *__restrict__ pair_ptr, int2 *__restrict__ pairs,
+                           WorkItem *__restrict__ work, int32_t *__restrict__ wpos,
+                           double *__restrict__ A, double *__restrict__ b) {
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stp = (long long)gridDim.x * blockDim.x;
+    const int npad = o.np - o.n;
+    for (long long i = t0; i <= o.np; i += stp) {   // rows, and the terminal row entry
+        const int r = o.R + (int)i;
+        if (i < o.n) {
+            rowptr[r] = o.B + s.rowptr[i];
+            diagpos[r] = o.B + s.diagpos[i];
+            lrow[r] = o.Lb + s.lrow[i];
+            urow[r] = o.Ub + s.urow[i];
+        } else {
+            const int k = (int)i - o.n;
+            rowptr[r] = o.B + o.nnzb + k;
+            lrow[r] = o.Lb + o.nl;
+            urow[r] = o.Ub + o.nu;
+            if (i < o.np) {
+                diagpos[r] = o.B + o.nnzb + k;
+                for (int c = 0; c < BS; c++) b[(size_t)r * BS + c] = 0.0;
+            }
+        }
+    }
+    for (long long p = t0; p <= (long long)o.nnzb + npad; p += stp) {   // blocks, pair_ptr's end
+        const int q = o.B + (int)p;
+        if (p < o.nnzb) {
+            colind[q] = o.R + s.colind[p];
+            pair_ptr[q] = o.Pb + s.pair_ptr[p];
+            const int w = s.wpos[p];
+            wpos[q] = w >= 0 ? o.Wb + w : -1;
+        } else if (p < (long long)o.nnzb + npad) {
+            const int k = (int)(p - o.nnzb);
+            colind[q] = o.R + o.n + k;
+            pair_ptr[q] = o.Pb + o.npairs;
+            wpos[q] = o.Wb + o.nwork + k;
+            for (int e = 0; e < BB; e++) A[(size_t)q * BB + e] = (e % 5 == 0) ? 1.0 : 0.0;
+        } else {
+            pair_ptr[q] = o.Pb + o.npairs;
+        }
+    }
+    for (long long l = t0; l < o.nl; l += stp) lcol[o.Lb + l] = o.R + s.lcol[l];
+    for (long long u = t0; u < o.nu; u += stp) ucol[o.Ub + u] = o.R + s.ucol[u];
+    for (long long t = t0; t < o.npairs; t += stp) {
+        const int2 pr = s.pairs[t];
+        pairs[o.Pb + t] = make_int2(pr.x + o.Lb, pr.y + o.Ub);
+    }
+    for (long long w = t0; w < (long long)o.nwork + npad; w += stp) {
+        WorkItem it;
+        if (w < o.nwork) {
+            it = s.work[w];
+            const int kind = it.kind_np & 3, np = it.kind_np >> 2;
+            it.j += o.R;
+            it.dst += kind == WORK_L ? o.Lb : (kind == WORK_D ? o.R : o.Ub);
+            it.t0 += o.Pb;
+            for (int k = 0; k < 2; k++)
+                if (k < np) it.pr[k] = make_int2(it.pr[k].x + o.Lb, it.pr[k].y + o.Ub);
+        } else {
+            const int i = o.R + o.n + (int)(w - o.nwork);
+            it.j = i;
+            it.dst = i;
+            it.kind_np = WORK_D;
+            it.t0 = o.Pb + o.npairs;
+            it.pr[0] = it.pr[1] = make_int2(0, 0);
+        }
+        work[o.Wb + w] = it;
+    }
+}
+
+struct SrvMember {
+    int id;
+    abilu_pattern p;                       // local analysis, owned
+    int n, nnzb, np, nl, nu, npairs, nwork, max_row;
+    int R, B, Lb, Ub, Pb, Wb;              // offsets in the current layout
+    int laid;                              // placed in the current layout
+    int warm;                              // its factors in the arena are a previous update's
+    long long blocks_p() const { return (long long)nnzb + (np - n); }
+    long long work_p() const { return (long long)nwork + (np - n); }
+};
+
+struct SrvCaps {
+    long long rows, blocks, nl, nu, pairs, work;
+    int sys, restart;
+    abilu_dtype dtype;
+};
+
+static inline long long rnd64(long long v) { return (v + 63) / 64 * 64; }
+
+static abilu_status server_caps(const abilu_server_opts *o, SrvCaps *c) {
+    if (!o) return fail(ABILU_EINVAL, "server: NULL options");
+    if (o->max_cells < 64 || o->max_blocks < 64 || o->max_systems < 1 || o->restart < 1 ||
+        o->restart > BMAXM || o->max_lower < 0 || o->max_upper < 0 || o->max_pairs < 0 ||
+        o->max_work < 0)
+        return fail(ABILU_EINVAL, "server: need max_cells, max_blocks >= 64, max_systems >= 1, "
+                    "restart in 1..%d, non-negative optional capacities", BMAXM);
+    if (o->factor_dtype != ABILU_F64 && o->factor_dtype != ABILU_F32 && o->factor_dtype != ABILU_BF16)
+        return fail(ABILU_EINVAL, "server: bad factor dtype");
+    c->rows = rnd64(o->max_cells);
+    c->blocks = o->max_blocks + (c->rows - o->max_cells);
+    // symmetric patterns (the grids' cell graphs) have as many L as U blocks
+    c->nl = o->max_lower ? o->max_lower : c->blocks / 2;
+    c->nu = o->max_upper ? o->max_upper : c->blocks / 2;
+    c->pairs = o->max_pairs ? o->max_pairs : c->blocks;
+    c->work = o->max_work ? o->max_work : c->blocks;
+    c->sys = o->max_systems;
+    c->restart = o->restart;
+    c->dtype = (abilu_dtype)o->factor_dtype;
+    if (c->rows + 256 > 0x7fffffffLL / BB || c->blocks + 256 > 0x7fffffffLL / BB ||
+        c->pairs > 0x7fffffffLL || c->work > 0x7fffffffLL)
+        return fail(ABILU_EINVAL, "server: capacities exceed 32-bit block indices");
+    return ABILU_OK;
+}
+
+}  // namespace abilu
+
+struct abilu_server_s {
+    abilu_batch b;
+    SrvCaps cap;
+    std::vector<SrvMember> mem;   // admitted, in admission order
+    std::vector<int> layout;      // ids in the current layout order
+    int next_id;
+    int *chunk_init;              // device, one per 64-row chunk
+    int *staging;                 // pinned host: chunk_sys, sys_chunk0, chunk_init
+    int device;
+};
+
+static void server_free(abilu_server sv) {
+    if (!sv) return;
+    for (auto &m : sv->mem)
+        if (m.p) abilu_pattern_destroy(m.p);
+    if (sv->b) batch_free(sv->b);
+    if (sv->staging) cudaFreeHost(sv->staging);
+    delete sv;
+}
+
+extern "C" void abilu_server_destroy(abilu_server sv) { server_free(sv); }
+
+// device bytes of an arena with these capacities (the allocations below)
+static long long arena_bytes(const SrvCaps &c) {
+    auto r = [](long long b) { return (b + 255) / 256 * 256; };
+    const long long chunks = c.rows / 64;
+    const long long esz = c.dtype == ABILU_F64 ? 8 : (c.dtype == ABILU_F32 ? 4 : 2);
+    const long long vt = c.dtype == ABILU_F64 ? 8 : 4;
+    const bool narrow = c.dtype != ABILU_F64;
+    long long b = 0;
+    // batch arrays
+    b += r(4 * (c.rows + 70)) + r(4 * (c.blocks + 4)) + r(8 * BB * c.blocks) + 2 * r(8 * BS * c.rows);
+    b += r(4 * (chunks + 1)) + 2 * r(4 * (c.sys + 1)) + r((long long)sizeof(BState) * c.sys);
+    b += r(8 * PSTRIDE * (chunks + 1)) + r(16) + r(4 * (chunks + 1));
+    b += r(8 * BS * c.rows * (2 * (long long)c.restart + 2));   // Krylov workspace
+    // pattern arrays
+    b += r(4 * c.rows) + 2 * r(4 * (c.rows + 70)) + r(4 * (c.nl + 8)) + r(4 * (c.nu + 8));
+    b += r(4 * (c.blocks + 2)) + r(8 * (c.pairs + 1)) + r(32 * (c.work + 1)) + r(4 * (c.blocks + 1));
+    // factors (abilu_factors_create's single allocation)
+    const long long bl = r(esz * BB * c.nl), bu = r(esz * BB * c.nu), bd = r(esz * BB * c.rows);
+    const long long bv = r(vt * BS * c.rows);
+    b += 2 * bl + 2 * bu + 3 * bd + 4 * bv + r(8 * 8) + r((long long)solve_state_bytes()) +
+         r(8LL * 66 * red_ctas()) + (narrow ? r(4 * BB * c.blocks) + r(4 * BS * c.rows) : 0) +
+         (c.dtype == ABILU_F32 ? bu : 0) + r(4 * ((c.work + 31) / 32 + 1));
+    return b;
+}
+
+extern "C" abilu_status abilu_server_arena_bytes(const abilu_server_opts *o, int64_t *bytes) {
+    if (!bytes) return fail(ABILU_EINVAL, "server_arena_bytes: NULL argument");
+    SrvCaps c;
+    abilu_status s = server_caps(o, &c);
+    if (s != ABILU_OK) return s;
+    *bytes = arena_bytes(c);
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_server_create(const abilu_server_opts *o, abilu_stream stream,
+                                            abilu_server *out) {
+    if (!out) return fail(ABILU_EINVAL, "server_create: out is NULL");
+    *out = nullptr;
+    SrvCaps c;
+    abilu_status s = server_caps(o, &c);
+    if (s != ABILU_OK) return s;
+    cudaStream_t st = S(stream);
+    abilu_server sv = new abilu_server_s();
+    sv->cap = c;
+    sv->next_id = 0;
+    cudaGetDevice(&sv->device);
+    abilu_batch b = new abilu_batch_s();
+    sv->b = b;
+    b->arena = 1;
+    b->no_graph = 1;   // the layout changes between steps; host-driven cycles
+    b->nsys = 0;
+    b->chunk0.push_back(0);
+    const long long chunks = c.rows / 64;
+    auto cu = [&](cudaError_t e, const char *w) -> abilu_status {
+        return e == cudaSuccess ? ABILU_OK : cuda_fail(e, w);
+    };
+    auto alloc = [&](std::vector<void *> &v, void **p, size_t bytes) -> abilu_status {
+        cudaError_t e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "server_create: cudaMalloc");
+        v.push_back(*p);
+        return ABILU_OK;
+    };
+#define TRY(x)                                                  \
+    do {                                                        \
+        abilu_status s_ = (x);                                  \
+        if (s_ != ABILU_OK) { server_free(sv); return s_; }     \
+    } while (0)
+    std::vector<void *> &ba = b->allocs;
+    TRY(alloc(ba, (void **)&b->rowptr, sizeof(int32_t) * (c.rows + 70)));
+    TRY(alloc(ba, (void **)&b->colind, sizeof(int32_t) * (c.blocks + 4)));
+    TRY(alloc(ba, (void **)&b->A, sizeof(double) * BB * c.blocks));
+    TRY(alloc(ba, (void **)&b->b, sizeof(double) * BS * c.rows));
+    TRY(alloc(ba, (void **)&b->x, sizeof(double) * BS * c.rows));
+    TRY(alloc(ba, (void **)&b->chunk_sys, sizeof(int) * (chunks + 1)));
+    TRY(alloc(ba, (void **)&b->sys_chunk0, sizeof(int) * (c.sys + 1)));
+    TRY(alloc(ba, (void **)&b->S, sizeof(BState) * c.sys));
+    TRY(alloc(ba, (void **)&b->partials, sizeof(double) * PSTRIDE * (chunks + 1)));
+    TRY(alloc(ba, (void **)&b->sys_done, sizeof(int) * (c.sys + 1)));
+    TRY(alloc(ba, (void **)&b->bflag, sizeof(int) * 4));
+    TRY(alloc(ba, (void **)&sv->chunk_init, sizeof(int) * (chunks + 1)));
+    TRY(cu(cudaMalloc(&b->krylov, sizeof(double) * BS * c.rows * (2 * (size_t)c.restart + 2)),
+           "server_create: Krylov workspace"));
+    b->krylov_m = c.restart;
+    TRY(cu(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "stream"));
+    TRY(cu(cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking), "stream"));
+    TRY(cu(cudaHostAlloc((void **)&b->hs_done, sizeof(int) * c.sys, cudaHostAllocMapped), "hostalloc"));
+    TRY(cu(cudaHostAlloc((void **)&b->hs_fin, sizeof(int) * c.sys, cudaHostAllocMapped), "hostalloc"));
+    // staging: chunk_sys [chunks], sys_chunk0 [systems + 1], chunk_init [chunks]
+    TRY(cu(cudaHostAlloc((void **)&sv->staging, sizeof(int) * (2 * chunks + c.sys + 1),
+                         cudaHostAllocDefault), "hostalloc"));
+    // the arena's pattern: arrays with the capacities, analysed by relocation
+    abilu_pattern p = new abilu_pattern_s();
+    memset(&p->v, 0, sizeof p->v);
+    auto pv = new std::vector<void *>();
+    p->mem = pv;
+    p->device = sv->device;
+    b->pat = p;
+    int32_t *diagpos, *lrow, *urow, *lcol, *ucol, *pair_ptr, *wpos;
+    int2 *pairs;
+    WorkItem *work;
+    TRY(alloc(*pv, (void **)&diagpos, sizeof(int32_t) * c.rows));
+    TRY(alloc(*pv, (void **)&lrow, sizeof(int32_t) * (c.rows + 70)));
+    TRY(alloc(*pv, (void **)&urow, sizeof(int32_t) * (c.rows + 70)));
+    TRY(alloc(*pv, (void **)&lcol, sizeof(int32_t) * (c.nl + 8)));
+    TRY(alloc(*pv, (void **)&ucol, sizeof(int32_t) * (c.nu + 8)));
+    TRY(alloc(*pv, (void **)&pair_ptr, sizeof(int32_t) * (c.blocks + 2)));
+    TRY(alloc(*pv, (void **)&pairs, sizeof(int2) * (c.pairs + 1)));
+    TRY(alloc(*pv, (void **)&work, sizeof(WorkItem) * (c.work + 1)));
+    TRY(alloc(*pv, (void **)&wpos, sizeof(int32_t) * (c.blocks + 1)));
+    p->v.rowptr = b->rowptr;
+    p->v.colind = b->colind;
+    p->v.diagpos = diagpos;
+    p->v.lrow = lrow;
+    p->v.urow = urow;
+    p->v.lcol = lcol;
+    p->v.ucol = ucol;
+    p->v.pair_ptr = pair_ptr;
+    p->v.pairs = pairs;
+    p->v.work = work;
+    p->v.wpos = wpos;
+    // factor storage for the capacities, then the pattern is empty until a step
+    p->v.n = (int32_t)c.rows;
+    p->v.nnzb = (int32_t)c.blocks;
+    p->v.nl = (int32_t)c.nl;
+    p->v.nu = (int32_t)c.nu;
+    p->v.nwork = (int32_t)c.work;
+    TRY(abilu_factors_create(p, c.dtype, &b->fac));
+    p->v.n = p->v.nnzb = p->v.nl = p->v.nu = p->v.nwork = 0;
+    p->v.npairs = 0;
+    TRY(cu(cudaMemsetAsync(b->A, 0, sizeof(double) * BB * c.blocks, st), "memset A"));
+    TRY(cu(cudaStreamSynchronize(st), "sync"));
+#undef TRY
+    *out = sv;
+    return ABILU_OK;
+}
+
+static void server_totals(const abilu_server sv, long long t[7]) {
+    for (int k = 0; k < 7; k++) t[k] = 0;
+    for (const auto &m : sv->mem) {
+        t[0] += m.np;
+        t[1] += m.blocks_p();
+        t[2] += m.nl;
+        t[3] += m.nu;
+        t[4] += m.npairs;
+        t[5] += m.work_p();
+        t[6] += 1;
+    }
+}
+
+extern "C" abilu_status abilu_server_usage(abilu_server sv, int64_t *out) {
+    if (!sv || !out) return fail(ABILU_EINVAL, "server_usage: NULL argument");
+    const SrvCaps &c = sv->cap;
+    const long long cap[7] = {c.rows, c.blocks, c.nl, c.nu, c.pairs, c.work, c.sys};
+    long long t[7];
+    server_totals(sv, t);
+    for (int k = 0; k < 7; k++) {
+        out[k] = cap[k];
+        out[7 + k] = t[k];
+    }
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_server_add(abilu_server sv, int32_t n, int32_t nnzb,
+                                         const int32_t *rowptr, const int32_t *colind,
+                                         abilu_stream stream, int32_t *id) {
+    if (!sv || !rowptr || !colind || !id) return fail(ABILU_EINVAL, "server_add: NULL argument");
+    if (n < 1 || nnzb < n) return fail(ABILU_EINVAL, "server_add: need n >= 1 and nnzb >= n");
+    const SrvCaps &c = sv->cap;
+    long long t[7];
+    server_totals(sv, t);
+    const long long np = rnd64(n), bp = nnzb + (np - n);
+    if (t[6] + 1 > c.sys || t[0] + np > c.rows || t[1] + bp > c.blocks)
+        return fail(ABILU_ENOMEM, "server_add: the arena has no room for %d cells / %d blocks now "
+                    "(%lld of %lld rows, %lld of %lld blocks, %lld of %d systems in use)", n, nnzb,
+                    t[0], c.rows, t[1], c.blocks, t[6], c.sys);
+    abilu_pattern p = nullptr;
+    abilu_status s = abilu_pattern_create(n, nnzb, rowptr, colind, stream, &p);
+    if (s != ABILU_OK) return s;
+    SrvMember m = {};
+    m.id = sv->next_id;
+    m.p = p;
+    m.n = n;
+    m.nnzb = nnzb;
+    m.np = (int)np;
+    m.nl = p->v.nl;
+    m.nu = p->v.nu;
+    m.npairs = (int)p->v.npairs;
+    m.nwork = p->v.nwork;
+    m.max_row = p->max_row;
+    if (t[2] + m.nl > c.nl || t[3] + m.nu > c.nu || t[4] + m.npairs > c.pairs ||
+        t[5] + m.work_p() > c.work) {
+        abilu_pattern_destroy(p);
+        return fail(ABILU_ENOMEM, "server_add: the arena has no room for the system's L/U blocks, "
+                    "product pairs or work items now");
+    }
+    sv->next_id++;
+    sv->mem.push_back(m);
+    *id = m.id;
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_server_remove(abilu_server sv, int32_t id) {
+    if (!sv) return fail(ABILU_EINVAL, "server_remove: NULL server");
+    for (size_t k = 0; k < sv->mem.size(); k++) {
+        if (sv->mem[k].id != id) continue;
+        abilu_pattern_destroy(sv->mem[k].p);
+        sv->mem.erase(sv->mem.begin() + (long)k);
+        return ABILU_OK;
+    }
+    return fail(ABILU_EINVAL, "server_remove: no system %d", id);
+}
+
+// Lay the systems `order` (indices into sv->mem) out packed, as described
+// above.  Asynchronous on st.
+static abilu_status server_relayout(abilu_server sv, const std::vector<int> &order,
+                                    cudaStream_t st) {
+    abilu_batch b = sv->b;
+    abilu_factors f = b->fac;
+    abilu_pattern P = b->pat;
+    const int k = (int)order.size();
+    std::vector<Reloc> rel(k);
+    long long R = 0, B = 0, Lb = 0, Ub = 0, Pb = 0, Wb = 0;
+    int maxrow = 0;
+    for (int q = 0; q < k; q++) {
+        const SrvMember &m = sv->mem[order[q]];
+        rel[q] = Reloc{(int)R, m.n, m.np, (int)B, m.nnzb, (int)Lb, m.nl, (int)Ub, m.nu, (int)Pb,
+                       m.npairs, (int)Wb, m.nwork};
+        R += m.np;
+        B += m.blocks_p();
+        Lb += m.nl;
+        Ub += m.nu;
+        Pb += m.npairs;
+        Wb += m.work_p();
+        maxrow = m.max_row > maxrow ? m.max_row : maxrow;
+    }
+    // the warm factors of continuing systems: current buffer, old place ->
+    // other buffer, new place
+    const int c = f->cur, o = 1 - c;
+    const size_t eb = f->esz * BB;
+    char **L = reinterpret_cast<char **>(f->L), **U = reinterpret_cast<char **>(f->U);
+    char **D = reinterpret_cast<char **>(f->D);
+    for (int q = 0; q < k; q++) {
+        const SrvMember &m = sv->mem[order[q]];
+        if (!m.laid || !m.warm) continue;
+        if (m.nl)
+            ABILU_CUDA(cudaMemcpyAsync(L[o] + rel[q].Lb * eb, L[c] + (size_t)m.Lb * eb, m.nl * eb,
+                                       cudaMemcpyDeviceToDevice, st));
+        if (m.nu)
+            ABILU_CUDA(cudaMemcpyAsync(U[o] + rel[q].Ub * eb, U[c] + (size_t)m.Ub * eb, m.nu * eb,
+                                       cudaMemcpyDeviceToDevice, st));
+        ABILU_CUDA(cudaMemcpyAsync(D[o] + (size_t)rel[q].R * eb, D[c] + (size_t)m.R * eb,
+                                   (size_t)m.np * eb, cudaMemcpyDeviceToDevice, st));
+    }
+    f->cur = o;
+    PatternView &v = P->v;
+    for (int q = 0; q < k; q++) {
+        const SrvMember &m = sv->mem[order[q]];
+        const Reloc &r = rel[q];
+        long long work = r.np + 1;
+        if (r.nnzb + (r.np - r.n) + 1 > work) work = r.nnzb + (r.np - r.n) + 1;
+        if (r.nwork + (r.np - r.n) > work) work = r.nwork + (r.np - r.n);
+        if (r.npairs > work) work = r.npairs;
+        int grid = (int)((work + 255) / 256);
+        if (grid > 4 * red_ctas()) grid = 4 * red_ctas();
+        k_relocate<<<counted(grid), 256, 0, st>>>(
+            m.p->v, r, b->rowptr, b->colind, const_cast<int32_t *>(v.diagpos),
+            const_cast<int32_t *>(v.lrow), const_cast<int32_t *>(v.urow),
+            const_cast<int32_t *>(v.lcol), const_cast<int32_t *>(v.ucol),
+            const_cast<int32_t *>(v.pair_ptr), const_cast<int2 *>(v.pairs),
+            const_cast<WorkItem *>(v.work), const_cast<int32_t *>(v.wpos), b->A, b->b);
+        ABILU_LAUNCH_CHECK("k_relocate");
+    }
+    // chunk tables
+    const int nck = (int)(R / 64);
+    int *h_chunk_sys = sv->staging, *h_c0 = sv->staging + sv->cap.rows / 64;
+    for (int q = 0; q < k; q++) {
+        const int c0 = rel[q].R / 64, c1 = c0 + rel[q].np / 64;
+        for (int ch = c0; ch < c1; ch++) h_chunk_sys[ch] = q;
+        h_c0[q] = c0;
+    }
+    h_c0[k] = nck;
+    ABILU_CUDA(cudaMemcpyAsync(b->chunk_sys, h_chunk_sys, sizeof(int) * nck, cudaMemcpyHostToDevice, st));
+    ABILU_CUDA(cudaMemcpyAsync(b->sys_chunk0, h_c0, sizeof(int) * (k + 1), cudaMemcpyHostToDevice, st));
+    // the batch's sizes and per-system tables, the pattern's counts
+    b->nsys = k;
+    b->rows = (int)R;
+    b->blocks = (int)B;
+    b->nchunks = nck;
+    b->n.assign(k, 0);
+    b->nnzb.assign(k, 0);
+    b->row_off.assign(k, 0);
+    b->nnz_off.assign(k, 0);
+    b->chunk0.assign(k + 1, nck);
+    for (int q = 0; q < k; q++) {
+        SrvMember &m = sv->mem[order[q]];
+        const Reloc &r = rel[q];
+        b->n[q] = m.n;
+        b->nnzb[q] = m.nnzb;
+        b->row_off[q] = r.R;
+        b->nnz_off[q] = r.B;
+        b->chunk0[q] = r.R / 64;
+        m.R = r.R;
+        m.B = r.B;
+        m.Lb = r.Lb;
+        m.Ub = r.Ub;
+        m.Pb = r.Pb;
+        m.Wb = r.Wb;
+        m.laid = 1;
+    }
+    v.n = (int32_t)R;
+    v.nnzb = (int32_t)B;
+    v.nl = (int32_t)Lb;
+    v.nu = (int32_t)Ub;
+    v.npairs = Pb;
+    v.nwork = (int32_t)Wb;
+    P->max_row = maxrow;
+    sv->layout.clear();
+    for (int q = 0; q < k; q++) sv->layout.push_back(sv->mem[order[q]].id);
+    return ABILU_OK;
+}
+
+extern "C" abilu_status abilu_server_step(abilu_server sv, int32_t k, const int32_t *ids,
+                                          const double *const *A, const double *const *rhs,
+                                          double *const *x, const fgmres_opts *opts,
+                                          fgmres_result *res, abilu_stream stream) {
+    if (!sv || !ids || !A || !rhs || !x || !opts || !res)
+        return fail(ABILU_EINVAL, "server_step: NULL argument");
+    if (k < 1 || k != (int)sv->mem.size())
+        return fail(ABILU_EINVAL, "server_step: the step must list every admitted system once "
+                    "(%d listed, %zu admitted)", k, sv->mem.size());
+    if (!opts->build) return fail(ABILU_EINVAL, "server_step: every step builds (opts->build = 1)");
+    cudaStream_t st = S(stream);
+    std::vector<int> order(k);
+    for (int q = 0; q < k; q++) {
+        int idx = -1;
+        for (size_t t = 0; t < sv->mem.size(); t++)
+            if (sv->mem[t].id == ids[q]) idx = (int)t;
+        if (idx < 0) return fail(ABILU_EINVAL, "server_step: system %d is not admitted", ids[q]);
+        for (int t = 0; t < q; t++)
+            if (order[t] == idx) return fail(ABILU_EINVAL, "server_step: system %d listed twice", ids[q]);
+        if (!A[q] || !rhs[q] || !x[q]) return fail(ABILU_EINVAL, "server_step: NULL array of system %d", ids[q]);
+        order[q] = idx;
+    }
+    bool same = (int)sv->layout.size() == k;
+    for (int q = 0; same && q < k; q++) same = sv->layout[q] == ids[q];
+    abilu_status s;
+    if (!same && (s = server_relayout(sv, order, st)) != ABILU_OK) return s;
+    abilu_batch b = sv->b;
+    // this step's values and right-hand sides (device or pinned host memory)
+    for (int q = 0; q < k; q++) {
+        const SrvMember &m = sv->mem[order[q]];
+        ABILU_CUDA(cudaMemcpyAsync(b->A + (size_t)m.B * BB, A[q], sizeof(double) * BB * m.nnzb,
+                                   cudaMemcpyDefault, st));
+        ABILU_CUDA(cudaMemcpyAsync(b->b + (size_t)m.R * BS, rhs[q], sizeof(double) * BS * m.n,
+                                   cudaMemcpyDefault, st));
+    }
+    // new systems start from A, continuing ones from their factors (warm start)
+    int *h_init = sv->staging + sv->cap.rows / 64 + sv->cap.sys + 1;
+    for (int q = 0; q < k; q++) {
+        const SrvMember &m = sv->mem[order[q]];
+        for (int ch = m.R / 64; ch < (m.R + m.np) / 64; ch++) h_init[ch] = m.warm ? 0 : 1;
+    }
+    ABILU_CUDA(cudaMemcpyAsync(sv->chunk_init, h_init, sizeof(int) * b->nchunks,
+                               cudaMemcpyHostToDevice, st));
+    b->fac->chunk_init = sv->chunk_init;
+    fgmres_opts o = *opts;
+    o.init = ABILU_INIT_FROM_A;
+    s = batch_solve_core(b, &o, res, st);
+    b->fac->chunk_init = nullptr;
+    if (s != ABILU_OK && s != ABILU_ENOCONV && s != ABILU_WARN_SINGULAR) return s;
+    for (int q = 0; q < k; q++) {
+        SrvMember &m = sv->mem[order[q]];
+        ABILU_CUDA(cudaMemcpyAsync(x[q], b->x + (size_t)m.R * BS, sizeof(double) * BS * m.n,
+                                   cudaMemcpyDefault, st));
+        m.warm = 1;
+    }
+    ABILU_CUDA(cudaStreamSynchronize(st));
+    return s;
 }

@@ -33,6 +33,7 @@ template <> struct BuildArith<double> { using C = double; };
 
 constexpr int BUILD_THREADS = 256;
 constexpr int BUILD_ROWS = BUILD_THREADS / 4;  // rows per CTA (= chunk of the async queue)
+static_assert(BUILD_ROWS == SKIP_CHUNK_ROWS, "a build CTA's rows are one 64-row chunk");
 
 // Inverse of a 4x4 block by the adjugate: Laplace expansion by the 2x2 minors
 // of rows {0,1} and {2,3}; inverse = adj / det.  det == 0 or non-finite marks
@@ -524,9 +525,12 @@ template <typename T>
 __global__ void __launch_bounds__(BUILD_THREADS, sizeof(T) == 8 ? 3 : 4)
 k_build_prepare(PatternView P, const double *__restrict__ A, float *__restrict__ A32,
                 T *__restrict__ L, T *__restrict__ U, T *__restrict__ Uother, T *__restrict__ D,
-                T *__restrict__ Udiag, int init_from_a, unsigned long long *nsing) {
+                T *__restrict__ Udiag, int init_all, const int *__restrict__ chunk_init,
+                unsigned long long *nsing) {
     pdl_wait();
     pdl_trigger();
+    // a CTA's 64 rows are one chunk of a server's arena (BUILD_ROWS = 64)
+    const int init_from_a = chunk_init ? chunk_init[blockIdx.x] : init_all;
     __shared__ double sh_u[BuildShared<T>::D];
     __shared__ double sh_d[BuildShared<T>::D];
     __shared__ __align__(16) float sh_q[BuildShared<T>::F];
@@ -743,7 +747,7 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
     const int c = f->cur;
     launch_pdl(k_build_prepare<T>, grid, BUILD_THREADS, 0, st,
         P, A, A32, L[c], U[c], mode == ABILU_SYNC ? U[1 - c] : nullptr, D[c], Ud,
-        init == ABILU_INIT_FROM_A ? 1 : 0, f->ctr);
+        init == ABILU_INIT_FROM_A ? 1 : 0, f->chunk_init, f->ctr);
     ABILU_LAUNCH_CHECK("k_build_prepare");
     if constexpr (narrow) {
         if (nsweeps > 0) {

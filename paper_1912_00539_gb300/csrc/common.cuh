@@ -115,6 +115,10 @@ struct abilu_factors_s {
     unsigned long long spin_limit;
     int stall_flags;           // failure injection: the next ordered async build's chunk
                                // flags start one sweep behind (abilu_factors_inject_stall)
+    // per 64-row chunk (device, NULL: the build's init for every row): 1 = the
+    // chunk's rows start from A, 0 = from the factors in place (the systems of
+    // a server step: new ones from A, continuing ones warm-started)
+    const int *chunk_init;
     void *mem;
 };
 

@@ -94,12 +94,24 @@ def test_batch_specs_ranges():
     assert all(10 <= s["cfl"] <= 1e4 for s in specs)
 
 
-def test_serving_footprint_model():
+def test_server_arena_sizing():
+    """The server's arena bytes grow linearly with its capacity, shrink with
+    narrower factors, and the budget sizing picks the largest arena that fits
+    (host arithmetic only, no GPU call)."""
     import __graft_entry__ as g
     g._build_ext().build()              # the package loads the CUDA library (no GPU call here)
-    from paper_1912_00539_gb300.serving import footprint_bytes as fb
-    small, big = fb(1000, 4000), fb(100000, 400000)
-    assert 90 * small < big < 110 * small
-    assert fb(1000, 4000, "f64") > fb(1000, 4000, "f32") > fb(1000, 4000, "bf16")
-    # 512x512 grid: a couple of GB
-    assert 1e9 < fb(524288, 2095104) < 4e9
+    import paper_1912_00539_gb300.abilu as ab
+    from paper_1912_00539_gb300 import serving
+    small = ab.server_arena_bytes(64 * 1000, 4 * 64 * 1000)
+    big = ab.server_arena_bytes(64 * 100000, 4 * 64 * 100000)
+    assert 95 * small < big < 101 * small
+    f64, f32, bf16 = (ab.server_arena_bytes(65536, 262144, dtype=d) for d in ("f64", "f32", "bf16"))
+    assert f64 > f32 > bf16
+    # the Krylov basis of FGMRES(30), 62 vectors of 32 bytes per cell, dominates
+    assert 62 * 32 * 65536 < f32 < 2.5 * 62 * 32 * 65536
+    for budget in (3e8, 4e9):
+        c = serving.arena_cells_for_budget(budget)
+        assert c % 64 == 0
+        assert ab.server_arena_bytes(c, int(4.2 * c)) <= budget
+        assert ab.server_arena_bytes(c + 64, int(4.2 * (c + 64))) > budget
+    assert serving.arena_cells_for_budget(1e3) == 0
