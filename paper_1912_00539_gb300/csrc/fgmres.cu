@@ -196,13 +196,16 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
 
 // Partial dot products of K consecutive basis vectors with w for this CTA.
 // K is a compile-time width so no predicated-off FP64 FMA is issued.
-template <int K, bool PIPE>
+// NORM: also ||w||^2 in the same pass (slot K of the accumulators; its
+// partial goes to slot MAXM + 1), for the single-reduction step.
+template <int K, bool PIPE, bool NORM = false>
 __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long long nv2,
                                           int k0, const double2 *__restrict__ w2,
                                           double *sh_w, double *sh_o, double *partials) {
-    double acc[K];
+    constexpr int KA = K + (NORM ? 1 : 0);
+    double acc[KA];
 #pragma unroll
-    for (int k = 0; k < K; k++) acc[k] = 0.0;
+    for (int k = 0; k < KA; k++) acc[k] = 0.0;
     const long long st = (long long)gridDim.x * blockDim.x;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     // PIPE (the kernels of one to four basis vectors): software-pipelined, the
@@ -228,6 +231,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
                 }
 #pragma unroll
                 for (int k = 0; k < K; k++) acc[k] = fma(vc[k].y, wc.y, fma(vc[k].x, wc.x, acc[k]));
+                if constexpr (NORM) acc[K] = fma(wc.y, wc.y, fma(wc.x, wc.x, acc[K]));
                 e = en;
                 if (e >= nv2) break;
             }
@@ -249,6 +253,10 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
                 acc[k] = fma(va[k].y, wa.y, fma(va[k].x, wa.x, acc[k]));
                 acc[k] = fma(vb[k].y, wb.y, fma(vb[k].x, wb.x, acc[k]));
             }
+            if constexpr (NORM) {
+                acc[K] = fma(wa.y, wa.y, fma(wa.x, wa.x, acc[K]));
+                acc[K] = fma(wb.y, wb.y, fma(wb.x, wb.x, acc[K]));
+            }
         }
     }
     for (; e < nv2; e += st) {   // wide tiles (K + 1 loads in flight already) and tails
@@ -258,9 +266,47 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
             const double2 v = V2[(size_t)(k0 + k) * nv2 + e];
             acc[k] = fma(v.y, wv.y, fma(v.x, wv.x, acc[k]));
         }
+        if constexpr (NORM) acc[K] = fma(wv.y, wv.y, fma(wv.x, wv.x, acc[K]));
     }
-    block_sum<K, false>(acc, sh_w, sh_o, K);   // k_dots is held to 64 registers
+    block_sum<KA, false>(acc, sh_w, sh_o, KA);   // k_dots is held to 64 registers
     if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
+    if (NORM && threadIdx.x == 0) partials[(size_t)blockIdx.x * (MAXM + 2) + MAXM + 1] = sh_o[K];
+}
+
+// The Givens update of column j of the Hessenberg matrix (from the
+// Gram-Schmidt coefficients h, plus h2 after a second pass) with
+// h_{j+1,j} = hn, the residual estimate and the end-of-cycle test.  One
+// thread of the last CTA.
+__device__ __forceinline__ void givens_column(SolveState *S, int j, int two_pass, double hn) {
+    // the previous rotations, i = 0 .. j-1, each mixing entries i and i+1 of
+    // the new column: entry i+1 is still the Gram-Schmidt coefficient when
+    // rotation i reaches it, so one carried value replaces a column array
+    // (which lived in local memory)
+    double a = S->h[0] + (two_pass ? S->h2[0] : 0.0);
+    for (int i = 0; i < j; i++) {
+        const double c = S->h[i + 1] + (two_pass ? S->h2[i + 1] : 0.0);
+        S->H[i * MAXM + j] = S->cs[i] * a + S->sn[i] * c;
+        a = -S->sn[i] * a + S->cs[i] * c;
+    }
+    const double c = hn;
+    const double d = sqrt(a * a + c * c);
+    double cs = 1.0, sn = 0.0;
+    if (d != 0.0) { cs = a / d; sn = c / d; }
+    S->cs[j] = cs;
+    S->sn[j] = sn;
+    S->H[j * MAXM + j] = cs * a + sn * c;
+    const double gj = S->g[j];
+    S->g[j + 1] = -sn * gj;
+    S->g[j] = cs * gj;
+    S->iters += 1;
+    S->kdim = j + 1;
+    S->est = fabs(S->g[j + 1]) / S->bnorm;
+    S->breakdown = hn == 0.0 ? 1 : 0;
+    S->done = (fabs(S->g[j + 1]) <= S->rtol * S->bnorm || hn == 0.0 ||
+               S->iters >= S->max_iters || j + 1 >= S->m) ? 1 : 0;
+    S->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
+    S->counter = 0;
+    publish(S);
 }
 
 // h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2).  The grid is
@@ -318,6 +364,164 @@ static void launch_dots(int nred, cudaStream_t st, const double *V, long long nv
         launch_pdl(k_dots<4>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
     else
         launch_pdl(k_dots<0>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
+}
+
+// Single-reduction Gram-Schmidt step (one classical pass, the solve's default):
+// h[k] = <V_k, w> for k < jp1 and ||w||^2 in one pass over V_0..V_j and w;
+// the last CTA forms h_{j+1,j} = sqrt(||w||^2 - sum_k h_k^2) (Pythagoras: w - V h
+// is orthogonal to V_0..V_j when they are orthonormal) and the Givens update of
+// column j, so the norm needs neither a pass over the updated w nor a second
+// reduction.  A difference below 1e-12 ||w||^2 (more than twelve digits
+// cancelled, or negative) is taken as a breakdown: the cycle ends at this
+// column and the explicit FP64 residual at its end decides whether it
+// restarts.  NW as in k_dots.
+template <int NW>
+__global__ void __launch_bounds__(RED_THREADS, 4)
+k_dots_norm(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
+            SolveState *S, double *partials) {
+    pdl_wait();
+    pdl_trigger();
+    if (S->done) return;   // set by an earlier kernel: a plain load
+    constexpr int T = NW > 0 ? NW : TILE;
+    __shared__ double sh_w[RED_WARPS * (T + 1)], sh_o[T + 1];
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    const double2 *V2 = reinterpret_cast<const double2 *>(V);
+    if constexpr (NW > 0) {
+        dots_tile<NW, true, true>(V2, nv2, 0, w2, sh_w, sh_o, partials);
+    } else {
+        // the norm with the last tile (the first ones are full)
+        for (int k0 = 0; k0 < jp1; k0 += TILE) {
+            const int kn = jp1 - k0 < TILE ? jp1 - k0 : TILE;
+            if (k0 + TILE < jp1) {
+                dots_tile<TILE, false>(V2, nv2, k0, w2, sh_w, sh_o, partials);
+                continue;
+            }
+            switch (kn) {
+            case 1: dots_tile<1, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 2: dots_tile<2, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 3: dots_tile<3, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 4: dots_tile<4, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            case 5: dots_tile<5, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            default: dots_tile<6, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
+            }
+        }
+    }
+    if (!last_cta(S)) return;
+    for (int k0 = 0; k0 < jp1; k0 += T) {
+        const int kn = jp1 - k0 < T ? jp1 - k0 : T;
+        reduce_partials<T>(partials, MAXM + 2, k0, kn, sh_w, sh_o);
+        if (threadIdx.x < kn) S->h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        __syncthreads();
+    }
+    reduce_partials<1>(partials, MAXM + 2, MAXM + 1, 1, sh_w, sh_o);
+    if (threadIdx.x != 0) return;
+    const double ww = sh_o[0];
+    double hh = 0.0;
+    for (int k = 0; k < jp1; k++) hh = fma(S->h[k], S->h[k], hh);
+    const double d = ww - hh;
+    givens_column(S, jp1 - 1, 0, d > 1e-12 * ww ? sqrt(d) : 0.0);
+}
+
+static void launch_dots_norm(int nred, cudaStream_t st, const double *V, long long nv2, int jp1,
+                             const double *w, SolveState *S, double *partials) {
+    if (jp1 == 1)
+        launch_pdl(k_dots_norm<1>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
+    else if (jp1 == 2)
+        launch_pdl(k_dots_norm<2>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
+    else if (jp1 == 3)
+        launch_pdl(k_dots_norm<3>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
+    else if (jp1 == 4)
+        launch_pdl(k_dots_norm<4>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
+    else
+        launch_pdl(k_dots_norm<0>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
+}
+
+// v_{j+1} = (w - sum_k h[k] V_k) * hn_inv and its FP32 copy (the next
+// preconditioner's input) in one pass; w itself is not written back.  J =
+// 1 .. 3: j + 1 == J, software-pipelined like update_pipelined; 0: any j.
+template <int J>
+__global__ void __launch_bounds__(RED_THREADS, 4)
+k_update_scale(const double *__restrict__ V, long long nv2, int j, const double *__restrict__ w,
+               double *__restrict__ vnext, float *__restrict__ v32, SolveState *S) {
+    pdl_wait();
+    pdl_trigger();
+    if (S->done) return;   // the cycle ended at this column: no next vector
+    __shared__ double sh_h[MAXM + 1];
+    const int jp1 = j + 1;
+    for (int k = threadIdx.x; k < jp1; k += blockDim.x) sh_h[k] = S->h[k];
+    __syncthreads();
+    const double sc = S->hn_inv;
+    const double2 *w2 = reinterpret_cast<const double2 *>(w);
+    const double2 *V2 = reinterpret_cast<const double2 *>(V);
+    double2 *o2 = reinterpret_cast<double2 *>(vnext);
+    float2 *o32 = reinterpret_cast<float2 *>(v32);
+    const long long st = (long long)gridDim.x * blockDim.x;
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    auto out = [&](long long i, double2 t) {
+        const double2 r = make_double2(t.x * sc, t.y * sc);
+        o2[i] = r;
+        if (v32) o32[i] = make_float2(to_f32_int(r.x), to_f32_int(r.y));
+    };
+    if constexpr (J > 0) {
+        if (e >= nv2) return;
+        double h[J];
+#pragma unroll
+        for (int k = 0; k < J; k++) h[k] = sh_h[k];
+        double2 wn = w2[e], vn[J];
+#pragma unroll
+        for (int k = 0; k < J; k++) vn[k] = V2[(size_t)k * nv2 + e];
+        for (;;) {
+            double2 t = wn, vc[J];
+#pragma unroll
+            for (int k = 0; k < J; k++) vc[k] = vn[k];
+            const long long en = e + st;
+            if (en < nv2) {
+                wn = w2[en];
+#pragma unroll
+                for (int k = 0; k < J; k++) vn[k] = V2[(size_t)k * nv2 + en];
+            }
+#pragma unroll
+            for (int k = 0; k < J; k++) {
+                t.x -= h[k] * vc[k].x;
+                t.y -= h[k] * vc[k].y;
+            }
+            out(e, t);
+            e = en;
+            if (e >= nv2) break;
+        }
+        return;
+    }
+    for (; e + st < nv2; e += 2 * st) {  // two grid strides per iteration
+        double2 ta = w2[e], tb = w2[e + st];
+        for (int k = 0; k < jp1; k++) {
+            const double2 va = V2[(size_t)k * nv2 + e], vb = V2[(size_t)k * nv2 + e + st];
+            ta.x -= sh_h[k] * va.x;
+            ta.y -= sh_h[k] * va.y;
+            tb.x -= sh_h[k] * vb.x;
+            tb.y -= sh_h[k] * vb.y;
+        }
+        out(e, ta);
+        out(e + st, tb);
+    }
+    if (e < nv2) {
+        double2 t = w2[e];
+        for (int k = 0; k < jp1; k++) {
+            const double2 v = V2[(size_t)k * nv2 + e];
+            t.x -= sh_h[k] * v.x;
+            t.y -= sh_h[k] * v.y;
+        }
+        out(e, t);
+    }
+}
+
+static void launch_update_scale(int nred, cudaStream_t st, const double *V, long long nv2, int j,
+                                const double *w, double *vnext, float *v32, SolveState *S) {
+    switch (j + 1) {
+    case 1: launch_pdl(k_update_scale<1>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
+    case 2: launch_pdl(k_update_scale<2>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
+    case 3: launch_pdl(k_update_scale<3>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
+    default: launch_pdl(k_update_scale<0>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
+    }
 }
 
 // w_e -= sum_k h[k] V_k,e for this thread's elements e (grid stride), J = j + 1
@@ -416,36 +620,7 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
     if (!last_cta(S)) return;
     reduce_partials<1>(partials, MAXM + 2, MAXM + 1, 1, sh_w, sh_o);
     if (threadIdx.x != 0) return;
-    const double hn = sqrt(sh_o[0]);
-    // the previous rotations, i = 0 .. j-1, each mixing entries i and i+1 of
-    // the new column: entry i+1 is still the Gram-Schmidt coefficient when
-    // rotation i reaches it, so one carried value replaces a column array
-    // (which lived in local memory)
-    double a = S->h[0] + (pass == 1 ? S->h2[0] : 0.0);
-    for (int i = 0; i < j; i++) {
-        const double c = S->h[i + 1] + (pass == 1 ? S->h2[i + 1] : 0.0);
-        S->H[i * MAXM + j] = S->cs[i] * a + S->sn[i] * c;
-        a = -S->sn[i] * a + S->cs[i] * c;
-    }
-    const double c = hn;
-    const double d = sqrt(a * a + c * c);
-    double cs = 1.0, sn = 0.0;
-    if (d != 0.0) { cs = a / d; sn = c / d; }
-    S->cs[j] = cs;
-    S->sn[j] = sn;
-    S->H[j * MAXM + j] = cs * a + sn * c;
-    const double gj = S->g[j];
-    S->g[j + 1] = -sn * gj;
-    S->g[j] = cs * gj;
-    S->iters += 1;
-    S->kdim = j + 1;
-    S->est = fabs(S->g[j + 1]) / S->bnorm;
-    S->breakdown = hn == 0.0 ? 1 : 0;
-    S->done = (fabs(S->g[j + 1]) <= S->rtol * S->bnorm || hn == 0.0 ||
-               S->iters >= S->max_iters || j + 1 >= S->m) ? 1 : 0;
-    S->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
-    S->counter = 0;
-    publish(S);
+    givens_column(S, j, pass == 1, sqrt(sh_o[0]));
 }
 
 // k_update for step j (the pipelined kernels for one to three basis vectors)
@@ -618,13 +793,16 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
-            launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
-            launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, !opts->reorth);
-            if (opts->reorth) {
+            if (!opts->reorth) {   // one pass, one reduction (see k_dots_norm)
+                launch_dots_norm(nred, st, V, nv2, j + 1, w, SS, ws->partials);
+                launch_update_scale(nred, st, V, nv2, j, w, V + (size_t)(j + 1) * nv, v32, SS);
+            } else {               // CGS2: two passes, the norm of the updated w
+                launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
+                launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 0);
                 launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 1);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 1, 1);
+                launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
             }
-            launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step"); break; }
             e = cudaEventRecord(ev[j & 1], st);
