@@ -249,7 +249,7 @@ abilu_status abilu_factors_set_spin_limit(abilu_factors f, int64_t limit);
 /* Failure injection for tests of the bounded waits (no counterpart in the
  * paper).  With `enable` nonzero, the next asynchronous build of block factors
  * on `f` that uses the ordered variant (the work list has fewer than four
- * 32-block chunks per resident warp, i.e. every small system) starts its
+ * 128-block chunks per resident warp, i.e. every small system) starts its
  * per-chunk sweep flags one sweep behind, a value no warp ever publishes: the
  * first wait of every chunk polls `spin_limit` times, gives up, counts a
  * timeout and the warp stops.  That build leaves the factors partly swept,

@@ -216,6 +216,10 @@ k_b_dots(const double *__restrict__ V, size_t nv, int j, const double *__restric
     if (threadIdx.x == 0) St->counter = 0;
 }
 
+__device__ __forceinline__ void b_givens(BState *St, int s, int j, int two_pass, double hn,
+                                         const BConf &cf, int *hs_done, int *sys_done,
+                                         int *bflag);
+
 // w -= sum_k h[k] V_k per system; on the final pass ||w||, and the system's last
 // chunk applies the Givens update of column j and the convergence test
 __global__ void __launch_bounds__(RED_THREADS)
@@ -246,14 +250,21 @@ k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ 
     if (!last_cta_of(St, c1 - c0)) return;
     reduce_sys<1, PSTRIDE>(partials, c0, c1, BMAXM + 1, 1, sh_w, sh_o);
     if (threadIdx.x != 0) return;
-    const double hn = sqrt(sh_o[0]);
+    b_givens(St, s, j, pass == 1, sqrt(sh_o[0]), cf, hs_done, sys_done, bflag);
+}
+
+// The Givens update of system s's column j with h_{j+1,j} = hn, its estimate
+// and cycle-end test (one thread of the system's last CTA)
+__device__ __forceinline__ void b_givens(BState *St, int s, int j, int two_pass, double hn,
+                                         const BConf &cf, int *hs_done, int *sys_done,
+                                         int *bflag) {
     // the previous rotations, i = 0 .. j-1, each mixing entries i and i+1 of
     // the new column: entry i+1 is still the Gram-Schmidt coefficient when
     // rotation i reaches it, so one carried value replaces a column array
     // (which lived in local memory)
-    double a = St->h[0] + (pass == 1 ? St->h2[0] : 0.0);
+    double a = St->h[0] + (two_pass ? St->h2[0] : 0.0);
     for (int i = 0; i < j; i++) {
-        const double c = St->h[i + 1] + (pass == 1 ? St->h2[i + 1] : 0.0);
+        const double c = St->h[i + 1] + (two_pass ? St->h2[i + 1] : 0.0);
         St->H[i * BMAXM + j] = St->cs[i] * a + St->sn[i] * c;
         a = -St->sn[i] * a + St->cs[i] * c;
     }
@@ -281,6 +292,80 @@ k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ 
         reinterpret_cast<volatile int *>(hs_done)[s] = 1;
         __threadfence_system();
     }
+}
+
+// The single-reduction step of the batch (one classical pass; see
+// k_dots_norm in fgmres.cu): h[k] = <V_k, w>_s and ||w||_s^2 in one pass, the
+// system's last chunk forms h_{j+1,j} = sqrt(||w||^2 - sum h_k^2) (a
+// difference below 1e-12 ||w||^2 is a breakdown) and the Givens update.
+__global__ void __launch_bounds__(RED_THREADS)
+k_b_dots_norm(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w,
+              BState *S, const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
+              double *partials, BConf cf, int *hs_done, int *sys_done, int *bflag) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ double sh_w[RED_WARPS * BTILE], sh_o[BTILE];
+    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    BState *St = S + s;
+    if (St->done) return;
+    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
+    const double wv = w[e];
+    const int jp1 = j + 1;
+    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
+        switch (jp1 - k0 < BTILE ? jp1 - k0 : BTILE) {
+        case 1: b_dots_tile<1>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 2: b_dots_tile<2>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 3: b_dots_tile<3>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 4: b_dots_tile<4>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 5: b_dots_tile<5>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 6: b_dots_tile<6>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        case 7: b_dots_tile<7>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        default: b_dots_tile<8>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
+        }
+    }
+    {
+        double nrm[1] = {wv * wv};
+        block_sum<1>(nrm, sh_w, sh_o, 1);
+        if (threadIdx.x == 0) partials[(size_t)chunk * PSTRIDE + BMAXM + 1] = sh_o[0];
+    }
+    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    if (!last_cta_of(St, c1 - c0)) return;
+    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
+        const int kn = jp1 - k0 < BTILE ? jp1 - k0 : BTILE;
+        reduce_sys<BTILE, PSTRIDE>(partials, c0, c1, k0, kn, sh_w, sh_o);
+        if (threadIdx.x < kn) St->h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        __syncthreads();
+    }
+    reduce_sys<1, PSTRIDE>(partials, c0, c1, BMAXM + 1, 1, sh_w, sh_o);
+    if (threadIdx.x != 0) return;
+    const double ww = sh_o[0];
+    double hh = 0.0;
+    for (int k = 0; k < jp1; k++) hh = fma(St->h[k], St->h[k], hh);
+    const double d = ww - hh;
+    b_givens(St, s, j, 0, d > 1e-12 * ww ? sqrt(d) : 0.0, cf, hs_done, sys_done, bflag);
+}
+
+// v_{j+1} = (w - sum_k h[k] V_k) * hn_inv per system and its FP32 copy (w is
+// not written back)
+__global__ void __launch_bounds__(RED_THREADS)
+k_b_update_scale(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w,
+                 double *__restrict__ vnext, float *__restrict__ v32, const BState *S,
+                 const int *__restrict__ chunk_sys) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ double sh_h[BMAXM + 1];
+    const int chunk = blockIdx.x;
+    const BState *St = S + chunk_sys[chunk];
+    if (St->done) return;
+    const int jp1 = j + 1;
+    for (int k = threadIdx.x; k < jp1; k += blockDim.x) sh_h[k] = St->h[k];
+    __syncthreads();
+    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
+    double t = w[e];
+    for (int k = 0; k < jp1; k++) t = fma(-sh_h[k], V[(size_t)k * nv + e], t);
+    const double r = t * St->hn_inv;
+    vnext[e] = r;
+    if (v32) v32[e] = to_f32_int(r);
 }
 
 // y = R^{-1} g per system (one thread per system)
@@ -548,20 +633,23 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
                                     (abilu_mode)opts->mode, st, skip);
     if (s != ABILU_OK) return s;
     if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
-    launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
-        b->partials, 0);
-    launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys, b->sys_chunk0,
-        b->partials, cf, 0, !opts->reorth, b->hs_done,
-        b->sys_done, b->bflag);
-    if (opts->reorth) {
+    if (!opts->reorth) {   // one pass, one reduction per system
+        launch_pdl(k_b_dots_norm, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
+            b->sys_chunk0, b->partials, cf, b->hs_done, b->sys_done, b->bflag);
+        launch_pdl(k_b_update_scale, nck, RED_THREADS, 0, st, V, nv, j, w,
+            V + (size_t)(j + 1) * nv, v32, b->S, b->chunk_sys);
+    } else {               // CGS2: two passes, the norm of the updated w
+        launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
+            b->sys_chunk0, b->partials, 0);
+        launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
+            b->sys_chunk0, b->partials, cf, 0, 0, b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
             b->sys_chunk0, b->partials, 1);
         launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-            b->sys_chunk0, b->partials, cf, 1, 1,
-            b->hs_done, b->sys_done, b->bflag);
+            b->sys_chunk0, b->partials, cf, 1, 1, b->hs_done, b->sys_done, b->bflag);
+        launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
+            b->chunk_sys);
     }
-    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
-        b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch step");
     return ABILU_OK;
 }
