@@ -386,6 +386,28 @@ def run_profile_solves(args):
     return 0
 
 
+def run_profile_batch(args):
+    """Warm-up plus --profile-batch solves of the 64-system batch with fixed
+    settings (4 build, 3+3 apply sweeps, sync; no autotuning): the command the
+    batch's launch list is taken on."""
+    import torch
+    import abilu_inputs as gen
+    import paper_1912_00539_gb300 as ab
+    systems = gen.batch_systems(64)
+    dev = [(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda(),
+            torch.from_numpy(s.vals).cuda(), torch.from_numpy(s.b).cuda()) for s in systems]
+    batch = ab.Batch([(d[0], d[1]) for d in dev], dtype="f32")
+    for k, d in enumerate(dev):
+        batch.set_system(k, d[2], d[3])
+    for _ in range(args.warmup + args.profile_batch):
+        res = batch.solve(restart=RESTART, rtol=RTOL, build_sweeps=4, apply_sweeps_lower=3,
+                          apply_sweeps_upper=3, mode="sync")
+    torch.cuda.synchronize()
+    print(json.dumps({"solves": args.warmup + args.profile_batch,
+                      "cells": sum(s.n for s in systems), "iters_max": max(r.iters for r in res)}))
+    return 0
+
+
 def run_profile_mg(args):
     """Warm-up plus --profile-mg FGMRES solves preconditioned by the V-cycle
     (512x512 workload, FP32 factors, synchronous 2+2 smoothing, 6 build sweeps
@@ -426,7 +448,9 @@ def run_batched(args, nsys=64, steps=3):
     cells = sum(s.n for s in systems)
     from paper_1912_00539_gb300 import autotune
     t0 = time.perf_counter()
-    choice = autotune.tune_batch(batch, cells, restart=RESTART, rtol=RTOL)
+    cfls = [s.cfl for s in systems]
+    choice = autotune.tune_batch(batch, cells, restart=RESTART, rtol=RTOL,
+                                 cfl_range=(min(cfls), max(cfls)))
     ttune = time.perf_counter() - t0
     opts = dict(restart=RESTART, rtol=RTOL, build_sweeps=choice.build_sweeps,
                 apply_sweeps_lower=choice.apply_sweeps, apply_sweeps_upper=choice.apply_sweeps,
@@ -461,6 +485,8 @@ def run_batched(args, nsys=64, steps=3):
     t1 = e0.elapsed_time(e1) / steps
     return {"workload": f"batch of {nsys} systems, {cells} cells", "cells": cells,
             "autotuned": {"build_sweeps": choice.build_sweeps, "apply_sweeps": choice.apply_sweeps,
+                          "build_chunk": choice.build_chunk,
+                          "key": autotune.cfl_bucket(min(cfls), max(cfls)),
                           "mode": choice.mode, "tuning_s": round(ttune, 1)},
             "batch_ms": round(tb, 3), "batch_systems_per_s": round(nsys / (tb * 1e-3), 1),
             "one_by_one_ms": round(t1, 3), "one_by_one_systems_per_s": round(nsys / (t1 * 1e-3), 1),
@@ -1182,6 +1208,8 @@ def main():
                     help="skip the viscous, batched and serving sections of the default line")
     ap.add_argument("--kernels-only", action="store_true")
     ap.add_argument("--profile-solves", type=int, default=0)
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="warm-up plus this many solves of the 64-system batch, for ncu")
     ap.add_argument("--profile-mg", type=int, default=0,
                     help="warm-up plus this many multigrid-preconditioned solves, for ncu")
     ap.add_argument("--batched", action="store_true", help="only the batched workload")
@@ -1206,6 +1234,8 @@ def main():
         return run_profile_solves(args)
     if args.profile_mg:
         return run_profile_mg(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     if args.batched:
         print(json.dumps(run_batched(args)))
         return 0

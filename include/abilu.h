@@ -246,6 +246,14 @@ abilu_status abilu_factors_status(abilu_factors f, int64_t *singular_blocks, abi
  * its own duration and leaves the handle's value as it was.  limit >= 0. */
 abilu_status abilu_factors_set_spin_limit(abilu_factors f, int64_t limit);
 
+/* Launch shape of the asynchronous block build (FP32/BF16 factors): the work
+ * blocks a warp takes per ticket from the build's queue (a multiple of 32 in
+ * 32..512; 0 restores the default, 128).  Any value gives a legal asynchronous
+ * iteration (Algorithm 4 with blocks); it trades the contention on the one
+ * ticket counter against load balance.  An autotuner's knob
+ * (abilu_batch_set_build_chunk sets it on a batch's factors). */
+abilu_status abilu_factors_set_build_chunk(abilu_factors f, int32_t blocks);
+
 /* Failure injection for tests of the bounded waits (no counterpart in the
  * paper).  With `enable` nonzero, the next asynchronous build of block factors
  * on `f` that uses the ordered variant (the work list has fewer than four
@@ -486,6 +494,7 @@ abilu_status abilu_batch_set_system(abilu_batch b, int32_t s, const double *A_va
 abilu_status abilu_batch_solve(abilu_batch b, const fgmres_opts *opts, fgmres_result *res,
                                abilu_stream stream);
 abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x, abilu_stream stream);
+abilu_status abilu_batch_set_build_chunk(abilu_batch b, int32_t blocks);
 
 /*
  * Continuous batching: a server whose every step solves one value update of

@@ -42,7 +42,8 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "fgmres_solve_mg", "abilu_parilut_default_opts", "abilu_parilut",
            "abilu_pattern_arrays", "abilu_factors_inject_stall", "abilu_factors_set_spin_limit",
            "abilu_server_arena_bytes", "abilu_server_create", "abilu_server_destroy",
-           "abilu_server_add", "abilu_server_remove", "abilu_server_step", "abilu_server_usage")
+           "abilu_server_add", "abilu_server_remove", "abilu_server_step", "abilu_server_usage",
+           "abilu_factors_set_build_chunk", "abilu_batch_set_build_chunk")
 
 
 class FgmresOpts(C.Structure):
@@ -119,6 +120,10 @@ _lib.abilu_server_usage.argtypes = [_vp, C.POINTER(_i64)]
 for _nm in ("abilu_server_arena_bytes", "abilu_server_create", "abilu_server_add",
             "abilu_server_remove", "abilu_server_step", "abilu_server_usage"):
     getattr(_lib, _nm).restype = C.c_int
+_lib.abilu_factors_set_build_chunk.argtypes = [_vp, _i32]
+_lib.abilu_factors_set_build_chunk.restype = C.c_int
+_lib.abilu_batch_set_build_chunk.argtypes = [_vp, _i32]
+_lib.abilu_batch_set_build_chunk.restype = C.c_int
 _lib.abilu_factors_set_spin_limit.argtypes = [_vp, _i64]
 _lib.abilu_factors_set_spin_limit.restype = C.c_int
 _lib.abilu_factors_inject_stall.argtypes = [_vp, C.c_int]
@@ -317,6 +322,10 @@ class Factors:
         and applications gives up (0: the library default)."""
         _check(_lib.abilu_factors_set_spin_limit(self.handle, int(limit)))
 
+    def set_build_chunk(self, blocks: int = 0):
+        """Work blocks per ticket of the asynchronous build (0: the default)."""
+        _check(_lib.abilu_factors_set_build_chunk(self.handle, int(blocks)))
+
     def inject_stall(self, enable: bool = True):
         """Failure injection for tests of the bounded waits
         (abilu_factors_inject_stall): the next ordered asynchronous build's
@@ -500,6 +509,10 @@ class Batch:
         out = (C.c_int64 * 4)()
         _check(_lib.abilu_batch_counts(self.handle, out))
         return dict(zip(("nsys", "rows", "blocks", "chunks"), list(out)))
+
+    def set_build_chunk(self, blocks: int = 0):
+        """Work blocks per ticket of the batch's asynchronous build (0: default)."""
+        _check(_lib.abilu_batch_set_build_chunk(self.handle, int(blocks)))
 
     def set_system(self, s, A=None, b=None, stream=None):
         import torch

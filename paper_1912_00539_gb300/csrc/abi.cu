@@ -214,6 +214,14 @@ extern "C" abilu_status abilu_factors_set_spin_limit(abilu_factors f, int64_t li
     return ABILU_OK;
 }
 
+extern "C" abilu_status abilu_factors_set_build_chunk(abilu_factors f, int32_t blocks) {
+    if (!f) return fail(ABILU_EINVAL, "factors_set_build_chunk: NULL handle");
+    if (blocks != 0 && (blocks < 32 || blocks > 512 || blocks % 32 != 0))
+        return fail(ABILU_EINVAL, "factors_set_build_chunk: blocks must be 0 or a multiple of 32 in 32..512");
+    f->build_chunk = blocks;
+    return ABILU_OK;
+}
+
 extern "C" abilu_status abilu_factors_inject_stall(abilu_factors f, int enable) {
     if (!f) return fail(ABILU_EINVAL, "factors_inject_stall: NULL handle");
     f->stall_flags = enable ? 1 : 0;

@@ -603,6 +603,11 @@ extern "C" abilu_status abilu_batch_set_system(abilu_batch b, int32_t s, const d
     return ABILU_OK;
 }
 
+extern "C" abilu_status abilu_batch_set_build_chunk(abilu_batch b, int32_t blocks) {
+    if (!b) return fail(ABILU_EINVAL, "batch_set_build_chunk: NULL batch");
+    return abilu_factors_set_build_chunk(b->fac, blocks);
+}
+
 extern "C" abilu_status abilu_batch_get_solution(abilu_batch b, int32_t s, double *x,
                                                  abilu_stream stream) {
     if (!b || s < 0 || s >= b->nsys || !x) return fail(ABILU_EINVAL, "batch_get_solution: bad argument");

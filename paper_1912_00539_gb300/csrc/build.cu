@@ -418,20 +418,20 @@ k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__res
 // completed sweeps, and publishes s + 1 after its writes.  A wait points only
 // to a smaller ticket, held by a resident warp, so every wait ends.  No bulk
 // copy is in flight in this kernel, so a warp that gives up can simply return.
-constexpr int WARP_CHUNK = 128;
+constexpr int WARP_CHUNK = 128;   // default work blocks per ticket (abilu_factors_set_build_chunk)
 
 template <typename T, bool ORDERED>
 __global__ void __launch_bounds__(BUILD_THREADS, 5)   // 48 registers: measured fastest (4, 6 slower)
 k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T *D, T *Udiag,
                      int nsweeps, int max_warps, unsigned long long *nsing,
                      unsigned long long *ticket, unsigned long long *err, int *done,
-                     unsigned long long limit) {
+                     unsigned long long limit, int wchunk) {
     pdl_wait();
     pdl_trigger();
     __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
     // at most one warp per chunk: more would sweep the same blocks at once
     if (blockIdx.x * (BUILD_THREADS / 32) + (threadIdx.x >> 5) >= max_warps) return;
-    const long long nchunks = (P.nwork + WARP_CHUNK - 1) / WARP_CHUNK;
+    const long long nchunks = (P.nwork + wchunk - 1) / wchunk;
     const long long total = nchunks * nsweeps;
     const int lane = threadIdx.x & 31;
     float *myq = sh_q + (threadIdx.x >> 2) * QUAD_SCRATCH;
@@ -442,7 +442,7 @@ k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T
         if (t >= total) break;
         const int sweep = (int)(t / nchunks), chunk = (int)(t % nchunks);
         const bool last = sweep == nsweeps - 1;
-        const int base = chunk * WARP_CHUNK + (lane >> 2);
+        const int base = chunk * wchunk + (lane >> 2);
         if constexpr (ORDERED) {  // wait for this chunk's previous sweep
             int ok = 1;
             if (lane == 0) {
@@ -456,7 +456,7 @@ k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T
             if (!__shfl_sync(0xffffffffu, ok, 0)) return;
         }
 #pragma unroll 1
-        for (int k = 0; k < WARP_CHUNK / 8; k++) {
+        for (int k = 0; k < wchunk / 8; k++) {
             const int w = base + 8 * k;
             if (w < P.nwork)
                 build_block<T, true>(P, w, A32, L, U, D, L, U, D, last ? Udiag : nullptr, myq, nsing);
@@ -654,7 +654,8 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
             ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &per_sm, k_build_blocks_async<T, false>, BUILD_THREADS, 0));
         ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int wchunks = (P.nwork + WARP_CHUNK - 1) / WARP_CHUNK;
+        const int wc = f->build_chunk ? f->build_chunk : WARP_CHUNK;
+        const int wchunks = (P.nwork + wc - 1) / wc;
         int warps = per_sm * sms * (BUILD_THREADS / 32);
         if (warps > wchunks) warps = wchunks;
         if (warps < 1) warps = 1;
@@ -678,11 +679,11 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
         if (done)
             launch_pdl(k_build_blocks_async<T, true>, ctas, BUILD_THREADS, 0, st,
                 P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done,
-                lim);
+                lim, wc);
         else
             launch_pdl(k_build_blocks_async<T, false>, ctas, BUILD_THREADS, 0, st,
                 P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done,
-                lim);
+                lim, wc);
         ABILU_LAUNCH_CHECK("k_build_blocks_async");
     }
     return ABILU_OK;

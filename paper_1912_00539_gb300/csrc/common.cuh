@@ -119,6 +119,7 @@ struct abilu_factors_s {
     // chunk's rows start from A, 0 = from the factors in place (the systems of
     // a server step: new ones from A, continuing ones warm-started)
     const int *chunk_init;
+    int build_chunk;           // work blocks per ticket of the asynchronous block build (0: 128)
     void *mem;
 };
 

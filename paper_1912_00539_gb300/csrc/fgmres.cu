@@ -276,8 +276,12 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
 // The Givens update of column j of the Hessenberg matrix (from the
 // Gram-Schmidt coefficients h, plus h2 after a second pass) with
 // h_{j+1,j} = hn, the residual estimate and the end-of-cycle test.  One
-// thread of the last CTA.
-__device__ __forceinline__ void givens_column(SolveState *S, int j, int two_pass, double hn) {
+// thread of the last CTA.  With `pub` the status goes to the host-mapped
+// mirror here; otherwise the next kernel's first CTA publishes it at its start
+// (publish_early), off this kernel's serial tail: the system-scope fence of
+// the host-mapped stores then overlaps that kernel's work.
+__device__ __forceinline__ void givens_column(SolveState *S, int j, int two_pass, double hn,
+                                              bool pub = true) {
     // the previous rotations, i = 0 .. j-1, each mixing entries i and i+1 of
     // the new column: entry i+1 is still the Gram-Schmidt coefficient when
     // rotation i reaches it, so one carried value replaces a column array
@@ -306,7 +310,13 @@ __device__ __forceinline__ void givens_column(SolveState *S, int j, int two_pass
                S->iters >= S->max_iters || j + 1 >= S->m) ? 1 : 0;
     S->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
     S->counter = 0;
-    publish(S);
+    if (pub) publish(S);
+}
+
+// In the first CTA of the kernel after a Gram-Schmidt step: the step's status
+// to the host-mapped mirror (see givens_column)
+__device__ __forceinline__ void publish_early(SolveState *S) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) publish(S);
 }
 
 // h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2).  The grid is
@@ -419,7 +429,7 @@ k_dots_norm(const double *__restrict__ V, long long nv2, int jp1, const double *
     double hh = 0.0;
     for (int k = 0; k < jp1; k++) hh = fma(S->h[k], S->h[k], hh);
     const double d = ww - hh;
-    givens_column(S, jp1 - 1, 0, d > 1e-12 * ww ? sqrt(d) : 0.0);
+    givens_column(S, jp1 - 1, 0, d > 1e-12 * ww ? sqrt(d) : 0.0, false);   // k_update_scale publishes
 }
 
 static void launch_dots_norm(int nred, cudaStream_t st, const double *V, long long nv2, int jp1,
@@ -445,6 +455,7 @@ k_update_scale(const double *__restrict__ V, long long nv2, int j, const double 
                double *__restrict__ vnext, float *__restrict__ v32, SolveState *S) {
     pdl_wait();
     pdl_trigger();
+    publish_early(S);      // the previous kernel's step status
     if (S->done) return;   // the cycle ended at this column: no next vector
     __shared__ double sh_h[MAXM + 1];
     const int jp1 = j + 1;

@@ -175,3 +175,55 @@ def test_full_batch_of_64_uneven_systems(ab):
         Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 4)
         _, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, 3, 3, restart=30, rtol=1e-6)
         assert abs(res[k].iters - ro.iters) <= max(1, ro.iters // 10), (k, res[k].iters, ro.iters)
+
+
+def test_autotuner_picks_a_converging_candidate_and_keeps_its_launch_shape(tmp_path):
+    """The batch autotuner over sweep counts, mode and the asynchronous build's
+    ticket size: the choice converges, is the fastest of those timed, its
+    build chunk stays set on the batch, and the cache keyed by size and CFL
+    range returns it without timing again."""
+    import torch
+    import paper_1912_00539_gb300 as ab
+    from paper_1912_00539_gb300 import autotune
+    systems = [gen.small_system(30, 20, seed=1, cfl=10.0), gen.small_system(41, 13, seed=2, cfl=1e3)]
+    dev = [(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda()) for s in systems]
+    batch = ab.Batch(dev, dtype="f32")
+    for k, s in enumerate(systems):
+        batch.set_system(k, torch.from_numpy(s.vals).cuda(), torch.from_numpy(s.b).cuda())
+    grid = [(2, 2, "sync", 0), (4, 3, "async", 64), (4, 3, "async", 256)]
+    cache = str(tmp_path / "tune.json")
+    cells = sum(s.n for s in systems)
+    ch = autotune.tune_batch(batch, cells, cfl_range=(10.0, 1e3), grid=grid, cache_path=cache)
+    assert (ch.build_sweeps, ch.apply_sweeps, ch.mode, ch.build_chunk) in grid
+    res = batch.solve(build_sweeps=ch.build_sweeps, apply_sweeps_lower=ch.apply_sweeps,
+                      apply_sweeps_upper=ch.apply_sweeps, mode=ch.mode)
+    assert all(r.converged for r in res)
+    again = autotune.tune_batch(batch, cells, cfl_range=(10.0, 1e3), grid=[(6, 4, "sync", 0)],
+                                cache_path=cache)
+    assert again == ch          # from the cache, not re-timed on the new grid
+    other = autotune.tune_batch(batch, cells, cfl_range=(1e3, 1e4), grid=[(6, 4, "sync", 0)],
+                                cache_path=cache)
+    assert (other.build_sweeps, other.mode) == (6, "sync")   # another CFL range: tuned anew
+
+
+def test_build_chunk_sizes_give_converging_async_builds():
+    """Every allowed ticket size is a legal asynchronous iteration: the
+    factors reach sequential block ILU(0) with enough sweeps; bad sizes are
+    refused."""
+    import torch
+    import oracle
+    import paper_1912_00539_gb300.abilu as ab
+    s = gen.small_system(37, 11, seed=2)
+    pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
+    A = torch.from_numpy(s.vals).cuda()
+    Xs, Ds, _ = oracle.bilu0_seq(s.rowptr, s.colind, s.vals)
+    fac = ab.Factors(pat, "f32")
+    for c in (32, 64, 256, 512):
+        fac.set_build_chunk(c)
+        fac.build(A, 2 * s.n + 4, mode="async")
+        X, _ = fac.export()
+        X = X.cpu().numpy()
+        assert np.abs(X - Xs).max() / np.abs(Xs).max() < 1e-4, c
+    for bad in (16, 48, 1024):
+        with pytest.raises(ab.AbiluError):
+            fac.set_build_chunk(bad)

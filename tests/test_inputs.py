@@ -115,3 +115,12 @@ def test_server_arena_sizing():
         assert ab.server_arena_bytes(c, int(4.2 * c)) <= budget
         assert ab.server_arena_bytes(c + 64, int(4.2 * (c + 64))) > budget
     assert serving.arena_cells_for_budget(1e3) == 0
+
+
+def test_autotune_cache_keys():
+    from paper_1912_00539_gb300 import autotune
+    assert autotune.cfl_bucket(10.0, 1e4) == "cfl1e1-1e4"
+    assert autotune.cfl_bucket(12.0, 900.0) == "cfl1e1-1e3"
+    k = autotune._key("GB300", "f32", 524288, autotune.cfl_bucket(100.0, 100.0))
+    assert k == "GB300|f32|2^19|cfl1e2-1e2"
+    assert len({c for _, _, m, c in autotune.DEFAULT_GRID if m == "async"}) == 3
