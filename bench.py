@@ -50,9 +50,10 @@ def _dist():
 # captured again)
 PROFILED_TRAFFIC = {
     "spmv_f64": 295.448832e6 + 15.170560e6,          # k_spmv<1>
-    "build_sweeps_f32": 1.351872e9 + 509.619456e6,   # k_build_blocks_async<float, 0>, 6 sweeps
-    "lower_sweeps_f32": 133.699072e6 + 10.779392e6,  # k_tri_staged lower, 3 sweeps
-    "upper_sweeps_f32": 79.993856e6 + 4.602112e6,    # k_tri_staged upper (scaled), 3 sweeps
+    "build_sweeps_f32": 1.503612e9 + 534.555392e6,   # k_build_blocks_async<float, 1>, 6 sweeps,
+                                                     # tickets of 128 work blocks
+    "lower_sweeps_f32": None,                        # k_tri_staged: changed (bounded-wait drain)
+    "upper_sweeps_f32": None,                        # since its last capture
 }
 
 
