@@ -514,6 +514,11 @@ abilu_status abilu_batch_set_build_chunk(abilu_batch b, int32_t blocks);
  *     for abilu_pattern_create) once, into its own pattern handle, and admits
  *     it; ABILU_ENOMEM (nothing changed) when the admitted systems would no
  *     longer fit the arena.  *id (host) names the system.  Synchronises stream.
+ *   abilu_server_add_pattern admits a pattern analysed beforehand by
+ *     abilu_pattern_create (for example on another host thread and stream
+ *     while a step runs): on success the server owns the handle (it is
+ *     released with the system); on ABILU_ENOMEM the caller still owns it.
+ *     No device work.
  *   abilu_server_remove releases the system's pattern handle at once; its
  *     share of the arena is free from the next step on.
  *   abilu_server_step solves, in one batched solve, one update of every
@@ -551,6 +556,7 @@ abilu_status abilu_server_create(const abilu_server_opts *opts, abilu_stream str
 void abilu_server_destroy(abilu_server s);
 abilu_status abilu_server_add(abilu_server s, int32_t n, int32_t nnzb, const int32_t *rowptr,
                               const int32_t *colind, abilu_stream stream, int32_t *id);
+abilu_status abilu_server_add_pattern(abilu_server s, abilu_pattern p, int32_t *id);
 abilu_status abilu_server_remove(abilu_server s, int32_t id);
 abilu_status abilu_server_step(abilu_server s, int32_t k, const int32_t *ids,
                                const double *const *A, const double *const *rhs,

@@ -43,7 +43,8 @@ EXPORTS = ("abilu_version", "abilu_last_error", "abilu_kernel_launches", "abilu_
            "abilu_pattern_arrays", "abilu_factors_inject_stall", "abilu_factors_set_spin_limit",
            "abilu_server_arena_bytes", "abilu_server_create", "abilu_server_destroy",
            "abilu_server_add", "abilu_server_remove", "abilu_server_step", "abilu_server_usage",
-           "abilu_factors_set_build_chunk", "abilu_batch_set_build_chunk")
+           "abilu_factors_set_build_chunk", "abilu_batch_set_build_chunk",
+           "abilu_server_add_pattern")
 
 
 class FgmresOpts(C.Structure):
@@ -113,6 +114,8 @@ _lib.abilu_server_destroy.argtypes = [_vp]
 _lib.abilu_server_destroy.restype = None
 _lib.abilu_server_add.argtypes = [_vp, _i32, _i32, _vp, _vp, _vp, C.POINTER(_i32)]
 _lib.abilu_server_remove.argtypes = [_vp, _i32]
+_lib.abilu_server_add_pattern.argtypes = [_vp, _vp, C.POINTER(_i32)]
+_lib.abilu_server_add_pattern.restype = C.c_int
 _lib.abilu_server_step.argtypes = [_vp, _i32, C.POINTER(_i32), C.POINTER(_vp), C.POINTER(_vp),
                                    C.POINTER(_vp), C.POINTER(FgmresOpts), C.POINTER(FgmresResult),
                                    _vp]
@@ -585,6 +588,19 @@ class NativeServer:
         if st == ENOMEM:
             return None
         _check(st)
+        return v.value
+
+    def add_pattern(self, pattern):
+        """Admit a pattern analysed beforehand (a Pattern, e.g. made on another
+        thread and stream); the server takes the handle over.  Returns the
+        id, or None when the arena has no room for it now (the caller keeps
+        the Pattern)."""
+        v = C.c_int32()
+        st = _lib.abilu_server_add_pattern(self.handle, pattern.handle, C.byref(v))
+        if st == ENOMEM:
+            return None
+        _check(st)
+        pattern.handle = None          # owned by the server now
         return v.value
 
     def remove(self, sid):

@@ -2,6 +2,8 @@
 // SpMV, export.  Pattern analysis lives in pattern.cu, FGMRES in fgmres.cu.
 #include <string.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace abilu {
@@ -19,15 +21,19 @@ int max_restart();
 
 constexpr int MAXM_PARTIAL_STRIDE = 66;  // MAXM + 2 doubles per CTA
 
+// (cached once; the caches of launch shapes are atomics: different handles
+// may be driven from different host threads)
 int red_ctas() {
-    static int cached = 0;
-    if (!cached) {
+    static std::atomic<int> cached{0};
+    int v = cached.load(std::memory_order_relaxed);
+    if (!v) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cached = 4 * (sms > 0 ? sms : 1);
+        v = 4 * (sms > 0 ? sms : 1);
+        cached.store(v, std::memory_order_relaxed);
     }
-    return cached;
+    return v;
 }
 
 static inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -1215,22 +1215,53 @@ extern "C" abilu_status abilu_server_usage(abilu_server sv, int64_t *out) {
     return ABILU_OK;
 }
 
-extern "C" abilu_status abilu_server_add(abilu_server sv, int32_t n, int32_t nnzb,
-                                         const int32_t *rowptr, const int32_t *colind,
-                                         abilu_stream stream, int32_t *id) {
-    if (!sv || !rowptr || !colind || !id) return fail(ABILU_EINVAL, "server_add: NULL argument");
-    if (n < 1 || nnzb < n) return fail(ABILU_EINVAL, "server_add: need n >= 1 and nnzb >= n");
+// room in the arena for one more system of n cells and nnzb blocks (the
+// counts that need no analysis)
+static abilu_status server_room(abilu_server sv, long long n, long long nnzb, const char *who) {
     const SrvCaps &c = sv->cap;
     long long t[7];
     server_totals(sv, t);
     const long long np = rnd64(n), bp = nnzb + (np - n);
     if (t[6] + 1 > c.sys || t[0] + np > c.rows || t[1] + bp > c.blocks)
-        return fail(ABILU_ENOMEM, "server_add: the arena has no room for %d cells / %d blocks now "
-                    "(%lld of %lld rows, %lld of %lld blocks, %lld of %d systems in use)", n, nnzb,
-                    t[0], c.rows, t[1], c.blocks, t[6], c.sys);
-    abilu_pattern p = nullptr;
-    abilu_status s = abilu_pattern_create(n, nnzb, rowptr, colind, stream, &p);
+        return fail(ABILU_ENOMEM, "%s: the arena has no room for %lld cells / %lld blocks now "
+                    "(%lld of %lld rows, %lld of %lld blocks, %lld of %d systems in use)", who, n,
+                    nnzb, t[0], c.rows, t[1], c.blocks, t[6], c.sys);
+    return ABILU_OK;
+}
+
+static abilu_status server_admit(abilu_server sv, abilu_pattern p, int32_t *id);
+
+extern "C" abilu_status abilu_server_add(abilu_server sv, int32_t n, int32_t nnzb,
+                                         const int32_t *rowptr, const int32_t *colind,
+                                         abilu_stream stream, int32_t *id) {
+    if (!sv || !rowptr || !colind || !id) return fail(ABILU_EINVAL, "server_add: NULL argument");
+    if (n < 1 || nnzb < n) return fail(ABILU_EINVAL, "server_add: need n >= 1 and nnzb >= n");
+    abilu_status s = server_room(sv, n, nnzb, "server_add");
     if (s != ABILU_OK) return s;
+    abilu_pattern p = nullptr;
+    s = abilu_pattern_create(n, nnzb, rowptr, colind, stream, &p);
+    if (s != ABILU_OK) return s;
+    s = server_admit(sv, p, id);
+    if (s != ABILU_OK) abilu_pattern_destroy(p);
+    return s;
+}
+
+extern "C" abilu_status abilu_server_add_pattern(abilu_server sv, abilu_pattern p, int32_t *id) {
+    if (!sv || !p || !id) return fail(ABILU_EINVAL, "server_add_pattern: NULL argument");
+    if (p->device != sv->device)
+        return fail(ABILU_EINVAL, "server_add_pattern: the pattern lives on another device");
+    abilu_status s = server_room(sv, p->v.n, p->v.nnzb, "server_add_pattern");
+    if (s != ABILU_OK) return s;
+    return server_admit(sv, p, id);
+}
+
+// admit an analysed pattern (the server owns it on success)
+static abilu_status server_admit(abilu_server sv, abilu_pattern p, int32_t *id) {
+    const SrvCaps &c = sv->cap;
+    long long t[7];
+    server_totals(sv, t);
+    const int n = p->v.n, nnzb = p->v.nnzb;
+    const long long np = rnd64(n);
     SrvMember m = {};
     m.id = sv->next_id;
     m.p = p;
@@ -1243,11 +1274,9 @@ extern "C" abilu_status abilu_server_add(abilu_server sv, int32_t n, int32_t nnz
     m.nwork = p->v.nwork;
     m.max_row = p->max_row;
     if (t[2] + m.nl > c.nl || t[3] + m.nu > c.nu || t[4] + m.npairs > c.pairs ||
-        t[5] + m.work_p() > c.work) {
-        abilu_pattern_destroy(p);
+        t[5] + m.work_p() > c.work)
         return fail(ABILU_ENOMEM, "server_add: the arena has no room for the system's L/U blocks, "
                     "product pairs or work items now");
-    }
     sv->next_id++;
     sv->mem.push_back(m);
     *id = m.id;

@@ -23,6 +23,8 @@
 // place, reading whatever is current through volatile loads, with the rows cut
 // into chunks handed out by a ticket counter across all sweeps, so no barrier
 // separates sweeps (Algorithm 4 with blocks, Eq. async_blockilu_fp).
+#include <atomic>
+
 #include "common.cuh"
 #include "pipe.cuh"
 
@@ -647,12 +649,14 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
             f->cur = o;
         }
     } else {
-        static int per_sm = -1;
-        int dev = 0, sms = 0;
+        static std::atomic<int> per_sm_cache{-1};
+        int dev = 0, sms = 0, per_sm = per_sm_cache.load(std::memory_order_relaxed);
         cudaGetDevice(&dev);
-        if (per_sm < 0)   // the ordered variant is held to the same occupancy
+        if (per_sm < 0) {   // the ordered variant is held to the same occupancy
             ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &per_sm, k_build_blocks_async<T, false>, BUILD_THREADS, 0));
+            per_sm_cache.store(per_sm, std::memory_order_relaxed);
+        }
         ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const int wc = f->build_chunk ? f->build_chunk : WARP_CHUNK;
         const int wchunks = (P.nwork + wc - 1) / wc;
@@ -707,12 +711,14 @@ static abilu_status sweeps_t(abilu_factors f, const AT *Asrc, int nsweeps, abilu
             f->cur = o;
         }
     } else {
-        static int per_sm = -1;
-        int dev = 0, sms = 0;
+        static std::atomic<int> per_sm_cache{-1};
+        int dev = 0, sms = 0, per_sm = per_sm_cache.load(std::memory_order_relaxed);
         cudaGetDevice(&dev);
-        if (per_sm < 0)
+        if (per_sm < 0) {
             ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_async<T, AT>,
                                                                      BUILD_THREADS, 0));
+            per_sm_cache.store(per_sm, std::memory_order_relaxed);
+        }
         ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         // at most one CTA per chunk: more would sweep the same rows at once
         int ctas = per_sm * sms;

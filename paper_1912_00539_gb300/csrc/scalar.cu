@@ -27,6 +27,8 @@
 // of each (y = r, x = y_i / U_ii) is formed directly.
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace abilu {
@@ -272,11 +274,13 @@ abilu_status scalar_build(abilu_factors f, const double *A, int nsweeps, abilu_m
         }
         return ABILU_OK;
     }
-    static int per_sm = -1;
-    int dev = 0, sms = 0;
+    static std::atomic<int> per_sm_cache{-1};
+    int dev = 0, sms = 0, per_sm = per_sm_cache.load(std::memory_order_relaxed);
     cudaGetDevice(&dev);
-    if (per_sm < 0)
+    if (per_sm < 0) {
         ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sbuild_async, S_THREADS, 0));
+        per_sm_cache.store(per_sm, std::memory_order_relaxed);
+    }
     ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int ctas = per_sm * sms;
     if (ctas > grid) ctas = grid;   // at most one CTA per chunk
@@ -290,13 +294,15 @@ abilu_status scalar_build(abilu_factors f, const double *A, int nsweeps, abilu_m
 }
 
 template <bool UPPER> static int sweep_ctas() {
-    static int c = -1;
+    static std::atomic<int> cache{-1};
+    int c = cache.load(std::memory_order_relaxed);
     if (c < 0) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ssweep_async<UPPER>, S_THREADS, 0);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         c = per_sm * sms > 0 ? per_sm * sms : 1;
+        cache.store(c, std::memory_order_relaxed);
     }
     return c;
 }

@@ -121,7 +121,8 @@ class Server:
     def __init__(self, hbm_budget_bytes: float, dtype: str = "f32", mode: str = "async",
                  build_sweeps: int = 4, apply_sweeps: int = 3, restart: int = 30,
                  rtol: float = 1e-6, max_systems: int = 64, keep_solutions: bool = False,
-                 blocks_per_cell: float = 4.2, pattern_reserve: float = 0.1):
+                 blocks_per_cell: float = 4.2, pattern_reserve: float = 0.1, groups: int = 4):
+        self.groups = int(groups)
         self.budget = float(hbm_budget_bytes)
         self.dtype = dtype
         self.mode = mode
@@ -132,96 +133,169 @@ class Server:
         self.max_systems = max_systems
         self.keep = keep_solutions
         self.pattern_budget = pattern_reserve * self.budget
-        self.cells = arena_cells_for_budget((1.0 - pattern_reserve) * self.budget, dtype, restart,
-                                            blocks_per_cell, max_systems)
+        # each group's arena: an equal share of the rest of the budget
+        self.cells = arena_cells_for_budget((1.0 - pattern_reserve) * self.budget / self.groups,
+                                            dtype, restart, blocks_per_cell, max_systems)
         self.blocks = int(blocks_per_cell * self.cells)
-        self.arena_bytes = ab.server_arena_bytes(self.cells, self.blocks, max_systems, dtype,
-                                                 restart)
-        self.engine = None
+        self.arena_bytes = self.groups * ab.server_arena_bytes(self.cells, self.blocks,
+                                                               max_systems, dtype, restart)
+        self.engines = None
         self.memory_samples = []    # (time, device bytes in use) before every step
 
     def _engine(self):
-        if self.engine is None:
-            self.engine = ab.NativeServer(self.cells, self.blocks, self.max_systems, self.dtype,
-                                          self.restart)
-        return self.engine
+        if self.engines is None:
+            self.engines = [ab.NativeServer(self.cells, self.blocks, self.max_systems, self.dtype,
+                                            self.restart) for _ in range(self.groups)]
+        return self.engines
 
-    def run(self, requests):
+    def run(self, requests, lookahead: int = 16):
         """Serve `requests` (arrival times relative to now); returns results in
-        request order and the wall time of the whole stream."""
+        request order and the wall time of the whole stream.
+
+        Every group is an arena of its own, stepped by its own host thread on
+        its own stream, so that one group's host-to-device copies of a step's
+        values overlap another group's solve (the copies of a step must
+        follow the previous step: update k+1 exists once update k is solved).
+        Admission is first come, first served: the head of the queue joins the
+        least loaded group with room.  The pattern of an arrived request is
+        analysed on a helper thread and stream while steps run (up to
+        `lookahead` requests ahead), so admission costs no analysis."""
+        import concurrent.futures
+        import threading
         import torch
-        eng = self._engine()
+        engines = self._engine()
         reqs = sorted(requests, key=lambda r: r.arrival)
         # the producer hands over each update in pinned host memory
         host = {r.rid: [(_pinned(v), _pinned(b)) for v, b in r.updates] for r in reqs}
         xout = {r.rid: torch.empty((r.n, 4), dtype=torch.float64).pin_memory() for r in reqs}
-        queue = collections.deque(reqs)
-        active = []
+        lock = threading.Lock()
+        st = {"queue": collections.deque(reqs), "analysed": {}, "pat_used": 0.0,
+              "load": [0] * self.groups, "active": [0] * self.groups}
         results = {}
-        pat_used = 0.0
+        errors = []
         opts = dict(restart=self.restart, rtol=self.rtol, build_sweeps=self.build_sweeps,
                     apply_sweeps_lower=self.apply_sweeps, apply_sweeps_upper=self.apply_sweeps,
                     mode=self.mode)
+        helper = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+        hstream = torch.cuda.Stream()
+        dev = torch.cuda.current_device()
+
+        def analyse(r):
+            torch.cuda.set_device(dev)
+            with torch.cuda.stream(hstream):
+                rp = torch.from_numpy(r.rowptr).cuda()
+                ci = torch.from_numpy(r.colind).cuda()
+                return ab.Pattern(rp, ci, stream=hstream)
+
         t0 = time.perf_counter()
 
         def now():
             return time.perf_counter() - t0
 
-        while queue or active:
+        def admit(g, eng, active):
+            """Under the lock: analyses ahead, then admissions into group g."""
             t = now()
-            while queue and queue[0].arrival <= t:
-                r = queue[0]
-                pb = pattern_bytes(r.n, r.nnzb)
-                if active and pat_used + pb > self.pattern_budget:
+            q, an = st["queue"], st["analysed"]
+            for r in list(q)[:lookahead]:
+                if r.arrival > t:
                     break
-                sid = eng.add(torch.from_numpy(r.rowptr).cuda(), torch.from_numpy(r.colind).cuda())
+                pb = pattern_bytes(r.n, r.nnzb)
+                if r.rid not in an and (st["pat_used"] + pb <= self.pattern_budget
+                                        or (not an and not any(st["active"]))):
+                    an[r.rid] = helper.submit(analyse, r)
+                    st["pat_used"] += pb
+            while q and q[0].arrival <= t and q[0].rid in an:
+                r = q[0]
+                fut = an[r.rid]
+                if not fut.done():
+                    if active:
+                        break              # its analysis still runs: this group steps first
+                    fut.result()
+                # the least loaded group with room takes it: this one only if
+                # no other group has less work (the others try after their steps)
+                if any(st["load"][h] < st["load"][g] for h in range(self.groups) if h != g) \
+                        and active:
+                    break
+                sid = eng.add_pattern(fut.result())
                 if sid is None:
-                    if not active:
-                        raise ValueError(f"request {r.rid} ({r.n} cells) does not fit the arena "
+                    if not active and not any(st["active"]):
+                        raise ValueError(f"request {r.rid} ({r.n} cells) does not fit an arena "
                                          f"({self.cells} cells)")
-                    break          # first come, first served: wait for a departure
-                queue.popleft()
-                pat_used += pb
-                active.append({"r": r, "id": sid, "k": 0, "ready": r.arrival, "pb": pb,
+                    break                  # no room here now
+                q.popleft()
+                del an[r.rid]
+                st["load"][g] += r.n
+                st["active"][g] += 1
+                active.append({"r": r, "id": sid, "k": 0, "ready": r.arrival,
+                               "pb": pattern_bytes(r.n, r.nnzb),
                                "res": RequestResult(r.rid, r.n, r.arrival, now(), 0.0)})
-            if not active:
-                wait = queue[0].arrival - now()
-                if wait > 0:
-                    time.sleep(min(wait, 0.001))
-                continue
-            free, total = torch.cuda.mem_get_info()
-            self.memory_samples.append((now(), total - free))
-            out = eng.step([a["id"] for a in active],
-                           [host[a["r"].rid][a["k"]][0] for a in active],
-                           [host[a["r"].rid][a["k"]][1] for a in active],
-                           [xout[a["r"].rid] for a in active], **opts)
-            tend = now()
-            k = len(active)
-            for a, o in zip(active, out):
-                res = a["res"]
-                res.update_ms.append(1e3 * (tend - a["ready"]))
-                res.iters.append(o.iters)
-                res.rel_resid.append(o.rel_resid_true)
-                res.steps.append(k)
-                if self.keep:
-                    res.x.append(xout[a["r"].rid].numpy().copy())
-                a["k"] += 1
-                a["ready"] = tend
-            still = []
-            for a in active:
-                if a["k"] == len(a["r"].updates):
-                    eng.remove(a["id"])
-                    pat_used -= a["pb"]
-                    a["res"].finished = tend
-                    results[a["r"].rid] = a["res"]
-                else:
-                    still.append(a)
-            active = still
+
+        def worker(g):
+            try:
+                torch.cuda.set_device(dev)
+                eng = engines[g]
+                gstream = torch.cuda.Stream()
+                active = []
+                while True:
+                    with lock:
+                        admit(g, eng, active)
+                        if not active and not st["queue"]:
+                            return
+                    if not active:
+                        time.sleep(0.0002)
+                        continue
+                    free, total = torch.cuda.mem_get_info()
+                    with lock:
+                        self.memory_samples.append((now(), total - free))
+                    out = eng.step([a["id"] for a in active],
+                                   [host[a["r"].rid][a["k"]][0] for a in active],
+                                   [host[a["r"].rid][a["k"]][1] for a in active],
+                                   [xout[a["r"].rid] for a in active], stream=gstream, **opts)
+                    tend = now()
+                    k = len(active)
+                    still = []
+                    for a, o in zip(active, out):
+                        res = a["res"]
+                        res.update_ms.append(1e3 * (tend - a["ready"]))
+                        res.iters.append(o.iters)
+                        res.rel_resid.append(o.rel_resid_true)
+                        res.steps.append(k)
+                        if self.keep:
+                            res.x.append(xout[a["r"].rid].numpy().copy())
+                        a["k"] += 1
+                        a["ready"] = tend
+                        if a["k"] == len(a["r"].updates):
+                            eng.remove(a["id"])
+                            res.finished = tend
+                            with lock:
+                                st["pat_used"] -= a["pb"]
+                                st["load"][g] -= a["r"].n
+                                st["active"][g] -= 1
+                                results[a["r"].rid] = res
+                        else:
+                            still.append(a)
+                    active = still
+            except Exception as e:   # surfaced after the run
+                errors.append(e)
+                with lock:
+                    st["queue"].clear()
+
+        threads = [threading.Thread(target=worker, args=(g,), daemon=True)
+                   for g in range(self.groups)]
+        try:
+            for th in threads:
+                th.start()
+            for th in threads:
+                th.join()
+        finally:
+            helper.shutdown(wait=True)
+        if errors:
+            raise errors[0]
         wall = now()
         return [results[r.rid] for r in requests], wall
 
     def close(self):
-        self.engine = None
+        self.engines = None
 
 
 def serve_one_at_a_time(requests, dtype: str = "f64", mode: str = "sync", build_sweeps: int = 4,

@@ -41,17 +41,21 @@ def test_same_result_alone_and_in_the_mix():
         srv = serving.Server(hbm_budget_bytes=2e9, dtype="f32", mode="sync", keep_solutions=True)
         res, _ = srv.run([r])
         alone[r.rid] = res[0]
-    srv = serving.Server(hbm_budget_bytes=2e9, dtype="f32", mode="sync", keep_solutions=True)
-    mix, wall = srv.run(reqs)
-    for r, m in zip(reqs, mix):
-        a = alone[r.rid]
-        assert m.iters == a.iters, r.rid
-        for xa, xm in zip(a.x, m.x):
-            np.testing.assert_array_equal(xa, xm)
-    _check_residuals(reqs, mix)
-    # the requests shared steps, and the arena was laid out again as they left
-    steps = [s for m in mix for s in m.steps]
-    assert max(steps) >= 4 and len(set(steps)) >= 3
+    for groups in (1, 2):   # one arena, or two stepped on their own threads and streams
+        srv = serving.Server(hbm_budget_bytes=2e9, dtype="f32", mode="sync", keep_solutions=True,
+                             groups=groups)
+        mix, wall = srv.run(reqs)
+        for r, m in zip(reqs, mix):
+            a = alone[r.rid]
+            assert m.iters == a.iters, (groups, r.rid)
+            for xa, xm in zip(a.x, m.x):
+                np.testing.assert_array_equal(xa, xm)
+        _check_residuals(reqs, mix)
+        steps = [s for m in mix for s in m.steps]
+        if groups == 1:   # the requests shared steps; the arena was laid out again as they left
+            assert max(steps) >= 4 and len(set(steps)) >= 3
+        else:             # both groups stepped
+            assert max(steps) >= 2
 
 
 def test_async_mix_converges_within_tolerance():
@@ -95,7 +99,7 @@ def test_admission_waits_for_room_and_memory_stays_in_the_budget():
     budget = (ab.server_arena_bytes(cap, int(4.2 * cap), 64, "f32", 30) + 4096) / 0.9
     torch.cuda.synchronize()
     free0, total = torch.cuda.mem_get_info()
-    srv = serving.Server(hbm_budget_bytes=budget, dtype="f32", mode="sync")
+    srv = serving.Server(hbm_budget_bytes=budget, dtype="f32", mode="sync", groups=1)
     assert srv.cells == cap
     srv._engine()
     torch.cuda.synchronize()
@@ -136,10 +140,13 @@ def test_step_rejects_a_partial_list():
     assert u["used"]["systems"] == 2 and u["used"]["rows"] == 256   # 96 and 90 cells, 128 rows each
     big = gen.small_system(45, 45, seed=3)      # 4,050 cells: 4,096 rows > 4,096 - 256 free
     assert eng.add(torch.from_numpy(big.rowptr).cuda(), torch.from_numpy(big.colind).cuda()) is None
+    pbig = ab.Pattern(torch.from_numpy(big.rowptr).cuda(), torch.from_numpy(big.colind).cuda())
+    assert eng.add_pattern(pbig) is None and pbig.handle    # refused: the caller keeps it
     eng.remove(ids[1])                          # room again once a system leaves
     assert eng.usage()["used"]["rows"] == 128
     fits = gen.small_system(40, 40, seed=3)     # 3,200 cells
-    assert eng.add(torch.from_numpy(fits.rowptr).cuda(), torch.from_numpy(fits.colind).cuda()) is not None
+    pfit = ab.Pattern(torch.from_numpy(fits.rowptr).cuda(), torch.from_numpy(fits.colind).cuda())
+    assert eng.add_pattern(pfit) is not None and not pfit.handle   # the server owns it now
 
 
 @pytest.mark.slow
