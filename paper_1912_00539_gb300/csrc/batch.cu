@@ -9,9 +9,10 @@
 // that step for every system at once: the single-system kernels run
 // unchanged, one launch for the whole batch (the large systems load-balance
 // the small ones across the GPU).  The padding makes every 64-row chunk belong
-// to one system, so the Krylov kernels below give each CTA one chunk and keep a
-// separate FGMRES state per system: per-system dot products and norms (the
-// partials of a system's chunks summed in order by the last of them to finish),
+// to one system, so the Krylov kernels below keep a separate FGMRES state per
+// system: per-system dot products and norms (each CTA of a reducing kernel
+// sums a run of up to 16 of one system's chunks, and the partials of a
+// system's runs are summed in order by the last of them to finish),
 // per-system Hessenberg, Givens rotations and convergence.  The systems iterate
 // in lockstep; a system that has converged (or left its cycle) skips its
 // chunks in the Krylov kernels.  Padding rows have b = 0 and stay x = 0, so they
@@ -58,6 +59,19 @@ struct BConf {
     int max_iters, m;
 };
 
+// The reducing kernels (residual, Gram-Schmidt dots, norms) give each CTA a
+// super-chunk: up to SUPER_CHUNKS consecutive 64-row chunks of one system, so
+// one block reduction covers up to 4,096 values (one per 256 values made the
+// reductions' latency, not memory, bound those kernels).  A system's
+// super-chunks split its chunks from its first one, whatever its place in
+// the batch, so its reductions are the same alone and in any batch.
+constexpr int SUPER_CHUNKS = 16;
+struct BTab {
+    const int *sc_first;   // [nsc + 1] first chunk of each super-chunk
+    const int *sc_sys;     // [nsc] its system
+    const int *sys_sc0;    // [nsys + 1] first super-chunk of each system
+};
+
 __device__ __forceinline__ bool last_cta_of(BState *St, int nck) {
     __shared__ bool am_last;
     __threadfence();
@@ -89,33 +103,33 @@ __device__ __forceinline__ void reduce_sys(const double *partials, int c0, int c
 // the system's last chunk sets beta, the convergence state and a new cycle
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
-             const double *__restrict__ x, double *__restrict__ r_out, BState *S,
-             const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
+             const double *__restrict__ x, double *__restrict__ r_out, BState *S, BTab T,
              double *partials, BConf cf, int init, int *hs_done, int *hs_fin, int *sys_done,
              int *bflag) {
     pdl_wait();
     pdl_trigger();
     __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
-    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (!init && St->finished) return;  // whole system skips
-    const int i = chunk * CHUNK_ROWS + (threadIdx.x >> 2), q = threadIdx.x & 3;
+    const int q = threadIdx.x & 3;
     double v[2] = {0.0, 0.0};
-    {
+    for (int chunk = T.sc_first[sc]; chunk < T.sc_first[sc + 1]; chunk++) {
+        const int i = chunk * CHUNK_ROWS + (threadIdx.x >> 2);
         // a solve starts from x = 0, where r = b needs no product
         const double acc = init ? 0.0 : row_dot_blocks(P, A, x, i, q);
         const size_t o = (size_t)i * BS + q;
         const double bi = b[o], ri = bi - acc;
         r_out[o] = ri;
-        v[0] = ri * ri;
-        v[1] = bi * bi;
+        v[0] = fma(ri, ri, v[0]);
+        v[1] = fma(bi, bi, v[1]);
     }
     block_sum<2>(v, sh_w, sh_o, 2);
     if (threadIdx.x == 0) {
-        partials[(size_t)chunk * 2 + 0] = sh_o[0];
-        partials[(size_t)chunk * 2 + 1] = sh_o[1];
+        partials[(size_t)sc * 2 + 0] = sh_o[0];
+        partials[(size_t)sc * 2 + 1] = sh_o[1];
     }
-    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];
     if (!last_cta_of(St, c1 - c0)) return;
     reduce_sys<2, 2>(partials, c0, c1, 0, 2, sh_w, sh_o);
     if (threadIdx.x == 0) {
@@ -167,44 +181,56 @@ k_b_scale(const double *vin, double *vout, float *v32, const BState *S,
     if (v32) v32[e] = to_f32_int(t);
 }
 
+// partial dots <V_k0+k, w> over the super-chunk's chunks c0..c1-1 (one value
+// per thread per chunk), one block reduction, partials of super-chunk sc
 template <int K>
 __device__ __forceinline__ void b_dots_tile(const double *__restrict__ V, size_t nv, int k0,
-                                            double wv, size_t e, double *sh_w, double *sh_o,
-                                            double *partials, int chunk) {
+                                            const double *__restrict__ w, int c0, int c1,
+                                            double *sh_w, double *sh_o, double *partials, int sc) {
     double acc[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) acc[k] = V[(size_t)(k0 + k) * nv + e] * wv;
+    for (int k = 0; k < K; k++) acc[k] = 0.0;
+    for (int c = c0; c < c1; c++) {
+        const size_t e = (size_t)c * CHUNK_VALS + threadIdx.x;
+        const double wv = w[e];
+#pragma unroll
+        for (int k = 0; k < K; k++) acc[k] = fma(V[(size_t)(k0 + k) * nv + e], wv, acc[k]);
+    }
     block_sum<K>(acc, sh_w, sh_o, K);
-    if (threadIdx.x < K) partials[(size_t)chunk * PSTRIDE + k0 + threadIdx.x] = sh_o[threadIdx.x];
+    if (threadIdx.x < K) partials[(size_t)sc * PSTRIDE + k0 + threadIdx.x] = sh_o[threadIdx.x];
+}
+
+// the dots tiles of jp1 basis vectors over a super-chunk
+__device__ __forceinline__ void b_dots_tiles(const double *__restrict__ V, size_t nv, int jp1,
+                                             const double *__restrict__ w, int c0, int c1,
+                                             double *sh_w, double *sh_o, double *partials, int sc) {
+    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
+        switch (jp1 - k0 < BTILE ? jp1 - k0 : BTILE) {
+        case 1: b_dots_tile<1>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 2: b_dots_tile<2>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 3: b_dots_tile<3>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 4: b_dots_tile<4>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 5: b_dots_tile<5>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 6: b_dots_tile<6>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 7: b_dots_tile<7>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        default: b_dots_tile<8>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        }
+    }
 }
 
 // h[k] = <V_k, w>_s for k <= j, per system (pass 0 -> h, 1 -> h2)
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_dots(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w, BState *S,
-         const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0, double *partials,
-         int pass) {
+         BTab T, double *partials, int pass) {
     pdl_wait();
     pdl_trigger();
     __shared__ double sh_w[RED_WARPS * BTILE], sh_o[BTILE];
-    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (St->done) return;
-    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
-    const double wv = w[e];
     const int jp1 = j + 1;
-    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
-        switch (jp1 - k0 < BTILE ? jp1 - k0 : BTILE) {
-        case 1: b_dots_tile<1>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 2: b_dots_tile<2>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 3: b_dots_tile<3>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 4: b_dots_tile<4>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 5: b_dots_tile<5>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 6: b_dots_tile<6>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 7: b_dots_tile<7>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        default: b_dots_tile<8>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        }
-    }
-    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    b_dots_tiles(V, nv, jp1, w, T.sc_first[sc], T.sc_first[sc + 1], sh_w, sh_o, partials, sc);
+    const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];
     if (!last_cta_of(St, c1 - c0)) return;
     double *h = pass == 0 ? St->h : St->h2;
     for (int k0 = 0; k0 < jp1; k0 += BTILE) {
@@ -224,29 +250,31 @@ __device__ __forceinline__ void b_givens(BState *St, int s, int j, int two_pass,
 // chunk applies the Givens update of column j and the convergence test
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ w, BState *S,
-           const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
-           double *partials, BConf cf, int pass, int final_pass, int *hs_done, int *sys_done,
-           int *bflag) {
+           BTab T, double *partials, BConf cf, int pass, int final_pass, int *hs_done,
+           int *sys_done, int *bflag) {
     pdl_wait();
     pdl_trigger();
     __shared__ double sh_h[BMAXM + 1];
     __shared__ double sh_w[RED_WARPS], sh_o[1];
-    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (St->done) return;
     const int jp1 = j + 1;
     const double *hsrc = pass == 0 ? St->h : St->h2;
     for (int k = threadIdx.x; k < jp1; k += blockDim.x) sh_h[k] = hsrc[k];
     __syncthreads();
-    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
-    double t = w[e];
-    for (int k = 0; k < jp1; k++) t = fma(-sh_h[k], V[(size_t)k * nv + e], t);
-    w[e] = t;
+    double nrm[1] = {0.0};
+    for (int chunk = T.sc_first[sc]; chunk < T.sc_first[sc + 1]; chunk++) {
+        const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
+        double t = w[e];
+        for (int k = 0; k < jp1; k++) t = fma(-sh_h[k], V[(size_t)k * nv + e], t);
+        w[e] = t;
+        nrm[0] = fma(t, t, nrm[0]);
+    }
     if (!final_pass) return;
-    double nrm[1] = {t * t};
     block_sum<1>(nrm, sh_w, sh_o, 1);
-    if (threadIdx.x == 0) partials[(size_t)chunk * PSTRIDE + BMAXM + 1] = sh_o[0];
-    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    if (threadIdx.x == 0) partials[(size_t)sc * PSTRIDE + BMAXM + 1] = sh_o[0];
+    const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];
     if (!last_cta_of(St, c1 - c0)) return;
     reduce_sys<1, PSTRIDE>(partials, c0, c1, BMAXM + 1, 1, sh_w, sh_o);
     if (threadIdx.x != 0) return;
@@ -300,35 +328,27 @@ __device__ __forceinline__ void b_givens(BState *St, int s, int j, int two_pass,
 // difference below 1e-12 ||w||^2 is a breakdown) and the Givens update.
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_dots_norm(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w,
-              BState *S, const int *__restrict__ chunk_sys, const int *__restrict__ sys_chunk0,
-              double *partials, BConf cf, int *hs_done, int *sys_done, int *bflag) {
+              BState *S, BTab T, double *partials, BConf cf, int *hs_done, int *sys_done,
+              int *bflag) {
     pdl_wait();
     pdl_trigger();
     __shared__ double sh_w[RED_WARPS * BTILE], sh_o[BTILE];
-    const int chunk = blockIdx.x, s = chunk_sys[chunk];
+    const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (St->done) return;
-    const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
-    const double wv = w[e];
     const int jp1 = j + 1;
-    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
-        switch (jp1 - k0 < BTILE ? jp1 - k0 : BTILE) {
-        case 1: b_dots_tile<1>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 2: b_dots_tile<2>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 3: b_dots_tile<3>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 4: b_dots_tile<4>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 5: b_dots_tile<5>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 6: b_dots_tile<6>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        case 7: b_dots_tile<7>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        default: b_dots_tile<8>(V, nv, k0, wv, e, sh_w, sh_o, partials, chunk); break;
-        }
-    }
+    const int f0 = T.sc_first[sc], f1 = T.sc_first[sc + 1];
+    b_dots_tiles(V, nv, jp1, w, f0, f1, sh_w, sh_o, partials, sc);
     {
-        double nrm[1] = {wv * wv};
+        double nrm[1] = {0.0};
+        for (int c = f0; c < f1; c++) {
+            const double wv = w[(size_t)c * CHUNK_VALS + threadIdx.x];
+            nrm[0] = fma(wv, wv, nrm[0]);
+        }
         block_sum<1>(nrm, sh_w, sh_o, 1);
-        if (threadIdx.x == 0) partials[(size_t)chunk * PSTRIDE + BMAXM + 1] = sh_o[0];
+        if (threadIdx.x == 0) partials[(size_t)sc * PSTRIDE + BMAXM + 1] = sh_o[0];
     }
-    const int c0 = sys_chunk0[s], c1 = sys_chunk0[s + 1];
+    const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];
     if (!last_cta_of(St, c1 - c0)) return;
     for (int k0 = 0; k0 < jp1; k0 += BTILE) {
         const int kn = jp1 - k0 < BTILE ? jp1 - k0 : BTILE;
@@ -448,6 +468,8 @@ struct abilu_batch_s {
     int32_t *rowptr, *colind;   // concatenation (device)
     double *A, *b, *x;          // concatenation (device)
     int *chunk_sys, *sys_chunk0;
+    int *sc_tab;                // super-chunks: sc_first [nsc + 1], sc_sys [nsc], sys_sc0 [nsys + 1]
+    int nsc;
     BState *S;
     double *partials;
     double *krylov;
@@ -466,6 +488,35 @@ struct abilu_batch_s {
     std::vector<void *> allocs;
     int arena;                  // 1: a server's arena (capacity allocation, re-laid out)
 };
+
+// The super-chunk tables of the current systems (their chunk ranges in
+// b->chunk0) into `h` (host, 2 * nchunks + nsys + 2 ints at least), then to
+// the device on `st` (h must stay valid until the copy is done).
+static abilu_status batch_super_chunks(abilu_batch b, int *h, cudaStream_t st) {
+    const int nsys = b->nsys;
+    std::vector<int> first, sys, s0(nsys + 1);
+    for (int q = 0; q < nsys; q++) {
+        s0[q] = (int)first.size();
+        for (int c = b->chunk0[q]; c < b->chunk0[q + 1]; c += SUPER_CHUNKS) {
+            first.push_back(c);
+            sys.push_back(q);
+        }
+    }
+    const int nsc = (int)first.size();
+    s0[nsys] = nsc;
+    first.push_back(b->chunk0[nsys]);
+    memcpy(h, first.data(), sizeof(int) * (nsc + 1));
+    memcpy(h + nsc + 1, sys.data(), sizeof(int) * nsc);
+    memcpy(h + 2 * nsc + 1, s0.data(), sizeof(int) * (nsys + 1));
+    ABILU_CUDA(cudaMemcpyAsync(b->sc_tab, h, sizeof(int) * (2 * nsc + nsys + 2),
+                               cudaMemcpyHostToDevice, st));
+    b->nsc = nsc;
+    return ABILU_OK;
+}
+
+static BTab batch_tab(abilu_batch b) {
+    return BTab{b->sc_tab, b->sc_tab + b->nsc + 1, b->sc_tab + 2 * b->nsc + 1};
+}
 
 static void batch_free(abilu_batch b) {
     if (!b) return;
@@ -544,6 +595,7 @@ extern "C" abilu_status abilu_batch_create(int32_t nsys, const int32_t *n, const
     TRY(alloc((void **)&b->x, sizeof(double) * BS * rows));
     TRY(alloc((void **)&b->chunk_sys, sizeof(int) * b->nchunks));
     TRY(alloc((void **)&b->sys_chunk0, sizeof(int) * (nsys + 1)));
+    TRY(alloc((void **)&b->sc_tab, sizeof(int) * (2 * (size_t)b->nchunks + nsys + 2)));
     TRY(alloc((void **)&b->S, sizeof(BState) * nsys));
     TRY(alloc((void **)&b->partials, sizeof(double) * PSTRIDE * b->nchunks));
     TRY(alloc((void **)&b->sys_done, sizeof(int) * nsys));
@@ -573,6 +625,8 @@ extern "C" abilu_status abilu_batch_create(int32_t nsys, const int32_t *n, const
     TRY(cu(cudaMemcpyAsync(b->rowptr + rows, &last, sizeof last, cudaMemcpyHostToDevice, st), "rowptr end"));
     TRY(cu(cudaMemcpyAsync(b->sys_chunk0, b->chunk0.data(), sizeof(int) * (nsys + 1),
                            cudaMemcpyHostToDevice, st), "chunk table"));
+    std::vector<int> h_sc(2 * (size_t)b->nchunks + nsys + 2);
+    TRY(batch_super_chunks(b, h_sc.data(), st));
     TRY(cu(cudaStreamSynchronize(st), "sync"));
     TRY(abilu_pattern_create(b->rows, b->blocks, b->rowptr, b->colind, stream, &b->pat));
     TRY(abilu_factors_create(b->pat, dtype, &b->fac));
@@ -638,20 +692,20 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
                                     (abilu_mode)opts->mode, st, skip);
     if (s != ABILU_OK) return s;
     if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
+    const BTab T = batch_tab(b);
+    const int nsc = b->nsc;
     if (!opts->reorth) {   // one pass, one reduction per system
-        launch_pdl(k_b_dots_norm, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-            b->sys_chunk0, b->partials, cf, b->hs_done, b->sys_done, b->bflag);
+        launch_pdl(k_b_dots_norm, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf,
+            b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_update_scale, nck, RED_THREADS, 0, st, V, nv, j, w,
             V + (size_t)(j + 1) * nv, v32, b->S, b->chunk_sys);
     } else {               // CGS2: two passes, the norm of the updated w
-        launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-            b->sys_chunk0, b->partials, 0);
-        launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-            b->sys_chunk0, b->partials, cf, 0, 0, b->hs_done, b->sys_done, b->bflag);
-        launch_pdl(k_b_dots, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-            b->sys_chunk0, b->partials, 1);
-        launch_pdl(k_b_update, nck, RED_THREADS, 0, st, V, nv, j, w, b->S, b->chunk_sys,
-            b->sys_chunk0, b->partials, cf, 1, 1, b->hs_done, b->sys_done, b->bflag);
+        launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 0);
+        launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 0, 0,
+            b->hs_done, b->sys_done, b->bflag);
+        launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 1);
+        launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 1, 1,
+            b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
             b->chunk_sys);
     }
@@ -669,9 +723,8 @@ static abilu_status enqueue_restart(abilu_batch b, const BConf &cf, cudaStream_t
     k_b_ysolve<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
     launch_pdl(k_b_xupdate, nck, RED_THREADS, 0, st, Z, nv, b->x, b->S, b->chunk_sys);
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
-    launch_pdl(k_b_residual, nck, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
-        b->sys_chunk0, b->partials, cf, 0, b->hs_done,
-        b->hs_fin, b->sys_done, b->bflag);
+    launch_pdl(k_b_residual, b->nsc, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, batch_tab(b),
+        b->partials, cf, 0, b->hs_done, b->hs_fin, b->sys_done, b->bflag);
     launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch restart");
     return ABILU_OK;
@@ -795,9 +848,8 @@ static abilu_status batch_solve_core(abilu_batch b, const fgmres_opts *opts, fgm
     ABILU_CUDA(cudaMemsetAsync(b->S, 0, sizeof(BState) * nsys, st));
     k_b_init<<<counted((nsys + 127) / 128), 128, 0, st>>>(b->S, nsys);
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
-    launch_pdl(k_b_residual, nck, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, b->chunk_sys,
-        b->sys_chunk0, b->partials, cf, 1, b->hs_done,
-        b->hs_fin, b->sys_done, b->bflag);
+    launch_pdl(k_b_residual, b->nsc, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, batch_tab(b),
+        b->partials, cf, 1, b->hs_done, b->hs_fin, b->sys_done, b->bflag);
     launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
     ABILU_LAUNCH_CHECK("batch init");
     // the cycle graph: captured once per (restart, sweeps, mode, reorth, factor
@@ -1128,6 +1180,7 @@ extern "C" abilu_status abilu_server_create(const abilu_server_opts *o, abilu_st
     TRY(alloc(ba, (void **)&b->x, sizeof(double) * BS * c.rows));
     TRY(alloc(ba, (void **)&b->chunk_sys, sizeof(int) * (chunks + 1)));
     TRY(alloc(ba, (void **)&b->sys_chunk0, sizeof(int) * (c.sys + 1)));
+    TRY(alloc(ba, (void **)&b->sc_tab, sizeof(int) * (2 * (size_t)chunks + c.sys + 2)));
     TRY(alloc(ba, (void **)&b->S, sizeof(BState) * c.sys));
     TRY(alloc(ba, (void **)&b->partials, sizeof(double) * PSTRIDE * (chunks + 1)));
     TRY(alloc(ba, (void **)&b->sys_done, sizeof(int) * (c.sys + 1)));
@@ -1140,8 +1193,9 @@ extern "C" abilu_status abilu_server_create(const abilu_server_opts *o, abilu_st
     TRY(cu(cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking), "stream"));
     TRY(cu(cudaHostAlloc((void **)&b->hs_done, sizeof(int) * c.sys, cudaHostAllocMapped), "hostalloc"));
     TRY(cu(cudaHostAlloc((void **)&b->hs_fin, sizeof(int) * c.sys, cudaHostAllocMapped), "hostalloc"));
-    // staging: chunk_sys [chunks], sys_chunk0 [systems + 1], chunk_init [chunks]
-    TRY(cu(cudaHostAlloc((void **)&sv->staging, sizeof(int) * (2 * chunks + c.sys + 1),
+    // staging: chunk_sys [chunks], sys_chunk0 [systems + 1], chunk_init [chunks],
+    // super-chunk tables [2 chunks + systems + 2]
+    TRY(cu(cudaHostAlloc((void **)&sv->staging, sizeof(int) * (4 * chunks + 2 * c.sys + 3),
                          cudaHostAllocDefault), "hostalloc"));
     // the arena's pattern: arrays with the capacities, analysed by relocation
     abilu_pattern p = new abilu_pattern_s();
@@ -1398,6 +1452,9 @@ static abilu_status server_relayout(abilu_server sv, const std::vector<int> &ord
     v.npairs = Pb;
     v.nwork = (int32_t)Wb;
     P->max_row = maxrow;
+    abilu_status sst = batch_super_chunks(b, sv->staging + 2 * (sv->cap.rows / 64) + sv->cap.sys + 1,
+                                          st);
+    if (sst != ABILU_OK) return sst;
     sv->layout.clear();
     for (int q = 0; q < k; q++) sv->layout.push_back(sv->mem[order[q]].id);
     return ABILU_OK;
