@@ -50,8 +50,8 @@ def _dist():
 # captured again)
 PROFILED_TRAFFIC = {
     "spmv_f64": 295.448832e6 + 15.170560e6,          # k_spmv<1>
-    "build_sweeps_f32": 1.503612e9 + 534.555392e6,   # k_build_blocks_async<float, 1>, 6 sweeps,
-                                                     # tickets of 128 work blocks
+    "build_sweeps_f32": None,                        # k_build_blocks_async: windowed order,
+                                                     # since its last capture
     "lower_sweeps_f32": None,                        # k_tri_staged: changed (bounded-wait drain)
     "upper_sweeps_f32": None,                        # since its last capture
 }

@@ -248,16 +248,22 @@ abilu_status abilu_factors_set_spin_limit(abilu_factors f, int64_t limit);
 
 /* Launch shape of the asynchronous block build (FP32/BF16 factors): the work
  * blocks a warp takes per ticket from the build's queue (a multiple of 32 in
- * 32..512; 0 restores the default, 128).  Any value gives a legal asynchronous
- * iteration (Algorithm 4 with blocks); it trades the contention on the one
- * ticket counter against load balance.  An autotuner's knob
+ * 32..512; 0 restores the default, 128).  A ticket is made of sub-chunks of
+ * 64 consecutive blocks (32 for sizes that are not multiples of 64) spread
+ * evenly over the work list, so the blocks in flight cover one short span in
+ * each part of the list.  Any value gives a legal asynchronous iteration
+ * (Algorithm 4 with blocks); it trades the contention on the one ticket
+ * counter against load balance and against how many of the rows a block
+ * reads were already updated in the current sweep (a shorter span in flight
+ * per part of the list leaves a lower ILU fixed-point residual after the same
+ * sweeps).  An autotuner's knob
  * (abilu_batch_set_build_chunk sets it on a batch's factors). */
 abilu_status abilu_factors_set_build_chunk(abilu_factors f, int32_t blocks);
 
 /* Failure injection for tests of the bounded waits (no counterpart in the
  * paper).  With `enable` nonzero, the next asynchronous build of block factors
  * on `f` that uses the ordered variant (the work list has fewer than four
- * 128-block chunks per resident warp, i.e. every small system) starts its
+ * tickets per resident warp: every small system) starts its
  * per-chunk sweep flags one sweep behind, a value no warp ever publishes: the
  * first wait of every chunk polls `spin_limit` times, gives up, counts a
  * timeout and the warp stops.  That build leaves the factors partly swept,

@@ -14,9 +14,11 @@ of similar workloads reuse it.
 
 Launch shape: the asynchronous block build hands out its work in tickets of
 `build_chunk` work blocks per warp (abilu_factors_set_build_chunk); small
-tickets balance the load but contend on the one ticket counter, large ones
-the reverse, and the best size moves with the system's size, so it is a
-candidate of the asynchronous mode.  The other kernels' shapes are fixed by
+tickets balance the load, and leave a lower ILU residual after the same
+sweeps (the tickets in flight span fewer blocks, so more of the rows a block
+reads are already updated in the current sweep), but contend on the one
+ticket counter; the best size moves with the system's size and with the
+sweep count, so it is a candidate of the asynchronous mode.  The other kernels' shapes are fixed by
 the data: 4 threads per block row (one per row of a 4x4 block: a 16-byte FP32
 or 32-byte FP64 row per thread, quad shuffles for the block products; 8 or 16
 threads would split a row below one element per thread) and 64 rows per CTA

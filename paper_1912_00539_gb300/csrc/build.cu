@@ -405,11 +405,23 @@ k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__res
 
 // In place.  Each warp takes tickets t = 0 .. nsweeps*nchunks-1 in order from
 // one counter (no CTA barrier, so warps never wait for each other); ticket t
-// is chunk (t mod nchunks) of sweep t / nchunks, a chunk being 128 consecutive
-// work blocks, done in 16 steps of 8 (one block per quad, consecutive blocks,
-// so a step stays within one kind of the kind-sorted list).  128 blocks per
-// ticket keep the contended counter's atomics few (measured at 512x512, 6
-// sweeps: 449 us with 32, 437-440 with 64 and 128, 503 with 256).
+// is chunk c = t mod nchunks of sweep t / nchunks.  A chunk is `wchunk` work
+// blocks in sub-chunks of `sub` consecutive blocks (64, one kind-sorted group
+// of the list, or 32 for sizes that are not multiples of 64) taken at a stride
+// of nchunks sub-chunks: sub-chunks c, c + nchunks, c + 2 nchunks, ...  Each
+// sub-chunk is done in steps of 8 blocks (one block per quad, consecutive
+// blocks, so a step stays within one kind).
+//
+// Why the stride: the ILU fixed-point residual after a given number of sweeps
+// falls as the blocks in flight (resident warps x blocks per ticket) span
+// fewer consecutive blocks, because then more of the rows a block reads were
+// already updated in the current sweep (the in-place iteration's Gauss-Seidel
+// effect).  At 512x512 (1.31 M work blocks, 6,080 warps), 6 sweeps, tickets
+// of 128 consecutive blocks left an ILU residual of 44 in 437.7 us, of 64
+// blocks 4.1 in 442-444 us (twice the atomics on the one contended counter).
+// A 128-block ticket made of two 64-block sub-chunks half the list apart (the
+// default) keeps the 128-block atomic count while each half of the list sees
+// the 64-block span: 4.9 in 429.7 us.
 //
 // ORDERED (with `done`): the sweeps of one chunk run in order.  Tickets of
 // the same chunk in consecutive sweeps are nchunks apart, so when chunks are
@@ -422,7 +434,17 @@ k_build_blocks_sync(PatternView P, const float *__restrict__ A32, const T *__res
 // copy is in flight in this kernel, so a warp that gives up can simply return.
 constexpr int WARP_CHUNK = 128;   // default work blocks per ticket (abilu_factors_set_build_chunk)
 
-template <typename T, bool ORDERED>
+// Sub-chunk size of a ticket of `wchunk` blocks (a multiple of 32) and the
+// number of tickets per sweep: the kernel and its launcher share this.
+__host__ __device__ __forceinline__ int build_sub(int wchunk) { return wchunk % 64 == 0 ? 64 : 32; }
+__host__ __device__ __forceinline__ long long build_tickets(int nwork, int wchunk) {
+    const int sub = build_sub(wchunk);
+    const long long nsub = (nwork + sub - 1) / sub;
+    const int per = wchunk / sub;
+    return (nsub + per - 1) / per;
+}
+
+template <typename T, bool ORDERED, int SUB>
 __global__ void __launch_bounds__(BUILD_THREADS, 5)   // 48 registers: measured fastest (4, 6 slower)
 k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T *D, T *Udiag,
                      int nsweeps, int max_warps, unsigned long long *nsing,
@@ -433,8 +455,9 @@ k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T
     __shared__ __align__(16) float sh_q[WORK_PER_CTA * QUAD_SCRATCH];
     // at most one warp per chunk: more would sweep the same blocks at once
     if (blockIdx.x * (BUILD_THREADS / 32) + (threadIdx.x >> 5) >= max_warps) return;
-    const long long nchunks = (P.nwork + wchunk - 1) / wchunk;
+    const long long nchunks = build_tickets(P.nwork, wchunk);
     const long long total = nchunks * nsweeps;
+    const int stride = (int)nchunks * SUB;   // blocks between a ticket's sub-chunks
     const int lane = threadIdx.x & 31;
     float *myq = sh_q + (threadIdx.x >> 2) * QUAD_SCRATCH;
     for (;;) {
@@ -444,7 +467,6 @@ k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T
         if (t >= total) break;
         const int sweep = (int)(t / nchunks), chunk = (int)(t % nchunks);
         const bool last = sweep == nsweeps - 1;
-        const int base = chunk * wchunk + (lane >> 2);
         if constexpr (ORDERED) {  // wait for this chunk's previous sweep
             int ok = 1;
             if (lane == 0) {
@@ -457,9 +479,14 @@ k_build_blocks_async(PatternView P, const float *__restrict__ A32, T *L, T *U, T
             }
             if (!__shfl_sync(0xffffffffu, ok, 0)) return;
         }
+        // step k: sub-chunk chunk + (k / steps) nchunks, its 8 blocks k mod
+        // steps (32-bit: block indices stay below (nsub + wchunk / 32) * 64,
+        // and nwork <= nnzb < 2^31 - 2^16)
+        constexpr int SSH = SUB == 64 ? 3 : 2;   // log2(steps per sub-chunk)
+        const int base = chunk * SUB + (lane >> 2);
 #pragma unroll 1
         for (int k = 0; k < wchunk / 8; k++) {
-            const int w = base + 8 * k;
+            const int w = base + (k >> SSH) * stride + ((k & ((1 << SSH) - 1)) << 3);
             if (w < P.nwork)
                 build_block<T, true>(P, w, A32, L, U, D, L, U, D, last ? Udiag : nullptr, myq, nsing);
         }
@@ -654,12 +681,12 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
         cudaGetDevice(&dev);
         if (per_sm < 0) {   // the ordered variant is held to the same occupancy
             ABILU_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, k_build_blocks_async<T, false>, BUILD_THREADS, 0));
+                &per_sm, k_build_blocks_async<T, false, 64>, BUILD_THREADS, 0));
             per_sm_cache.store(per_sm, std::memory_order_relaxed);
         }
         ABILU_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const int wc = f->build_chunk ? f->build_chunk : WARP_CHUNK;
-        const int wchunks = (P.nwork + wc - 1) / wc;
+        const int wchunks = (int)build_tickets(P.nwork, wc);
         int warps = per_sm * sms * (BUILD_THREADS / 32);
         if (warps > wchunks) warps = wchunks;
         if (warps < 1) warps = 1;
@@ -680,14 +707,13 @@ static abilu_status block_sweeps_t(abilu_factors f, const float *A32, int nsweep
         }
         const int c = f->cur;
         const unsigned long long lim = spin_limit_or_default(f->spin_limit);
-        if (done)
-            launch_pdl(k_build_blocks_async<T, true>, ctas, BUILD_THREADS, 0, st,
-                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done,
-                lim, wc);
-        else
-            launch_pdl(k_build_blocks_async<T, false>, ctas, BUILD_THREADS, 0, st,
-                P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done,
-                lim, wc);
+        auto kern = done ? (build_sub(wc) == 64 ? k_build_blocks_async<T, true, 64>
+                                                : k_build_blocks_async<T, true, 32>)
+                         : (build_sub(wc) == 64 ? k_build_blocks_async<T, false, 64>
+                                                : k_build_blocks_async<T, false, 32>);
+        launch_pdl(kern, ctas, BUILD_THREADS, 0, st,
+            P, A32, L[c], U[c], D[c], Ud, nsweeps, warps, f->ctr, f->ctr + 1, f->ctr + 4, done,
+            lim, wc);
         ABILU_LAUNCH_CHECK("k_build_blocks_async");
     }
     return ABILU_OK;

@@ -300,6 +300,11 @@ extern "C" abilu_status abilu_pattern_create(int32_t n, int32_t nnzb, const int3
     if (!out) return fail(ABILU_EINVAL, "pattern_create: out is NULL");
     *out = nullptr;
     if (n < 1 || nnzb < n) return fail(ABILU_EINVAL, "pattern_create: need n >= 1 and nnzb >= n (n=%d nnzb=%d)", n, nnzb);
+    // block indices of the build's work list stay 32-bit with slack for its
+    // last ticket (far beyond any system that fits the device: 2^31 blocks of
+    // A alone are 275 GB)
+    if (nnzb > INT32_MAX - (1 << 16))
+        return fail(ABILU_EINVAL, "pattern_create: nnzb=%d above 2^31 - 2^16", nnzb);
     if (!rowptr || !colind) return fail(ABILU_EINVAL, "pattern_create: NULL rowptr/colind");
     cudaStream_t st = S(stream);
     abilu_pattern p = new abilu_pattern_s();
