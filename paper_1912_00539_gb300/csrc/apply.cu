@@ -454,9 +454,14 @@ template <bool UPPER, bool SCALED, bool SYNC, typename T> static int staged_ctas
 }
 
 
+// y_ready (asynchronous mode, FP32/BF16 factors, nl >= 2): the caller already
+// wrote y[0] = the FP32 right-hand side and zeroed the two ticket counters in
+// an earlier kernel on `st` (FGMRES does it where it writes that right-hand
+// side), so k_async_start, which would only do the same, is not launched.
 template <typename T>
 static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_in, double *z,
-                            int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip) {
+                            int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip,
+                            bool y_ready = false) {
     using VT = typename ApplyArith<T>::VT;
     const PatternView &P = f->p->v;
     const int c = f->cur;
@@ -500,10 +505,12 @@ static abilu_status apply_t(abilu_factors f, const double *r, const float *r32_i
         VT *x1 = nu >= 2 ? x[0] : nullptr;     // x^1, updated in place by the upper sweeps
         VT *yh = SC && nu >= 2 ? y[1] : nullptr;
         double *z1 = nu == 1 ? z : nullptr;
-        launch_pdl(k_async_start<T, VT>, grid, APPLY_THREADS, 0, st,
-            P, D, rv, y[0], nl == 1 ? x1 : nullptr, nl == 1 ? yh : nullptr, nl == 1 ? z1 : nullptr,
-            tk, skip);
-        ABILU_LAUNCH_CHECK("k_async_start");
+        if (!(y_ready && sizeof(VT) == 4 && nl >= 2)) {
+            launch_pdl(k_async_start<T, VT>, grid, APPLY_THREADS, 0, st,
+                P, D, rv, y[0], nl == 1 ? x1 : nullptr, nl == 1 ? yh : nullptr, nl == 1 ? z1 : nullptr,
+                tk, skip);
+            ABILU_LAUNCH_CHECK("k_async_start");
+        }
         unsigned long long *err = f->ctr + 4;
         const unsigned long long lim = spin_limit_or_default(f->spin_limit);
         if (nl >= 2) {
@@ -616,6 +623,22 @@ abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, 
     case ABILU_BF16: return apply_t<__nv_bfloat16>(f, r, r32, z, nl, nu, mode, st, skip);
     }
     return fail(ABILU_EINVAL, "apply: bad dtype");
+}
+
+// The application when apply_y_ready(f, nl, mode) holds and the caller wrote
+// y[0] and zeroed the tickets (see apply_t)
+abilu_status apply_dispatch_ready(abilu_factors f, const double *r, const float *r32, double *z,
+                                  int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip) {
+    if (f->dtype == ABILU_F32)
+        return apply_t<float>(f, r, r32, z, nl, nu, mode, st, skip, true);
+    return apply_t<__nv_bfloat16>(f, r, r32, z, nl, nu, mode, st, skip, true);
+}
+
+// Whether an application can start from a y[0] and tickets prepared by the
+// caller: asynchronous block factors in FP32/BF16 with at least two lower
+// updates (with one, the start kernel also forms x^1)
+bool apply_y_ready(abilu_factors f, int nl, int nu, abilu_mode mode) {
+    return !f->scalar && f->dtype != ABILU_F64 && mode == ABILU_ASYNC && nl >= 2 && nu >= 1;
 }
 
 }  // namespace abilu

@@ -148,6 +148,11 @@ struct Precond {
                        Skip skip);
     void *ctx;
     float *v32;
+    // optional: a second destination of the FP32 copy (the application's
+    // in-place iterate) and two ticket counters to zero, both done by the
+    // FGMRES kernel that writes v32, so the application needs no start kernel
+    float *y0;
+    unsigned long long *tickets;
 };
 
 __device__ __forceinline__ bool skip_all(const Skip &s) {

@@ -30,6 +30,9 @@ abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu
                             abilu_init init, cudaStream_t st);
 abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
                             int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
+abilu_status apply_dispatch_ready(abilu_factors f, const double *r, const float *r32, double *z,
+                                  int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
+bool apply_y_ready(abilu_factors f, int nl, int nu, abilu_mode mode);
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
                          double beta, double *y, cudaStream_t st, Skip skip);
 abilu_status ensure_krylov(abilu_factors f, int m);
@@ -163,13 +166,22 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
     }
 }
 
+// the preconditioner's ticket counters zeroed for its next application
+// (Precond::tickets; the kernels that write its right-hand side)
+__device__ __forceinline__ void zero_tickets(unsigned long long *tk) {
+    if (tk && blockIdx.x == 0 && threadIdx.x < 2) tk[threadIdx.x] = 0ull;
+}
+
 // v_out = v_in * S->hn_inv; with FP32/BF16 factors also v32 = (float) v_out,
-// the right-hand side the next preconditioner application reads
+// the right-hand side the next preconditioner application reads (and the
+// same into y0, the application's in-place iterate, when given)
 __global__ void __launch_bounds__(RED_THREADS)
-k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *S) {
+k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *S, float *y0,
+        unsigned long long *tk) {
     pdl_wait();
     pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
+    zero_tickets(tk);
     const double s = S->hn_inv;
     const double2 *a = reinterpret_cast<const double2 *>(vin);
     double2 *o = reinterpret_cast<double2 *>(vout);
@@ -189,7 +201,11 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
             if (e + u * st >= nv2) break;
             const double2 r = make_double2(t[u].x * s, t[u].y * s);
             o[e + u * st] = r;
-            if (v32) o32[e + u * st] = make_float2(to_f32_int(r.x), to_f32_int(r.y));
+            if (v32) {
+                const float2 f = make_float2(to_f32_int(r.x), to_f32_int(r.y));
+                o32[e + u * st] = f;
+                if (y0) reinterpret_cast<float2 *>(y0)[e + u * st] = f;
+            }
         }
     }
 }
@@ -452,11 +468,13 @@ static void launch_dots_norm(int nred, cudaStream_t st, const double *V, long lo
 template <int J>
 __global__ void __launch_bounds__(RED_THREADS, 4)
 k_update_scale(const double *__restrict__ V, long long nv2, int j, const double *__restrict__ w,
-               double *__restrict__ vnext, float *__restrict__ v32, SolveState *S) {
+               double *__restrict__ vnext, float *__restrict__ v32, SolveState *S,
+               float *__restrict__ y0, unsigned long long *tk) {
     pdl_wait();
     pdl_trigger();
     publish_early(S);      // the previous kernel's step status
     if (S->done) return;   // the cycle ended at this column: no next vector
+    zero_tickets(tk);
     __shared__ double sh_h[MAXM + 1];
     const int jp1 = j + 1;
     for (int k = threadIdx.x; k < jp1; k += blockDim.x) sh_h[k] = S->h[k];
@@ -466,12 +484,17 @@ k_update_scale(const double *__restrict__ V, long long nv2, int j, const double 
     const double2 *V2 = reinterpret_cast<const double2 *>(V);
     double2 *o2 = reinterpret_cast<double2 *>(vnext);
     float2 *o32 = reinterpret_cast<float2 *>(v32);
+    float2 *y2 = reinterpret_cast<float2 *>(y0);
     const long long st = (long long)gridDim.x * blockDim.x;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     auto out = [&](long long i, double2 t) {
         const double2 r = make_double2(t.x * sc, t.y * sc);
         o2[i] = r;
-        if (v32) o32[i] = make_float2(to_f32_int(r.x), to_f32_int(r.y));
+        if (v32) {
+            const float2 f = make_float2(to_f32_int(r.x), to_f32_int(r.y));
+            o32[i] = f;
+            if (y2) y2[i] = f;
+        }
     };
     if constexpr (J > 0) {
         if (e >= nv2) return;
@@ -526,12 +549,13 @@ k_update_scale(const double *__restrict__ V, long long nv2, int j, const double 
 }
 
 static void launch_update_scale(int nred, cudaStream_t st, const double *V, long long nv2, int j,
-                                const double *w, double *vnext, float *v32, SolveState *S) {
+                                const double *w, double *vnext, float *v32, SolveState *S,
+                                float *y0, unsigned long long *tk) {
     switch (j + 1) {
-    case 1: launch_pdl(k_update_scale<1>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
-    case 2: launch_pdl(k_update_scale<2>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
-    case 3: launch_pdl(k_update_scale<3>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
-    default: launch_pdl(k_update_scale<0>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S); break;
+    case 1: launch_pdl(k_update_scale<1>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S, y0, tk); break;
+    case 2: launch_pdl(k_update_scale<2>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S, y0, tk); break;
+    case 3: launch_pdl(k_update_scale<3>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S, y0, tk); break;
+    default: launch_pdl(k_update_scale<0>, nred, RED_THREADS, 0, st, V, nv2, j, w, vnext, v32, S, y0, tk); break;
     }
 }
 
@@ -752,10 +776,12 @@ struct IluPc {
     abilu_factors f;
     int nl, nu;
     abilu_mode mode;
+    bool y_ready;   // the FGMRES kernels that write v32 also prepare y[0] and the tickets
 };
 static abilu_status ilu_pc(void *ctx, const double *v, const float *v32, double *z,
                            cudaStream_t st, Skip skip) {
     const IluPc *c = static_cast<const IluPc *>(ctx);
+    if (c->y_ready) return apply_dispatch_ready(c->f, v, v32, z, c->nl, c->nu, c->mode, st, skip);
     return apply_dispatch(c->f, v, v32, z, c->nl, c->nu, c->mode, st, skip);
 }
 
@@ -785,7 +811,7 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
     if (opts->zero_guess) ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
     launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1,
         opts->zero_guess ? 1 : 0);
-    launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS);
+    launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS, pc.y0, pc.tickets);
     ABILU_LAUNCH_CHECK("fgmres init");
     // the look-ahead events live in the workspace handle (made on first use)
     for (int k = 0; k < 2; k++)
@@ -806,13 +832,15 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
             if (!opts->reorth) {   // one pass, one reduction (see k_dots_norm)
                 launch_dots_norm(nred, st, V, nv2, j + 1, w, SS, ws->partials);
-                launch_update_scale(nred, st, V, nv2, j, w, V + (size_t)(j + 1) * nv, v32, SS);
+                launch_update_scale(nred, st, V, nv2, j, w, V + (size_t)(j + 1) * nv, v32, SS,
+                                    pc.y0, pc.tickets);
             } else {               // CGS2: two passes, the norm of the updated w
                 launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 0);
                 launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 1);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 1, 1);
-                launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS);
+                launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS,
+                           pc.y0, pc.tickets);
             }
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { ret = cuda_fail(e, "fgmres step"); break; }
@@ -841,7 +869,7 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
         if (ret != ABILU_OK) break;
         launch_pdl(k_xupdate, nred, RED_THREADS, 0, st, Z, nv2, x, SS);
         launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 0, 0);
-        launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS);
+        launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS, pc.y0, pc.tickets);
         // the handles' counters into the status with every cycle's result, so
         // the synchronisation that ends the last cycle also ends the solve
         for (int k = 0; k < ncnt; k++)
@@ -914,8 +942,12 @@ extern "C" abilu_status fgmres_solve(abilu_pattern p, const double *A, abilu_fac
         s = build_dispatch(f, A, opts->build_sweeps, mode, (abilu_init)opts->init, st);
         if (s != ABILU_OK) { f->spin_limit = keep_limit; return s; }
     }
-    IluPc ctx{f, opts->apply_sweeps_lower, opts->apply_sweeps_upper, mode};
-    const Precond pc{ilu_pc, &ctx, reinterpret_cast<float *>(f->r32)};  // v32: NULL for FP64 factors
+    const bool ready = apply_y_ready(f, opts->apply_sweeps_lower, opts->apply_sweeps_upper, mode);
+    IluPc ctx{f, opts->apply_sweeps_lower, opts->apply_sweeps_upper, mode, ready};
+    // v32: NULL for FP64 factors; y0 and the tickets: the asynchronous
+    // application's in-place lower iterate and its ticket counters
+    const Precond pc{ilu_pc, &ctx, reinterpret_cast<float *>(f->r32),
+                     ready ? reinterpret_cast<float *>(f->y[0]) : nullptr, ready ? f->ctr + 2 : nullptr};
     s = fgmres_run(p->v, A, f, pc, b, x, opts, res, st, &f, 1);
     f->spin_limit = keep_limit;
     return s;
