@@ -32,6 +32,9 @@ abilu_status build_dispatch(abilu_factors f, const double *A, int nsweeps, abilu
                             abilu_init init, cudaStream_t st);
 abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, double *z,
                             int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
+abilu_status apply_dispatch_ready(abilu_factors f, const double *r, const float *r32, double *z,
+                                  int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
+bool apply_y_ready(abilu_factors f, int nl, int nu, abilu_mode mode);
 abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
                          double beta, double *y, cudaStream_t st, Skip skip);
 void apply_warm(abilu_dtype dt);
@@ -166,19 +169,32 @@ __global__ void k_b_flags_reset(int *bflag) {
     }
 }
 
-// v_out = v_in * hn_inv of the chunk's system (and the FP32 copy for the apply)
+// The apply's two ticket counters zeroed for its next application (first
+// CTA, whatever its system's state), when the kernels that write its FP32
+// right-hand side also prepare its start (see apply_dispatch_ready)
+__device__ __forceinline__ void b_zero_tickets(unsigned long long *tk) {
+    if (tk && blockIdx.x == 0 && threadIdx.x < 2) tk[threadIdx.x] = 0ull;
+}
+
+// v_out = v_in * hn_inv of the chunk's system (and the FP32 copy for the
+// apply, also into y0, the asynchronous apply's in-place iterate, when given)
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_scale(const double *vin, double *vout, float *v32, const BState *S,
-          const int *__restrict__ chunk_sys) {
+          const int *__restrict__ chunk_sys, float *y0, unsigned long long *tk) {
     pdl_wait();
     pdl_trigger();
+    b_zero_tickets(tk);
     const int chunk = blockIdx.x;
     const BState *St = S + chunk_sys[chunk];
     if (St->done) return;
     const size_t e = (size_t)chunk * CHUNK_VALS + threadIdx.x;
     const double t = vin[e] * St->hn_inv;
     vout[e] = t;
-    if (v32) v32[e] = to_f32_int(t);
+    if (v32) {
+        const float f = to_f32_int(t);
+        v32[e] = f;
+        if (y0) y0[e] = f;
+    }
 }
 
 // partial dots <V_k0+k, w> over the super-chunk's chunks c0..c1-1 (one value
@@ -370,9 +386,10 @@ k_b_dots_norm(const double *__restrict__ V, size_t nv, int j, const double *__re
 __global__ void __launch_bounds__(RED_THREADS)
 k_b_update_scale(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w,
                  double *__restrict__ vnext, float *__restrict__ v32, const BState *S,
-                 const int *__restrict__ chunk_sys) {
+                 const int *__restrict__ chunk_sys, float *__restrict__ y0, unsigned long long *tk) {
     pdl_wait();
     pdl_trigger();
+    b_zero_tickets(tk);
     __shared__ double sh_h[BMAXM + 1];
     const int chunk = blockIdx.x;
     const BState *St = S + chunk_sys[chunk];
@@ -385,7 +402,11 @@ k_b_update_scale(const double *__restrict__ V, size_t nv, int j, const double *_
     for (int k = 0; k < jp1; k++) t = fma(-sh_h[k], V[(size_t)k * nv + e], t);
     const double r = t * St->hn_inv;
     vnext[e] = r;
-    if (v32) v32[e] = to_f32_int(r);
+    if (v32) {
+        const float f = to_f32_int(r);
+        v32[e] = f;
+        if (y0) y0[e] = f;
+    }
 }
 
 // y = R^{-1} g per system (one thread per system)
@@ -677,6 +698,20 @@ static bool all_set(const int *flags, int n) {
     return true;
 }
 
+// The asynchronous application's in-place iterate and ticket counters when
+// the kernels that write its FP32 right-hand side also prepare its start
+// (apply_dispatch_ready), else nulls (the application's own start kernel)
+struct BStart {
+    float *y0;
+    unsigned long long *tk;
+};
+static BStart batch_start(abilu_batch b, const fgmres_opts *opts) {
+    if (!apply_y_ready(b->fac, opts->apply_sweeps_lower, opts->apply_sweeps_upper,
+                       (abilu_mode)opts->mode))
+        return BStart{nullptr, nullptr};
+    return BStart{reinterpret_cast<float *>(b->fac->y[0]), b->fac->ctr + 2};
+}
+
 // One Arnoldi step j of every active system.  Every kernel skips the chunks of
 // systems that have left the cycle (and returns at once when all have).
 static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const BConf &cf, int j,
@@ -687,9 +722,10 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
     double *V = b->krylov, *Z = V + (size_t)(m + 1) * nv, *w = Z + (size_t)m * nv;
     float *v32 = reinterpret_cast<float *>(b->fac->r32);
     const Skip skip{b->bflag, b->chunk_sys, b->sys_done};
-    abilu_status s = apply_dispatch(b->fac, V + (size_t)j * nv, v32, Z + (size_t)j * nv,
-                                    opts->apply_sweeps_lower, opts->apply_sweeps_upper,
-                                    (abilu_mode)opts->mode, st, skip);
+    const BStart y = batch_start(b, opts);
+    abilu_status s = (y.y0 ? apply_dispatch_ready : apply_dispatch)(
+        b->fac, V + (size_t)j * nv, v32, Z + (size_t)j * nv, opts->apply_sweeps_lower,
+        opts->apply_sweeps_upper, (abilu_mode)opts->mode, st, skip);
     if (s != ABILU_OK) return s;
     if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
     const BTab T = batch_tab(b);
@@ -698,7 +734,7 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
         launch_pdl(k_b_dots_norm, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf,
             b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_update_scale, nck, RED_THREADS, 0, st, V, nv, j, w,
-            V + (size_t)(j + 1) * nv, v32, b->S, b->chunk_sys);
+            V + (size_t)(j + 1) * nv, v32, b->S, b->chunk_sys, y.y0, y.tk);
     } else {               // CGS2: two passes, the norm of the updated w
         launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 0);
         launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 0, 0,
@@ -707,14 +743,16 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
         launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 1, 1,
             b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
-            b->chunk_sys);
+            b->chunk_sys, y.y0, y.tk);
     }
     ABILU_LAUNCH_CHECK("batch step");
     return ABILU_OK;
 }
 
 // End of a cycle: x += Z y per system, true residual, new v_0, new cycle flags.
-static abilu_status enqueue_restart(abilu_batch b, const BConf &cf, cudaStream_t st) {
+static abilu_status enqueue_restart(abilu_batch b, const fgmres_opts *opts, const BConf &cf,
+                                    cudaStream_t st) {
+    const BStart ys = batch_start(b, opts);
     const PatternView &P = b->pat->v;
     const int m = cf.m, nck = b->nchunks, nsys = b->nsys;
     const size_t nv = (size_t)b->rows * BS;
@@ -725,7 +763,7 @@ static abilu_status enqueue_restart(abilu_batch b, const BConf &cf, cudaStream_t
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
     launch_pdl(k_b_residual, b->nsc, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, batch_tab(b),
         b->partials, cf, 0, b->hs_done, b->hs_fin, b->sys_done, b->bflag);
-    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
+    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys, ys.y0, ys.tk);
     ABILU_LAUNCH_CHECK("batch restart");
     return ABILU_OK;
 }
@@ -784,7 +822,7 @@ static abilu_status capture_cycle(abilu_batch b, const fgmres_opts *opts, const 
         cudaError_t e2 = cudaStreamEndCapture(bs, &body);
         if (e == cudaSuccess) e = e2;
     }
-    if (st == ABILU_OK && e == cudaSuccess) st = enqueue_restart(b, cf, cs);
+    if (st == ABILU_OK && e == cudaSuccess) st = enqueue_restart(b, opts, cf, cs);
     cudaGraph_t g = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(cs, &g);
     const long long captured = (long long)(launches() - l0);
@@ -837,6 +875,7 @@ static abilu_status batch_solve_core(abilu_batch b, const fgmres_opts *opts, fgm
     float *v32 = reinterpret_cast<float *>(b->fac->r32);
     const BConf cf = {opts->rtol, opts->max_iters, m};
     const int nck = b->nchunks, nsys = b->nsys;
+    const BStart ys = batch_start(b, opts);
     abilu_status s;
     if (opts->build) {
         ABILU_CUDA(cudaMemsetAsync(b->fac->ctr, 0, sizeof(unsigned long long), st));
@@ -850,7 +889,7 @@ static abilu_status batch_solve_core(abilu_batch b, const fgmres_opts *opts, fgm
     k_b_flags_reset<<<counted(1), 32, 0, st>>>(b->bflag);
     launch_pdl(k_b_residual, b->nsc, RED_THREADS, 0, st, P, b->A, b->b, b->x, V, b->S, batch_tab(b),
         b->partials, cf, 1, b->hs_done, b->hs_fin, b->sys_done, b->bflag);
-    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys);
+    launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys, ys.y0, ys.tk);
     ABILU_LAUNCH_CHECK("batch init");
     // the cycle graph: captured once per (restart, sweeps, mode, reorth, factor
     // buffer), replayed for every cycle of every later solve
@@ -900,7 +939,7 @@ static abilu_status batch_solve_core(abilu_batch b, const fgmres_opts *opts, fgm
             cudaEventDestroy(ev[1]);
             if (ret != ABILU_OK) break;
             if (e != cudaSuccess) { ret = cuda_fail(e, "batch step wait"); break; }
-            if ((ret = enqueue_restart(b, cf, st)) != ABILU_OK) break;
+            if ((ret = enqueue_restart(b, opts, cf, st)) != ABILU_OK) break;
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { ret = cuda_fail(e, "batch cycle"); break; }
