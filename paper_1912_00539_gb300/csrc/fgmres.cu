@@ -73,6 +73,12 @@ __device__ __forceinline__ void publish(SolveState *S) {
     __threadfence_system();
 }
 
+// In the first CTA of the kernel after a Gram-Schmidt step or a residual: that
+// kernel's status to the host-mapped mirror (see givens_column)
+__device__ __forceinline__ void publish_early(SolveState *S) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) publish(S);
+}
+
 // last-CTA election after this CTA stored its partials
 __device__ __forceinline__ bool last_cta(SolveState *S) {
     __shared__ bool am_last;
@@ -89,10 +95,10 @@ __device__ __forceinline__ bool last_cta(SolveState *S) {
 // order (the loads of R of them issued before their adds), then a fixed-order
 // block reduction: deterministic for a fixed grid.  Every thread of the CTA
 // calls it.
-template <int K>
+// R: CTAs whose partials are loaded before any add; TREE as in block_sum
+template <int K, int R = (K <= 2 ? 4 : 1), bool TREE = (K <= 2)>
 __device__ __forceinline__ void reduce_partials(const double *partials, int stride, int k0,
                                                 int kn, double *sh_w, double *out) {
-    constexpr int R = K <= 2 ? 4 : 1;   // CTAs whose partials are loaded before any add
     double v[K];
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = 0.0;
@@ -110,17 +116,21 @@ __device__ __forceinline__ void reduce_partials(const double *partials, int stri
 #pragma unroll
             for (int k = 0; k < K; k++) v[k] += t[r][k];
     }
-    block_sum<K>(v, sh_w, out, kn);
+    block_sum<K, TREE>(v, sh_w, out, kn);
 }
 
 // ---------------------------------------------------------------- residual
 // r = b - A x into r_out (= V_0 unnormalised), ||r||^2 and (init) ||b||^2.
 // The last CTA sets beta, the convergence flag and starts the next cycle.
 // Launched with 3 CTAs per SM (its registers allow 3 resident: one wave).
+// Every FP64 operation counts on this GPU (two FP64 lanes per SM): with x = 0
+// (ZERO) r = b and ||r||^2 = ||b||^2 is accumulated once; after a cycle
+// (init = 0) ||b||^2 is not formed.
+template <bool ZERO>
 __global__ void __launch_bounds__(RED_THREADS, 3)
 k_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
            const double *__restrict__ x, double *__restrict__ r_out, SolveState *S,
-           double *partials, int init, int x_is_zero) {
+           double *partials, int init) {
     pdl_wait();
     pdl_trigger();
     // a restart after a cycle in which no step ran (the initial guess had
@@ -130,15 +140,39 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
     const int q = threadIdx.x & 3;
     double v[2] = {0.0, 0.0};
     const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
-    for (int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2); i < P.n; i += rows_per_grid) {
-        // the SpMV kernel's arithmetic (x = 0: r = b, no product)
-        const double s = x_is_zero ? 0.0 : row_dot_blocks(P, A, x, i, q);
-        const size_t o = (size_t)i * BS + q;
-        const double bi = b[o];
-        const double ri = bi - s;
-        r_out[o] = ri;
-        v[0] += ri * ri;
-        v[1] += bi * bi;
+    int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2);
+    if constexpr (ZERO) {
+        // r = b: four rows' loads in flight per thread before any store (one
+        // per iteration left each thread waiting on a load 18 times in a
+        // row: 24 us for the 512x512 grid); the same rows in the same order
+        constexpr int U = 4;
+        for (; i < P.n; i += U * rows_per_grid) {
+            double bu[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int iu = i + u * rows_per_grid;
+                bu[u] = iu < P.n ? b[(size_t)iu * BS + q] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int iu = i + u * rows_per_grid;
+                if (iu >= P.n) break;
+                r_out[(size_t)iu * BS + q] = bu[u];
+                v[0] += bu[u] * bu[u];
+            }
+        }
+        v[1] = v[0];
+    } else {
+        for (; i < P.n; i += rows_per_grid) {
+            // the SpMV kernel's arithmetic
+            const double s = row_dot_blocks(P, A, x, i, q);
+            const size_t o = (size_t)i * BS + q;
+            const double bi = b[o];
+            const double ri = bi - s;
+            r_out[o] = ri;
+            v[0] += ri * ri;
+            if (init) v[1] += bi * bi;
+        }
     }
     block_sum<2>(v, sh_w, sh_o, 2);
     if (threadIdx.x == 0) {
@@ -146,23 +180,36 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
         partials[blockIdx.x * 2 + 1] = sh_o[1];
     }
     if (!last_cta(S)) return;
+    // the last CTA: g_1.. zeroed by the whole CTA, the scalars staged while
+    // the partials are reduced; thread 0's chain then reads no global memory,
+    // and the status is published by the next kernel's first CTA (k_scale)
+    for (int k = 1 + threadIdx.x; k <= MAXM; k += blockDim.x) S->g[k] = 0.0;
+    __shared__ double sh_b[2];   // bnorm (restart), rtol
+    __shared__ int sh_i[2];      // iters, max_iters
+    switch (threadIdx.x) {
+    case 0: sh_b[0] = S->bnorm; break;
+    case 1: sh_b[1] = S->rtol; break;
+    case 2: sh_i[0] = S->iters; break;
+    case 3: sh_i[1] = S->max_iters; break;
+    default: break;
+    }
     reduce_partials<2>(partials, 2, 0, 2, sh_w, sh_o);
     if (threadIdx.x == 0) {
         const double rr = sh_o[0];
-        if (init) S->bnorm = sqrt(sh_o[1]);
+        const double bnorm = init ? sqrt(sh_o[1]) : sh_b[0];
+        if (init) S->bnorm = bnorm;
         else S->restarts += 1;
-        S->beta = sqrt(rr);
-        S->converged = S->beta <= S->rtol * S->bnorm ? 1 : 0;
-        if (S->bnorm == 0.0) S->converged = 1;
-        S->done = (S->converged || S->iters >= S->max_iters) ? 1 : 0;
-        S->hn_inv = S->beta > 0.0 ? 1.0 / S->beta : 0.0;
+        const double beta = sqrt(rr);
+        S->beta = beta;
+        S->hn_inv = beta > 0.0 ? 1.0 / beta : 0.0;
+        const int converged = (beta <= sh_b[1] * bnorm || bnorm == 0.0) ? 1 : 0;
+        S->converged = converged;
+        S->done = (converged || sh_i[0] >= sh_i[1]) ? 1 : 0;
         S->kdim = 0;
         S->breakdown = 0;
-        S->g[0] = S->beta;
-        for (int k = 1; k <= MAXM; k++) S->g[k] = 0.0;
-        if (init) S->est = S->bnorm > 0.0 ? S->beta / S->bnorm : 0.0;
+        S->g[0] = beta;
+        if (init) S->est = bnorm > 0.0 ? beta / bnorm : 0.0;
         S->counter = 0;
-        publish(S);
     }
 }
 
@@ -180,6 +227,7 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
         unsigned long long *tk) {
     pdl_wait();
     pdl_trigger();
+    publish_early(S);      // the previous kernel's status (k_residual: a new cycle's)
     if (S->done) return;   // set by an earlier kernel: a plain load
     zero_tickets(tk);
     const double s = S->hn_inv;
@@ -213,7 +261,8 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
 // Partial dot products of K consecutive basis vectors with w for this CTA.
 // K is a compile-time width so no predicated-off FP64 FMA is issued.
 // NORM: also ||w||^2 in the same pass (slot K of the accumulators; its
-// partial goes to slot MAXM + 1), for the single-reduction step.
+// partial goes to slot k0 + K, right after the tile's dots: the last tile's,
+// so slot jp1), for the single-reduction step.
 template <int K, bool PIPE, bool NORM = false>
 __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long long nv2,
                                           int k0, const double2 *__restrict__ w2,
@@ -286,7 +335,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
     }
     block_sum<KA, false>(acc, sh_w, sh_o, KA);   // k_dots is held to 64 registers
     if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
-    if (NORM && threadIdx.x == 0) partials[(size_t)blockIdx.x * (MAXM + 2) + MAXM + 1] = sh_o[K];
+    if (NORM && threadIdx.x == 0) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + K] = sh_o[K];
 }
 
 // The Givens update of column j of the Hessenberg matrix (from the
@@ -329,11 +378,65 @@ __device__ __forceinline__ void givens_column(SolveState *S, int j, int two_pass
     if (pub) publish(S);
 }
 
-// In the first CTA of the kernel after a Gram-Schmidt step: the step's status
-// to the host-mapped mirror (see givens_column)
-__device__ __forceinline__ void publish_early(SolveState *S) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) publish(S);
+// What givens_column reads of the solve state besides the new column, staged
+// in shared memory by the last CTA of a reduction while it reduces the
+// partials, so that the serial FP64 chain of one thread reads no global
+// memory (an FP64 operation takes 64 cycles on this GPU and an L2 load
+// several hundred; with the loads in the chain the update took 4-9 us)
+struct GivensIn {
+    double cs[MAXM], sn[MAXM], gj, bnorm, rtol;
+    int iters, max_iters, m;
+};
+__device__ __forceinline__ void givens_stage(const SolveState *S, int j, GivensIn *G) {
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+        G->cs[i] = S->cs[i];
+        G->sn[i] = S->sn[i];
+    }
+    switch (threadIdx.x) {
+    case 0: G->gj = S->g[j]; break;
+    case 1: G->bnorm = S->bnorm; break;
+    case 2: G->rtol = S->rtol; break;
+    case 3: G->iters = S->iters; break;
+    case 4: G->max_iters = S->max_iters; break;
+    case 5: G->m = S->m; break;
+    default: break;
+    }
 }
+
+// givens_column (one pass, the status published by the next kernel) from the
+// staged inputs and the coefficients h[0..j] in shared memory: the same
+// operations in the same order, so the same results bit for bit
+__device__ __forceinline__ void givens_column_staged(SolveState *S, int j, const double *h,
+                                                     const GivensIn *G, double hn) {
+    // independent of the rotations: overlaps their chain
+    S->hn_inv = hn != 0.0 ? 1.0 / hn : 0.0;
+    double a = h[0];
+    for (int i = 0; i < j; i++) {
+        const double c = h[i + 1];
+        S->H[i * MAXM + j] = G->cs[i] * a + G->sn[i] * c;
+        a = -G->sn[i] * a + G->cs[i] * c;
+    }
+    const double c = hn;
+    const double d = sqrt(a * a + c * c);
+    double cs = 1.0, sn = 0.0;
+    if (d != 0.0) { cs = a / d; sn = c / d; }
+    S->cs[j] = cs;
+    S->sn[j] = sn;
+    S->H[j * MAXM + j] = cs * a + sn * c;
+    const double gj = G->gj;
+    const double g1 = -sn * gj;
+    S->g[j + 1] = g1;
+    S->g[j] = cs * gj;
+    const int iters = G->iters + 1;
+    S->iters = iters;
+    S->kdim = j + 1;
+    S->est = fabs(g1) / G->bnorm;
+    S->breakdown = hn == 0.0 ? 1 : 0;
+    S->done = (fabs(g1) <= G->rtol * G->bnorm || hn == 0.0 || iters >= G->max_iters ||
+               j + 1 >= G->m) ? 1 : 0;
+    S->counter = 0;
+}
+
 
 // h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2).  The grid is
 // 4 CTAs per SM and all of them must be resident at once (one wave), so the
@@ -433,19 +536,32 @@ k_dots_norm(const double *__restrict__ V, long long nv2, int jp1, const double *
         }
     }
     if (!last_cta(S)) return;
+    // the last CTA: the Givens inputs staged while the partials are reduced;
+    // each tile's dots in one reduction, the last one with ||w||^2 (slot jp1),
+    // every thread's partials loaded before any add (3 CTAs of 608 per thread;
+    // two rounds of 2 for the general kernel's seven values, in its 64 registers;
+    // the cross-warp sums as shuffle trees)
+    __shared__ GivensIn G;
+    __shared__ double sh_h[MAXM + 1], sh_ww;
+    givens_stage(S, jp1 - 1, &G);
     for (int k0 = 0; k0 < jp1; k0 += T) {
         const int kn = jp1 - k0 < T ? jp1 - k0 : T;
-        reduce_partials<T>(partials, MAXM + 2, k0, kn, sh_w, sh_o);
-        if (threadIdx.x < kn) S->h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        const bool lastt = k0 + T >= jp1;
+        reduce_partials<T + 1, (T + 1 <= 5 ? 3 : 2), true>(partials, MAXM + 2, k0,
+                                                           lastt ? kn + 1 : kn, sh_w, sh_o);
+        if (threadIdx.x < kn) {
+            S->h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+            sh_h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        }
+        if (lastt && threadIdx.x == 0) sh_ww = sh_o[kn];
         __syncthreads();
     }
-    reduce_partials<1>(partials, MAXM + 2, MAXM + 1, 1, sh_w, sh_o);
     if (threadIdx.x != 0) return;
-    const double ww = sh_o[0];
+    const double ww = sh_ww;
     double hh = 0.0;
-    for (int k = 0; k < jp1; k++) hh = fma(S->h[k], S->h[k], hh);
+    for (int k = 0; k < jp1; k++) hh = fma(sh_h[k], sh_h[k], hh);
     const double d = ww - hh;
-    givens_column(S, jp1 - 1, 0, d > 1e-12 * ww ? sqrt(d) : 0.0, false);   // k_update_scale publishes
+    givens_column_staged(S, jp1 - 1, sh_h, &G, d > 1e-12 * ww ? sqrt(d) : 0.0);   // k_update_scale publishes
 }
 
 static void launch_dots_norm(int nred, cudaStream_t st, const double *V, long long nv2, int jp1,
@@ -809,8 +925,10 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
     ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
     if (opts->zero_guess) ABILU_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nv, st));
-    launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1,
-        opts->zero_guess ? 1 : 0);
+    if (opts->zero_guess)
+        launch_pdl(k_residual<true>, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1);
+    else
+        launch_pdl(k_residual<false>, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1);
     launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS, pc.y0, pc.tickets);
     ABILU_LAUNCH_CHECK("fgmres init");
     // the look-ahead events live in the workspace handle (made on first use)
@@ -868,7 +986,7 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
         }
         if (ret != ABILU_OK) break;
         launch_pdl(k_xupdate, nred, RED_THREADS, 0, st, Z, nv2, x, SS);
-        launch_pdl(k_residual, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 0, 0);
+        launch_pdl(k_residual<false>, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 0);
         launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS, pc.y0, pc.tickets);
         // the handles' counters into the status with every cycle's result, so
         // the synchronisation that ends the last cycle also ends the solve
