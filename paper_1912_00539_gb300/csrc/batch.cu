@@ -111,7 +111,7 @@ k_b_residual(PatternView P, const double *__restrict__ A, const double *__restri
              int *bflag) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
+    __shared__ double sh_w[RED_THREADS * 2], sh_o[2];
     const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (!init && St->finished) return;  // whole system skips
@@ -240,7 +240,7 @@ k_b_dots(const double *__restrict__ V, size_t nv, int j, const double *__restric
          BTab T, double *partials, int pass) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double sh_w[RED_WARPS * BTILE], sh_o[BTILE];
+    __shared__ double sh_w[RED_THREADS * BTILE], sh_o[BTILE];
     const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (St->done) return;
@@ -271,7 +271,7 @@ k_b_update(const double *__restrict__ V, size_t nv, int j, double *__restrict__ 
     pdl_wait();
     pdl_trigger();
     __shared__ double sh_h[BMAXM + 1];
-    __shared__ double sh_w[RED_WARPS], sh_o[1];
+    __shared__ double sh_w[RED_THREADS], sh_o[1];
     const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (St->done) return;
@@ -348,7 +348,7 @@ k_b_dots_norm(const double *__restrict__ V, size_t nv, int j, const double *__re
               int *bflag) {
     pdl_wait();
     pdl_trigger();
-    __shared__ double sh_w[RED_WARPS * BTILE], sh_o[BTILE];
+    __shared__ double sh_w[RED_THREADS * BTILE], sh_o[BTILE];
     const int sc = blockIdx.x, s = T.sc_sys[sc];
     BState *St = S + s;
     if (St->done) return;

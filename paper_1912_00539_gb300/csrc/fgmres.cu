@@ -95,8 +95,8 @@ __device__ __forceinline__ bool last_cta(SolveState *S) {
 // order (the loads of R of them issued before their adds), then a fixed-order
 // block reduction: deterministic for a fixed grid.  Every thread of the CTA
 // calls it.
-// R: CTAs whose partials are loaded before any add; TREE as in block_sum
-template <int K, int R = (K <= 2 ? 4 : 1), bool TREE = (K <= 2)>
+// R: CTAs whose partials are loaded before any add
+template <int K, int R = (K <= 2 ? 4 : 1)>
 __device__ __forceinline__ void reduce_partials(const double *partials, int stride, int k0,
                                                 int kn, double *sh_w, double *out) {
     double v[K];
@@ -116,7 +116,7 @@ __device__ __forceinline__ void reduce_partials(const double *partials, int stri
 #pragma unroll
             for (int k = 0; k < K; k++) v[k] += t[r][k];
     }
-    block_sum<K, TREE>(v, sh_w, out, kn);
+    block_sum<K>(v, sh_w, out, kn);
 }
 
 // ---------------------------------------------------------------- residual
@@ -136,7 +136,7 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
     // a restart after a cycle in which no step ran (the initial guess had
     // already converged) would recompute the same residual: keep the state
     if (!init && S->kdim == 0) return;
-    __shared__ double sh_w[RED_WARPS * 2], sh_o[2];
+    __shared__ double sh_w[RED_THREADS * 2], sh_o[2];
     const int q = threadIdx.x & 3;
     double v[2] = {0.0, 0.0};
     const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
@@ -333,7 +333,7 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
         }
         if constexpr (NORM) acc[K] = fma(wv.y, wv.y, fma(wv.x, wv.x, acc[K]));
     }
-    block_sum<KA, false>(acc, sh_w, sh_o, KA);   // k_dots is held to 64 registers
+    block_sum<KA>(acc, sh_w, sh_o, KA);
     if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
     if (NORM && threadIdx.x == 0) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + K] = sh_o[K];
 }
@@ -452,7 +452,7 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
     pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
     constexpr int T = NW > 0 ? NW : TILE;
-    __shared__ double sh_w[RED_WARPS * T], sh_o[T];
+    __shared__ double sh_w[RED_THREADS * T], sh_o[T];
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const double2 *V2 = reinterpret_cast<const double2 *>(V);
     if constexpr (NW > 0) {
@@ -512,7 +512,7 @@ k_dots_norm(const double *__restrict__ V, long long nv2, int jp1, const double *
     pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
     constexpr int T = NW > 0 ? NW : TILE;
-    __shared__ double sh_w[RED_WARPS * (T + 1)], sh_o[T + 1];
+    __shared__ double sh_w[RED_THREADS * (T + 1)], sh_o[T + 1];
     const double2 *w2 = reinterpret_cast<const double2 *>(w);
     const double2 *V2 = reinterpret_cast<const double2 *>(V);
     if constexpr (NW > 0) {
@@ -539,16 +539,15 @@ k_dots_norm(const double *__restrict__ V, long long nv2, int jp1, const double *
     // the last CTA: the Givens inputs staged while the partials are reduced;
     // each tile's dots in one reduction, the last one with ||w||^2 (slot jp1),
     // every thread's partials loaded before any add (3 CTAs of 608 per thread;
-    // two rounds of 2 for the general kernel's seven values, in its 64 registers;
-    // the cross-warp sums as shuffle trees)
+    // two rounds of 2 for the general kernel's seven values, in its 64 registers)
     __shared__ GivensIn G;
     __shared__ double sh_h[MAXM + 1], sh_ww;
     givens_stage(S, jp1 - 1, &G);
     for (int k0 = 0; k0 < jp1; k0 += T) {
         const int kn = jp1 - k0 < T ? jp1 - k0 : T;
         const bool lastt = k0 + T >= jp1;
-        reduce_partials<T + 1, (T + 1 <= 5 ? 3 : 2), true>(partials, MAXM + 2, k0,
-                                                           lastt ? kn + 1 : kn, sh_w, sh_o);
+        reduce_partials<T + 1, (T + 1 <= 5 ? 3 : 2)>(partials, MAXM + 2, k0,
+                                                     lastt ? kn + 1 : kn, sh_w, sh_o);
         if (threadIdx.x < kn) {
             S->h[k0 + threadIdx.x] = sh_o[threadIdx.x];
             sh_h[k0 + threadIdx.x] = sh_o[threadIdx.x];
@@ -727,7 +726,7 @@ k_update(const double *__restrict__ V, long long nv2, int j, double *__restrict_
     pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
     __shared__ double sh_h[MAXM + 1];
-    __shared__ double sh_w[RED_WARPS], sh_o[1];
+    __shared__ double sh_w[RED_THREADS], sh_o[1];
     const int jp1 = j + 1;
     const double *hsrc = pass == 0 ? S->h : S->h2;
     for (int k = threadIdx.x; k < jp1; k += blockDim.x) sh_h[k] = hsrc[k];
