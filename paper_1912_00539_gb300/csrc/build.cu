@@ -780,8 +780,10 @@ static abilu_status build_t(abilu_factors f, const double *A, int nsweeps, abilu
     constexpr bool narrow = sizeof(T) < 8;
     float *A32 = narrow ? reinterpret_cast<float *>(f->A32) : nullptr;
     const int c = f->cur;
+    // U_ii of the initial guess only when no sweep follows: the last sweep
+    // stores the build's U_ii (33.5 MB fewer writes at 512x512)
     launch_pdl(k_build_prepare<T>, grid, BUILD_THREADS, 0, st,
-        P, A, A32, L[c], U[c], mode == ABILU_SYNC ? U[1 - c] : nullptr, D[c], Ud,
+        P, A, A32, L[c], U[c], mode == ABILU_SYNC ? U[1 - c] : nullptr, D[c], nsweeps > 0 ? nullptr : Ud,
         init == ABILU_INIT_FROM_A ? 1 : 0, f->chunk_init, f->ctr);
     ABILU_LAUNCH_CHECK("k_build_prepare");
     if constexpr (narrow) {

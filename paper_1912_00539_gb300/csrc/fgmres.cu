@@ -795,24 +795,29 @@ k_xupdate(const double *__restrict__ Z, long long nv2, double *__restrict__ x, S
     pdl_wait();
     pdl_trigger();
     __shared__ double y[MAXM];
-    __shared__ double sR[MAXM * MAXM / 2 + MAXM], sg[MAXM];   // R's upper triangle, g
+    __shared__ double sR[MAXM * MAXM / 2 + MAXM], sg[MAXM], sinv[MAXM];   // R's upper triangle, g
     const int kd = S->kdim;
     if (kd == 0) return;
-    // R and g into shared memory by the whole CTA (one round of loads), then
-    // the back substitution by one thread from there: its chain of dependent
-    // FP64 operations no longer waits on global loads
+    // R and g into shared memory by the whole CTA (one round of loads), the
+    // reciprocals of R's diagonal by kd threads at once, then the back
+    // substitution by one thread from there: its chain of dependent FP64
+    // operations waits on no global load and on no division (an FP64 division
+    // is a chain of dependent FP64 operations of 64 cycles each on this GPU)
     for (int t = threadIdx.x; t < kd * kd; t += blockDim.x) {
         const int i = t / kd, k = t % kd;
         if (k >= i) sR[i * kd - i * (i - 1) / 2 + (k - i)] = S->H[i * MAXM + k];
     }
-    for (int t = threadIdx.x; t < kd; t += blockDim.x) sg[t] = S->g[t];
+    for (int t = threadIdx.x; t < kd; t += blockDim.x) {
+        sg[t] = S->g[t];
+        sinv[t] = 1.0 / S->H[t * MAXM + t];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = kd - 1; i >= 0; i--) {
             const double *Ri = sR + i * kd - i * (i - 1) / 2 - i;   // Ri[k] = R[i][k], k >= i
             double s = sg[i];
             for (int k = i + 1; k < kd; k++) s -= Ri[k] * y[k];
-            y[i] = s / Ri[i];
+            y[i] = s * sinv[i];
         }
     }
     __syncthreads();
