@@ -379,10 +379,10 @@ __device__ __forceinline__ void build_block(const PatternView &P, int w,
         st_row_sel<VOL>(Lout + (size_t)dst * BB + q * BS, o);
     } else if (kind == WORK_U) {
         st_row_sel<VOL>(Uout + (size_t)dst * BB + q * BS, s);
-    } else {  // U_ii = S, Dinv_i = inv(U_ii), refined in the last sweep of a synchronous
-              // build (Udiag passed) and in every asynchronous update
+    } else {  // U_ii = S, Dinv_i = inv(U_ii), refined only in a build's last sweep, in
+              // either mode (Udiag passed): earlier inverses only feed the next updates
         float x[4];
-        if (quad_inv4_refined(s, x, sh_q, VOL || Udiag != nullptr) && q == 0) atomicAdd(nsing, 1ull);
+        if (quad_inv4_refined(s, x, sh_q, Udiag != nullptr) && q == 0) atomicAdd(nsing, 1ull);
         st_row_sel<VOL>(Dout + (size_t)dst * BB + q * BS, x);
         if (Udiag) st_row_sel<false>(Udiag + (size_t)dst * BB + q * BS, s);
     }
