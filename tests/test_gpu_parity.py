@@ -340,6 +340,34 @@ def test_fgmres_matches_oracle(ab, dsys, dtype, mode):
         assert res.iters == ro.iters
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("nl,nu", [(1, 1), (1, 3), (2, 1), (2, 3), (4, 4)])
+def test_fgmres_async_application_starts(ab, dsys, dtype, nl, nu):
+    """An asynchronous application starts from y = b and zeroed ticket counters:
+    with one lower update its own start kernel does that (and forms x^1);
+    with two or more, inside FGMRES, the kernels that write the FP32
+    right-hand side do it.  On the same factors, both converge like the
+    oracle's FGMRES with the same sweep counts (iterations within 10%), and
+    the solution is checked with the oracle's SpMV."""
+    s = dsys.s
+    fac = ab.Factors(dsys.pat, dtype)
+    fac.build(dsys.A, 4, mode="sync")
+    X, D = fac.export()    # the oracle's FGMRES runs on the same (rounded) factors
+    _, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, X.cpu().numpy(), D.cpu().numpy(), s.b,
+                          nl, nu, restart=30, rtol=1e-6)
+    x = dsys.vec()
+    res = ab.fgmres_solve(dsys.pat, dsys.A, fac, dsys.b, x, restart=30, rtol=1e-6,
+                          apply_sweeps_lower=nl, apply_sweeps_upper=nu, mode="async", build=False)
+    assert res.converged and res.rel_resid_true <= 1e-6
+    r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
+    assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
+    if dtype == "bf16":
+        assert res.iters <= 2 * ro.iters + 2
+        return
+    slack = max(1, int(np.ceil(0.1 * ro.iters)))
+    assert abs(res.iters - ro.iters) <= slack, (res.iters, ro.iters)
+
+
 def test_fgmres_sync_bit_reproducible(ab):
     d = Dev(ab, gen.small_system(30, 20, seed=7))
     fac = ab.Factors(d.pat, "f32")
