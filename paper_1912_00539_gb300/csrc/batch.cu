@@ -498,7 +498,7 @@ struct abilu_batch_s {
     int *hs_done, *hs_fin;      // pinned, host-mapped
     int *sys_done, *bflag;      // device: per-system cycle exit; {all done, active count}
     cudaGraphExec_t graph;      // one restart cycle, captured on first use
-    int gkey[8];
+    int gkey[12];
     long long g_fixed, g_step;  // kernels per replay outside the steps; per step run
     cudaStream_t cap_stream;    // capture happens here: the caller's stream may be the
                                 // legacy default stream, which cannot be captured
@@ -712,6 +712,9 @@ static BStart batch_start(abilu_batch b, const fgmres_opts *opts) {
     return BStart{reinterpret_cast<float *>(b->fac->y[0]), b->fac->ctr + 2};
 }
 
+// The Gram-Schmidt form of a solve's Arnoldi steps (see gs_form_for)
+static int gs_form(const fgmres_opts *opts) { return gs_form_for(opts->reorth, opts->rtol); }
+
 // One Arnoldi step j of every active system.  Every kernel skips the chunks of
 // systems that have left the cycle (and returns at once when all have).
 static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const BConf &cf, int j,
@@ -730,11 +733,18 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
     if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
     const BTab T = batch_tab(b);
     const int nsc = b->nsc;
-    if (!opts->reorth) {   // one pass, one reduction per system
+    const int form = gs_form(opts);
+    if (form == GS_SINGLE) {   // one pass, one reduction per system
         launch_pdl(k_b_dots_norm, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf,
             b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_update_scale, nck, RED_THREADS, 0, st, V, nv, j, w,
             V + (size_t)(j + 1) * nv, v32, b->S, b->chunk_sys, y.y0, y.tk);
+    } else if (form == GS_CLASSICAL) {   // one pass, the norm of the updated w
+        launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 0);
+        launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 0, 1,
+            b->hs_done, b->sys_done, b->bflag);
+        launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
+            b->chunk_sys, y.y0, y.tk);
     } else {               // CGS2: two passes, the norm of the updated w
         launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 0);
         launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 0, 0,
@@ -891,11 +901,15 @@ static abilu_status batch_solve_core(abilu_batch b, const fgmres_opts *opts, fgm
         b->partials, cf, 1, b->hs_done, b->hs_fin, b->sys_done, b->bflag);
     launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, V, V, v32, b->S, b->chunk_sys, ys.y0, ys.tk);
     ABILU_LAUNCH_CHECK("batch init");
-    // the cycle graph: captured once per (restart, sweeps, mode, reorth, factor
-    // buffer), replayed for every cycle of every later solve
-    const int key[8] = {m, opts->apply_sweeps_lower, opts->apply_sweeps_upper, opts->mode,
-                        opts->reorth, (int)b->fac->cur, (int)(opts->spin_limit >> 32),
-                        (int)(opts->spin_limit & 0xffffffff)};
+    // the cycle graph: captured once per (restart, sweeps, mode, Gram-Schmidt
+    // form, factor buffer, spin limit, tolerance, iteration limit: the kernels
+    // take the last two by value), replayed for every cycle of every later solve
+    unsigned long long rbits;
+    memcpy(&rbits, &opts->rtol, sizeof rbits);
+    const int key[12] = {m, opts->apply_sweeps_lower, opts->apply_sweeps_upper, opts->mode,
+                         gs_form(opts), (int)b->fac->cur, (int)(opts->spin_limit >> 32),
+                         (int)(opts->spin_limit & 0xffffffff), (int)(rbits >> 32),
+                         (int)(rbits & 0xffffffff), opts->max_iters, 0};
     if (b->graph && memcmp(key, b->gkey, sizeof key) != 0) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;

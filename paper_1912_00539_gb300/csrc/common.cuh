@@ -143,6 +143,25 @@ struct Skip {
 // Arnoldi step on the solve's stream; its kernels return at once while
 // skip.flag is set.  v32 (NULL: none) receives an FP32 copy of each
 // normalised v from FGMRES (the input FP32/BF16 factors read).
+// The Gram-Schmidt form of FGMRES's Arnoldi step (single-system and batch
+// solves).  GS_SINGLE: one classical pass and one reduction, h_{j+1,j} =
+// sqrt(||w||^2 - sum_k h_k^2).  That formula assumes an orthonormal basis, and
+// a classical Gram-Schmidt basis loses orthogonality as the residual falls:
+// in FP64 emulations of the solver (seven systems, 6-14 steps) the formula's
+// relative error in h_{j+1,j} was about 1e-17 / (the relative residual
+// estimate after the step), and at tolerances of 1e-8 a 96-cell system
+// missed convergence inside a 30-step cycle.  Since the estimate stays above
+// rtol within a cycle, the form is taken only for rtol >= 1e-7 (error below
+// about 1e-10; the workloads' 1e-6 included).  GS_CLASSICAL: one classical
+// pass with the explicit norm of the updated w (a second reduction and a
+// scaling pass), for tighter tolerances.  GS_CGS2: two classical passes
+// (opts->reorth).
+enum : int { GS_SINGLE = 0, GS_CLASSICAL = 1, GS_CGS2 = 2 };
+constexpr double GS_SINGLE_MIN_RTOL = 1e-7;
+inline int gs_form_for(int reorth, double rtol) {
+    return reorth ? GS_CGS2 : (rtol >= GS_SINGLE_MIN_RTOL ? GS_SINGLE : GS_CLASSICAL);
+}
+
 struct Precond {
     abilu_status (*fn)(void *ctx, const double *v, const float *v32, double *z, cudaStream_t st,
                        Skip skip);

@@ -925,6 +925,7 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
     const int nres = nred / 4 * 3;   // k_residual: 3 CTAs per SM
     const Skip skip{&SS->done, nullptr, nullptr};
     float *v32 = pc.v32;
+    const int form = gs_form_for(opts->reorth, opts->rtol);
 
     ABILU_CUDA(cudaMemsetAsync(SS, 0, sizeof(SolveState), st));
     k_solve_init<<<counted(1), 1, 0, st>>>(SS, hs, opts->rtol, opts->max_iters, m);
@@ -952,10 +953,15 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
             s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
             if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
-            if (!opts->reorth) {   // one pass, one reduction (see k_dots_norm)
+            if (form == GS_SINGLE) {            // one pass, one reduction (see k_dots_norm)
                 launch_dots_norm(nred, st, V, nv2, j + 1, w, SS, ws->partials);
                 launch_update_scale(nred, st, V, nv2, j, w, V + (size_t)(j + 1) * nv, v32, SS,
                                     pc.y0, pc.tickets);
+            } else if (form == GS_CLASSICAL) {  // one pass, the norm of the updated w
+                launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
+                launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 1);
+                launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS,
+                           pc.y0, pc.tickets);
             } else {               // CGS2: two passes, the norm of the updated w
                 launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 0);

@@ -97,6 +97,36 @@ def test_batch_value_update_and_warm_start(ab):
         assert np.linalg.norm(r) / np.linalg.norm(s.b) <= 1e-6
 
 
+@pytest.mark.parametrize("rtol", [1e-8, 1e-10])
+def test_batch_tight_tolerances_and_the_graph_key(ab, rtol):
+    """Tolerances below 1e-7 take the classical Gram-Schmidt step with the
+    explicit norm: every system converges to rtol (checked with the oracle's
+    SpMV) in the same iterations as its single-system solve (synchronous
+    FP64).  The batch first solves at 1e-6 (single-reduction step), so the
+    second solve must not replay the first one's captured cycle: the graph
+    key holds the tolerance and the Gram-Schmidt form."""
+    import torch
+    systems = _systems()[:4]
+    devs = [_dev(s) for s in systems]
+    batch = ab.Batch([(d[0], d[1]) for d in devs], dtype="f64")
+    for k, d in enumerate(devs):
+        batch.set_system(k, d[2], d[3])
+    base = dict(restart=30, build_sweeps=4, apply_sweeps_lower=3, apply_sweeps_upper=3,
+                mode="sync")
+    batch.solve(rtol=1e-6, **base)
+    res = batch.solve(rtol=rtol, **base)
+    for k, (s, d) in enumerate(zip(systems, devs)):
+        x = torch.empty_like(d[3])
+        batch.solution(k, x)
+        r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
+        assert res[k].converged and np.linalg.norm(r) / np.linalg.norm(s.b) <= rtol * 1.001, k
+        pat = ab.Pattern(d[0], d[1])
+        fac = ab.Factors(pat, "f64")
+        xa = torch.zeros_like(d[3])
+        ra = ab.fgmres_solve(pat, d[2], fac, d[3], xa, rtol=rtol, **base)
+        assert res[k].iters == ra.iters, (k, res[k].iters, ra.iters)
+
+
 def test_batch_rejects_bad_input(ab):
     import torch
     s = gen.small_system(3, 3, seed=34)
