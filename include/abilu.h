@@ -296,7 +296,12 @@ typedef struct {
     int32_t mode;               /* abilu_mode for build and apply */
     int32_t build;              /* 1: build the factors from A inside the solve; 0: use them as they are */
     int32_t init;               /* abilu_init for that build */
-    int32_t reorth;             /* 0: one classical Gram-Schmidt pass; 1: two passes (CGS2) */
+    int32_t reorth;             /* 0: one classical Gram-Schmidt pass; 1: two passes (CGS2).
+                                   With 0 and rtol >= 1e-7 the pass is one reduction:
+                                   h_{j+1,j} = sqrt(||w||^2 - sum_k h_k^2), formed with the
+                                   dot products; below 1e-7 h_{j+1,j} is the explicit norm of
+                                   the updated w (that formula assumes an orthonormal basis,
+                                   which a classical basis loses as the residual falls) */
     int32_t zero_guess;         /* 1: start from x0 = 0 (x is overwritten; r0 = b, no SpMV) */
     int64_t spin_limit;         /* polls of a bounded device-side wait before it gives up and
                                    the solve returns ABILU_ETIMEOUT (the ordered asynchronous

@@ -3,15 +3,17 @@
 //
 // Per Arnoldi step j:  z_j = M^{-1} v_j (block ILU sweeps, any precision),
 // w = A z_j (FP64 SpMV), classical Gram-Schmidt h = V^T w, w -= V h (one pass,
-// or two with reorth), h_{j+1,j} = ||w||, Givens rotation of the new column,
-// residual estimate |g_{j+1}|, v_{j+1} = w / h_{j+1,j}.  At the end of a cycle
-// y = R^{-1} g, x += Z y, and the true residual b - A x is formed in FP64; an
-// estimate that passed but is not confirmed by it restarts the cycle.
+// or two with reorth), h_{j+1,j} = ||w|| (for rtol >= 1e-7 formed with the dot
+// products in one reduction, see k_dots_norm and gs_form_for), Givens rotation
+// of the new column, residual estimate |g_{j+1}|, v_{j+1} = w / h_{j+1,j}.  At
+// the end of a cycle y = R^{-1} g, x += Z y, and the true residual b - A x is
+// formed in FP64; an estimate that passed but is not confirmed by it restarts
+// the cycle.
 //
 // Every reduction runs on a fixed grid with a fixed order (per-thread partial
-// sums, warp shuffles, per-CTA partials, and the last CTA to finish adding the
-// partials in CTA order), so a synchronous-mode solve is bit-reproducible run
-// to run.  The small Hessenberg/Givens state lives on the device; the last CTA
+// sums, a block sum staged in shared memory, per-CTA partials, and the last
+// CTA to finish adding the partials in CTA order), so a synchronous-mode solve
+// is bit-reproducible run to run.  The small Hessenberg/Givens state lives on the device; the last CTA
 // of each reduction updates it, so the host only enqueues kernels.  The host
 // learns that a cycle ended from a pinned host-mapped status word, read one
 // step late (after step j+1 is already enqueued), so the GPU never idles on
