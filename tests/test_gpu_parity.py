@@ -380,8 +380,8 @@ def test_fgmres_sync_bit_reproducible(ab):
 
 
 @pytest.mark.parametrize("rtol", [1e-8, 1e-10])
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_fgmres_tight_tolerances(ab, dsys, rtol, dtype):
+@pytest.mark.parametrize("dtype,mode", [("f64", "sync"), ("f32", "sync"), ("f32", "async")])
+def test_fgmres_tight_tolerances(ab, dsys, rtol, dtype, mode):
     """Below rtol 1e-7 the Arnoldi step forms h_{j+1,j} as the explicit norm
     of the updated w: the iteration count stays within 10% of the oracle's
     (modified Gram-Schmidt, same sweeps) and the true residual reaches rtol.
@@ -396,12 +396,13 @@ def test_fgmres_tight_tolerances(ab, dsys, rtol, dtype):
     x = dsys.vec()
     res = ab.fgmres_solve(dsys.pat, dsys.A, fac, dsys.b, x, restart=30, rtol=rtol,
                           build_sweeps=nb, apply_sweeps_lower=na, apply_sweeps_upper=na,
-                          mode="sync")
+                          mode=mode)
     r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
     assert res.converged and np.linalg.norm(r) / np.linalg.norm(s.b) <= rtol * 1.001
-    if dtype == "f32" and rtol < 1e-9:
-        # FP32 factors: the preconditioner's rounding, not the Arnoldi step,
-        # sets how far the count may drift at 1e-10
+    if dtype == "f32" and (rtol < 1e-9 or mode == "async"):
+        # FP32 factors: the preconditioner's rounding (and in asynchronous
+        # mode its schedule), not the Arnoldi step, sets how far the count
+        # may drift
         assert res.iters <= 2 * ro.iters + 2, (res.iters, ro.iters)
         return
     slack = max(1, int(np.ceil(0.1 * ro.iters)))
