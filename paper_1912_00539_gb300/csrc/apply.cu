@@ -278,7 +278,11 @@ template <typename T> struct __align__(128) PipeStage {   // every field 16-byte
     float rhs[APPLY_ROWS * BS];
     int32_t rowp[PIPE_ROWP];
     long long ticket;     // -1: no more work
-    int32_t fb, cb, staged, pad;
+    int32_t fb, cb, staged;
+    int32_t chunk, last;  // the ticket's chunk and whether it is the chunk's last sweep, formed
+                          // once by the producer (a 64-bit division per chunk and consumer
+                          // warp was a large share of the consumers' instructions)
+    int32_t pad[3];
 };
 
 template <bool UPPER, bool SCALED, bool SYNC, typename T>
@@ -325,7 +329,8 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
                 armed[s]++;
                 break;
             }
-            const int c = (int)(t % nchunks);
+            const long long sw = SYNC ? 0 : t / nchunks;   // SYNC: t < nchunks
+            const int c = (int)(t - sw * nchunks);
             const int chunk = (UPPER && !SYNC) ? (int)(nchunks - 1 - c) : c;
             const int i0 = chunk * APPLY_ROWS, i1 = min(i0 + APPLY_ROWS, P.n);
             const int fb = rowp[i0], fe = rowp[i1];
@@ -335,6 +340,8 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
             S.fb = fb;
             S.cb = cb;
             S.staged = staged;
+            S.chunk = chunk;
+            S.last = SYNC ? (sync_last != 0) : (sw == nsweeps - 1);
             unsigned bytes = 0;
             const bool run = !skip_chunk(skip, chunk);
             if (run) {
@@ -362,11 +369,9 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
         const int s = k & 1, u = k >> 1;
         if (!mbar_wait(&full[s], u & 1, err, limit)) return;
         const PipeStage<T> &S = st[s];
-        const long long t = S.ticket;
-        if (t < 0) return;
-        const int c = (int)(t % nchunks);
-        const int chunk = (UPPER && !SYNC) ? (int)(nchunks - 1 - c) : c;
-        const bool last = SYNC ? sync_last != 0 : t / nchunks == nsweeps - 1;
+        if (S.ticket < 0) return;
+        const int chunk = S.chunk;
+        const bool last = S.last != 0;
         const int i = chunk * APPLY_ROWS + r;
         if (i < P.n && !skip_chunk(skip, chunk)) {
             const int l0 = S.rowp[r], l1 = S.rowp[r + 1];
