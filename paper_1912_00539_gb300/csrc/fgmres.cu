@@ -13,12 +13,12 @@
 // Every reduction runs on a fixed grid with a fixed order (per-thread partial
 // sums, a block sum staged in shared memory, per-CTA partials, and the last
 // CTA to finish adding the partials in CTA order), so a synchronous-mode solve
-// is bit-reproducible run to run.  The small Hessenberg/Givens state lives on the device; the last CTA
-// of each reduction updates it, so the host only enqueues kernels.  The host
-// learns that a cycle ended from a pinned host-mapped status word, read one
-// step late (after step j+1 is already enqueued), so the GPU never idles on
-// the host; kernels of steps past the end of a cycle see the device flag and
-// return at once.
+// is bit-reproducible run to run.  The small Hessenberg/Givens state lives on
+// the device; the last CTA of each reduction updates it, so the host only
+// enqueues kernels.  The host learns that a cycle ended from a pinned
+// host-mapped status word, read one step late (after step j+1 is already
+// enqueued), so the GPU never idles on the host; kernels of steps past the
+// end of a cycle see the device flag and return at once.
 #include <math.h>
 #include <string.h>
 
