@@ -506,14 +506,17 @@ def _rd(d):
             for k, v in d.items()}
 
 
-def run_serving(args, n_requests=48, rates=(0.25, 0.5, 1.0, 1.5)):
+def run_serving(args, n_requests=48, rates=(0.25, 0.5, 1.0, 1.5), reps=3):
     """Poisson stream of requests (4k-1M cells log-uniform, 5 value updates
     each, CFL x4 per update), FP32 factors, served by continuous batching (every
     step one update of every admitted request in shared launches, warm-started
     factors, admission by room in an arena sized to the HBM budget); against
     plain FP64 ABILU (synchronous sweeps) solving the requests one at a time on
     the same GPU.  Capacity = solves/s with every request queued at t = 0; the
-    arrival rates are fractions of it."""
+    arrival rates are fractions of it.  Every configuration runs `reps` times
+    and reports its median run (by solves/s), with the solves/s of all runs:
+    the host's own load moves single runs (one run of the 20-request stream at
+    the 1.0x rate stalled for 0.35 s on a loaded host)."""
     import torch
     import abilu_inputs as gen
     from paper_1912_00539_gb300 import serving
@@ -533,10 +536,16 @@ def run_serving(args, n_requests=48, rates=(0.25, 0.5, 1.0, 1.5)):
 
     budget = 0.25 * torch.cuda.get_device_properties(0).total_memory
     cfg = dict(build_sweeps=args.batch_build_sweeps, apply_sweeps=args.batch_apply_sweeps)
+    def median_run(run):
+        runs = sorted((serving.summarize(*run()) for _ in range(reps)),
+                      key=lambda r: r["solves_per_s"])
+        med = dict(runs[len(runs) // 2])
+        med["runs_solves_per_s"] = [round(r["solves_per_s"], 1) for r in runs]
+        return med
+
     srv = serving.Server(budget, dtype="f32", mode=args.mode, **cfg)
     srv.run(at_rate(1e9)[:3])                       # warm-up (kernels, host paths)
-    res, wall = srv.run(at_rate(1e9))               # capacity: all queued at t = 0
-    cap = serving.summarize(res, wall)
+    cap = median_run(lambda: srv.run(at_rate(1e9)))   # capacity: all queued at t = 0
     req_rate = cap["requests"] / cap["wall_s"]
     out = {"workload": f"{n_requests} requests, 4k-1M cells (log-uniform), 5 updates each",
            "cells": int(sum(r.n for r in unit)), "updates": n_upd, "generation_s": round(tgen, 1),
@@ -544,17 +553,16 @@ def run_serving(args, n_requests=48, rates=(0.25, 0.5, 1.0, 1.5)):
                      "budget_bytes": budget},
            "f32_capacity": _rd(cap)}
     for frac in rates:
-        res, wall = srv.run(at_rate(frac * req_rate))
-        out[f"f32_rate_{frac}x"] = _rd(serving.summarize(res, wall))
+        out[f"f32_rate_{frac}x"] = _rd(median_run(lambda: srv.run(at_rate(frac * req_rate))))
     srv.close()
     # the baseline: plain FP64 ABILU, one request at a time (all queued at t = 0
     # for its capacity, and at the 1.0x arrival rate)
     serving.serve_one_at_a_time(at_rate(1e9)[:2], dtype="f64", mode="sync", **cfg)
-    res, wall = serving.serve_one_at_a_time(at_rate(1e9), dtype="f64", mode="sync", **cfg)
-    out["f64_one_at_a_time_capacity"] = _rd(serving.summarize(res, wall))
-    res, wall = serving.serve_one_at_a_time(at_rate(1.0 * req_rate), dtype="f64", mode="sync",
-                                            **cfg)
-    out["f64_one_at_a_time_rate_1.0x"] = _rd(serving.summarize(res, wall))
+    out["f64_one_at_a_time_capacity"] = _rd(median_run(
+        lambda: serving.serve_one_at_a_time(at_rate(1e9), dtype="f64", mode="sync", **cfg)))
+    out["f64_one_at_a_time_rate_1.0x"] = _rd(median_run(
+        lambda: serving.serve_one_at_a_time(at_rate(1.0 * req_rate), dtype="f64", mode="sync",
+                                            **cfg)))
     out["f32_serving_over_f64_one_at_a_time"] = round(
         cap["solves_per_s"] / out["f64_one_at_a_time_capacity"]["solves_per_s"], 3)
     return out
