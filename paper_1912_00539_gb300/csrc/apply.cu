@@ -317,23 +317,34 @@ k_tri_staged(PatternView P, const T *__restrict__ F, const T *__restrict__ D,
         // a timed-out wait) it waits for the copies of the last ones, so the
         // CTA keeps its shared memory until every copy it issued has landed
         int armed[2] = {0, 0};
+        // the next chunk's ticket is taken one chunk ahead, and a chunk's row
+        // pointers are read before waiting for its stage, so the atomic's and
+        // the loads' latency overlap the consumers' work on earlier chunks
+        long long tn = SYNC ? (long long)blockIdx.x : (long long)atomicAdd(ticket, 1ull);
         for (int k = 0;; k++) {
             const int s = k & 1, u = k >> 1;
+            const long long t = tn;
+            const bool more = t < total;
+            long long sw = 0;
+            int chunk = 0, i0 = 0, i1 = 0, fb = 0, fe = 0;
+            if (more) {
+                tn = SYNC ? t + gridDim.x : (long long)atomicAdd(ticket, 1ull);
+                sw = SYNC ? 0 : t / nchunks;   // SYNC: t < nchunks
+                const int c = (int)(t - sw * nchunks);
+                chunk = (UPPER && !SYNC) ? (int)(nchunks - 1 - c) : c;
+                i0 = chunk * APPLY_ROWS;
+                i1 = min(i0 + APPLY_ROWS, P.n);
+                fb = rowp[i0];
+                fe = rowp[i1];
+            }
             if (u >= 1 && !mbar_wait(&empty[s], (u - 1) & 1, err, limit)) break;
             PipeStage<T> &S = st[s];
-            const long long t = SYNC ? (long long)blockIdx.x + (long long)k * gridDim.x
-                                     : (long long)atomicAdd(ticket, 1ull);
-            if (t >= total) {
+            if (!more) {
                 S.ticket = -1;
                 mbar_arrive(&full[s]);
                 armed[s]++;
                 break;
             }
-            const long long sw = SYNC ? 0 : t / nchunks;   // SYNC: t < nchunks
-            const int c = (int)(t - sw * nchunks);
-            const int chunk = (UPPER && !SYNC) ? (int)(nchunks - 1 - c) : c;
-            const int i0 = chunk * APPLY_ROWS, i1 = min(i0 + APPLY_ROWS, P.n);
-            const int fb = rowp[i0], fe = rowp[i1];
             const bool staged = fe - fb <= PIPE_CAP;
             const int cb = fb & ~3, ce = (fe + 3) & ~3;
             S.ticket = t;
