@@ -52,8 +52,8 @@ PROFILED_TRAFFIC = {
     "spmv_f64": 295.448832e6 + 15.170560e6,          # k_spmv<1>
     "build_sweeps_f32": 1.392420e9 + 531.461376e6,    # k_build_blocks_async<float, 1, 64>,
                                                        # 6 sweeps, strided 128-block tickets
-    "lower_sweeps_f32": None,                          # k_tri_staged: producer prefetch
-    "upper_sweeps_f32": None,                          # since the capture
+    "lower_sweeps_f32": 131.777024e6 + 6.098432e6,     # k_tri_staged<0, 0, 0, float>, 3 sweeps
+    "upper_sweeps_f32": 81.267456e6 + 1.445632e6,      # k_tri_staged<1, 1, 0, float>, 3 sweeps
 }
 
 
