@@ -297,7 +297,10 @@ __device__ __forceinline__ void build_finish_rows(int row0, int n, const typenam
     if constexpr (sizeof(T) < 8) {
         if (i < n) {
             float d[4];
-            if (quad_inv4_refined(u, d, sh_q + (threadIdx.x >> 2) * QUAD_SCRATCH) && q == 0)
+            // refined where the inverse is final (Udiag passed: the last sweep,
+            // or a prepare pass that no sweep follows)
+            if (quad_inv4_refined(u, d, sh_q + (threadIdx.x >> 2) * QUAD_SCRATCH, Udiag != nullptr) &&
+                q == 0)
                 atomicAdd(nsing, 1ull);
             st_row_sel<VOL>(Dout + (size_t)i * BB + q * BS, d);
             if (Udiag) st_row_sel<false>(Udiag + (size_t)i * BB + q * BS, u);
