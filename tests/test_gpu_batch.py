@@ -236,10 +236,13 @@ def test_autotuner_picks_a_converging_candidate_and_keeps_its_launch_shape(tmp_p
     assert (other.build_sweeps, other.mode) == (6, "sync")   # another CFL range: tuned anew
 
 
-def test_build_chunk_sizes_give_converging_async_builds():
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-4), ("bf16", 2e-2)])
+def test_build_chunk_sizes_give_converging_async_builds(dtype, tol):
     """Every allowed ticket size is a legal asynchronous iteration: the
-    factors reach sequential block ILU(0) with enough sweeps; bad sizes are
-    refused."""
+    factors reach sequential block ILU(0) with enough sweeps, whether a ticket
+    is one sub-chunk (32, 64), several 64-block sub-chunks spread over the
+    work list (128, 256, 512) or several 32-block ones (96, 160); bad sizes
+    are refused."""
     import torch
     import oracle
     import paper_1912_00539_gb300.abilu as ab
@@ -247,13 +250,14 @@ def test_build_chunk_sizes_give_converging_async_builds():
     pat = ab.Pattern(torch.from_numpy(s.rowptr).cuda(), torch.from_numpy(s.colind).cuda())
     A = torch.from_numpy(s.vals).cuda()
     Xs, Ds, _ = oracle.bilu0_seq(s.rowptr, s.colind, s.vals)
-    fac = ab.Factors(pat, "f32")
-    for c in (32, 64, 256, 512):
+    fac = ab.Factors(pat, dtype)
+    for c in (32, 64, 96, 128, 160, 256, 512):
         fac.set_build_chunk(c)
         fac.build(A, 2 * s.n + 4, mode="async")
-        X, _ = fac.export()
-        X = X.cpu().numpy()
-        assert np.abs(X - Xs).max() / np.abs(Xs).max() < 1e-4, c
+        X, D = fac.export()
+        X, D = X.cpu().numpy(), D.cpu().numpy()
+        assert np.abs(X - Xs).max() / np.abs(Xs).max() < tol, c
+        assert np.abs(D - Ds).max() / np.abs(Ds).max() < tol, c
     for bad in (16, 48, 1024):
         with pytest.raises(ab.AbiluError):
             fac.set_build_chunk(bad)
