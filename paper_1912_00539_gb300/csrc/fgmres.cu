@@ -440,6 +440,56 @@ __device__ __forceinline__ void givens_column_staged(SolveState *S, int j, const
 }
 
 
+// The last CTA of a dot-product pass: h[k] = sum over CTAs of the partials of
+// slot k, k < jp1, in tiles of T (pass 0 -> S->h, pass 1 -> S->h2).  sh_w
+// holds RED_THREADS * T doubles.
+template <int T>
+__device__ __forceinline__ void dots_last(SolveState *S, const double *partials, int jp1, int pass,
+                                          double *sh_w, double *sh_o) {
+    double *h = pass == 0 ? S->h : S->h2;
+    for (int k0 = 0; k0 < jp1; k0 += T) {
+        const int kn = jp1 - k0 < T ? jp1 - k0 : T;
+        reduce_partials<T>(partials, MAXM + 2, k0, kn, sh_w, sh_o);
+        if (threadIdx.x < kn) h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) S->counter = 0;
+}
+
+// The last CTA of a single-reduction step: the dots of slots k < jp1 and
+// ||w||^2 (slot jp1) reduced in tiles of T, the last tile with the norm; the
+// Givens inputs staged while the partials are reduced; every thread's partials
+// loaded before any add (3 CTAs of 608 per thread; two rounds of 2 for seven
+// values in 64 registers); then h_{j+1,j} = sqrt(||w||^2 - sum_k h_k^2) and
+// the Givens update of column j by one thread.  sh_w holds RED_THREADS *
+// (T + 1) doubles.  A difference below 1e-12 ||w||^2 (more than twelve digits
+// cancelled, or negative) is taken as a breakdown.
+template <int T>
+__device__ __forceinline__ void dots_norm_last(SolveState *S, const double *partials, int jp1,
+                                               double *sh_w, double *sh_o) {
+    __shared__ GivensIn G;
+    __shared__ double sh_h[MAXM + 1], sh_ww;
+    givens_stage(S, jp1 - 1, &G);
+    for (int k0 = 0; k0 < jp1; k0 += T) {
+        const int kn = jp1 - k0 < T ? jp1 - k0 : T;
+        const bool lastt = k0 + T >= jp1;
+        reduce_partials<T + 1, (T + 1 <= 5 ? 3 : 2)>(partials, MAXM + 2, k0,
+                                                     lastt ? kn + 1 : kn, sh_w, sh_o);
+        if (threadIdx.x < kn) {
+            S->h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+            sh_h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        }
+        if (lastt && threadIdx.x == 0) sh_ww = sh_o[kn];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double ww = sh_ww;
+    double hh = 0.0;
+    for (int k = 0; k < jp1; k++) hh = fma(sh_h[k], sh_h[k], hh);
+    const double d = ww - hh;
+    givens_column_staged(S, jp1 - 1, sh_h, &G, d > 1e-12 * ww ? sqrt(d) : 0.0);   // the next kernel publishes
+}
+
 // h[k] = <V_k, w>, k < jp1 (pass 0 -> S->h, pass 1 -> S->h2).  The grid is
 // 4 CTAs per SM and all of them must be resident at once (one wave), so the
 // kernel is held to 64 registers.  NW = 0: any jp1, in tiles of up to TILE
@@ -472,14 +522,7 @@ k_dots(const double *__restrict__ V, long long nv2, int jp1, const double *__res
         }
     }
     if (!last_cta(S)) return;
-    double *h = pass == 0 ? S->h : S->h2;
-    for (int k0 = 0; k0 < jp1; k0 += T) {
-        const int kn = jp1 - k0 < T ? jp1 - k0 : T;
-        reduce_partials<T>(partials, MAXM + 2, k0, kn, sh_w, sh_o);
-        if (threadIdx.x < kn) h[k0 + threadIdx.x] = sh_o[threadIdx.x];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) S->counter = 0;
+    dots_last<T>(S, partials, jp1, pass, sh_w, sh_o);
 }
 
 // k_dots for jp1 basis vectors (the pipelined kernels for one to four)
@@ -538,31 +581,7 @@ k_dots_norm(const double *__restrict__ V, long long nv2, int jp1, const double *
         }
     }
     if (!last_cta(S)) return;
-    // the last CTA: the Givens inputs staged while the partials are reduced;
-    // each tile's dots in one reduction, the last one with ||w||^2 (slot jp1),
-    // every thread's partials loaded before any add (3 CTAs of 608 per thread;
-    // two rounds of 2 for the general kernel's seven values, in its 64 registers)
-    __shared__ GivensIn G;
-    __shared__ double sh_h[MAXM + 1], sh_ww;
-    givens_stage(S, jp1 - 1, &G);
-    for (int k0 = 0; k0 < jp1; k0 += T) {
-        const int kn = jp1 - k0 < T ? jp1 - k0 : T;
-        const bool lastt = k0 + T >= jp1;
-        reduce_partials<T + 1, (T + 1 <= 5 ? 3 : 2)>(partials, MAXM + 2, k0,
-                                                     lastt ? kn + 1 : kn, sh_w, sh_o);
-        if (threadIdx.x < kn) {
-            S->h[k0 + threadIdx.x] = sh_o[threadIdx.x];
-            sh_h[k0 + threadIdx.x] = sh_o[threadIdx.x];
-        }
-        if (lastt && threadIdx.x == 0) sh_ww = sh_o[kn];
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double ww = sh_ww;
-    double hh = 0.0;
-    for (int k = 0; k < jp1; k++) hh = fma(sh_h[k], sh_h[k], hh);
-    const double d = ww - hh;
-    givens_column_staged(S, jp1 - 1, sh_h, &G, d > 1e-12 * ww ? sqrt(d) : 0.0);   // k_update_scale publishes
+    dots_norm_last<T>(S, partials, jp1, sh_w, sh_o);   // k_update_scale publishes
 }
 
 static void launch_dots_norm(int nred, cudaStream_t st, const double *V, long long nv2, int jp1,
@@ -578,6 +597,69 @@ static void launch_dots_norm(int nred, cudaStream_t st, const double *V, long lo
     else
         launch_pdl(k_dots_norm<0>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
 }
+
+// w = A z_j and, in the same pass over the rows, the first Gram-Schmidt pass's
+// dots h[k] = <V_k, w>, k < KF = j + 1, plus ||w||^2 with NORM (the
+// single-reduction step): each product is consumed where it is formed, so w
+// is written once and not read back by a second kernel, and one launch ramp
+// and tail go.  Both halves are bound by the FP64 pipe (two lanes per SM),
+// which they now share.  A quad of threads per block row as in the SpMV
+// kernel (row q of each 4x4 block, the same FMA chain, spmv.cuh), rows in a
+// grid stride.
+// Per thread the sums run over its rows in order, then the block sum and the
+// last CTA's reduction of the partials (slots 0..KF-1, the norm in slot KF),
+// so the result is deterministic for a fixed grid.  Launched like the
+// residual kernel, 3 CTAs per SM in one wave: 80 registers hold a row's four
+// blocks, its x gathers and the basis entries in flight (at 64 registers and
+// 4 CTAs per SM every width spilled, and the solve was 0.5% slower).  Steps
+// with j + 1 > SPMV_DOTS_MAX run the SpMV and the tiled dot kernels instead.
+constexpr int SPMV_DOTS_MAX = 5;
+template <int KF, bool NORM>
+__global__ void __launch_bounds__(RED_THREADS, 3)
+k_spmv_dots(PatternView P, const double *__restrict__ A, const double *__restrict__ z,
+            double *__restrict__ w, const double *__restrict__ V, long long nv, SolveState *S,
+            double *partials) {
+    pdl_wait();
+    pdl_trigger();
+    if (S->done) return;   // set by an earlier kernel: a plain load
+    constexpr int KA = KF + (NORM ? 1 : 0);
+    __shared__ double sh_w[RED_THREADS * KA], sh_o[KA];
+    const int q = threadIdx.x & 3;
+    double acc[KA];
+#pragma unroll
+    for (int k = 0; k < KA; k++) acc[k] = 0.0;
+    const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
+    for (int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2); i < P.n; i += rows_per_grid) {
+        const size_t o = (size_t)i * BS + q;
+        double v[KF];   // issued with the row's matrix loads
+#pragma unroll
+        for (int k = 0; k < KF; k++) v[k] = __ldg(V + (size_t)k * nv + o);
+        const double s = row_dot_blocks(P, A, z, i, q);
+        w[o] = s;
+#pragma unroll
+        for (int k = 0; k < KF; k++) acc[k] = fma(v[k], s, acc[k]);
+        if constexpr (NORM) acc[KF] = fma(s, s, acc[KF]);
+    }
+    block_sum<KA>(acc, sh_w, sh_o, KA);
+    if (threadIdx.x < KA) partials[(size_t)blockIdx.x * (MAXM + 2) + threadIdx.x] = sh_o[threadIdx.x];
+    if (!last_cta(S)) return;
+    if constexpr (NORM) dots_norm_last<KF>(S, partials, KF, sh_w, sh_o);   // k_update_scale publishes
+    else dots_last<KF>(S, partials, KF, 0, sh_w, sh_o);
+}
+
+template <bool NORM>
+static void launch_spmv_dots_n(int nred, cudaStream_t st, const PatternView &P, const double *A,
+                               const double *z, double *w, const double *V, long long nv, int jp1,
+                               SolveState *S, double *partials) {
+    switch (jp1) {
+    case 1: launch_pdl(k_spmv_dots<1, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
+    case 2: launch_pdl(k_spmv_dots<2, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
+    case 3: launch_pdl(k_spmv_dots<3, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
+    case 4: launch_pdl(k_spmv_dots<4, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
+    default: launch_pdl(k_spmv_dots<5, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
+    }
+}
+static_assert(SPMV_DOTS_MAX == 5, "one instance per width");
 
 // v_{j+1} = (w - sum_k h[k] V_k) * hn_inv and its FP32 copy (the next
 // preconditioner's input) in one pass; w itself is not written back.  J =
@@ -954,18 +1036,32 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
         for (; j < m; j++) {
             s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
-            if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) { ret = s; break; }
+            // w = A z_j with the first pass's dots (and the norm) in one kernel
+            // for the first SPMV_DOTS_MAX steps of a cycle; later, wider steps
+            // run the product and the tiled dot kernels
+            const bool fused = j + 1 <= SPMV_DOTS_MAX;
+            if (fused) {
+                if (form == GS_SINGLE)
+                    launch_spmv_dots_n<true>(nres, st, P, A, Z + (size_t)j * nv, w, V, nv, j + 1, SS,
+                                             ws->partials);
+                else
+                    launch_spmv_dots_n<false>(nres, st, P, A, Z + (size_t)j * nv, w, V, nv, j + 1, SS,
+                                              ws->partials);
+            } else if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) {
+                ret = s;
+                break;
+            }
             if (form == GS_SINGLE) {            // one pass, one reduction (see k_dots_norm)
-                launch_dots_norm(nred, st, V, nv2, j + 1, w, SS, ws->partials);
+                if (!fused) launch_dots_norm(nred, st, V, nv2, j + 1, w, SS, ws->partials);
                 launch_update_scale(nred, st, V, nv2, j, w, V + (size_t)(j + 1) * nv, v32, SS,
                                     pc.y0, pc.tickets);
             } else if (form == GS_CLASSICAL) {  // one pass, the norm of the updated w
-                launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
+                if (!fused) launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 1);
                 launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS,
                            pc.y0, pc.tickets);
             } else {               // CGS2: two passes, the norm of the updated w
-                launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
+                if (!fused) launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 0);
                 launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 1);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 1, 1);

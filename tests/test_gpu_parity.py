@@ -425,6 +425,33 @@ def test_fgmres_restarts_and_reorth(ab):
         assert abs(res.iters - ro.iters) <= max(2, ro.iters // 10), (res.iters, ro.iters)
 
 
+@pytest.mark.parametrize("form", ["single", "classical", "cgs2"])
+@pytest.mark.parametrize("nx,ny", [(30, 20), (240, 160)])
+def test_fgmres_fused_and_separate_steps(ab, form, nx, ny):
+    """Cycles longer than five Arnoldi steps: the first five form w = A z_j
+    with the first pass's dot products (and ||w||^2 in the single-reduction
+    form) in one kernel, later steps run the product and the dot kernels
+    apart.  In FP64 the whole cycle follows the oracle's (modified
+    Gram-Schmidt) iteration count in each Gram-Schmidt form: rtol 1e-6 takes
+    the single-reduction step, 1e-8 the classical one with the explicit norm,
+    reorth CGS2.  The 76,800-row system gives each thread of the fused kernel
+    three rows of its grid stride and crosses a restart at 30."""
+    s = gen.small_system(nx, ny, seed=3, cfl=1e4)
+    d = Dev(ab, s)
+    rtol = 1e-6 if form == "single" else 1e-8
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 1)
+    _, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, 1, 1, restart=30, rtol=rtol)
+    assert ro.iters > 5
+    fac = ab.Factors(d.pat, "f64")
+    x = d.vec()
+    res = ab.fgmres_solve(d.pat, d.A, fac, d.b, x, restart=30, rtol=rtol, build_sweeps=1,
+                          apply_sweeps_lower=1, apply_sweeps_upper=1, mode="sync",
+                          reorth=form == "cgs2")
+    r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
+    assert res.converged and np.linalg.norm(r) / np.linalg.norm(s.b) <= rtol * 1.001
+    assert abs(res.iters - ro.iters) <= max(1, ro.iters // 10), (res.iters, ro.iters)
+
+
 def test_fgmres_max_iters_reports_noconv(ab):
     d = Dev(ab, gen.small_system(12, 10, seed=9, cfl=1.0))
     fac = ab.Factors(d.pat, "f64")
