@@ -35,8 +35,6 @@ abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, 
 abilu_status apply_dispatch_ready(abilu_factors f, const double *r, const float *r32, double *z,
                                   int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
 bool apply_y_ready(abilu_factors f, int nl, int nu, abilu_mode mode);
-abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
-                         double beta, double *y, cudaStream_t st, Skip skip);
 void apply_warm(abilu_dtype dt);
 size_t solve_state_bytes();
 int red_ctas();
@@ -198,17 +196,19 @@ k_b_scale(const double *vin, double *vout, float *v32, const BState *S,
 }
 
 // partial dots <V_k0+k, w> over the super-chunk's chunks c0..c1-1 (one value
-// per thread per chunk), one block reduction, partials of super-chunk sc
-template <int K>
+// per thread per chunk), one block reduction, partials of super-chunk sc.
+// CG: w was written earlier in the same kernel (by this thread): read through
+// L2, never the read-only path
+template <int K, bool CG = false>
 __device__ __forceinline__ void b_dots_tile(const double *__restrict__ V, size_t nv, int k0,
-                                            const double *__restrict__ w, int c0, int c1,
+                                            const double *w, int c0, int c1,
                                             double *sh_w, double *sh_o, double *partials, int sc) {
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; k++) acc[k] = 0.0;
     for (int c = c0; c < c1; c++) {
         const size_t e = (size_t)c * CHUNK_VALS + threadIdx.x;
-        const double wv = w[e];
+        const double wv = CG ? __ldcg(w + e) : w[e];
 #pragma unroll
         for (int k = 0; k < K; k++) acc[k] = fma(V[(size_t)(k0 + k) * nv + e], wv, acc[k]);
     }
@@ -216,22 +216,38 @@ __device__ __forceinline__ void b_dots_tile(const double *__restrict__ V, size_t
     if (threadIdx.x < K) partials[(size_t)sc * PSTRIDE + k0 + threadIdx.x] = sh_o[threadIdx.x];
 }
 
-// the dots tiles of jp1 basis vectors over a super-chunk
+// the dots tiles of basis vectors kbeg..jp1-1 over a super-chunk
+template <bool CG = false>
 __device__ __forceinline__ void b_dots_tiles(const double *__restrict__ V, size_t nv, int jp1,
-                                             const double *__restrict__ w, int c0, int c1,
-                                             double *sh_w, double *sh_o, double *partials, int sc) {
-    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
+                                             const double *w, int c0, int c1,
+                                             double *sh_w, double *sh_o, double *partials, int sc,
+                                             int kbeg = 0) {
+    for (int k0 = kbeg; k0 < jp1; k0 += BTILE) {
         switch (jp1 - k0 < BTILE ? jp1 - k0 : BTILE) {
-        case 1: b_dots_tile<1>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
-        case 2: b_dots_tile<2>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
-        case 3: b_dots_tile<3>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
-        case 4: b_dots_tile<4>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
-        case 5: b_dots_tile<5>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
-        case 6: b_dots_tile<6>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
-        case 7: b_dots_tile<7>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
-        default: b_dots_tile<8>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 1: b_dots_tile<1, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 2: b_dots_tile<2, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 3: b_dots_tile<3, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 4: b_dots_tile<4, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 5: b_dots_tile<5, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 6: b_dots_tile<6, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        case 7: b_dots_tile<7, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
+        default: b_dots_tile<8, CG>(V, nv, k0, w, c0, c1, sh_w, sh_o, partials, sc); break;
         }
     }
+}
+
+// The system's last CTA of a dots pass: h[k] (pass 0) or h2[k] (pass 1), k < jp1,
+// from the partials of super-chunks c0..c1-1
+__device__ __forceinline__ void b_dots_last(BState *St, int jp1, int pass, const double *partials,
+                                            int c0, int c1, double *sh_w, double *sh_o) {
+    double *h = pass == 0 ? St->h : St->h2;
+    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
+        const int kn = jp1 - k0 < BTILE ? jp1 - k0 : BTILE;
+        reduce_sys<BTILE, PSTRIDE>(partials, c0, c1, k0, kn, sh_w, sh_o);
+        if (threadIdx.x < kn) h[k0 + threadIdx.x] = sh_o[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) St->counter = 0;
 }
 
 // h[k] = <V_k, w>_s for k <= j, per system (pass 0 -> h, 1 -> h2)
@@ -248,14 +264,7 @@ k_b_dots(const double *__restrict__ V, size_t nv, int j, const double *__restric
     b_dots_tiles(V, nv, jp1, w, T.sc_first[sc], T.sc_first[sc + 1], sh_w, sh_o, partials, sc);
     const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];
     if (!last_cta_of(St, c1 - c0)) return;
-    double *h = pass == 0 ? St->h : St->h2;
-    for (int k0 = 0; k0 < jp1; k0 += BTILE) {
-        const int kn = jp1 - k0 < BTILE ? jp1 - k0 : BTILE;
-        reduce_sys<BTILE, PSTRIDE>(partials, c0, c1, k0, kn, sh_w, sh_o);
-        if (threadIdx.x < kn) h[k0 + threadIdx.x] = sh_o[threadIdx.x];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) St->counter = 0;
+    b_dots_last(St, jp1, pass, partials, c0, c1, sh_w, sh_o);
 }
 
 __device__ __forceinline__ void b_givens(BState *St, int s, int j, int two_pass, double hn,
@@ -338,34 +347,15 @@ __device__ __forceinline__ void b_givens(BState *St, int s, int j, int two_pass,
     }
 }
 
-// The single-reduction step of the batch (one classical pass; see
-// k_dots_norm in fgmres.cu): h[k] = <V_k, w>_s and ||w||_s^2 in one pass, the
-// system's last chunk forms h_{j+1,j} = sqrt(||w||^2 - sum h_k^2) (a
-// difference below 1e-12 ||w||^2 is a breakdown) and the Givens update.
-__global__ void __launch_bounds__(RED_THREADS)
-k_b_dots_norm(const double *__restrict__ V, size_t nv, int j, const double *__restrict__ w,
-              BState *S, BTab T, double *partials, BConf cf, int *hs_done, int *sys_done,
-              int *bflag) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ double sh_w[RED_THREADS * BTILE], sh_o[BTILE];
-    const int sc = blockIdx.x, s = T.sc_sys[sc];
-    BState *St = S + s;
-    if (St->done) return;
+// The system's last CTA of a single-reduction step: h[k], k <= j, and ||w||^2
+// (slot BMAXM + 1) from the partials of super-chunks c0..c1-1, then
+// h_{j+1,j} = sqrt(||w||^2 - sum h_k^2) (a difference below 1e-12 ||w||^2 is a
+// breakdown) and the Givens update
+__device__ __forceinline__ void b_dots_norm_last(BState *St, int s, int j, const double *partials,
+                                                 int c0, int c1, double *sh_w, double *sh_o,
+                                                 const BConf &cf, int *hs_done, int *sys_done,
+                                                 int *bflag) {
     const int jp1 = j + 1;
-    const int f0 = T.sc_first[sc], f1 = T.sc_first[sc + 1];
-    b_dots_tiles(V, nv, jp1, w, f0, f1, sh_w, sh_o, partials, sc);
-    {
-        double nrm[1] = {0.0};
-        for (int c = f0; c < f1; c++) {
-            const double wv = w[(size_t)c * CHUNK_VALS + threadIdx.x];
-            nrm[0] = fma(wv, wv, nrm[0]);
-        }
-        block_sum<1>(nrm, sh_w, sh_o, 1);
-        if (threadIdx.x == 0) partials[(size_t)sc * PSTRIDE + BMAXM + 1] = sh_o[0];
-    }
-    const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];
-    if (!last_cta_of(St, c1 - c0)) return;
     for (int k0 = 0; k0 < jp1; k0 += BTILE) {
         const int kn = jp1 - k0 < BTILE ? jp1 - k0 : BTILE;
         reduce_sys<BTILE, PSTRIDE>(partials, c0, c1, k0, kn, sh_w, sh_o);
@@ -379,6 +369,76 @@ k_b_dots_norm(const double *__restrict__ V, size_t nv, int j, const double *__re
     for (int k = 0; k < jp1; k++) hh = fma(St->h[k], St->h[k], hh);
     const double d = ww - hh;
     b_givens(St, s, j, 0, d > 1e-12 * ww ? sqrt(d) : 0.0, cf, hs_done, sys_done, bflag);
+}
+
+// w = A z for the super-chunk's rows (a quad of threads per block row, one
+// 64-row chunk per pass, the SpMV kernel's FMA chain, spmv.cuh) and, from the
+// same registers, the dots with V_0..V_{KF-1} and, with NORM, ||w||^2; w is
+// stored once.  The same value-to-thread map as the dot tiles (value e =
+// chunk * 256 + thread), so a later tile of the same kernel re-reads only
+// this thread's own entries of w.
+template <int KF, bool NORM>
+__device__ __forceinline__ void b_spmv_tile(const PatternView &P, const double *__restrict__ A,
+                                            const double *__restrict__ z, double *w,
+                                            const double *__restrict__ V, size_t nv, int c0, int c1,
+                                            double *sh_w, double *sh_o, double *partials, int sc) {
+    constexpr int KA = KF + (NORM ? 1 : 0);
+    double acc[KA];
+#pragma unroll
+    for (int k = 0; k < KA; k++) acc[k] = 0.0;
+    const int q = threadIdx.x & 3;
+    for (int c = c0; c < c1; c++) {
+        const int i = c * CHUNK_ROWS + (threadIdx.x >> 2);
+        const size_t e = (size_t)c * CHUNK_VALS + threadIdx.x;   // = i * BS + q
+        double v[KF];   // issued with the row's matrix loads
+#pragma unroll
+        for (int k = 0; k < KF; k++) v[k] = __ldg(V + (size_t)k * nv + e);
+        const double r = row_dot_blocks(P, A, z, i, q);
+        w[e] = r;
+#pragma unroll
+        for (int k = 0; k < KF; k++) acc[k] = fma(v[k], r, acc[k]);
+        if constexpr (NORM) acc[KF] = fma(r, r, acc[KF]);
+    }
+    block_sum<KA>(acc, sh_w, sh_o, KA);
+    if (threadIdx.x < KF) partials[(size_t)sc * PSTRIDE + threadIdx.x] = sh_o[threadIdx.x];
+    if (NORM && threadIdx.x == 0) partials[(size_t)sc * PSTRIDE + BMAXM + 1] = sh_o[KF];
+}
+
+// The Arnoldi product of the batch fused with the first Gram-Schmidt pass (the
+// single-system solve's k_spmv_dots): w = A z_j per super-chunk with the dots
+// of the first min(j + 1, B_FUSED) basis vectors (and ||w||^2 with NORM) in
+// the same pass; the tiles past B_FUSED re-read the CTA's own entries of w
+// through L2.  The system's last CTA then reduces the partials: with NORM,
+// h and h_{j+1,j} = sqrt(||w||^2 - sum h_k^2) and the Givens update (the
+// single-reduction step, b_dots_norm_last), else h of the first pass
+// (b_dots_last).  One launch and one pass over w fewer per step than the
+// product followed by the dots.  3 CTAs per SM: 80 registers
+// hold a row's four blocks, its x gathers and the basis entries in flight.
+constexpr int B_FUSED = 4;
+template <bool NORM>
+__global__ void __launch_bounds__(RED_THREADS, 3)
+k_b_spmv_dots(PatternView P, const double *__restrict__ A, const double *__restrict__ z,
+              double *w, const double *__restrict__ V, size_t nv, int j, BState *S, BTab T,
+              double *partials, BConf cf, int *hs_done, int *sys_done, int *bflag) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ double sh_w[RED_THREADS * BTILE], sh_o[BTILE];
+    const int sc = blockIdx.x, s = T.sc_sys[sc];
+    BState *St = S + s;
+    if (St->done) return;
+    const int jp1 = j + 1;
+    const int f0 = T.sc_first[sc], f1 = T.sc_first[sc + 1];
+    switch (jp1 < B_FUSED ? jp1 : B_FUSED) {
+    case 1: b_spmv_tile<1, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
+    case 2: b_spmv_tile<2, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
+    case 3: b_spmv_tile<3, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
+    default: b_spmv_tile<4, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
+    }
+    if (jp1 > B_FUSED) b_dots_tiles<true>(V, nv, jp1, w, f0, f1, sh_w, sh_o, partials, sc, B_FUSED);
+    const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];
+    if (!last_cta_of(St, c1 - c0)) return;
+    if constexpr (NORM) b_dots_norm_last(St, s, j, partials, c0, c1, sh_w, sh_o, cf, hs_done, sys_done, bflag);
+    else b_dots_last(St, jp1, 0, partials, c0, c1, sh_w, sh_o);
 }
 
 // v_{j+1} = (w - sum_k h[k] V_k) * hn_inv per system and its FP32 copy (w is
@@ -730,23 +790,27 @@ static abilu_status enqueue_step(abilu_batch b, const fgmres_opts *opts, const B
         b->fac, V + (size_t)j * nv, v32, Z + (size_t)j * nv, opts->apply_sweeps_lower,
         opts->apply_sweeps_upper, (abilu_mode)opts->mode, st, skip);
     if (s != ABILU_OK) return s;
-    if ((s = spmv_launch(P, b->A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) return s;
     const BTab T = batch_tab(b);
     const int nsc = b->nsc;
     const int form = gs_form(opts);
+    // w = A z_j with the first Gram-Schmidt pass's dots (and ||w||^2 in the
+    // single-reduction form) in one kernel
+    const double *zj = Z + (size_t)j * nv;
+    if (form == GS_SINGLE)
+        launch_pdl(k_b_spmv_dots<true>, nsc, RED_THREADS, 0, st, P, b->A, zj, w, V, nv, j, b->S, T,
+            b->partials, cf, b->hs_done, b->sys_done, b->bflag);
+    else
+        launch_pdl(k_b_spmv_dots<false>, nsc, RED_THREADS, 0, st, P, b->A, zj, w, V, nv, j, b->S, T,
+            b->partials, cf, b->hs_done, b->sys_done, b->bflag);
     if (form == GS_SINGLE) {   // one pass, one reduction per system
-        launch_pdl(k_b_dots_norm, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf,
-            b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_update_scale, nck, RED_THREADS, 0, st, V, nv, j, w,
             V + (size_t)(j + 1) * nv, v32, b->S, b->chunk_sys, y.y0, y.tk);
     } else if (form == GS_CLASSICAL) {   // one pass, the norm of the updated w
-        launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 0);
         launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 0, 1,
             b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_scale, nck, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, b->S,
             b->chunk_sys, y.y0, y.tk);
     } else {               // CGS2: two passes, the norm of the updated w
-        launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 0);
         launch_pdl(k_b_update, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, cf, 0, 0,
             b->hs_done, b->sys_done, b->bflag);
         launch_pdl(k_b_dots, nsc, RED_THREADS, 0, st, V, nv, j, w, b->S, T, b->partials, 1);

@@ -127,6 +127,37 @@ def test_batch_tight_tolerances_and_the_graph_key(ab, rtol):
         assert res[k].iters == ra.iters, (k, res[k].iters, ra.iters)
 
 
+@pytest.mark.parametrize("rtol,reorth", [(1e-6, False), (1e-8, False), (1e-8, True)])
+def test_batch_steps_wider_than_the_fused_tile(ab, rtol, reorth):
+    """Each Arnoldi step of the batch forms w = A z_j in the kernel that takes
+    the first four dot products of the first Gram-Schmidt pass (and ||w||^2 in
+    the single-reduction form); wider steps re-read the CTA's own entries of w
+    for the remaining tiles.  In every Gram-Schmidt form (single reduction at
+    1e-6, classical with the explicit norm at 1e-8, CGS2) each system takes
+    its single-system iteration count (synchronous FP64) and reaches rtol, and
+    at least one system runs steps past the fourth."""
+    import torch
+    systems = _systems()[:4]
+    devs = [_dev(s) for s in systems]
+    batch = ab.Batch([(d[0], d[1]) for d in devs], dtype="f64")
+    for k, d in enumerate(devs):
+        batch.set_system(k, d[2], d[3])
+    opts = dict(restart=30, rtol=rtol, build_sweeps=2, apply_sweeps_lower=1, apply_sweeps_upper=1,
+                mode="sync", reorth=reorth)
+    res = batch.solve(**opts)
+    assert max(r.iters for r in res) > 4
+    for k, (s, d) in enumerate(zip(systems, devs)):
+        x = torch.empty_like(d[3])
+        batch.solution(k, x)
+        r = s.b - oracle.spmv(s.rowptr, s.colind, s.vals, x.cpu().numpy())
+        assert res[k].converged and np.linalg.norm(r) / np.linalg.norm(s.b) <= rtol * 1.001, k
+        pat = ab.Pattern(d[0], d[1])
+        fac = ab.Factors(pat, "f64")
+        xa = torch.zeros_like(d[3])
+        ra = ab.fgmres_solve(pat, d[2], fac, d[3], xa, **opts)
+        assert res[k].iters == ra.iters, (k, res[k].iters, ra.iters)
+
+
 def test_batch_rejects_bad_input(ab):
     import torch
     s = gen.small_system(3, 3, seed=34)
