@@ -4,7 +4,7 @@
 // Per Arnoldi step j:  z_j = M^{-1} v_j (block ILU sweeps, any precision),
 // w = A z_j (FP64 SpMV), classical Gram-Schmidt h = V^T w, w -= V h (one pass,
 // or two with reorth), h_{j+1,j} = ||w|| (for rtol >= 1e-7 formed with the dot
-// products in one reduction, see k_dots_norm and gs_form_for), Givens rotation
+// products in one reduction, see k_spmv_dots and gs_form_for), Givens rotation
 // of the new column, residual estimate |g_{j+1}|, v_{j+1} = w / h_{j+1,j}.  At
 // the end of a cycle y = R^{-1} g, x += Z y, and the true residual b - A x is
 // formed in FP64; an estimate that passed but is not confirmed by it restarts
@@ -35,8 +35,6 @@ abilu_status apply_dispatch(abilu_factors f, const double *r, const float *r32, 
 abilu_status apply_dispatch_ready(abilu_factors f, const double *r, const float *r32, double *z,
                                   int nl, int nu, abilu_mode mode, cudaStream_t st, Skip skip);
 bool apply_y_ready(abilu_factors f, int nl, int nu, abilu_mode mode);
-abilu_status spmv_launch(const PatternView &P, const double *A, double alpha, const double *x,
-                         double beta, double *y, cudaStream_t st, Skip skip);
 abilu_status ensure_krylov(abilu_factors f, int m);
 int red_ctas();
 
@@ -262,17 +260,13 @@ k_scale(const double *vin, double *vout, float *v32, long long nv2, SolveState *
 
 // Partial dot products of K consecutive basis vectors with w for this CTA.
 // K is a compile-time width so no predicated-off FP64 FMA is issued.
-// NORM: also ||w||^2 in the same pass (slot K of the accumulators; its
-// partial goes to slot k0 + K, right after the tile's dots: the last tile's,
-// so slot jp1), for the single-reduction step.
-template <int K, bool PIPE, bool NORM = false>
+template <int K, bool PIPE>
 __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long long nv2,
                                           int k0, const double2 *__restrict__ w2,
                                           double *sh_w, double *sh_o, double *partials) {
-    constexpr int KA = K + (NORM ? 1 : 0);
-    double acc[KA];
+    double acc[K];
 #pragma unroll
-    for (int k = 0; k < KA; k++) acc[k] = 0.0;
+    for (int k = 0; k < K; k++) acc[k] = 0.0;
     const long long st = (long long)gridDim.x * blockDim.x;
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     // PIPE (the kernels of one to four basis vectors): software-pipelined, the
@@ -298,7 +292,6 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
                 }
 #pragma unroll
                 for (int k = 0; k < K; k++) acc[k] = fma(vc[k].y, wc.y, fma(vc[k].x, wc.x, acc[k]));
-                if constexpr (NORM) acc[K] = fma(wc.y, wc.y, fma(wc.x, wc.x, acc[K]));
                 e = en;
                 if (e >= nv2) break;
             }
@@ -320,10 +313,6 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
                 acc[k] = fma(va[k].y, wa.y, fma(va[k].x, wa.x, acc[k]));
                 acc[k] = fma(vb[k].y, wb.y, fma(vb[k].x, wb.x, acc[k]));
             }
-            if constexpr (NORM) {
-                acc[K] = fma(wa.y, wa.y, fma(wa.x, wa.x, acc[K]));
-                acc[K] = fma(wb.y, wb.y, fma(wb.x, wb.x, acc[K]));
-            }
         }
     }
     for (; e < nv2; e += st) {   // wide tiles (K + 1 loads in flight already) and tails
@@ -333,11 +322,9 @@ __device__ __forceinline__ void dots_tile(const double2 *__restrict__ V2, long l
             const double2 v = V2[(size_t)(k0 + k) * nv2 + e];
             acc[k] = fma(v.y, wv.y, fma(v.x, wv.x, acc[k]));
         }
-        if constexpr (NORM) acc[K] = fma(wv.y, wv.y, fma(wv.x, wv.x, acc[K]));
     }
-    block_sum<KA>(acc, sh_w, sh_o, KA);
+    block_sum<K>(acc, sh_w, sh_o, K);
     if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
-    if (NORM && threadIdx.x == 0) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + K] = sh_o[K];
 }
 
 // The Givens update of column j of the Hessenberg matrix (from the
@@ -456,14 +443,18 @@ __device__ __forceinline__ void dots_last(SolveState *S, const double *partials,
     if (threadIdx.x == 0) S->counter = 0;
 }
 
-// The last CTA of a single-reduction step: the dots of slots k < jp1 and
-// ||w||^2 (slot jp1) reduced in tiles of T, the last tile with the norm; the
-// Givens inputs staged while the partials are reduced; every thread's partials
-// loaded before any add (3 CTAs of 608 per thread; two rounds of 2 for seven
-// values in 64 registers); then h_{j+1,j} = sqrt(||w||^2 - sum_k h_k^2) and
-// the Givens update of column j by one thread.  sh_w holds RED_THREADS *
-// (T + 1) doubles.  A difference below 1e-12 ||w||^2 (more than twelve digits
-// cancelled, or negative) is taken as a breakdown.
+// The last CTA of a single-reduction step (one classical Gram-Schmidt pass and
+// one reduction, the solve's default for rtol >= 1e-7, gs_form_for): the dots
+// of slots k < jp1 and ||w||^2 (slot jp1) reduced in tiles of T, the last tile
+// with the norm; the Givens inputs staged while the partials are reduced;
+// every thread's partials loaded before any add (R CTAs per thread in one
+// round); then h_{j+1,j} = sqrt(||w||^2 - sum_k h_k^2) (Pythagoras: w - V h is
+// orthogonal to V_0..V_j when they are orthonormal, so the norm needs neither
+// a pass over the updated w nor a second reduction) and the Givens update of
+// column j by one thread.  sh_w holds RED_THREADS * (T + 1) doubles.  A
+// difference below 1e-12 ||w||^2 (more than twelve digits cancelled, or
+// negative) is taken as a breakdown: the cycle ends at this column and the
+// explicit FP64 residual at its end decides whether it restarts.
 template <int T>
 __device__ __forceinline__ void dots_norm_last(SolveState *S, const double *partials, int jp1,
                                                double *sh_w, double *sh_o) {
@@ -540,90 +531,59 @@ static void launch_dots(int nred, cudaStream_t st, const double *V, long long nv
         launch_pdl(k_dots<0>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials, pass);
 }
 
-// Single-reduction Gram-Schmidt step (one classical pass, the solve's default):
-// h[k] = <V_k, w> for k < jp1 and ||w||^2 in one pass over V_0..V_j and w;
-// the last CTA forms h_{j+1,j} = sqrt(||w||^2 - sum_k h_k^2) (Pythagoras: w - V h
-// is orthogonal to V_0..V_j when they are orthonormal) and the Givens update of
-// column j, so the norm needs neither a pass over the updated w nor a second
-// reduction.  A difference below 1e-12 ||w||^2 (more than twelve digits
-// cancelled, or negative) is taken as a breakdown: the cycle ends at this
-// column and the explicit FP64 residual at its end decides whether it
-// restarts.  NW as in k_dots.
-template <int NW>
-__global__ void __launch_bounds__(RED_THREADS, 4)
-k_dots_norm(const double *__restrict__ V, long long nv2, int jp1, const double *__restrict__ w,
-            SolveState *S, double *partials) {
-    pdl_wait();
-    pdl_trigger();
-    if (S->done) return;   // set by an earlier kernel: a plain load
-    constexpr int T = NW > 0 ? NW : TILE;
-    __shared__ double sh_w[RED_THREADS * (T + 1)], sh_o[T + 1];
-    const double2 *w2 = reinterpret_cast<const double2 *>(w);
-    const double2 *V2 = reinterpret_cast<const double2 *>(V);
-    if constexpr (NW > 0) {
-        dots_tile<NW, true, true>(V2, nv2, 0, w2, sh_w, sh_o, partials);
-    } else {
-        // the norm with the last tile (the first ones are full)
-        for (int k0 = 0; k0 < jp1; k0 += TILE) {
-            const int kn = jp1 - k0 < TILE ? jp1 - k0 : TILE;
-            if (k0 + TILE < jp1) {
-                dots_tile<TILE, false>(V2, nv2, k0, w2, sh_w, sh_o, partials);
-                continue;
-            }
-            switch (kn) {
-            case 1: dots_tile<1, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-            case 2: dots_tile<2, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-            case 3: dots_tile<3, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-            case 4: dots_tile<4, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-            case 5: dots_tile<5, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-            default: dots_tile<6, false, true>(V2, nv2, k0, w2, sh_w, sh_o, partials); break;
-            }
-        }
+// Partial dots <V_k0+k, w>, k < K, over this thread's rows of the fused
+// kernel's grid stride (the same value-to-thread map as its product pass), for
+// the tiles past the first: w was written earlier in the same kernel by this
+// thread, so it is read back through L2 (never the read-only path).
+template <int K>
+__device__ __forceinline__ void rows_dots_tile(int n, const double *__restrict__ V, long long nv,
+                                               int k0, const double *w, double *sh_w, double *sh_o,
+                                               double *partials) {
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) acc[k] = 0.0;
+    const int q = threadIdx.x & 3;
+    const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
+    for (int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2); i < n; i += rows_per_grid) {
+        const size_t o = (size_t)i * BS + q;
+        const double wv = __ldcg(w + o);
+#pragma unroll
+        for (int k = 0; k < K; k++) acc[k] = fma(__ldg(V + (size_t)(k0 + k) * nv + o), wv, acc[k]);
     }
-    if (!last_cta(S)) return;
-    dots_norm_last<T>(S, partials, jp1, sh_w, sh_o);   // k_update_scale publishes
-}
-
-static void launch_dots_norm(int nred, cudaStream_t st, const double *V, long long nv2, int jp1,
-                             const double *w, SolveState *S, double *partials) {
-    if (jp1 == 1)
-        launch_pdl(k_dots_norm<1>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
-    else if (jp1 == 2)
-        launch_pdl(k_dots_norm<2>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
-    else if (jp1 == 3)
-        launch_pdl(k_dots_norm<3>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
-    else if (jp1 == 4)
-        launch_pdl(k_dots_norm<4>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
-    else
-        launch_pdl(k_dots_norm<0>, nred, RED_THREADS, 0, st, V, nv2, jp1, w, S, partials);
+    block_sum<K>(acc, sh_w, sh_o, K);
+    if (threadIdx.x < K) partials[(size_t)blockIdx.x * (MAXM + 2) + k0 + threadIdx.x] = sh_o[threadIdx.x];
 }
 
 // w = A z_j and, in the same pass over the rows, the first Gram-Schmidt pass's
-// dots h[k] = <V_k, w>, k < KF = j + 1, plus ||w||^2 with NORM (the
-// single-reduction step): each product is consumed where it is formed, so w
-// is written once and not read back by a second kernel, and one launch ramp
-// and tail go.  Both halves are bound by the FP64 pipe (two lanes per SM),
-// which they now share.  A quad of threads per block row as in the SpMV
-// kernel (row q of each 4x4 block, the same FMA chain, spmv.cuh), rows in a
-// grid stride.
-// Per thread the sums run over its rows in order, then the block sum and the
-// last CTA's reduction of the partials (slots 0..KF-1, the norm in slot KF),
-// so the result is deterministic for a fixed grid.  Launched like the
-// residual kernel, 3 CTAs per SM in one wave: 80 registers hold a row's four
-// blocks, its x gathers and the basis entries in flight (at 64 registers and
-// 4 CTAs per SM every width spilled, and the solve was 0.5% slower).  Steps
-// with j + 1 > SPMV_DOTS_MAX run the SpMV and the tiled dot kernels instead.
+// dots h[k] = <V_k, w> for the first KF basis vectors, plus ||w||^2 with NORM
+// (the single-reduction step): each product is consumed where it is formed, so
+// w is written once and not read back by a second kernel, and one launch ramp
+// and tail go per step.  Both halves are bound by the FP64 pipe (two lanes
+// per SM), which they now share.  A quad of threads per block row as in the
+// SpMV kernel (row q of each 4x4 block, the same FMA chain, spmv.cuh), rows
+// in a grid stride.  KF = j + 1 <= SPMV_DOTS_MAX; WIDE (KF = SPMV_DOTS_MAX,
+// any wider step): the tiles of V_KF..V_j follow in the same kernel, each a
+// pass over the thread's own rows that re-reads its entries of w through L2.
+// Per thread the sums run over its rows in order, then the block sum; the
+// last CTA reduces the partials (slots 0..j, the norm in slot j + 1) and with
+// NORM forms h_{j+1,j} and the Givens update, so the result is deterministic
+// for a fixed grid.  Launched like the residual kernel, 3 CTAs per SM in one
+// wave: 80 registers hold a row's four blocks, its x gathers and the basis
+// entries in flight (at 64 registers and 4 CTAs per SM every width spilled,
+// and the solve was 0.5% slower).
 constexpr int SPMV_DOTS_MAX = 5;
-template <int KF, bool NORM>
+template <int KF, bool NORM, bool WIDE>
 __global__ void __launch_bounds__(RED_THREADS, 3)
 k_spmv_dots(PatternView P, const double *__restrict__ A, const double *__restrict__ z,
-            double *__restrict__ w, const double *__restrict__ V, long long nv, SolveState *S,
+            double *w, const double *__restrict__ V, long long nv, int jp1, SolveState *S,
             double *partials) {
     pdl_wait();
     pdl_trigger();
     if (S->done) return;   // set by an earlier kernel: a plain load
     constexpr int KA = KF + (NORM ? 1 : 0);
-    __shared__ double sh_w[RED_THREADS * KA], sh_o[KA];
+    constexpr int T = WIDE ? TILE : KF;   // the tail's reduction tiles
+    static_assert(KA <= TILE + 1, "the product pass's values fit the tail's staging");
+    __shared__ double sh_w[RED_THREADS * (T + 1)], sh_o[T + 1];
     const int q = threadIdx.x & 3;
     double acc[KA];
 #pragma unroll
@@ -641,25 +601,41 @@ k_spmv_dots(PatternView P, const double *__restrict__ A, const double *__restric
         if constexpr (NORM) acc[KF] = fma(s, s, acc[KF]);
     }
     block_sum<KA>(acc, sh_w, sh_o, KA);
-    if (threadIdx.x < KA) partials[(size_t)blockIdx.x * (MAXM + 2) + threadIdx.x] = sh_o[threadIdx.x];
+    double *pc = partials + (size_t)blockIdx.x * (MAXM + 2);
+    if (threadIdx.x < KF) pc[threadIdx.x] = sh_o[threadIdx.x];
+    if (NORM && threadIdx.x == 0) pc[WIDE ? jp1 : KF] = sh_o[KF];   // the norm's slot: j + 1
+    if constexpr (WIDE) {
+        for (int k0 = KF; k0 < jp1; k0 += TILE) {
+            switch (jp1 - k0 < TILE ? jp1 - k0 : TILE) {
+            case 1: rows_dots_tile<1>(P.n, V, nv, k0, w, sh_w, sh_o, partials); break;
+            case 2: rows_dots_tile<2>(P.n, V, nv, k0, w, sh_w, sh_o, partials); break;
+            case 3: rows_dots_tile<3>(P.n, V, nv, k0, w, sh_w, sh_o, partials); break;
+            case 4: rows_dots_tile<4>(P.n, V, nv, k0, w, sh_w, sh_o, partials); break;
+            case 5: rows_dots_tile<5>(P.n, V, nv, k0, w, sh_w, sh_o, partials); break;
+            default: rows_dots_tile<6>(P.n, V, nv, k0, w, sh_w, sh_o, partials); break;
+            }
+        }
+    }
     if (!last_cta(S)) return;
-    if constexpr (NORM) dots_norm_last<KF>(S, partials, KF, sh_w, sh_o);   // k_update_scale publishes
-    else dots_last<KF>(S, partials, KF, 0, sh_w, sh_o);
+    if constexpr (NORM) dots_norm_last<T>(S, partials, jp1, sh_w, sh_o);   // k_update_scale publishes
+    else dots_last<T>(S, partials, jp1, 0, sh_w, sh_o);
 }
 
+// k_spmv_dots for step j (jp1 = j + 1 basis vectors)
 template <bool NORM>
-static void launch_spmv_dots_n(int nred, cudaStream_t st, const PatternView &P, const double *A,
+static void launch_spmv_dots_n(int grid, cudaStream_t st, const PatternView &P, const double *A,
                                const double *z, double *w, const double *V, long long nv, int jp1,
                                SolveState *S, double *partials) {
     switch (jp1) {
-    case 1: launch_pdl(k_spmv_dots<1, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
-    case 2: launch_pdl(k_spmv_dots<2, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
-    case 3: launch_pdl(k_spmv_dots<3, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
-    case 4: launch_pdl(k_spmv_dots<4, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
-    default: launch_pdl(k_spmv_dots<5, NORM>, nred, RED_THREADS, 0, st, P, A, z, w, V, nv, S, partials); break;
+    case 1: launch_pdl(k_spmv_dots<1, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
+    case 2: launch_pdl(k_spmv_dots<2, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
+    case 3: launch_pdl(k_spmv_dots<3, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
+    case 4: launch_pdl(k_spmv_dots<4, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
+    case 5: launch_pdl(k_spmv_dots<5, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
+    default: launch_pdl(k_spmv_dots<5, NORM, true>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
     }
 }
-static_assert(SPMV_DOTS_MAX == 5, "one instance per width");
+static_assert(SPMV_DOTS_MAX == 5, "one instance per width up to SPMV_DOTS_MAX");
 
 // v_{j+1} = (w - sum_k h[k] V_k) * hn_inv and its FP32 copy (the next
 // preconditioner's input) in one pass; w itself is not written back.  J =
@@ -1036,32 +1012,22 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
         for (; j < m; j++) {
             s = pc.fn(pc.ctx, V + (size_t)j * nv, v32, Z + (size_t)j * nv, st, skip);
             if (s != ABILU_OK) { ret = s; break; }
-            // w = A z_j with the first pass's dots (and the norm) in one kernel
-            // for the first SPMV_DOTS_MAX steps of a cycle; later, wider steps
-            // run the product and the tiled dot kernels
-            const bool fused = j + 1 <= SPMV_DOTS_MAX;
-            if (fused) {
-                if (form == GS_SINGLE)
-                    launch_spmv_dots_n<true>(nres, st, P, A, Z + (size_t)j * nv, w, V, nv, j + 1, SS,
-                                             ws->partials);
-                else
-                    launch_spmv_dots_n<false>(nres, st, P, A, Z + (size_t)j * nv, w, V, nv, j + 1, SS,
-                                              ws->partials);
-            } else if ((s = spmv_launch(P, A, 1.0, Z + (size_t)j * nv, 0.0, w, st, skip)) != ABILU_OK) {
-                ret = s;
-                break;
-            }
-            if (form == GS_SINGLE) {            // one pass, one reduction (see k_dots_norm)
-                if (!fused) launch_dots_norm(nred, st, V, nv2, j + 1, w, SS, ws->partials);
+            // w = A z_j with the first pass's dots (and, in the single-reduction
+            // form, ||w||^2, h_{j+1,j} and the Givens update) in one kernel
+            if (form == GS_SINGLE)
+                launch_spmv_dots_n<true>(nres, st, P, A, Z + (size_t)j * nv, w, V, nv, j + 1, SS,
+                                         ws->partials);
+            else
+                launch_spmv_dots_n<false>(nres, st, P, A, Z + (size_t)j * nv, w, V, nv, j + 1, SS,
+                                          ws->partials);
+            if (form == GS_SINGLE) {            // one pass, one reduction (see k_spmv_dots)
                 launch_update_scale(nred, st, V, nv2, j, w, V + (size_t)(j + 1) * nv, v32, SS,
                                     pc.y0, pc.tickets);
             } else if (form == GS_CLASSICAL) {  // one pass, the norm of the updated w
-                if (!fused) launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 1);
                 launch_pdl(k_scale, nred, RED_THREADS, 0, st, w, V + (size_t)(j + 1) * nv, v32, nv2, SS,
                            pc.y0, pc.tickets);
             } else {               // CGS2: two passes, the norm of the updated w
-                if (!fused) launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 0);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 0, 0);
                 launch_dots(nred, st, V, nv2, j + 1, w, SS, ws->partials, 1);
                 launch_update(nred, st, V, nv2, j, w, SS, ws->partials, 1, 1);

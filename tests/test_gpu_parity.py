@@ -427,15 +427,16 @@ def test_fgmres_restarts_and_reorth(ab):
 
 @pytest.mark.parametrize("form", ["single", "classical", "cgs2"])
 @pytest.mark.parametrize("nx,ny", [(30, 20), (240, 160)])
-def test_fgmres_fused_and_separate_steps(ab, form, nx, ny):
-    """Cycles longer than five Arnoldi steps: the first five form w = A z_j
-    with the first pass's dot products (and ||w||^2 in the single-reduction
-    form) in one kernel, later steps run the product and the dot kernels
-    apart.  In FP64 the whole cycle follows the oracle's (modified
-    Gram-Schmidt) iteration count in each Gram-Schmidt form: rtol 1e-6 takes
-    the single-reduction step, 1e-8 the classical one with the explicit norm,
-    reorth CGS2.  The 76,800-row system gives each thread of the fused kernel
-    three rows of its grid stride and crosses a restart at 30."""
+def test_fgmres_steps_past_the_fused_width(ab, form, nx, ny):
+    """Cycles longer than five Arnoldi steps: every step forms w = A z_j with
+    the first pass's dot products (and ||w||^2 in the single-reduction form)
+    in one kernel; the first five basis vectors are dotted in the product's
+    own pass, wider steps re-read w for the tiles past the fifth.  In FP64 the
+    whole cycle follows the oracle's (modified Gram-Schmidt) iteration count
+    in each Gram-Schmidt form: rtol 1e-6 takes the single-reduction step, 1e-8
+    the classical one with the explicit norm, reorth CGS2.  The 76,800-row
+    system gives each thread of the fused kernel three rows of its grid stride
+    and crosses a restart at 30."""
     s = gen.small_system(nx, ny, seed=3, cfl=1e4)
     d = Dev(ab, s)
     rtol = 1e-6 if form == "single" else 1e-8
