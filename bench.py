@@ -515,7 +515,8 @@ def run_serving(args, n_requests=48, rates=(0.25, 0.5, 1.0, 1.5), reps=3):
     plain FP64 ABILU (synchronous sweeps) solving the requests one at a time on
     the same GPU.  Capacity = solves/s with every request queued at t = 0; the
     arrival rates are fractions of it.  Every configuration runs `reps` times
-    and reports its median run (by solves/s), with the solves/s of all runs:
+    and reports its median run (by solves/s), with the solves/s of all runs in
+    the order they ran:
     the host's own load moves single runs (one run of the 20-request stream at
     the 1.0x rate stalled for 0.35 s on a loaded host)."""
     import torch
@@ -538,9 +539,8 @@ def run_serving(args, n_requests=48, rates=(0.25, 0.5, 1.0, 1.5), reps=3):
     budget = 0.25 * torch.cuda.get_device_properties(0).total_memory
     cfg = dict(build_sweeps=args.batch_build_sweeps, apply_sweeps=args.batch_apply_sweeps)
     def median_run(run):
-        runs = sorted((serving.summarize(*run()) for _ in range(reps)),
-                      key=lambda r: r["solves_per_s"])
-        med = dict(runs[len(runs) // 2])
+        runs = [serving.summarize(*run()) for _ in range(reps)]   # in the order they ran
+        med = dict(sorted(runs, key=lambda r: r["solves_per_s"])[len(runs) // 2])
         med["runs_solves_per_s"] = [round(r["solves_per_s"], 1) for r in runs]
         return med
 
