@@ -1,7 +1,11 @@
-// Block sparse matrix-vector product y = alpha A x + beta y, FP64, 4x4 blocks.
+// Block sparse matrix-vector product y = alpha A x + beta y, FP64, 4x4 blocks
+// (the public bsr_spmv).
 //
 // FGMRES needs one product per iteration plus the residual at each restart
-// (Sec. 6 setup).  Bytes dominate: every block is 128 bytes of FP64 values
+// (Sec. 6 setup); inside the solve those run in the kernel that also takes the
+// Gram-Schmidt dot products (k_spmv_dots, fgmres.cu) and in the residual
+// kernels, all with this kernel's row product (spmv.cuh).  Bytes dominate:
+// every block is 128 bytes of FP64 values
 // plus a 4-byte column index, read exactly once; x (4N doubles) is gathered
 // through L1/L2.  A quad of threads handles one block row: thread q reads row q
 // of every block of the row (32 contiguous bytes; the quad together reads each
