@@ -570,8 +570,11 @@ __device__ __forceinline__ void rows_dots_tile(int n, const double *__restrict__
 // for a fixed grid.  Launched like the residual kernel, 3 CTAs per SM in one
 // wave: 80 registers hold a row's four blocks, its x gathers and the basis
 // entries in flight (at 64 registers and 4 CTAs per SM every width spilled,
-// and the solve was 0.5% slower).
-constexpr int SPMV_DOTS_MAX = 5;
+// and the solve was 0.5% slower).  SPMV_DOTS_MAX = 3: with four and five
+// basis vectors in the product's pass the accumulators spilled and the FP64
+// pipe's busy share fell from 89-92% to 84%; three there and the rest in a
+// tile that re-reads w measured 1.661 against 1.666 ms per solve.
+constexpr int SPMV_DOTS_MAX = 3;
 template <int KF, bool NORM, bool WIDE>
 __global__ void __launch_bounds__(RED_THREADS, 3)
 k_spmv_dots(PatternView P, const double *__restrict__ A, const double *__restrict__ z,
@@ -630,12 +633,10 @@ static void launch_spmv_dots_n(int grid, cudaStream_t st, const PatternView &P, 
     case 1: launch_pdl(k_spmv_dots<1, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
     case 2: launch_pdl(k_spmv_dots<2, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
     case 3: launch_pdl(k_spmv_dots<3, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
-    case 4: launch_pdl(k_spmv_dots<4, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
-    case 5: launch_pdl(k_spmv_dots<5, NORM, false>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
-    default: launch_pdl(k_spmv_dots<5, NORM, true>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
+    default: launch_pdl(k_spmv_dots<3, NORM, true>, grid, RED_THREADS, 0, st, P, A, z, w, V, nv, jp1, S, partials); break;
     }
 }
-static_assert(SPMV_DOTS_MAX == 5, "one instance per width up to SPMV_DOTS_MAX");
+static_assert(SPMV_DOTS_MAX == 3, "one instance per width up to SPMV_DOTS_MAX");
 
 // v_{j+1} = (w - sum_k h[k] V_k) * hn_inv and its FP32 copy (the next
 // preconditioner's input) in one pass; w itself is not written back.  J =
