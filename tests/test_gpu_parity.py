@@ -430,8 +430,8 @@ def test_fgmres_restarts_and_reorth(ab):
 def test_fgmres_steps_past_the_fused_width(ab, form, nx, ny):
     """Cycles longer than five Arnoldi steps: every step forms w = A z_j with
     the first pass's dot products (and ||w||^2 in the single-reduction form)
-    in one kernel; the first five basis vectors are dotted in the product's
-    own pass, wider steps re-read w for the tiles past the fifth.  In FP64 the
+    in one kernel; the first three basis vectors are dotted in the product's
+    own pass, wider steps re-read w for the tiles past the third.  In FP64 the
     whole cycle follows the oracle's (modified Gram-Schmidt) iteration count
     in each Gram-Schmidt form: rtol 1e-6 takes the single-reduction step, 1e-8
     the classical one with the explicit norm, reorth CGS2.  The 76,800-row
