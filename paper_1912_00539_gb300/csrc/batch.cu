@@ -412,9 +412,11 @@ __device__ __forceinline__ void b_spmv_tile(const PatternView &P, const double *
 // h and h_{j+1,j} = sqrt(||w||^2 - sum h_k^2) and the Givens update (the
 // single-reduction step, b_dots_norm_last), else h of the first pass
 // (b_dots_last).  One launch and one pass over w fewer per step than the
-// product followed by the dots.  3 CTAs per SM: 80 registers
-// hold a row's four blocks, its x gathers and the basis entries in flight.
-constexpr int B_FUSED = 4;
+// product followed by the dots.  3 CTAs per SM: 80 registers hold a row's
+// four blocks, its x gathers and the basis entries in flight.  B_FUSED = 3:
+// with four in the product's pass the kernel spilled 100-156 bytes, and the
+// 64-system batch took 7.59-7.62 against 7.57 ms per solve (asynchronous).
+constexpr int B_FUSED = 3;
 template <bool NORM>
 __global__ void __launch_bounds__(RED_THREADS, 3)
 k_b_spmv_dots(PatternView P, const double *__restrict__ A, const double *__restrict__ z,
@@ -431,8 +433,7 @@ k_b_spmv_dots(PatternView P, const double *__restrict__ A, const double *__restr
     switch (jp1 < B_FUSED ? jp1 : B_FUSED) {
     case 1: b_spmv_tile<1, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
     case 2: b_spmv_tile<2, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
-    case 3: b_spmv_tile<3, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
-    default: b_spmv_tile<4, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
+    default: b_spmv_tile<3, NORM>(P, A, z, w, V, nv, f0, f1, sh_w, sh_o, partials, sc); break;
     }
     if (jp1 > B_FUSED) b_dots_tiles<true>(V, nv, jp1, w, f0, f1, sh_w, sh_o, partials, sc, B_FUSED);
     const int c0 = T.sys_sc0[s], c1 = T.sys_sc0[s + 1];

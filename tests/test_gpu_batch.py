@@ -130,12 +130,12 @@ def test_batch_tight_tolerances_and_the_graph_key(ab, rtol):
 @pytest.mark.parametrize("rtol,reorth", [(1e-6, False), (1e-8, False), (1e-8, True)])
 def test_batch_steps_wider_than_the_fused_tile(ab, rtol, reorth):
     """Each Arnoldi step of the batch forms w = A z_j in the kernel that takes
-    the first four dot products of the first Gram-Schmidt pass (and ||w||^2 in
+    the first three dot products of the first Gram-Schmidt pass (and ||w||^2 in
     the single-reduction form); wider steps re-read the CTA's own entries of w
     for the remaining tiles.  In every Gram-Schmidt form (single reduction at
     1e-6, classical with the explicit norm at 1e-8, CGS2) each system takes
     its single-system iteration count (synchronous FP64) and reaches rtol, and
-    at least one system runs steps past the fourth."""
+    at least one system runs steps past the fourth (two past the fused tile)."""
     import torch
     systems = _systems()[:4]
     devs = [_dev(s) for s in systems]
