@@ -164,10 +164,12 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
         v[1] = v[0];
     } else {
         for (; i < P.n; i += rows_per_grid) {
+            const size_t o = (size_t)i * BS + q;
+            // b issued with the row's matrix loads (after the product: 81.7
+            // against 78.6 us per launch at 512x512, ncu)
+            const double bi = __ldg(b + o);
             // the SpMV kernel's arithmetic
             const double s = row_dot_blocks(P, A, x, i, q);
-            const size_t o = (size_t)i * BS + q;
-            const double bi = b[o];
             const double ri = bi - s;
             r_out[o] = ri;
             v[0] += ri * ri;
