@@ -1179,7 +1179,9 @@ def run_gpu(args):
     if rank == 0 and world == 1 and args.extras:
         extras["viscous"] = viscous_rcm_vs_line()
         extras["batched"] = run_batched(args)
-        extras["serving"] = run_serving(args, n_requests=20, rates=(0.5, 1.0))
+        # five timed runs per configuration: a 20-request run lasts about 0.1 s,
+        # and single runs lost up to 40% to stalls of the shared host
+        extras["serving"] = run_serving(args, n_requests=20, rates=(0.5, 1.0), reps=5)
 
     cpu = None
     x_gpu = x.cpu().numpy()
