@@ -453,6 +453,42 @@ def test_fgmres_steps_past_the_fused_width(ab, form, nx, ny):
     assert abs(res.iters - ro.iters) <= max(1, ro.iters // 10), (res.iters, ro.iters)
 
 
+XERR_SYSTEMS = {
+    "grid30x20_cfl1e4": lambda: gen.small_system(30, 20, seed=3, cfl=1e4),
+    "grid240x160_cfl1e4": lambda: gen.small_system(240, 160, seed=3, cfl=1e4),   # 76,800 rows
+    "inviscid_64x64": lambda: gen.workload("inviscid_64x64"),
+    "random_triangles": lambda: gen.random_pattern_system(150, 400, seed=4),
+    "grid37x11_ragged": lambda: gen.small_system(37, 11, seed=2),
+}
+
+
+@pytest.mark.parametrize("form", ["single", "classical", "cgs2"])
+@pytest.mark.parametrize("name", list(XERR_SYSTEMS))
+def test_fgmres_fp64_solution_equals_oracle(ab, name, form):
+    """The FP64 synchronous solve and the oracle's FGMRES (modified
+    Gram-Schmidt) produce the same iterates in exact arithmetic, whichever
+    Gram-Schmidt form the GPU takes (single reduction at rtol 1e-6, classical
+    with the explicit norm at 1e-8, CGS2): they stop at the same step and their
+    solutions differ by rounding only.  Measured 8.5e-16 to 2.1e-14 relative
+    (2-norm) over these systems, 10 to 20 iterations, so every width of the
+    fused product-and-dots kernel runs; the bound 1e-11 leaves three orders of
+    magnitude for rounding growth, while a wrong term of any dot product,
+    norm or Givens rotation moves x in its leading digits."""
+    s = XERR_SYSTEMS[name]()
+    d = Dev(ab, s)
+    rtol = 1e-6 if form == "single" else 1e-8
+    Xo, Do, _ = oracle.bilu_sync(s.rowptr, s.colind, s.vals, 2)
+    xo, ro = oracle.fgmres(s.rowptr, s.colind, s.vals, Xo, Do, s.b, 1, 1, restart=30, rtol=rtol)
+    fac = ab.Factors(d.pat, "f64")
+    x = d.vec()
+    res = ab.fgmres_solve(d.pat, d.A, fac, d.b, x, restart=30, rtol=rtol, build_sweeps=2,
+                          apply_sweeps_lower=1, apply_sweeps_upper=1, mode="sync",
+                          reorth=form == "cgs2")
+    assert res.converged and res.iters == ro.iters, (res.iters, ro.iters)
+    xn = x.cpu().numpy()
+    assert np.linalg.norm(xn - xo) / np.linalg.norm(xo) < 1e-11
+
+
 def test_fgmres_max_iters_reports_noconv(ab):
     d = Dev(ab, gen.small_system(12, 10, seed=9, cfl=1.0))
     fac = ab.Factors(d.pat, "f64")
