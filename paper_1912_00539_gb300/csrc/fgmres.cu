@@ -124,8 +124,9 @@ __device__ __forceinline__ void reduce_partials(const double *partials, int stri
 // The last CTA sets beta, the convergence flag and starts the next cycle.
 // Launched with 3 CTAs per SM (its registers allow 3 resident: one wave).
 // Every FP64 operation counts on this GPU (two FP64 lanes per SM): with x = 0
-// (ZERO) r = b and ||r||^2 = ||b||^2 is accumulated once; after a cycle
-// (init = 0) ||b||^2 is not formed.
+// (ZERO) r = b and ||r||^2 = ||b||^2 is accumulated once, and r_out is not
+// written (the caller scales b itself); after a cycle (init = 0) ||b||^2 is
+// not formed.
 template <bool ZERO>
 __global__ void __launch_bounds__(RED_THREADS, 3)
 k_residual(PatternView P, const double *__restrict__ A, const double *__restrict__ b,
@@ -142,7 +143,8 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
     const int rows_per_grid = gridDim.x * (RED_THREADS / 4);
     int i = blockIdx.x * (RED_THREADS / 4) + (threadIdx.x >> 2);
     if constexpr (ZERO) {
-        // r = b: four rows' loads in flight per thread before any store (one
+        // r = b, not stored (the scale kernel that forms v_0 = r / beta reads
+        // b itself); ||b||^2 with four rows' loads in flight per thread (one
         // per iteration left each thread waiting on a load 18 times in a
         // row: 24 us for the 512x512 grid); the same rows in the same order
         constexpr int U = 4;
@@ -157,7 +159,6 @@ k_residual(PatternView P, const double *__restrict__ A, const double *__restrict
             for (int u = 0; u < U; u++) {
                 const int iu = i + u * rows_per_grid;
                 if (iu >= P.n) break;
-                r_out[(size_t)iu * BS + q] = bu[u];
                 v[0] += bu[u] * bu[u];
             }
         }
@@ -997,7 +998,9 @@ abilu_status fgmres_run(const PatternView &P, const double *A, abilu_factors ws,
         launch_pdl(k_residual<true>, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1);
     else
         launch_pdl(k_residual<false>, nres, RED_THREADS, 0, st, P, A, b, x, V, SS, ws->partials, 1);
-    launch_pdl(k_scale, nred, RED_THREADS, 0, st, V, V, v32, nv2, SS, pc.y0, pc.tickets);
+    // v_0 = r / beta; with x = 0, r = b is read from b itself
+    launch_pdl(k_scale, nred, RED_THREADS, 0, st, opts->zero_guess ? b : V, V, v32, nv2, SS,
+               pc.y0, pc.tickets);
     ABILU_LAUNCH_CHECK("fgmres init");
     // the look-ahead events live in the workspace handle (made on first use)
     for (int k = 0; k < 2; k++)
