@@ -34,7 +34,6 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "inviscid_512x512"
 BUILD_SWEEPS, APPLY_SWEEPS, RESTART, RTOL = 6, 4, 30, 1e-6
-FUSED_STEPS = 5   # Arnoldi steps per cycle whose product is fused with the dots
 BUILD_TIMED_EVERY = 4   # timed solves per one whose build records its sweep events
 METRIC = "preconditioned FGMRES solves/s at 1e-6; sweep GB/s vs HBM peak; p50/p99 latency"
 
@@ -1100,11 +1099,11 @@ def run_gpu(args):
            "d2h_bytes_per_step": hx[0].numel() * 8}
 
     it = statistics.median(iters)
-    # launches of each kernel per solve (it Arnoldi steps, 2 residuals); the
-    # first FUSED_STEPS steps of a cycle form w = A z_j inside the kernel that
-    # also takes the Gram-Schmidt dots, so the stand-alone product runs only in
-    # the steps after them
-    spmv_steps = max(0, it - FUSED_STEPS)
+    # launches of each kernel per solve (it Arnoldi steps, 2 residuals); every
+    # Arnoldi step forms w = A z_j inside the kernel that also takes the
+    # Gram-Schmidt dots, so the stand-alone product (timed above for its
+    # roofline) runs in no step of the solve
+    spmv_steps = 0
     if args.mode == "async":
         per_solve = {"spmv_f64": spmv_steps, "build_sweeps_f32": 1, "build_prepare_f32": 1,
                      "lower_sweeps_f32": it, "upper_sweeps_f32": it}
